@@ -1,0 +1,931 @@
+// o2pic oracle — TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, sequential CPU implementation of one time step of the
+// 1D3V particle-in-cell Monte-Carlo-collision (PIC-MCC) model of a
+// capacitively coupled RF oxygen discharge (Bronold et al., "Particle-based
+// modeling of oxygen discharges", ICPIG 2007, Sec. 2).  It exists to check the
+// CUDA path.  Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline
+// / reference legs may load it.  It shares no code with the CUDA library: the
+// two are written separately from the same readings of the paper.
+//
+// Everything is ordinary loops over std::vectors in the order the method
+// states.  The particle arithmetic is templated on the precision R:
+//   R = float  : "mirror" mode, the precision the method fixes for particles
+//                (FP32 particles, FP64 Poisson); used for per-particle parity.
+//   R = double : FP64 reference, used to state the error of the FP32 results.
+// The Poisson solve and the charge reduction are always FP64 / exact integer.
+//
+// Paper passages followed (Sec. 2 unless stated):
+//   * one spatial coordinate 0 <= x <= L, all three velocity components kept;
+//   * one electrode driven by U sin(2 pi f t), the other grounded;
+//   * both electrodes totally absorbing, no secondary emission;
+//   * O2 background at n = p / kT, T = 300 K; metastable O2(a) at n_D = C n_O2;
+//   * collisions decoupled from free flights, collision time and type from
+//     kinetic considerations (null-collision Monte Carlo);
+//   * three kinetic species e, O-, O2+; reactions of Table 1;
+//   * Eq. 1 (associative detachment) and the Landau-Zener sigma_n enter as
+//     cross-section data;
+//   * ion-ion neutralization (17) as a binary, cell-local (DSMC-like) process.
+// Where the paper is silent the readings listed in the design notes are used
+// (leapfrog, CIC, Thomas, isotropic scattering, birth velocities, pairing).
+//
+// Parity status of each function is stated next to it.  All functions here
+// are pinned by tests under tests/ (closed forms, invariants, brute force);
+// the coupled discharge against the paper's figures is NOT pinned (the paper's
+// cross sections are unpublished).
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <cstdio>
+#include <vector>
+#include <algorithm>
+#include <limits>
+
+namespace {
+
+// ---------------------------------------------------------------- constants
+// CODATA 2018 exact / recommended values (SI).
+const double QE = 1.602176634e-19;     // elementary charge [C]
+const double KB = 1.380649e-23;        // Boltzmann constant [J/K]
+const double EPS0 = 8.8541878128e-12;  // vacuum permittivity [F/m]
+const double TWO_PI = 6.283185307179586476925286766559;
+
+enum { SP_E = 0, SP_OM = 1, SP_OP = 2, NSP = 3 };
+enum { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6 };
+enum { T_O2 = 0, T_O2_META = 1, T_ION = 2 };
+
+// Energy grid of the rate tables: 32 points per octave on [2^-10, 2^12] eV.
+const int GRID_OCT_LO = -10;
+const int GRID_OCTAVES = 22;
+const int GRID_SUB = 32;
+const int NGRID = GRID_OCTAVES * GRID_SUB + 1;   // 705 points, last = 2^12 eV
+const int MAXPROC = 16;
+const int MAX_TRIES = 32;                        // rejection-loop cap
+const double FIX_ONE = 65536.0;                  // CIC fixed point: 2^16 per particle
+
+// RNG stream tags (counter word 1).
+enum { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4 };
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
+// as easy as 1, 2, 3", SC'11: 10 rounds of the Philox S-box with multipliers
+// 0xD2511F53 / 0xCD9E8D57 and Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+struct U4 { uint32_t v[4]; };
+
+U4 philox4x32_10(const uint32_t ctr[4], const uint32_t key[2]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    U4 r; r.v[0] = c0; r.v[1] = c1; r.v[2] = c2; r.v[3] = c3;
+    return r;
+}
+
+// Sequential words of the stream keyed by (key0, seed) with counter
+// (step_lo, tag, block, step_hi); block b yields words 4b..4b+3.
+struct Stream {
+    uint32_t key[2];
+    uint32_t ctr[4];
+    U4 buf;
+    int pos;      // next word inside buf (4 = exhausted)
+    Stream(uint32_t key0, uint32_t seed, uint64_t step, uint32_t tag) {
+        key[0] = key0; key[1] = seed;
+        ctr[0] = (uint32_t)step; ctr[1] = tag; ctr[2] = 0; ctr[3] = (uint32_t)(step >> 32);
+        buf = philox4x32_10(ctr, key);
+        pos = 0;
+    }
+    uint32_t next() {
+        if (pos == 4) { ctr[2] += 1; buf = philox4x32_10(ctr, key); pos = 0; }
+        return buf.v[pos++];
+    }
+};
+
+// u32 -> uniform on [0, 1) with 24 random bits (exact in float and double).
+template <class R> R uniform(uint32_t w) { return (R)(w >> 8) * (R)(1.0 / 16777216.0); }
+
+// --------------------------------------------------------------- math (R)
+inline float fma_(float a, float b, float c) { return std::fmaf(a, b, c); }
+inline double fma_(double a, double b, double c) { return std::fma(a, b, c); }
+inline float sqrt_(float a) { return std::sqrt(a); }
+inline double sqrt_(double a) { return std::sqrt(a); }
+
+// Natural log in single precision by the atanh series (Abramowitz & Stegun
+// 4.1.27): x = 2^e m, m in [sqrt(1/2), sqrt(2)), t = (m-1)/(m+1),
+// ln m = 2 t (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9).  |t| <= 0.1716, so the
+// truncated tail is below 3e-9 relative.  Used only for x in (0, 1] (the
+// polar normal method).  Written here from the series; the CUDA path has
+// its own implementation of the same series so that both produce identical
+// single-precision normals.
+float ln_(float x) {
+    int e;
+    float m = std::frexp(x, &e);   // x = m 2^e, m in [0.5, 1)
+    m = m * 2.0f; e -= 1;          // m in [1, 2)
+    if (m > 1.41421356f) { m = m * 0.5f; e += 1; }
+    float t = (m - 1.0f) / (m + 1.0f);
+    float t2 = t * t;
+    float p = fma_(t2, 0.111111111f, 0.142857143f);
+    p = fma_(t2, p, 0.2f);
+    p = fma_(t2, p, 0.333333333f);
+    p = fma_(t2, p, 1.0f);
+    float lnm = (2.0f * t) * p;
+    return fma_((float)e, 0.693147182f, lnm);
+}
+double ln_(double x) { return std::log(x); }
+
+template <class R> R dot3(R ax, R ay, R az, R bx, R by, R bz) {
+    return fma_(ax, bx, fma_(ay, by, az * bz));
+}
+
+// Marsaglia (1972) point on the unit sphere from a uniform point of the unit
+// disk: (a, b), s = a^2 + b^2 < 1  ->  (2a sqrt(1-s), 2b sqrt(1-s), 1 - 2s).
+template <class R> void isotropic(Stream& st, R n[3], uint64_t& warn) {
+    for (int t = 0; t < MAX_TRIES; ++t) {
+        R a = (R)2 * uniform<R>(st.next()) - (R)1;
+        R b = (R)2 * uniform<R>(st.next()) - (R)1;
+        R s = fma_(a, a, b * b);
+        if (s < (R)1) {
+            R h = (R)2 * sqrt_((R)1 - s);
+            n[0] = a * h; n[1] = b * h; n[2] = (R)1 - (R)2 * s;
+            return;
+        }
+    }
+    warn += 1; n[0] = 0; n[1] = 0; n[2] = 1;
+}
+
+// Marsaglia-Bray polar method: a pair of independent standard normals.
+template <class R> void normal_pair(Stream& st, R& z0, R& z1, uint64_t& warn) {
+    for (int t = 0; t < MAX_TRIES; ++t) {
+        R a = (R)2 * uniform<R>(st.next()) - (R)1;
+        R b = (R)2 * uniform<R>(st.next()) - (R)1;
+        R s = fma_(a, a, b * b);
+        if (s > (R)0 && s < (R)1) {
+            R f = sqrt_(((R)(-2) * ln_(s)) / s);
+            z0 = a * f; z1 = b * f;
+            return;
+        }
+    }
+    warn += 1; z0 = 0; z1 = 0;
+}
+
+// Three Maxwellian velocity components with standard deviation sig.
+template <class R> void maxwellian(Stream& st, R sig, R v[3], uint64_t& warn) {
+    R z0, z1, z2, z3;
+    normal_pair<R>(st, z0, z1, warn);
+    normal_pair<R>(st, z2, z3, warn);
+    v[0] = sig * z0; v[1] = sig * z1; v[2] = sig * z2;
+}
+
+// ------------------------------------------------------------ rate tables
+// Grid point i: E_i = 2^(i/32 - 10) (1 + (i mod 32)/32) eV.
+double grid_energy(int i) {
+    int oct = i / GRID_SUB, sub = i % GRID_SUB;
+    return std::ldexp(1.0 + sub / (double)GRID_SUB, oct + GRID_OCT_LO);
+}
+
+// Position of E on the grid: index i and weight w in [0,1) with
+// E = E_i + w (E_{i+1} - E_i).  Exact in float and double (frexp/ldexp are
+// exact, 32 f and its floor are exact).  E below the grid -> point 0;
+// E at or above 2^12 eV -> last point (flagged by the caller).
+template <class R> void grid_locate(R E, int& i, R& w, bool& above) {
+    above = false;
+    if (!(E >= (R)std::ldexp(1.0, GRID_OCT_LO))) { i = 0; w = 0; return; }
+    if (E >= (R)std::ldexp(1.0, GRID_OCT_LO + GRID_OCTAVES)) { i = NGRID - 1; w = 0; above = true; return; }
+    int ex;
+    R m = std::frexp(E, &ex);           // E = m 2^ex, m in [0.5,1)
+    R f = m * (R)2 - (R)1;              // E = 2^(ex-1) (1+f)
+    R f32 = f * (R)GRID_SUB;
+    R fl = std::floor(f32);
+    i = (ex - 1 - GRID_OCT_LO) * GRID_SUB + (int)fl;
+    w = f32 - fl;
+}
+
+// Piecewise-linear value of table T (stride `stride`, column k) at E.
+template <class R> R grid_interp(const std::vector<R>& T, int stride, int k, int i, R w) {
+    if (i >= NGRID - 1) return T[(size_t)(NGRID - 1) * stride + k];
+    R a = T[(size_t)i * stride + k], b = T[(size_t)(i + 1) * stride + k];
+    return fma_(w, b - a, a);
+}
+
+// Linear interpolation of a user (E, sigma) table, constant beyond its ends,
+// zero below the process threshold.
+double sigma_at(const std::vector<double>& Et, const std::vector<double>& st, double thr, double E) {
+    if (E < thr) return 0.0;
+    size_t n = Et.size();
+    if (E <= Et[0]) return st[0];
+    if (E >= Et[n - 1]) return st[n - 1];
+    size_t b = std::upper_bound(Et.begin(), Et.end(), E) - Et.begin();
+    double Ea = Et[b - 1], Eb = Et[b], sa = st[b - 1], sb = st[b];
+    return sa + (sb - sa) * ((E - Ea) / (Eb - Ea));
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+struct oracle_config {
+    double L, f, U, p, T_gas, C_meta, dt, weight, area;
+    double m_e, m_OM, m_OP, M_gas;
+    int32_t n_cells, ion_subcycle;
+    uint32_t seed, reserved;
+};
+
+struct oracle_process {
+    int32_t species, kind, target, n;
+    double threshold_eV;
+    const double* E_eV;
+    const double* sigma_m2;
+};
+
+}  // extern "C"
+
+namespace {
+
+struct Proc {
+    int kind, target;
+    double thr;
+    std::vector<double> E, s;
+};
+
+template <class R> struct Particles {
+    std::vector<R> x, vx, vy, vz;
+    std::vector<uint32_t> id;
+    size_t size() const { return x.size(); }
+    void push(R px, R pvx, R pvy, R pvz, uint32_t pid) {
+        x.push_back(px); vx.push_back(pvx); vy.push_back(pvy); vz.push_back(pvz); id.push_back(pid);
+    }
+    void clear() { x.clear(); vx.clear(); vy.clear(); vz.clear(); id.clear(); }
+};
+
+struct Birth4 { double x, vx, vy, vz; };
+
+// Counter block (read by tests through oracle_counters).
+struct Counters {
+    uint64_t events[NSP][MAXPROC];
+    uint64_t absorbed[NSP][2];     // [species][0: x<0 wall, 1: x>=L wall]
+    uint64_t born[NSP];
+    uint64_t neutralized;          // pairs removed by (17)
+    uint64_t pair_candidates;      // pairs tested by (17)
+    uint64_t particle_steps;       // particles pushed
+    uint64_t warn_emax;            // energy above the table grid
+    uint64_t warn_tries;           // rejection loop exhausted
+    uint64_t warn_pair_gt1;        // neutralization probability > 1
+    uint64_t id_overflow;
+};
+
+template <class R> struct Oracle {
+    oracle_config cfg;
+    int Ng;
+    double dx, n_O2, n_meta;
+    double mass[NSP];
+    int charge[NSP];
+    // derived per-species constants in precision R
+    R dt_s[NSP], qmdt[NSP], kappa[NSP], a_m[NSP], a_M[NSP], delta_el, sig_gas, sig_birth[NSP];
+    R inv_dx, Lr, kappa_n, pair_factor;
+    // rate tables
+    std::vector<Proc> procs[NSP];
+    std::vector<R> cum[NSP];          // [NGRID][nproc] cumulative rate, precision R
+    std::vector<double> nu64[NSP];    // [NGRID][nproc] per-process rate, FP64
+    R numax[NSP], Pmax[NSP];
+    double numax64[NSP];
+    bool have_neutral;
+    Proc neutral;
+    std::vector<R> Ktab;              // [NGRID] sigma_n g
+    // state
+    Particles<R> sp[NSP];
+    uint32_t next_id[NSP];
+    uint64_t step;
+    std::vector<uint64_t> Q[NSP];
+    std::vector<double> phi, Efield;
+    std::vector<R> Eg;
+    std::vector<uint64_t> Qacc[NSP];
+    uint64_t acc_steps;
+    Counters cnt;
+    bool field_valid;
+
+    explicit Oracle(const oracle_config& c) : cfg(c) {
+        Ng = cfg.n_cells + 1;
+        dx = cfg.L / cfg.n_cells;
+        n_O2 = cfg.p / (KB * cfg.T_gas);
+        n_meta = cfg.C_meta * n_O2;
+        mass[SP_E] = cfg.m_e; mass[SP_OM] = cfg.m_OM; mass[SP_OP] = cfg.m_OP;
+        charge[SP_E] = -1; charge[SP_OM] = -1; charge[SP_OP] = +1;
+        for (int s = 0; s < NSP; ++s) {
+            double dts = cfg.dt * (s == SP_E ? 1.0 : (double)cfg.ion_subcycle);
+            dt_s[s] = (R)dts;
+            qmdt[s] = (R)((charge[s] * QE / mass[s]) * dts);
+            double mu = (s == SP_E) ? mass[s] : mass[s] * cfg.M_gas / (mass[s] + cfg.M_gas);
+            kappa[s] = (R)(0.5 * mu / QE);
+            a_m[s] = (R)(mass[s] / (mass[s] + cfg.M_gas));
+            a_M[s] = (R)(cfg.M_gas / (mass[s] + cfg.M_gas));
+            sig_birth[s] = (R)std::sqrt(KB * cfg.T_gas / mass[s]);
+            numax[s] = 0; Pmax[s] = 0; numax64[s] = 0;
+            Q[s].assign(Ng, 0); Qacc[s].assign(Ng, 0);
+            next_id[s] = 0;
+        }
+        delta_el = (R)(2.0 * cfg.m_e / cfg.M_gas);
+        sig_gas = (R)std::sqrt(KB * cfg.T_gas / cfg.M_gas);
+        inv_dx = (R)(1.0 / dx);
+        Lr = (R)cfg.L;
+        double mun = cfg.m_OM * cfg.m_OP / (cfg.m_OM + cfg.m_OP);
+        kappa_n = (R)(0.5 * mun / QE);
+        double dt_ion = cfg.dt * (double)cfg.ion_subcycle;
+        pair_factor = (R)(cfg.weight * dt_ion / (cfg.area * dx));
+        have_neutral = false;
+        step = 0; acc_steps = 0;
+        phi.assign(Ng, 0.0); Efield.assign(Ng, 0.0); Eg.assign(Ng, (R)0);
+        std::memset(&cnt, 0, sizeof(cnt));
+        field_valid = false;
+    }
+
+    // ---- rate tables: nu_k(E_i) = n_target sigma_k(E_i) g(E_i),
+    // g = sqrt(2 e E / mu) (mu = m_e for electrons: target at rest).
+    // Cumulative sums over the process order, maximum over grid points,
+    // P_max = 1 - exp(-nu_max dt_s)  (null-collision method).
+    int set_processes(const oracle_process* p, int n) {
+        for (int s = 0; s < NSP; ++s) { procs[s].clear(); cum[s].clear(); nu64[s].clear(); }
+        have_neutral = false;
+        for (int j = 0; j < n; ++j) {
+            const oracle_process& q = p[j];
+            if (q.n < 1 || q.species < 0 || q.species >= NSP) return -1;
+            Proc pr; pr.kind = q.kind; pr.target = q.target; pr.thr = q.threshold_eV;
+            pr.E.assign(q.E_eV, q.E_eV + q.n); pr.s.assign(q.sigma_m2, q.sigma_m2 + q.n);
+            for (int i = 1; i < q.n; ++i) if (!(pr.E[i] > pr.E[i - 1])) return -1;
+            if (q.kind == K_NEUTRALIZE) { neutral = pr; have_neutral = true; continue; }
+            if ((int)procs[q.species].size() >= MAXPROC) return -1;
+            procs[q.species].push_back(pr);
+        }
+        for (int s = 0; s < NSP; ++s) {
+            int np = (int)procs[s].size();
+            cum[s].assign((size_t)NGRID * std::max(np, 1), (R)0);
+            nu64[s].assign((size_t)NGRID * std::max(np, 1), 0.0);
+            double mu = (s == SP_E) ? mass[s] : mass[s] * cfg.M_gas / (mass[s] + cfg.M_gas);
+            double mx = 0.0;
+            for (int i = 0; i < NGRID; ++i) {
+                double Ei = grid_energy(i);
+                double g = std::sqrt(2.0 * QE * Ei / mu);
+                double acc = 0.0;
+                for (int k = 0; k < np; ++k) {
+                    const Proc& pr = procs[s][k];
+                    double ntar = (pr.target == T_O2_META) ? n_meta : n_O2;
+                    double nu = ntar * sigma_at(pr.E, pr.s, pr.thr, Ei) * g;
+                    nu64[s][(size_t)i * np + k] = nu;
+                    acc += nu;
+                    cum[s][(size_t)i * np + k] = (R)acc;
+                }
+                mx = std::max(mx, acc);
+            }
+            numax64[s] = mx;
+            numax[s] = (R)mx;
+            double dts = cfg.dt * (s == SP_E ? 1.0 : (double)cfg.ion_subcycle);
+            Pmax[s] = (R)(1.0 - std::exp(-mx * dts));
+        }
+        Ktab.assign(NGRID, (R)0);
+        if (have_neutral) {
+            double mun = cfg.m_OM * cfg.m_OP / (cfg.m_OM + cfg.m_OP);
+            for (int i = 0; i < NGRID; ++i) {
+                double Ei = grid_energy(i);
+                double g = std::sqrt(2.0 * QE * Ei / mun);
+                Ktab[i] = (R)(sigma_at(neutral.E, neutral.s, neutral.thr, Ei) * g);
+            }
+        }
+        return 0;
+    }
+
+    // ---- CIC weights, fixed point: r = trunc(frac * 2^16); node j gets
+    // 2^16 - r, node j+1 gets r (sum exactly 2^16 per particle).
+    void cell_of(R x, int& j, R& frac) const {
+        R s = x * inv_dx;
+        j = (int)s;
+        if (j > cfg.n_cells - 1) j = cfg.n_cells - 1;
+        frac = s - (R)j;
+    }
+    void deposit_one(std::vector<uint64_t>& q, R x) const {
+        int j; R frac; cell_of(x, j, frac);
+        uint32_t r = (uint32_t)(frac * (R)FIX_ONE);
+        q[j] += (uint64_t)(65536u - r);
+        q[j + 1] += (uint64_t)r;
+    }
+    void deposit_all() {
+        for (int s = 0; s < NSP; ++s) {
+            std::fill(Q[s].begin(), Q[s].end(), 0);
+            for (size_t i = 0; i < sp[s].size(); ++i) deposit_one(Q[s], sp[s].x[i]);
+        }
+    }
+
+    // ---- Poisson (FP64): interior nodes j = 1..N-1,
+    //   -phi_{j-1} + 2 phi_j - phi_{j+1} = rho_j dx^2 / eps0,
+    // phi_0 = U sin(2 pi f t) (driven electrode at x = 0), phi_N = 0 (grounded),
+    // solved by the Thomas algorithm; E = -dphi/dx by central differences,
+    // boundary nodes by Gauss's law over the half cell next to the wall.
+    void field_solve(double t) {
+        int N = cfg.n_cells;
+        std::vector<long long> Rn(Ng);
+        for (int j = 0; j < Ng; ++j)
+            Rn[j] = (long long)Q[SP_OP][j] - (long long)Q[SP_E][j] - (long long)Q[SP_OM][j];
+        double V0 = cfg.U * std::sin(TWO_PI * cfg.f * t);
+        solve_field(N, dx, cfg.weight, cfg.area, V0, Rn.data(), phi.data(), Efield.data());
+        for (int j = 0; j < Ng; ++j) Eg[j] = (R)Efield[j];
+        field_valid = true;
+    }
+
+    static void solve_field(int N, double dx, double w, double A, double V0, const long long* Rn,
+                            double* phi, double* E) {
+        std::vector<double> rhs(N + 1, 0.0), cp(N + 1, 0.0), dp(N + 1, 0.0);
+        for (int j = 1; j <= N - 1; ++j) {
+            double rho = QE * w * (double)Rn[j] / (FIX_ONE * A * dx);
+            rhs[j] = rho * dx * dx / EPS0;
+        }
+        phi[0] = V0; phi[N] = 0.0;
+        if (N >= 2) {
+            rhs[1] += V0;          // phi_0 moved to the right-hand side
+            rhs[N - 1] += 0.0;     // phi_N = 0
+            // Thomas: a = -1, b = 2, c = -1
+            double b = 2.0;
+            cp[1] = -1.0 / b;
+            dp[1] = rhs[1] / b;
+            for (int j = 2; j <= N - 1; ++j) {
+                double den = 2.0 - (-1.0) * cp[j - 1];
+                cp[j] = -1.0 / den;
+                dp[j] = (rhs[j] - (-1.0) * dp[j - 1]) / den;
+            }
+            phi[N - 1] = dp[N - 1];
+            for (int j = N - 2; j >= 1; --j) phi[j] = dp[j] - cp[j] * phi[j + 1];
+        }
+        for (int j = 1; j <= N - 1; ++j) E[j] = (phi[j - 1] - phi[j + 1]) / (2.0 * dx);
+        double q0 = QE * w * (double)Rn[0] / FIX_ONE;
+        double qN = QE * w * (double)Rn[N] / FIX_ONE;
+        E[0] = (phi[0] - phi[1]) / dx - q0 / (EPS0 * A);
+        E[N] = (phi[N - 1] - phi[N]) / dx + qN / (EPS0 * A);
+    }
+
+    // ---- table lookups
+    R cum_at(int s, int k, int i, R w) const {
+        return grid_interp<R>(cum[s], (int)procs[s].size(), k, i, w);
+    }
+
+    // ---- one particle: push, absorb, null-collision MCC.
+    // Returns false if the particle leaves the arrays (absorbed or consumed).
+    // Births are appended to `births[dst]` in generation order.
+
+    bool update_particle(int s, uint64_t n, R& x, R& vx, R& vy, R& vz, uint32_t id,
+                         std::vector<Birth4>* births, const std::vector<R>& Ef) {
+        // gather: E_p = E_j + frac (E_{j+1} - E_j)
+        int j; R frac; cell_of(x, j, frac);
+        R Ep = fma_(frac, Ef[j + 1] - Ef[j], Ef[j]);
+        // leapfrog: v^{n+1/2} = v^{n-1/2} + (q/m) E dt ; x^{n+1} = x^n + v^{n+1/2} dt
+        vx = fma_(qmdt[s], Ep, vx);
+        x = fma_(vx, dt_s[s], x);
+        cnt.particle_steps += 1;
+        // absorbing electrodes
+        if (x < (R)0) { cnt.absorbed[s][0] += 1; return false; }
+        if (x >= Lr) { cnt.absorbed[s][1] += 1; return false; }
+        return collide(s, n, x, vx, vy, vz, id, births);
+    }
+
+    bool collide(int s, uint64_t n, R x, R& vx, R& vy, R& vz, uint32_t id, std::vector<Birth4>* births) {
+        int np = (int)procs[s].size();
+        if (np == 0) return true;
+        Stream st(id, cfg.seed, n, (uint32_t)(s == SP_E ? TAG_E : (s == SP_OM ? TAG_OM : TAG_OP)));
+        R u0 = uniform<R>(st.next());
+        if (!(u0 < Pmax[s])) return true;          // no candidate
+        R u1 = uniform<R>(st.next());
+        uint64_t& warn = cnt.warn_tries;
+        R vt[3] = {0, 0, 0};
+        R E, gx = vx, gy = vy, gz = vz;
+        if (s != SP_E) {
+            maxwellian<R>(st, sig_gas, vt, warn);  // O2 target at T_gas
+            gx = vx - vt[0]; gy = vy - vt[1]; gz = vz - vt[2];
+        }
+        E = kappa[s] * dot3<R>(gx, gy, gz, gx, gy, gz);
+        int i; R w; bool above;
+        grid_locate<R>(E, i, w, above);
+        if (above) cnt.warn_emax += 1;
+        R target = u1 * numax[s];
+        int k = -1;
+        for (int kk = 0; kk < np; ++kk) {
+            if (target < cum_at(s, kk, i, w)) { k = kk; break; }
+        }
+        if (k < 0) return true;                     // null collision
+        const Proc& pr = procs[s][k];
+        if (E < (R)pr.thr) return true;             // below threshold: null
+        cnt.events[s][k] += 1;
+        switch (pr.kind) {
+        case K_ELASTIC: {
+            R nh[3]; isotropic<R>(st, nh, warn);
+            if (s == SP_E) {
+                // isotropic scattering off a heavy target at rest:
+                // |v'|^2 = |v|^2 (1 - (2 m/M)(1 - cos chi))
+                R v2 = dot3<R>(vx, vy, vz, vx, vy, vz);
+                R vm = sqrt_(v2);
+                R cosx = (vm > (R)0) ? dot3<R>(nh[0], nh[1], nh[2], vx, vy, vz) / vm : (R)0;
+                R fac = (R)1 - delta_el * ((R)1 - cosx);
+                R vn = vm * sqrt_(fac);
+                vx = vn * nh[0]; vy = vn * nh[1]; vz = vn * nh[2];
+            } else {
+                // isotropic in the centre-of-mass frame
+                R gm = sqrt_(dot3<R>(gx, gy, gz, gx, gy, gz));
+                R cmx = fma_(a_m[s], vx, a_M[s] * vt[0]);
+                R cmy = fma_(a_m[s], vy, a_M[s] * vt[1]);
+                R cmz = fma_(a_m[s], vz, a_M[s] * vt[2]);
+                R f = a_M[s] * gm;
+                vx = fma_(f, nh[0], cmx); vy = fma_(f, nh[1], cmy); vz = fma_(f, nh[2], cmz);
+            }
+            return true;
+        }
+        case K_EXCITE: {
+            R Ep = E - (R)pr.thr;
+            R nh[3]; isotropic<R>(st, nh, warn);
+            R vn = sqrt_(Ep / kappa[s]);
+            vx = vn * nh[0]; vy = vn * nh[1]; vz = vn * nh[2];
+            return true;
+        }
+        case K_IONIZE: {
+            R Er = E - (R)pr.thr;
+            R u = uniform<R>(st.next());
+            R Es = u * Er;
+            R Epr = Er - Es;
+            R n1[3], n2[3], vi[3];
+            isotropic<R>(st, n1, warn);
+            isotropic<R>(st, n2, warn);
+            maxwellian<R>(st, sig_birth[SP_OP], vi, warn);
+            R vp = sqrt_(Epr / kappa[SP_E]);
+            R vs = sqrt_(Es / kappa[SP_E]);
+            vx = vp * n1[0]; vy = vp * n1[1]; vz = vp * n1[2];
+            births[SP_E].push_back({(double)x, (double)(vs * n2[0]), (double)(vs * n2[1]), (double)(vs * n2[2])});
+            births[SP_OP].push_back({(double)x, (double)vi[0], (double)vi[1], (double)vi[2]});
+            return true;
+        }
+        case K_ATTACH: {
+            R vi[3]; maxwellian<R>(st, sig_birth[SP_OM], vi, warn);
+            births[SP_OM].push_back({(double)x, (double)vi[0], (double)vi[1], (double)vi[2]});
+            return false;
+        }
+        case K_DETACH: {
+            R Er = E - (R)pr.thr;
+            R nh[3]; isotropic<R>(st, nh, warn);
+            R vn = sqrt_(Er / kappa[SP_E]);
+            births[SP_E].push_back({(double)x, (double)(vn * nh[0]), (double)(vn * nh[1]), (double)(vn * nh[2])});
+            return false;
+        }
+        case K_CX: {
+            vx = vt[0]; vy = vt[1]; vz = vt[2];
+            return true;
+        }
+        default:
+            return true;
+        }
+    }
+
+    void process_species(int s, uint64_t n, std::vector<Birth4>* births) {
+        Particles<R> out;
+        Particles<R>& P = sp[s];
+        for (size_t i = 0; i < P.size(); ++i) {
+            R x = P.x[i], vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
+            if (update_particle(s, n, x, vx, vy, vz, P.id[i], births, Eg))
+                out.push(x, vx, vy, vz, P.id[i]);
+        }
+        P = out;
+    }
+
+    // ---- (17) O- + O2+ -> neutrals, cell-binned binary process.
+    // In each cell j, list the O- and the O2+ in array order; with
+    // m = min(n-, n+), M = max(n-, n+) and a cell shift r_j drawn per cell and
+    // step, the i-th member of the shorter list (i < m) is paired with member
+    // (i + r_j) mod M of the longer list (O- counts as shorter on a tie).  A
+    // pair reacts with probability P = M w sigma_n(E_rel) g dt_ion / (A dx),
+    // which gives n- n+ w <sigma g> dt / (A dx) reactions per cell and step.
+    void neutralize(uint64_t n) {
+        if (!have_neutral) return;
+        int Nc = cfg.n_cells;
+        std::vector<std::vector<size_t>> LM(Nc), LP(Nc);
+        for (size_t i = 0; i < sp[SP_OM].size(); ++i) { int j; R fr; cell_of(sp[SP_OM].x[i], j, fr); LM[j].push_back(i); }
+        for (size_t i = 0; i < sp[SP_OP].size(); ++i) { int j; R fr; cell_of(sp[SP_OP].x[i], j, fr); LP[j].push_back(i); }
+        std::vector<char> deadM(sp[SP_OM].size(), 0), deadP(sp[SP_OP].size(), 0);
+        for (int c = 0; c < Nc; ++c) {
+            size_t nm = LM[c].size(), npl = LP[c].size();
+            size_t m = std::min(nm, npl), M = std::max(nm, npl);
+            if (m == 0) continue;
+            Stream sh((uint32_t)c, cfg.seed, n, TAG_SHIFT);
+            uint32_t r = (uint32_t)(sh.next() % (uint32_t)M);
+            bool minus_short = (nm <= npl);
+            for (size_t i = 0; i < m; ++i) {
+                size_t partner = (i + r) % M;
+                size_t a = minus_short ? LM[c][i] : LM[c][partner];
+                size_t b = minus_short ? LP[c][partner] : LP[c][i];
+                uint32_t ida = sp[SP_OM].id[a];
+                Stream st(ida, cfg.seed, n, TAG_PAIR);
+                R u = uniform<R>(st.next());
+                R gx = sp[SP_OM].vx[a] - sp[SP_OP].vx[b];
+                R gy = sp[SP_OM].vy[a] - sp[SP_OP].vy[b];
+                R gz = sp[SP_OM].vz[a] - sp[SP_OP].vz[b];
+                R E = kappa_n * dot3<R>(gx, gy, gz, gx, gy, gz);
+                int gi; R gw; bool above;
+                grid_locate<R>(E, gi, gw, above);
+                if (above) cnt.warn_emax += 1;
+                R K = grid_interp<R>(Ktab, 1, 0, gi, gw);
+                R P = K * (pair_factor * (R)M);
+                cnt.pair_candidates += 1;
+                if (P > (R)1) cnt.warn_pair_gt1 += 1;
+                if (u < P) { deadM[a] = 1; deadP[b] = 1; cnt.neutralized += 1; }
+            }
+        }
+        filter(sp[SP_OM], deadM);
+        filter(sp[SP_OP], deadP);
+    }
+    static void filter(Particles<R>& P, const std::vector<char>& dead) {
+        Particles<R> out;
+        for (size_t i = 0; i < P.size(); ++i)
+            if (!dead[i]) out.push(P.x[i], P.vx[i], P.vy[i], P.vz[i], P.id[i]);
+        P = out;
+    }
+
+    void append_births(std::vector<Birth4>* births) {
+        for (int s = 0; s < NSP; ++s) {
+            for (const Birth4& b : births[s]) {
+                if (next_id[s] == 0xFFFFFFFFu) cnt.id_overflow += 1;
+                sp[s].push((R)b.x, (R)b.vx, (R)b.vy, (R)b.vz, next_id[s]++);
+                cnt.born[s] += 1;
+            }
+        }
+    }
+
+    void ensure_field() {
+        if (!field_valid) { deposit_all(); field_solve((double)step * cfg.dt); }
+    }
+
+    // ---- one time step n -> n+1.
+    void do_step() {
+        ensure_field();
+        uint64_t n = step;
+        bool ion_step = (n % (uint64_t)cfg.ion_subcycle) == 0;
+        std::vector<Birth4> births[NSP];
+        process_species(SP_E, n, births);
+        if (ion_step) {
+            process_species(SP_OM, n, births);
+            process_species(SP_OP, n, births);
+            neutralize(n);
+        }
+        append_births(births);
+        deposit_all();
+        field_solve((double)(n + 1) * cfg.dt);
+        for (int s = 0; s < NSP; ++s)
+            for (int j = 0; j < Ng; ++j) Qacc[s][j] += Q[s][j];
+        acc_steps += 1;
+        step = n + 1;
+    }
+};
+
+struct Handle {
+    int precision;   // 32 or 64
+    Oracle<float>* f;
+    Oracle<double>* d;
+};
+
+
+// One particle through push + absorb + MCC with a given gather field.
+template <class R>
+int update_one(Oracle<R>& O, int s, uint64_t n, const double* Ef, double* state, uint32_t id,
+               double* births, int* nb) {
+    std::vector<R> Eg(O.Ng);
+    for (int j = 0; j < O.Ng; ++j) Eg[j] = (R)Ef[j];
+    R x = (R)state[0], vx = (R)state[1], vy = (R)state[2], vz = (R)state[3];
+    std::vector<Birth4> b[NSP];
+    int alive = O.update_particle(s, n, x, vx, vy, vz, id, b, Eg) ? 1 : 0;
+    state[0] = x; state[1] = vx; state[2] = vy; state[3] = vz;
+    int k = 0;
+    for (int d = 0; d < NSP; ++d)
+        for (const Birth4& bb : b[d]) {
+            births[5 * k + 0] = d; births[5 * k + 1] = bb.x; births[5 * k + 2] = bb.vx;
+            births[5 * k + 3] = bb.vy; births[5 * k + 4] = bb.vz; ++k;
+        }
+    *nb = k;
+    return alive;
+}
+
+}  // namespace
+
+// ================================================================== exports
+extern "C" {
+
+void* oracle_create(const oracle_config* cfg, int precision) {
+    if (!cfg || cfg->n_cells < 1 || cfg->ion_subcycle < 1 || !(cfg->L > 0) || !(cfg->dt > 0)) return nullptr;
+    Handle* h = new Handle();
+    h->precision = precision;
+    h->f = nullptr; h->d = nullptr;
+    if (precision == 64) h->d = new Oracle<double>(*cfg);
+    else h->f = new Oracle<float>(*cfg);
+    return h;
+}
+
+void oracle_destroy(void* p) {
+    Handle* h = (Handle*)p;
+    if (!h) return;
+    delete h->f; delete h->d; delete h;
+}
+
+#define DISPATCH(h, expr) do { if ((h)->f) { auto& O = *(h)->f; expr; } else { auto& O = *(h)->d; expr; } } while (0)
+
+int oracle_set_processes(void* p, const oracle_process* procs, int n) {
+    Handle* h = (Handle*)p; int rc = 0;
+    DISPATCH(h, rc = O.set_processes(procs, n));
+    return rc;
+}
+
+int oracle_load(void* p, int s, const float* x, const float* vx, const float* vy, const float* vz,
+                const uint32_t* id, uint64_t n) {
+    Handle* h = (Handle*)p;
+    if (s < 0 || s >= NSP) return -1;
+    DISPATCH(h, {
+        O.sp[s].clear();
+        uint32_t mx = 0;
+        for (uint64_t i = 0; i < n; ++i) {
+            O.sp[s].push(x[i], vx[i], vy[i], vz[i], id[i]);
+            mx = std::max(mx, id[i] + 1u);
+        }
+        O.next_id[s] = mx;
+        O.field_valid = false;
+    });
+    return 0;
+}
+
+int oracle_set_next_id(void* p, int s, uint32_t v) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, O.next_id[s] = v);
+    return 0;
+}
+
+int oracle_step(void* p, uint64_t nsteps) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, for (uint64_t k = 0; k < nsteps; ++k) O.do_step());
+    return 0;
+}
+
+int oracle_set_step(void* p, uint64_t step) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, { O.step = step; O.field_valid = false; });
+    return 0;
+}
+
+uint64_t oracle_get_step(void* p) {
+    Handle* h = (Handle*)p; uint64_t v = 0;
+    DISPATCH(h, v = O.step);
+    return v;
+}
+
+uint64_t oracle_count(void* p, int s) {
+    Handle* h = (Handle*)p; uint64_t v = 0;
+    DISPATCH(h, v = O.sp[s].size());
+    return v;
+}
+
+// Particle state in double (exact for the float mode).
+int oracle_read(void* p, int s, double* x, double* vx, double* vy, double* vz, uint32_t* id) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, {
+        for (size_t i = 0; i < O.sp[s].size(); ++i) {
+            x[i] = O.sp[s].x[i]; vx[i] = O.sp[s].vx[i]; vy[i] = O.sp[s].vy[i]; vz[i] = O.sp[s].vz[i];
+            id[i] = O.sp[s].id[i];
+        }
+    });
+    return 0;
+}
+
+uint32_t oracle_next_id(void* p, int s) {
+    Handle* h = (Handle*)p; uint32_t v = 0;
+    DISPATCH(h, v = O.next_id[s]);
+    return v;
+}
+
+// Field of the current step: phi (FP64), E (FP64), and the E copy used by the gather.
+int oracle_read_field(void* p, double* phi, double* E, double* Egather) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, {
+        O.ensure_field();
+        for (int j = 0; j < O.Ng; ++j) { phi[j] = O.phi[j]; E[j] = O.Efield[j]; Egather[j] = (double)O.Eg[j]; }
+    });
+    return 0;
+}
+
+// Fixed-point node charges Q[3][Ng] of the current particles and the
+// accumulated moments Qacc[3][Ng]; returns the number of accumulated steps.
+uint64_t oracle_read_charge(void* p, uint64_t* Q, uint64_t* Qacc) {
+    Handle* h = (Handle*)p; uint64_t v = 0;
+    DISPATCH(h, {
+        O.ensure_field();
+        for (int s = 0; s < NSP; ++s)
+            for (int j = 0; j < O.Ng; ++j) {
+                Q[(size_t)s * O.Ng + j] = O.Q[s][j];
+                if (Qacc) Qacc[(size_t)s * O.Ng + j] = O.Qacc[s][j];
+            }
+        v = O.acc_steps;
+    });
+    return v;
+}
+
+int oracle_reset_moments(void* p) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, { for (int s = 0; s < NSP; ++s) std::fill(O.Qacc[s].begin(), O.Qacc[s].end(), 0); O.acc_steps = 0; });
+    return 0;
+}
+
+// Counters as a flat u64 array; layout = struct Counters.
+int oracle_counters(void* p, uint64_t* out, int n) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, {
+        int m = (int)(sizeof(Counters) / sizeof(uint64_t));
+        std::memcpy(out, &O.cnt, sizeof(uint64_t) * (size_t)std::min(n, m));
+    });
+    return (int)(sizeof(Counters) / sizeof(uint64_t));
+}
+
+// Rate table of species s: cumulative rates [NGRID][nproc] (precision R, as
+// double), per-process FP64 rates, nu_max and P_max.  Returns nproc.
+int oracle_table(void* p, int s, double* cum, double* nu, double* numax, double* pmax) {
+    Handle* h = (Handle*)p; int np = 0;
+    DISPATCH(h, {
+        np = (int)O.procs[s].size();
+        for (size_t i = 0; i < (size_t)NGRID * np; ++i) {
+            if (cum) cum[i] = (double)O.cum[s][i];
+            if (nu) nu[i] = O.nu64[s][i];
+        }
+        if (numax) *numax = O.numax64[s];
+        if (pmax) *pmax = (double)O.Pmax[s];
+    });
+    return np;
+}
+
+int oracle_neutral_table(void* p, double* K) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, { for (int i = 0; i < NGRID; ++i) K[i] = (double)O.Ktab[i]; });
+    return NGRID;
+}
+
+// One particle of species s through push + absorb + MCC at step n with the
+// gather field Ef[Ng] (given in double, rounded to R).  Returns 1 if the
+// particle stays, 0 if it leaves; births (up to 2) are written to
+// births[8] = {dst, x, vx, vy, vz, ...} and their number to *nb.  Used for
+// sampled checks at sizes where the whole oracle step is too slow.
+int oracle_update_particle(void* p, int s, uint64_t n, const double* Ef, double* state, uint32_t id,
+                           double* births, int* nb) {
+    Handle* h = (Handle*)p;
+    if (h->f) return update_one<float>(*h->f, s, n, Ef, state, id, births, nb);
+    return update_one<double>(*h->d, s, n, Ef, state, id, births, nb);
+}
+
+// ---- standalone pieces (pinned directly by tests)
+void oracle_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+    U4 r = philox4x32_10(ctr, key);
+    for (int i = 0; i < 4; ++i) out[i] = r.v[i];
+}
+
+float oracle_ln_f32(float x) { return ln_(x); }
+
+// n samples of the stream helpers (precision 32 or 64): kind 0 = isotropic
+// unit vectors (3 per sample), 1 = normal pairs (2 per sample).
+void oracle_sample(int kind, int precision, uint32_t seed, uint64_t n, double* out) {
+    uint64_t warn = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        Stream st((uint32_t)i, seed, 0, 7);
+        if (precision == 64) {
+            if (kind == 0) { double v[3]; isotropic<double>(st, v, warn); out[3*i] = v[0]; out[3*i+1] = v[1]; out[3*i+2] = v[2]; }
+            else { double a, b; normal_pair<double>(st, a, b, warn); out[2*i] = a; out[2*i+1] = b; }
+        } else {
+            if (kind == 0) { float v[3]; isotropic<float>(st, v, warn); out[3*i] = v[0]; out[3*i+1] = v[1]; out[3*i+2] = v[2]; }
+            else { float a, b; normal_pair<float>(st, a, b, warn); out[2*i] = a; out[2*i+1] = b; }
+        }
+    }
+}
+
+void oracle_solve_field(int n_cells, double dx, double weight, double area, double V0,
+                        const long long* Rnet, double* phi, double* E) {
+    Oracle<double>::solve_field(n_cells, dx, weight, area, V0, Rnet, phi, E);
+}
+
+// CIC fixed-point deposit of n float positions onto n_cells+1 nodes.
+void oracle_deposit(int n_cells, double L, const float* x, uint64_t n, uint64_t* Q) {
+    oracle_config c; std::memset(&c, 0, sizeof(c));
+    c.n_cells = n_cells; c.L = L; c.ion_subcycle = 1; c.dt = 1; c.area = 1; c.weight = 1;
+    c.m_e = 1; c.m_OM = 1; c.m_OP = 1; c.M_gas = 1; c.T_gas = 1; c.p = 1;
+    Oracle<float> O(c);
+    std::vector<uint64_t> q(n_cells + 1, 0);
+    for (uint64_t i = 0; i < n; ++i) O.deposit_one(q, x[i]);
+    for (int j = 0; j <= n_cells; ++j) Q[j] = q[j];
+}
+
+double oracle_grid_energy(int i) { return grid_energy(i); }
+int oracle_ngrid() { return NGRID; }
+int oracle_ncounters() { return (int)(sizeof(Counters) / sizeof(uint64_t)); }
+
+}  // extern "C"
