@@ -1,0 +1,390 @@
+"""Benchmark: particle-steps/s of the PIC-MCC particle loop on GB300.
+
+Workload (N=1): `scale_512` — 2.5 cm gap, 512 cells, U = 300 V, p = 20 Pa,
+metastable fraction 5%, 1000 steps per RF cycle, ions subcycled x10,
+4e6 e + 4e6 O- + 8e6 O2+ (quasi-neutral load), synthetic seeded inputs.
+One bench step = one RF cycle (1000 time steps: every step pushes the
+electrons, every 10th also the ions and runs the O-/O2+ neutralization; each
+step ends with the deposit and the Poisson solve).  The particle arrays
+(320 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Under torchrun each rank runs an independent replica (seed = rank): the
+method does not shard (one discharge is one coupled field solve), so N GPUs
+run N discharges and `value` sums their particle-steps over the max time.
+`--impl reference` times the CPU oracle (test infrastructure, single thread)
+on bounded samples of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_0705_0497_gb300 import inputs, xsec
+
+WORKLOAD = "scale_512"
+METRIC = "particle-steps/s (push+MCC+deposit) on 1 GB300, fraction of HBM roofline"
+UNIT = "particle-steps/s"
+BYTES_PER_PARTICLE_STEP = 40          # read + write of x, vx, vy, vz, id (algorithmic)
+DESIGN_BYTES_PER_PARTICLE_STEP = 28   # this design: read 20 B, write x, vx in place
+PROFILE = os.path.join(ROOT, "profiles", "push_e_scale_512.md")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("push.cu", "common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_0705_0497_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the electron kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None, None
+    vals = {}
+    for line in open(PROFILE):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    try:
+        if vals.get("kernel_source_sha256_16") != kernel_hash():
+            return None, None
+        return float(vals["dram_bytes_per_particle"]), vals
+    except (KeyError, ValueError):
+        return None, None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def allreduce(vals, op):
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return vals
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.cpu().tolist()
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def capacity(counts):
+    return tuple(int(n * 1.5) + (1 << 20) for n in counts)
+
+
+def run_cpu_oracle(cfg, counts, T, nsteps, seed=0):
+    """The oracle, single thread, on the first `nsteps` time steps of the
+    workload with its full initial load; returns particle-steps/s."""
+    import oracle
+    st = inputs.initial_state(cfg, counts, T, seed=seed)
+    o = oracle.Oracle(cfg, 32)
+    o.set_processes(xsec.oxygen_set())
+    for s, p in enumerate(st):
+        o.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])
+    del st
+    o.field()   # initial deposit + field solve (not timed)
+    c0 = o.counters()["particle_steps"]
+    t = time.perf_counter()
+    o.step(nsteps)
+    dt = time.perf_counter() - t
+    ps = o.counters()["particle_steps"] - c0
+    return ps / dt, ps, dt
+
+
+def bench_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    cfg, counts, T, _ = inputs.workload(WORKLOAD)
+    spc = cfg["steps_per_cycle"]
+    # one reference step = one time step of the workload (a bounded sample of a cycle)
+    per = []
+    import oracle
+    st = inputs.initial_state(cfg, counts, T)
+    o = oracle.Oracle(cfg, 32)
+    o.set_processes(xsec.oxygen_set())
+    for s, p in enumerate(st):
+        o.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])
+    del st
+    o.field()
+    o.step(args.warmup)
+    c0 = o.counters()["particle_steps"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        o.step(1)
+        per.append(time.perf_counter() - t)
+    wall = time.perf_counter() - t0
+    ps = o.counters()["particle_steps"] - c0
+    value = ps / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one time step (bounded sample of an RF cycle)",
+                       "n_cells": cfg["n_cells"], "particles": list(counts), "steps_per_cycle": spc,
+                       "ion_subcycle": cfg["ion_subcycle"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"time steps {args.warmup}..{args.warmup + args.steps - 1} of {WORKLOAD} "
+                                       "with the full 1.6e7-particle load"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_gpu(args, world, rank, local):
+    import torch
+    from paper_0705_0497_gb300 import api
+    torch.cuda.set_device(local)
+    cfg, counts, T, cycles = inputs.workload(WORKLOAD, seed=rank)
+    spc = cfg["steps_per_cycle"]
+    st = inputs.initial_state(cfg, counts, T, seed=rank)
+    g = api.Discharge(cfg, capacity(counts), device=local)
+    g.set_processes(xsec.oxygen_set())
+    g.load_state(st)
+    del st
+    stream = torch.cuda.Stream(device=local)
+    g.step(args.warmup * spc, stream)
+    g.synchronize()
+    live0 = [g.count(s) for s in range(3)]
+
+    # ---- timed region A: K RF cycles, device-resident, CUDA events on the stream
+    s0 = g.stats()
+    l0 = g.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.step(spc, stream)
+    ev1.record(stream)
+    g.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    s1 = g.stats()
+    launches = g.launch_count() - l0
+    ps = s1["particle_steps"] - s0["particle_steps"]
+    live1 = [g.count(s) for s in range(3)]
+
+    # ---- timed region B: the same loop with an event pair around every launch
+    kb = max(1, min(args.steps, 10))
+    g.set_timing(True)
+    sb0 = g.stats()
+    for _ in range(kb):
+        g.step(spc, stream)
+    g.synchronize()
+    tm = g.timing()
+    sb1 = g.stats()
+    g.set_timing(False)
+    pe = sb1["particle_steps_0"] - sb0["particle_steps_0"]
+
+    # ---- end to end through the C ABI with host (pinned) buffers: every step
+    # loads the state from the host, runs one RF cycle and reads the state
+    # and the cycle-averaged moments back
+    e2e_steps = max(1, min(args.steps, 5))
+    host = []
+    for s in range(3):
+        n = int(g.count(s) * 1.2) + 4096
+        d = {k: torch.empty(n, dtype=torch.float32).pin_memory().numpy() for k in ("x", "vx", "vy", "vz")}
+        d["id"] = torch.empty(n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        d["n"] = g.read_into(s, d)
+        host.append(d)
+    g.moments(reset=True)
+    torch.cuda.synchronize()
+    se0 = g.stats()["particle_steps"]
+    ps_e2e = 0
+    h2d = d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for s in range(3):
+            d = host[s]
+            n = d["n"]
+            g.load(s, d["x"][:n], d["vx"][:n], d["vy"][:n], d["vz"][:n], d["id"][:n])
+            h2d += 20 * n
+        c0 = g.stats()["particle_steps"]
+        g.step(spc, stream)
+        for s in range(3):
+            d = host[s]
+            need = g.count(s)
+            if need > len(d["x"]):
+                for k in ("x", "vx", "vy", "vz"):
+                    d[k] = torch.empty(int(need * 1.2), dtype=torch.float32).pin_memory().numpy()
+                d["id"] = torch.empty(int(need * 1.2), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+            d["n"] = g.read_into(s, d)
+            d2h += 20 * d["n"]
+        dens, _ = g.moments(reset=True)
+        d2h += dens.nbytes
+        ps_e2e += g.stats()["particle_steps"] - c0
+    e2e_wall = time.perf_counter() - t0
+    g.close()
+
+    # ---- aggregate over ranks (max time, summed work)
+    t_max = allreduce([ms], "max")[0]
+    ps_sum, pe_sum, e2e_ps_sum = allreduce([float(ps), float(pe), float(ps_e2e)], "sum")
+    e2e_t = allreduce([e2e_wall], "max")[0]
+    if rank != 0:
+        return 0
+    value = ps_sum / (t_max * 1e-3)
+    peak, peak_kind = measured_peaks()
+    ms_e, n_e = tm["push_e"]
+    achieved = (pe / n_e) * BYTES_PER_PARTICLE_STEP / (ms_e / n_e * 1e-3) / 1e9 if n_e else None
+    traffic_pp, prof = profile_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_push<e> (gather, push, absorb, MCC, deposit)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs: copy bandwidth)",
+                "traffic": (traffic_pp * pe / n_e) if (traffic_pp and n_e) else None,
+                "algorithmic_bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
+                "design_bytes_per_particle_step": DESIGN_BYTES_PER_PARTICLE_STEP,
+                "design_frac": ((pe / n_e) * DESIGN_BYTES_PER_PARTICLE_STEP / (ms_e / n_e * 1e-3) / 1e9 / peak)
+                if n_e else None,
+                "electron_particles_per_launch": pe / n_e if n_e else None,
+                "avg_launch_us": ms_e / n_e * 1e3 if n_e else None,
+                "kernel_share_of_step": ms_e / sum(v[0] for v in tm.values()) if n_e else None,
+                "per_kernel_ms_per_cycle": {k: v[0] / kb for k, v in tm.items() if v[1]}}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, cps, cdt = run_cpu_oracle(cfg, counts, T, 10)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first 10 time steps (one ion subcycle) of {WORKLOAD} with the full "
+                         f"{sum(counts):.3g}-particle load: {cps} particle-steps in {cdt:.1f} s"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one RF cycle = 1000 time steps",
+                       "L_m": cfg["L"], "n_cells": cfg["n_cells"], "U_V": cfg["U"], "p_Pa": cfg["p"],
+                       "C_meta": cfg["C_meta"], "ion_subcycle": cfg["ion_subcycle"],
+                       "initial_particles": list(counts), "live_at_timed_start": live0,
+                       "live_at_timed_end": live1, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (particle arrays 320 MB > 129 MB L2), no flush"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_ps_sum / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
+                    "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
+                    "what": "load state from pinned host memory, one RF cycle, read state + moments back"},
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return bench_reference(args, world, rank)
+    return bench_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * o2pic — C ABI of the GB300 (sm_103a) particle loop of the 1D3V PIC-MCC
+ * model of a capacitively coupled RF oxygen discharge.
+ *
+ * Method: F. X. Bronold et al., "Particle-based modeling of oxygen
+ * discharges", 28th ICPIG (2007), Sec. 2 (model), Table 1 (reactions),
+ * Eq. 1 (associative detachment).  One call of o2pic_step advances the
+ * discharge by whole time steps; each step is
+ *   field gather -> leapfrog push in x (v_x, v_y, v_z carried) ->
+ *   absorbing electrodes -> null-collision Monte Carlo against the O2
+ *   background (n = p/kT, T_gas = 300 K) and O2(a1Dg) at C n_O2 ->
+ *   births / removals -> (ion steps) cell-binned O- + O2+ neutralization (17)
+ *   -> CIC charge deposition -> Poisson solve with phi(0) = U sin(2 pi f t),
+ *   phi(L) = 0 -> cycle-accumulated density moments.
+ *
+ * Conventions for every function:
+ *   - return 0 (O2PIC_OK) or a negative O2PIC_E_* code; o2pic_strerror()
+ *     names it;
+ *   - SI units; energies of cross-section tables in eV;
+ *   - the context owns all device memory it allocates; pointers passed in are
+ *     borrowed for the duration of the call only (the call copies);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the context's own
+ *     stream); HOST pointers may be pageable or pinned; DEVICE pointers must
+ *     live on the context's device;
+ *   - species index: 0 = e, 1 = O-, 2 = O2+.
+ *   - work is enqueued asynchronously on the context's stream; device-side
+ *     errors (capacity overflow, id overflow, non-finite particles, a bounded
+ *     wait that gave up) are latched in the context and returned by the next
+ *     synchronizing call (o2pic_synchronize, o2pic_read_*, o2pic_get_stats).
+ *     After an error the particle state is unspecified; reload particles.
+ */
+#ifndef O2PIC_H
+#define O2PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define O2PIC_NSPECIES 3
+#define O2PIC_MAXPROC 16
+
+enum { O2PIC_E = 0, O2PIC_OM = 1, O2PIC_OP = 2 };
+
+/* Process kinds (Table 1 of the paper):
+ *   ELASTIC    (7), (8): isotropic; electrons in the lab frame off a target at
+ *              rest with recoil loss 2m/M (1 - cos chi), ions in the CM frame
+ *   EXCITE     (10)-(15): electron loses threshold_eV, isotropic
+ *   IONIZE     (21): e + O2 -> 2e + O2+, the excess energy split uniformly
+ *   ATTACH     (18): e + O2 -> O + O-
+ *   DETACH     (19), (20): O- + O2 / O2(a) -> ... + e
+ *   CX         (9): O2+ + O2 charge exchange (ion takes the target velocity)
+ *   NEUTRALIZE (17): O- + O2+ -> neutrals, binary, cell-local (give it with
+ *              species O-, target ION; sigma is the neutralization cross
+ *              section, e.g. the Landau-Zener form of the paper) */
+enum { O2PIC_ELASTIC = 0, O2PIC_EXCITE = 1, O2PIC_IONIZE = 2, O2PIC_ATTACH = 3,
+       O2PIC_DETACH = 4, O2PIC_CX = 5, O2PIC_NEUTRALIZE = 6 };
+
+/* Targets: ground-state O2 (density p/kT), metastable O2(a1Dg) (density
+ * C_meta p/kT, Sec. 2), or the other ion species (neutralization only). */
+enum { O2PIC_TARGET_O2 = 0, O2PIC_TARGET_O2_META = 1, O2PIC_TARGET_ION = 2 };
+
+enum { O2PIC_HOST = 0, O2PIC_DEVICE = 1 };
+
+#define O2PIC_OK 0
+#define O2PIC_E_INVALID_ARG (-1)
+#define O2PIC_E_CAPACITY (-2)
+#define O2PIC_E_ID_OVERFLOW (-3)
+#define O2PIC_E_NONFINITE (-4)
+#define O2PIC_E_CUDA (-5)
+#define O2PIC_E_TIMEOUT (-6)
+#define O2PIC_E_STATE (-7)
+
+typedef struct o2pic_ctx o2pic_ctx;
+
+/* Discharge configuration (Sec. 2): gap L [m], RF frequency f [Hz], voltage
+ * amplitude U [V] on the electrode at x = 0 (the one at x = L is grounded),
+ * pressure p [Pa], gas temperature T_gas [K] (300 in the paper), metastable
+ * fraction C_meta (n_Delta = C n_O2), time step dt [s], macro-particle weight
+ * [particles per m^2 of electrode], electrode area [m^2], masses [kg],
+ * n_cells grid cells (n_cells + 1 nodes), ions pushed every ion_subcycle
+ * steps with dt_ion = ion_subcycle dt, seed of the Philox streams,
+ * capacity[s] = maximum particles of species s (live + dead slots + births
+ * of one step), compact_check = steps between checks for dead slots
+ * (0 = default 16), device = CUDA ordinal. */
+typedef struct {
+    double L, f, U, p, T_gas, C_meta, dt, weight, area;
+    double m_e, m_OM, m_OP, M_gas;
+    int32_t n_cells, ion_subcycle;
+    uint32_t seed, compact_check;
+    uint64_t capacity[O2PIC_NSPECIES];
+    int32_t device, reserved;
+} o2pic_config;
+
+/* One cross-section table: sigma_m2[i] at E_eV[i] (n >= 1, E strictly
+ * increasing), linearly interpolated, constant beyond the ends, zero below
+ * threshold_eV. */
+typedef struct {
+    int32_t species, kind, target, n;
+    double threshold_eV;
+    const double* E_eV;
+    const double* sigma_m2;
+} o2pic_process;
+
+/* Counters since create (or the last load of all species); layout is fixed. */
+typedef struct {
+    uint64_t events[O2PIC_NSPECIES][O2PIC_MAXPROC]; /* real collisions per process */
+    uint64_t absorbed[O2PIC_NSPECIES][2];           /* [species][0: x<0, 1: x>=L] */
+    uint64_t born[O2PIC_NSPECIES];
+    uint64_t neutralized, pair_candidates, particle_steps;
+    uint64_t warn_emax;      /* energy above the 2^12 eV table grid */
+    uint64_t warn_tries;     /* a rejection loop hit its cap */
+    uint64_t warn_pair_gt1;  /* neutralization probability above 1 */
+    uint64_t id_overflow;
+    uint64_t step;
+    uint64_t live[O2PIC_NSPECIES];
+    uint64_t slots[O2PIC_NSPECIES];
+    uint64_t next_id[O2PIC_NSPECIES];
+    uint64_t error_flags;
+    uint64_t particle_steps_species[O2PIC_NSPECIES];  /* particles pushed, per species */
+} o2pic_stats;
+
+/* Fills `cfg` with the defaults (parity-case geometry, T_gas = 300 K, O, O2
+ * masses, capacity 0 = must be set). */
+int o2pic_config_init(o2pic_config* cfg);
+
+/* Validates `cfg`, selects the device, allocates all device memory
+ * (particles: 2 x 20 B x capacity per species) and returns a context in *out.
+ * Errors: INVALID_ARG (bad configuration; no CUDA call is made), CUDA. */
+int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out);
+
+/* Builds the per-species rate tables nu_k(E_i) = n_target sigma_k(E_i) g(E_i)
+ * on 32 points per octave over [2^-10, 2^12] eV (FP64, stored FP32 as
+ * cumulative sums), nu_max and P_max = 1 - exp(-nu_max dt_s) (null-collision
+ * method, Sec. 2), and the (17) rate-coefficient table; copies them to the
+ * device.  At most O2PIC_MAXPROC processes per species, one NEUTRALIZE.
+ * Errors: INVALID_ARG. */
+int o2pic_set_processes(o2pic_ctx* ctx, const o2pic_process* procs, int nproc);
+
+/* Replaces species `species` by n particles (SoA float32 x, vx, vy, vz and
+ * uint32 ids, unique within the species); velocities are taken as
+ * v^{n-1/2}.  mem_kind = O2PIC_HOST or O2PIC_DEVICE.  The next step starts
+ * with a fresh deposit and field solve.  New ids continue at max(id) + 1.
+ * Errors: INVALID_ARG (n > capacity, x outside [0, L), non-finite), CUDA. */
+int o2pic_load_particles(o2pic_ctx* ctx, int species, const float* x, const float* vx,
+                         const float* vy, const float* vz, const uint32_t* id, uint64_t n,
+                         int mem_kind, void* stream);
+
+/* Enqueues nsteps time steps (Sec. 2 loop; see the file header) on `stream`.
+ * Asynchronous; errors of the enqueued work appear at the next sync. */
+int o2pic_step(o2pic_ctx* ctx, uint64_t nsteps, void* stream);
+
+/* Waits for the context's work and returns the first latched error. */
+int o2pic_synchronize(o2pic_ctx* ctx);
+
+/* Live particles of `species` in array order (the order the method defines:
+ * survivors in order, then births in creation order), up to `cap`; *n gets
+ * the live count (even when it exceeds cap).  mem_kind as for load. */
+int o2pic_read_particles(o2pic_ctx* ctx, int species, float* x, float* vx, float* vy, float* vz,
+                         uint32_t* id, uint64_t cap, uint64_t* n, int mem_kind);
+
+/* Current field on the n_cells + 1 nodes: phi [V] (FP64) and E [V/m] (the
+ * FP32 copy the gather uses); either pointer may be NULL.  Host memory. */
+int o2pic_read_field(o2pic_ctx* ctx, double* phi, float* E);
+
+/* Fixed-point node charges (2^16 per macro-particle, CIC) of the current
+ * particles, Q[3][n_cells+1], and their sum over the steps since the last
+ * reset, Qacc[3][n_cells+1] (either may be NULL); *acc_steps = steps summed.
+ * Host memory. */
+int o2pic_read_charge(o2pic_ctx* ctx, uint64_t* Q, uint64_t* Qacc, uint64_t* acc_steps);
+
+/* Cycle-averaged densities (Figs. 3-4 of the paper) [m^-3] on the nodes,
+ * density[3][n_cells+1], from the accumulated charge (wall nodes hold half a
+ * cell); reset != 0 restarts the accumulation.  Host memory. */
+int o2pic_read_moments(o2pic_ctx* ctx, double* density, uint64_t* acc_steps, int reset);
+
+int o2pic_get_stats(o2pic_ctx* ctx, o2pic_stats* out);
+
+/* Sets the step counter (the RNG streams are keyed by it): with the
+ * particles of a saved state this resumes a run bit for bit. */
+int o2pic_set_step(o2pic_ctx* ctx, uint64_t step);
+
+/* Kernel timing with CUDA events on the launching stream: on != 0 records an
+ * event pair around every launch; o2pic_get_timing returns, per kernel kind
+ * (0 push e, 1 push O-, 2 push O2+, 3 pair scan, 4 pair, 5 field, 6 compact,
+ * 7 deposit), the summed milliseconds, launches and particles processed. */
+int o2pic_set_timing(o2pic_ctx* ctx, int on);
+int o2pic_get_timing(o2pic_ctx* ctx, double* ms, uint64_t* launches, uint64_t* items, int nkinds);
+
+/* Kernels launched by this context since create. */
+uint64_t o2pic_launch_count(o2pic_ctx* ctx);
+
+/* The library's random streams: out[4i..4i+3] = Philox4x32-10(ctr[4i..],
+ * key[2i..]) (Salmon et al., SC'11).  Device pointers, n <= 2^31. */
+int o2pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, uint64_t n, void* stream);
+
+/* The single-precision log used by the polar normal method (atanh series),
+ * out[i] = ln(x[i]) for x in (0, 1].  Device pointers. */
+int o2pic_ln_f32(const float* x, float* out, uint64_t n, void* stream);
+
+const char* o2pic_strerror(int code);
+
+void o2pic_destroy(o2pic_ctx* ctx);
+
+int o2pic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* O2PIC_H */

@@ -75,6 +75,7 @@ def lib():
         L.oracle_ln_f32.argtypes = [ctypes.c_float]
         L.oracle_sample.argtypes = [i32, i32, u32, u64, vp]
         L.oracle_solve_field.argtypes = [i32, dbl, dbl, dbl, dbl, vp, vp, vp]
+        L.oracle_solve_field_thomas.argtypes = [i32, dbl, dbl, dbl, dbl, vp, vp, vp]
         L.oracle_deposit.argtypes = [i32, dbl, vp, u64, vp]
         L.oracle_grid_energy.restype = dbl
         L.oracle_grid_energy.argtypes = [i32]
@@ -227,11 +228,14 @@ def sample(kind, precision, seed, n):
     return out.reshape(n, width)
 
 
-def solve_field(n_cells, dx, weight, area, V0, Rnet):
+def solve_field(n_cells, dx, weight, area, V0, Rnet, method="closed"):
+    """Field of net node charges Rnet (2^16 per particle): the method's closed
+    form ("closed") or the Thomas algorithm ("thomas")."""
     R = np.ascontiguousarray(Rnet, dtype=np.int64)
     phi = np.zeros(n_cells + 1)
     E = np.zeros(n_cells + 1)
-    lib().oracle_solve_field(n_cells, dx, weight, area, V0, _ptr(R), _ptr(phi), _ptr(E))
+    f = lib().oracle_solve_field if method == "closed" else lib().oracle_solve_field_thomas
+    f(n_cells, dx, weight, area, V0, _ptr(R), _ptr(phi), _ptr(E))
     return phi, E
 
 

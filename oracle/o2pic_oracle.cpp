@@ -426,9 +426,7 @@ template <class R> struct Oracle {
 
     // ---- Poisson (FP64): interior nodes j = 1..N-1,
     //   -phi_{j-1} + 2 phi_j - phi_{j+1} = rho_j dx^2 / eps0,
-    // phi_0 = U sin(2 pi f t) (driven electrode at x = 0), phi_N = 0 (grounded),
-    // solved by the Thomas algorithm; E = -dphi/dx by central differences,
-    // boundary nodes by Gauss's law over the half cell next to the wall.
+    // phi_0 = U sin(2 pi f t) (driven electrode at x = 0), phi_N = 0 (grounded).
     void field_solve(double t) {
         int N = cfg.n_cells;
         std::vector<long long> Rn(Ng);
@@ -440,8 +438,40 @@ template <class R> struct Oracle {
         field_valid = true;
     }
 
+    // Poisson (Sec. 2), Dirichlet at both walls.  With the net node charge R_j
+    // (2^16 units per macro-particle) the interior equations read
+    //   (phi_{j+1} - phi_j) - (phi_j - phi_{j-1}) = -c R_j,
+    //   c = e w dx / (A eps0 2^16),
+    // i.e. a discrete double integration: with S_m = sum_{k=1..m} R_k and
+    // T_j = sum_{m<j} S_m (exact integers), D_0 = phi_1 - phi_0 follows from
+    // phi_N = 0 and
+    //   phi_j = V0 + j D_0 - c T_j,   D_j = phi_{j+1} - phi_j = D_0 - c S_j.
+    // E = -dphi/dx by central differences inside, E_j = -(D_j + D_{j-1})/(2dx);
+    // at the walls from Gauss's law over the half cell, E_0 = (-D_0 - c R_0)/dx,
+    // E_N = (-D_{N-1} + c R_N)/dx.  This is the exact solution of the same
+    // tridiagonal system the Thomas algorithm solves (solve_field_thomas,
+    // kept to pin it); the only rounding is in the final FP64 expressions.
     static void solve_field(int N, double dx, double w, double A, double V0, const long long* Rn,
                             double* phi, double* E) {
+        const double c = QE * w * dx / (A * EPS0 * FIX_ONE);
+        std::vector<long long> S(N + 1, 0), T(N + 1, 0);
+        for (int m = 1; m <= N; ++m) S[m] = S[m - 1] + Rn[m];
+        for (int j = 1; j <= N; ++j) T[j] = T[j - 1] + S[j - 1];
+        const double D0 = (c * (double)T[N] - V0) / (double)N;
+        for (int j = 0; j <= N; ++j) {
+            if (j == 0) phi[j] = V0;
+            else if (j == N) phi[j] = 0.0;
+            else phi[j] = V0 + (double)j * D0 - c * (double)T[j];
+        }
+        for (int j = 1; j <= N - 1; ++j) E[j] = (c * (double)(S[j] + S[j - 1]) - 2.0 * D0) / (2.0 * dx);
+        E[0] = (-D0 - c * (double)Rn[0]) / dx;
+        E[N] = (c * (double)S[N - 1] - D0 + c * (double)Rn[N]) / dx;
+    }
+
+    // The same system by the Thomas algorithm (a = c = -1, b = 2) with the
+    // boundary values moved to the right-hand side; E as above.  Test use.
+    static void solve_field_thomas(int N, double dx, double w, double A, double V0, const long long* Rn,
+                                   double* phi, double* E) {
         std::vector<double> rhs(N + 1, 0.0), cp(N + 1, 0.0), dp(N + 1, 0.0);
         for (int j = 1; j <= N - 1; ++j) {
             double rho = QE * w * (double)Rn[j] / (FIX_ONE * A * dx);
@@ -449,16 +479,13 @@ template <class R> struct Oracle {
         }
         phi[0] = V0; phi[N] = 0.0;
         if (N >= 2) {
-            rhs[1] += V0;          // phi_0 moved to the right-hand side
-            rhs[N - 1] += 0.0;     // phi_N = 0
-            // Thomas: a = -1, b = 2, c = -1
-            double b = 2.0;
-            cp[1] = -1.0 / b;
-            dp[1] = rhs[1] / b;
+            rhs[1] += V0;
+            cp[1] = -1.0 / 2.0;
+            dp[1] = rhs[1] / 2.0;
             for (int j = 2; j <= N - 1; ++j) {
-                double den = 2.0 - (-1.0) * cp[j - 1];
+                double den = 2.0 + cp[j - 1];
                 cp[j] = -1.0 / den;
-                dp[j] = (rhs[j] - (-1.0) * dp[j - 1]) / den;
+                dp[j] = (rhs[j] + dp[j - 1]) / den;
             }
             phi[N - 1] = dp[N - 1];
             for (int j = N - 2; j >= 1; --j) phi[j] = dp[j] - cp[j] * phi[j + 1];
@@ -911,6 +938,11 @@ void oracle_sample(int kind, int precision, uint32_t seed, uint64_t n, double* o
 void oracle_solve_field(int n_cells, double dx, double weight, double area, double V0,
                         const long long* Rnet, double* phi, double* E) {
     Oracle<double>::solve_field(n_cells, dx, weight, area, V0, Rnet, phi, E);
+}
+
+void oracle_solve_field_thomas(int n_cells, double dx, double weight, double area, double V0,
+                               const long long* Rnet, double* phi, double* E) {
+    Oracle<double>::solve_field_thomas(n_cells, dx, weight, area, V0, Rnet, phi, E);
 }
 
 // CIC fixed-point deposit of n float positions onto n_cells+1 nodes.

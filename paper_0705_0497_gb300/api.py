@@ -1,0 +1,306 @@
+"""ctypes binding of libo2pic (C ABI in include/o2pic.h) — argument marshalling only.
+
+Every step of the particle loop runs in the library's CUDA kernels; this
+module converts Python/numpy/torch arguments to pointers and back.  There is
+no CPU fallback: if the library is missing the import of this module fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libo2pic.so")
+
+NSP = 3
+MAXPROC = 16
+E, OM, OP = 0, 1, 2
+HOST, DEVICE = 0, 1
+KERNEL_KINDS = ("push_e", "push_om", "push_op", "pair_scan", "pair", "field", "compact", "deposit")
+
+OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "ID_OVERFLOW", -4: "NONFINITE", -5: "CUDA", -6: "TIMEOUT",
+          -7: "STATE"}
+
+
+class O2picError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({lib().o2pic_strerror(code).decode()})")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("L", "f", "U", "p", "T_gas", "C_meta", "dt", "weight", "area", "m_e", "m_OM", "m_OP", "M_gas")] + [
+        ("n_cells", ctypes.c_int32), ("ion_subcycle", ctypes.c_int32),
+        ("seed", ctypes.c_uint32), ("compact_check", ctypes.c_uint32),
+        ("capacity", ctypes.c_uint64 * NSP), ("device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Process(ctypes.Structure):
+    _fields_ = [("species", ctypes.c_int32), ("kind", ctypes.c_int32), ("target", ctypes.c_int32),
+                ("n", ctypes.c_int32), ("threshold_eV", ctypes.c_double),
+                ("E_eV", ctypes.POINTER(ctypes.c_double)), ("sigma_m2", ctypes.POINTER(ctypes.c_double))]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("events", (ctypes.c_uint64 * MAXPROC) * NSP), ("absorbed", (ctypes.c_uint64 * 2) * NSP),
+                ("born", ctypes.c_uint64 * NSP), ("neutralized", ctypes.c_uint64),
+                ("pair_candidates", ctypes.c_uint64), ("particle_steps", ctypes.c_uint64),
+                ("warn_emax", ctypes.c_uint64), ("warn_tries", ctypes.c_uint64), ("warn_pair_gt1", ctypes.c_uint64),
+                ("id_overflow", ctypes.c_uint64), ("step", ctypes.c_uint64), ("live", ctypes.c_uint64 * NSP),
+                ("slots", ctypes.c_uint64 * NSP), ("next_id", ctypes.c_uint64 * NSP),
+                ("error_flags", ctypes.c_uint64), ("particle_steps_species", ctypes.c_uint64 * NSP)]
+
+    def as_dict(self):
+        d = {}
+        for s in range(NSP):
+            for k in range(MAXPROC):
+                d[f"events_{s}_{k}"] = int(self.events[s][k])
+            for w in range(2):
+                d[f"absorbed_{s}_{w}"] = int(self.absorbed[s][w])
+            d[f"born_{s}"] = int(self.born[s])
+            d[f"live_{s}"] = int(self.live[s])
+            d[f"slots_{s}"] = int(self.slots[s])
+            d[f"next_id_{s}"] = int(self.next_id[s])
+            d[f"particle_steps_{s}"] = int(self.particle_steps_species[s])
+        for n in ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
+                  "id_overflow", "step", "error_flags"):
+            d[n] = int(getattr(self, n))
+        return d
+
+
+_lib = None
+
+# (name, restype, argtypes) for every function of include/o2pic.h
+_vp, _u64, _i32, _u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+_P = ctypes.POINTER
+SIGNATURES = [
+    ("o2pic_config_init", _i32, [_P(Config)]),
+    ("o2pic_create", _i32, [_P(Config), _P(_vp)]),
+    ("o2pic_set_processes", _i32, [_vp, _P(Process), _i32]),
+    ("o2pic_load_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _i32, _vp]),
+    ("o2pic_step", _i32, [_vp, _u64, _vp]),
+    ("o2pic_synchronize", _i32, [_vp]),
+    ("o2pic_read_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _P(_u64), _i32]),
+    ("o2pic_read_field", _i32, [_vp, _vp, _vp]),
+    ("o2pic_read_charge", _i32, [_vp, _vp, _vp, _P(_u64)]),
+    ("o2pic_read_moments", _i32, [_vp, _vp, _P(_u64), _i32]),
+    ("o2pic_get_stats", _i32, [_vp, _P(Stats)]),
+    ("o2pic_set_step", _i32, [_vp, _u64]),
+    ("o2pic_set_timing", _i32, [_vp, _i32]),
+    ("o2pic_get_timing", _i32, [_vp, _vp, _vp, _vp, _i32]),
+    ("o2pic_launch_count", _u64, [_vp]),
+    ("o2pic_philox", _i32, [_vp, _vp, _vp, _u64, _vp]),
+    ("o2pic_ln_f32", _i32, [_vp, _vp, _u64, _vp]),
+    ("o2pic_strerror", ctypes.c_char_p, [_i32]),
+    ("o2pic_destroy", None, [_vp]),
+    ("o2pic_version", _i32, []),
+]
+
+
+def lib():
+    """The loaded libo2pic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with paper_0705_0497_gb300.build.build() "
+                              "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise O2picError(rc, what)
+
+
+def _host_f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _is_torch_cuda(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_config(cfg, capacity, device=0, compact_check=0):
+    c = Config()
+    for name in ("L", "f", "U", "p", "T_gas", "C_meta", "dt", "weight", "area", "m_e", "m_OM", "m_OP", "M_gas"):
+        setattr(c, name, float(cfg[name]))
+    c.n_cells = int(cfg["n_cells"])
+    c.ion_subcycle = int(cfg["ion_subcycle"])
+    c.seed = int(cfg["seed"])
+    c.compact_check = int(compact_check)
+    for s in range(NSP):
+        c.capacity[s] = int(capacity[s])
+    c.device = int(device)
+    return c
+
+
+class Discharge:
+    """One discharge on one GPU (a libo2pic context)."""
+
+    def __init__(self, cfg, capacity, device=0, compact_check=0):
+        self.cfg = dict(cfg)
+        self.Ng = int(cfg["n_cells"]) + 1
+        self._c = make_config(cfg, capacity, device, compact_check)
+        h = ctypes.c_void_p()
+        _check(lib().o2pic_create(ctypes.byref(self._c), ctypes.byref(h)), "o2pic_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().o2pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_processes(self, procs):
+        arr = (Process * max(len(procs), 1))()
+        keep = []
+        for i, p in enumerate(procs):
+            Ev = np.ascontiguousarray(p["E"], dtype=np.float64)
+            sv = np.ascontiguousarray(p["sigma"], dtype=np.float64)
+            keep += [Ev, sv]
+            arr[i].species, arr[i].kind, arr[i].target, arr[i].n = p["species"], p["kind"], p["target"], len(Ev)
+            arr[i].threshold_eV = float(p.get("threshold_eV", 0.0))
+            arr[i].E_eV = Ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[i].sigma_m2 = sv.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().o2pic_set_processes(self.h, arr, len(procs)), "o2pic_set_processes")
+
+    def load(self, species, x, vx, vy, vz, ids, stream=None):
+        """Host numpy arrays or CUDA torch tensors (float32 / int32-or-uint32 ids)."""
+        if _is_torch_cuda(x):
+            n = int(x.numel())
+            ptrs = [ctypes.c_void_p(t.data_ptr()) for t in (x, vx, vy, vz, ids)]
+            kind = DEVICE
+        else:
+            arrs = [_host_f32(v) for v in (x, vx, vy, vz)] + [np.ascontiguousarray(ids, dtype=np.uint32)]
+            n = len(arrs[0])
+            ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+            kind = HOST
+        _check(lib().o2pic_load_particles(self.h, species, *ptrs, n, kind, _stream_ptr(stream)), "o2pic_load_particles")
+
+    def load_state(self, state, stream=None):
+        for s, p in enumerate(state):
+            self.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"], stream)
+
+    def step(self, n=1, stream=None):
+        _check(lib().o2pic_step(self.h, int(n), _stream_ptr(stream)), "o2pic_step")
+
+    def synchronize(self):
+        _check(lib().o2pic_synchronize(self.h), "o2pic_synchronize")
+
+    def count(self, species):
+        n = ctypes.c_uint64()
+        _check(lib().o2pic_read_particles(self.h, species, None, None, None, None, None, 0, ctypes.byref(n), HOST),
+               "o2pic_read_particles")
+        return int(n.value)
+
+    def particles(self, species):
+        n = self.count(species)
+        out = {k: np.zeros(n, np.float32) for k in ("x", "vx", "vy", "vz")}
+        out["id"] = np.zeros(n, np.uint32)
+        m = ctypes.c_uint64()
+        _check(lib().o2pic_read_particles(self.h, species, *[out[k].ctypes.data_as(ctypes.c_void_p)
+                                                             for k in ("x", "vx", "vy", "vz", "id")],
+                                          n, ctypes.byref(m), HOST), "o2pic_read_particles")
+        return out
+
+    def read_into(self, species, d):
+        """Live particles into preallocated host arrays d["x"], ... d["id"]; returns the count."""
+        m = ctypes.c_uint64()
+        _check(lib().o2pic_read_particles(self.h, species, *[d[k].ctypes.data_as(ctypes.c_void_p)
+                                                             for k in ("x", "vx", "vy", "vz", "id")],
+                                          len(d["x"]), ctypes.byref(m), HOST), "o2pic_read_particles")
+        if m.value > len(d["x"]):
+            raise O2picError(-1, "read_into: host arrays too small")
+        return int(m.value)
+
+    def particles_into(self, species, x, vx, vy, vz, ids):
+        """Live particles into caller CUDA tensors (device to device); returns the live count."""
+        m = ctypes.c_uint64()
+        _check(lib().o2pic_read_particles(self.h, species, *[ctypes.c_void_p(t.data_ptr()) for t in (x, vx, vy, vz, ids)],
+                                          int(x.numel()), ctypes.byref(m), DEVICE), "o2pic_read_particles")
+        return int(m.value)
+
+    def field(self):
+        phi = np.zeros(self.Ng)
+        Ef = np.zeros(self.Ng, np.float32)
+        _check(lib().o2pic_read_field(self.h, phi.ctypes.data_as(ctypes.c_void_p), Ef.ctypes.data_as(ctypes.c_void_p)),
+               "o2pic_read_field")
+        return phi, Ef
+
+    def charge(self):
+        Q = np.zeros((NSP, self.Ng), np.uint64)
+        Qa = np.zeros((NSP, self.Ng), np.uint64)
+        steps = ctypes.c_uint64()
+        _check(lib().o2pic_read_charge(self.h, Q.ctypes.data_as(ctypes.c_void_p), Qa.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(steps)), "o2pic_read_charge")
+        return Q, Qa, int(steps.value)
+
+    def moments(self, reset=False):
+        d = np.zeros((NSP, self.Ng))
+        steps = ctypes.c_uint64()
+        _check(lib().o2pic_read_moments(self.h, d.ctypes.data_as(ctypes.c_void_p), ctypes.byref(steps), int(reset)),
+               "o2pic_read_moments")
+        return d, int(steps.value)
+
+    def stats(self):
+        st = Stats()
+        _check(lib().o2pic_get_stats(self.h, ctypes.byref(st)), "o2pic_get_stats")
+        return st.as_dict()
+
+    def set_step(self, n):
+        _check(lib().o2pic_set_step(self.h, int(n)), "o2pic_set_step")
+
+    def set_timing(self, on):
+        _check(lib().o2pic_set_timing(self.h, int(bool(on))), "o2pic_set_timing")
+
+    def timing(self):
+        k = len(KERNEL_KINDS)
+        ms = np.zeros(k)
+        n = np.zeros(k, np.uint64)
+        _check(lib().o2pic_get_timing(self.h, ms.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                                      None, k), "o2pic_get_timing")
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(KERNEL_KINDS)}
+
+    def launch_count(self):
+        return int(lib().o2pic_launch_count(self.h))
+
+
+def philox(ctr, key, stream=None):
+    """Philox4x32-10 on the device: ctr (n,4), key (n,2) uint32 torch CUDA tensors -> (n,4)."""
+    import torch
+    out = torch.empty_like(ctr)
+    _check(lib().o2pic_philox(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_void_p(key.data_ptr()),
+                              ctypes.c_void_p(out.data_ptr()), int(ctr.shape[0]), _stream_ptr(stream)), "o2pic_philox")
+    return out
+
+
+def ln_f32(x, stream=None):
+    import torch
+    out = torch.empty_like(x)
+    _check(lib().o2pic_ln_f32(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(x.numel()),
+                              _stream_ptr(stream)), "o2pic_ln_f32")
+    return out

@@ -1,0 +1,361 @@
+// End-of-step kernel (one block): charge commit, cycle moments, Poisson solve
+// and E on the nodes, removals of (17), and the commit of the step's births;
+// plus the stable compaction of dead slots and small utility kernels.
+//
+// Poisson (Sec. 2): interior nodes satisfy
+//     -phi_{j-1} + 2 phi_j - phi_{j+1} = rho_j dx^2 / eps0,
+// phi_0 = U sin(2 pi f t) (driven electrode at x = 0), phi_N = 0 (grounded).
+// With the net fixed-point charge R_j (2^16 per macro-particle, exact int64)
+// and c = e w dx / (A eps0 2^16), the system is solved in closed form by two
+// exact integer prefix sums:
+//     S_m = sum_{k=1..m} R_k,  T_j = sum_{m<j} S_m,
+//     D_0 = phi_1 - phi_0 = (c T_N - V0) / N,  phi_j = V0 + j D_0 - c T_j,
+//     E_j = (c (S_j + S_{j-1}) - 2 D_0) / (2 dx)           (1 <= j <= N-1),
+//     E_0 = (-D_0 - c R_0) / dx,  E_N = (c S_{N-1} - D_0 + c R_N) / dx
+// (wall nodes from Gauss's law over the half cell next to the wall).  This is
+// the exact solution of the linear system a Thomas sweep would solve; it
+// needs no serial FP64 recurrence (FP64 throughput on this GPU is low), its
+// only rounding is in the final FP64 expressions, each evaluated in the order
+// written here.  |S| <= 2^47 and |T| <= 2^58 for up to 2^31 particles and 8192
+// cells, so int64 holds both exactly.
+#include "common.cuh"
+
+namespace o2 {
+
+namespace {
+
+constexpr int FT = 1024;                          // threads of the field block
+constexpr int FPER = (MAX_NODES + FT - 1) / FT;   // nodes per thread (blocked)
+
+// Block-wide inclusive scan of a blocked int64 array (FPER values per thread).
+__device__ __forceinline__ void block_scan_ll(long long (&v)[FPER], long long* ws) {
+    long long run = 0;
+#pragma unroll
+    for (int i = 0; i < FPER; ++i) { run += v[i]; v[i] = run; }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long t = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    const long long off = (warp == 0 ? 0 : ws[warp - 1]) + (x - run);
+#pragma unroll
+    for (int i = 0; i < FPER; ++i) v[i] += off;
+    __syncthreads();
+}
+
+// mode 0: end of a step (pushed_mask = species pushed this step);
+// mode 1: after a load (all species freshly deposited into Qf).
+__global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
+    __shared__ long long ws[32];
+    __shared__ long long sh_last[4];
+    DevCtrl* C = P.ctrl;
+    const int N = P.Nc, Ng = P.Ng;
+    const int t = threadIdx.x;
+    const int j0 = t * FPER;
+
+    long long R[FPER];
+#pragma unroll
+    for (int i = 0; i < FPER; ++i) {
+        const int j = j0 + i;
+        long long net = 0;
+        if (j < Ng) {
+#pragma unroll
+            for (int s = 0; s < NSP; ++s) {
+                const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
+                unsigned long long q = fresh ? P.Qf[s][j] : P.Q[s][j];
+                q += P.Qb[s][j];
+                P.Q[s][j] = q;
+                P.Qf[s][j] = 0ull;
+                P.Qb[s][j] = 0ull;
+                if (mode == 0) P.Qacc[s][j] += q;
+                net += (s == SP_OP) ? (long long)q : -(long long)q;
+            }
+        }
+        R[i] = net;
+    }
+    // S_m = sum_{k=1..m} R_k: scan of R with R_0 left out
+    long long Sv[FPER];
+#pragma unroll
+    for (int i = 0; i < FPER; ++i) Sv[i] = (j0 + i >= 1 && j0 + i < Ng) ? R[i] : 0;
+    block_scan_ll(Sv, ws);
+    // T_j = sum_{m<j} S_m: exclusive scan of S over m = 0..N-1
+    long long Tv[FPER];
+#pragma unroll
+    for (int i = 0; i < FPER; ++i) Tv[i] = (j0 + i < N) ? Sv[i] : 0;
+    block_scan_ll(Tv, ws);     // inclusive: Tv[i] = sum_{m <= j} S_m  => T_{j+1}
+    // values needed across thread boundaries: S_{j-1} for the first node of a
+    // thread, T_j = inclusive(j-1), S_{N-1}, R_N, T_N
+    __shared__ long long sh_Sprev[FT], sh_Tprev[FT];
+    sh_Sprev[t] = Sv[FPER - 1];
+    sh_Tprev[t] = Tv[FPER - 1];
+#pragma unroll
+    for (int i = 0; i < FPER; ++i) {
+        const int j = j0 + i;
+        if (j == N - 1) { sh_last[0] = Sv[i]; sh_last[1] = Tv[i]; }   // S_{N-1}, T_N
+        if (j == N) sh_last[2] = R[i];
+    }
+    __syncthreads();
+    const double c = P.c_field, dx = P.dx;
+    const unsigned long long step = C->step;
+    // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load), evaluated
+    // on the host in FP64 and staged in a ring indexed by the step
+    const double V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
+    const long long TN = sh_last[1];
+    const double D0 = (c * (double)TN - V0) / (double)N;
+    const long long SNm1 = sh_last[0], RN = sh_last[2];
+#pragma unroll
+    for (int i = 0; i < FPER; ++i) {
+        const int j = j0 + i;
+        if (j >= Ng) break;
+        const long long Sprev = (i == 0) ? (t > 0 ? sh_Sprev[t - 1] : 0) : Sv[i - 1];
+        const long long Tj = (i == 0) ? (t > 0 ? sh_Tprev[t - 1] : 0) : Tv[i - 1];
+        double E;
+        if (j == 0) E = (-D0 - c * (double)R[i]) / dx;
+        else if (j == N) E = (c * (double)SNm1 - D0 + c * (double)RN) / dx;
+        else E = (c * (double)(Sv[i] + Sprev) - 2.0 * D0) / (2.0 * dx);
+        const double phi = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Tj);
+        P.Ef[j] = (float)E;
+        P.phi[j] = phi;
+    }
+    if (mode != 0) {
+        if (t == 0) for (int k = 0; k < NKK + NSP; ++k) C->ticket[k] = 0u;
+        return;
+    }
+
+    // (17) removals: mark both ions of every reacted pair dead
+    const unsigned nrem = (C->removals < P.max_removals) ? C->removals : P.max_removals;
+    const unsigned cm = C->cur[SP_OM], cp = C->cur[SP_OP];
+    for (unsigned r = t; r < nrem; r += FT) {
+        P.sp[SP_OM].x[cm][P.removal[2 * r]] = dead_marker();
+        P.sp[SP_OP].x[cp][P.removal[2 * r + 1]] = dead_marker();
+    }
+    __syncthreads();
+    if (t == 0) {
+        const unsigned long long bE = C->births[B_E_FROM_E] + C->births[B_E_FROM_OM];
+        const unsigned long long bOP = C->births[B_OP_FROM_E];
+        const unsigned long long bOM = C->births[B_OM_FROM_E];
+        const unsigned long long b[NSP] = {bE, bOM, bOP};
+        for (int s = 0; s < NSP; ++s) {
+            const unsigned long long rem = C->removed[s] + ((s != SP_E) ? (unsigned long long)nrem : 0ull);
+            unsigned long long ns = C->slots[s] + b[s];
+            unsigned long long nl = C->live[s] + b[s] - rem;
+            if (ns > P.sp[s].cap) {   // births beyond the capacity were dropped
+                C->error_flags |= ERR_CAPACITY;
+                nl -= (ns - P.sp[s].cap) < nl ? (ns - P.sp[s].cap) : nl;
+                ns = P.sp[s].cap;
+            }
+            C->slots[s] = ns;
+            C->live[s] = nl;
+            const unsigned long long nid = (unsigned long long)C->next_id[s] + b[s];
+            if (nid > 0xFFFFFFFFull) { C->error_flags |= ERR_ID; C->cnt.id_overflow += 1; }
+            C->next_id[s] = (unsigned)nid;
+            C->cnt.born[s] += b[s];
+            C->removed[s] = 0ull;
+        }
+        C->cnt.neutralized += nrem;
+        for (int k = 0; k < NB; ++k) C->births[k] = 0ull;
+        for (int k = 0; k < NKK + NSP; ++k) C->ticket[k] = 0u;
+        C->removals = 0u;
+        C->acc_steps += 1;
+        C->step = step + 1;
+        C->epoch += 1;
+    }
+}
+
+// Stable compaction of the live slots of one species into the other buffer
+// (mode 0, when more than a fraction of the slots is dead), or a stable copy
+// of the live particles into caller buffers (mode 1).  Tiles of TILE slots in
+// increasing order, decoupled look-back on the live counts.
+template <int S>
+__global__ void __launch_bounds__(BLOCK) k_compact(Params P, int mode, unsigned long long epoch_arg,
+                                                   unsigned* ticket_arg, unsigned long long* flag_arg,
+                                                   unsigned long long* val_arg, float* ox, float* ovx, float* ovy,
+                                                   float* ovz, uint32_t* oid, unsigned long long ocap,
+                                                   unsigned long long* out_count) {
+    __shared__ unsigned ws[32];
+    __shared__ unsigned sh_tile;
+    __shared__ unsigned long long sh_excl;
+    __shared__ int sh_ok;
+    DevCtrl* C = P.ctrl;
+    const unsigned long long nslots = C->slots[S];
+    const unsigned long long live = C->live[S];
+    if (mode == 0) {
+        const unsigned long long dead = nslots - live;
+        const bool many_dead = (double)dead > (double)P.compact_dead_frac * (double)nslots;
+        const bool near_full = dead > 0 && 4 * nslots > 3 * P.sp[S].cap;
+        if (!many_dead && !near_full) return;
+    }
+    const unsigned cb = C->cur[S];
+    const float* X = P.sp[S].x[cb];
+    const float* VX = P.sp[S].vx[cb];
+    const float* VY = P.sp[S].vy[cb];
+    const float* VZ = P.sp[S].vz[cb];
+    const uint32_t* ID = P.sp[S].id[cb];
+    float *DX, *DVX, *DVY, *DVZ; uint32_t* DID;
+    unsigned long long dcap;
+    unsigned* ticket; unsigned long long *flag, *val, epoch;
+    if (mode == 0) {
+        DX = P.sp[S].x[cb ^ 1u]; DVX = P.sp[S].vx[cb ^ 1u]; DVY = P.sp[S].vy[cb ^ 1u]; DVZ = P.sp[S].vz[cb ^ 1u];
+        DID = P.sp[S].id[cb ^ 1u]; dcap = P.sp[S].cap;
+        ticket = &C->ticket[NKK + S];
+        flag = P.lb_flag[KK_COMPACT]; val = P.lb_val[KK_COMPACT];
+        epoch = (C->epoch << 2) | (unsigned long long)S;
+    } else {
+        DX = ox; DVX = ovx; DVY = ovy; DVZ = ovz; DID = oid; dcap = ocap;
+        ticket = ticket_arg; flag = flag_arg; val = val_arg; epoch = epoch_arg;
+    }
+    const unsigned ntiles = (unsigned)ceil_div(nslots, TILE);
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) sh_tile = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned tile = sh_tile;
+        __syncthreads();
+        if (tile >= ntiles) break;
+        const unsigned long long base = (unsigned long long)tile * TILE;
+        const unsigned long long end = (base + TILE < nslots) ? base + TILE : nslots;
+        // pass 1: live count of the tile
+        unsigned cnt = 0;
+        for (int c = 0; c < CHUNKS_PER_TILE; ++c) {
+            const unsigned long long i0 = base + (unsigned long long)c * CHUNK + 4ull * tid;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (i0 + k < end && !is_dead(X[i0 + k])) ++cnt;
+        }
+        unsigned tile_total;
+        (void)block_excl_scan<BLOCK>(cnt, ws, &tile_total);
+        if (tid == 0) {
+            bool ok;
+            sh_excl = lookback(flag, val, tile, pack2(tile_total, 0u), epoch, &C->error_flags, &ok);
+            sh_ok = ok ? 1 : 0;
+            if (ok && tile == ntiles - 1) {
+                const unsigned long long total = (unsigned)sh_excl + (unsigned long long)tile_total;
+                if (mode == 0) {
+                    C->slots[S] = total;
+                    C->live[S] = total;
+                    C->cur[S] = cb ^ 1u;
+                } else {
+                    *out_count = total;
+                }
+            }
+        }
+        __syncthreads();
+        if (sh_ok) {
+            // pass 2: destinations in slot order, chunk by chunk in (thread, k) order
+            unsigned long long run = (unsigned)sh_excl;
+            for (int c = 0; c < CHUNKS_PER_TILE; ++c) {
+                const unsigned long long i0 = base + (unsigned long long)c * CHUNK + 4ull * tid;
+                unsigned m = 0;
+                bool lv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { lv[k] = (i0 + k < end) && !is_dead(X[i0 + k]); m += lv[k] ? 1u : 0u; }
+                unsigned ctot;
+                const unsigned off = block_excl_scan<BLOCK>(m, ws, &ctot);
+                unsigned long long d = run + off;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!lv[k]) continue;
+                    if (d < dcap) {
+                        DX[d] = X[i0 + k]; DVX[d] = VX[i0 + k]; DVY[d] = VY[i0 + k]; DVZ[d] = VZ[i0 + k];
+                        DID[d] = ID[i0 + k];
+                    }
+                    ++d;
+                }
+                run += ctot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Validation of freshly loaded particles (x in [0, L), finite velocities)
+// and the largest id (+1) for the species' next id.
+template <int S>
+__global__ void k_load_check(Params P, unsigned long long n) {
+    DevCtrl* C = P.ctrl;
+    const unsigned cb = C->cur[S];
+    const float* X = P.sp[S].x[cb];
+    const float* VX = P.sp[S].vx[cb];
+    const float* VY = P.sp[S].vy[cb];
+    const float* VZ = P.sp[S].vz[cb];
+    const uint32_t* ID = P.sp[S].id[cb];
+    unsigned mx = 0;
+    bool bad = false;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const float x = X[i];
+        if (!(x >= 0.0f && x < P.Lf) || !isfinite(VX[i]) || !isfinite(VY[i]) || !isfinite(VZ[i])) bad = true;
+        const unsigned v = ID[i] + 1u;
+        mx = v > mx ? v : mx;
+    }
+    if (bad) atomicOr(&C->error_flags, ERR_NONFINITE);
+    atomicMax(&C->next_id[S], mx);
+}
+
+__global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, unsigned long long n) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+        const uint4 r = philox4x32_10(c, make_uint2(key[2 * i], key[2 * i + 1]));
+        out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+    }
+}
+
+__global__ void k_ln(const float* x, float* out, unsigned long long n) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        out[i] = ln_series(x[i]);
+}
+
+}  // namespace
+
+void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s) {
+    k_field<<<1, FT, 0, s>>>(P, mode, pushed_mask);
+}
+
+void launch_compact(int species, const Params& P, int grid, cudaStream_t s) {
+    if (species == SP_E) k_compact<SP_E><<<grid, BLOCK, 0, s>>>(P, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+    else if (species == SP_OM) k_compact<SP_OM><<<grid, BLOCK, 0, s>>>(P, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+    else k_compact<SP_OP><<<grid, BLOCK, 0, s>>>(P, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+}
+
+void launch_gather(int species, const Params& P, int grid, unsigned long long epoch, unsigned* ticket,
+                   unsigned long long* flag, unsigned long long* val, float* x, float* vx, float* vy, float* vz,
+                   uint32_t* id, unsigned long long cap, unsigned long long* out_count, cudaStream_t s) {
+    if (species == SP_E) k_compact<SP_E><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, cap, out_count);
+    else if (species == SP_OM) k_compact<SP_OM><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, cap, out_count);
+    else k_compact<SP_OP><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, cap, out_count);
+}
+
+void launch_load_check(int species, const Params& P, unsigned long long n, cudaStream_t s) {
+    const int grid = (int)(n / 256 + 1 < 4096 ? n / 256 + 1 : 4096);
+    if (species == SP_E) k_load_check<SP_E><<<grid, 256, 0, s>>>(P, n);
+    else if (species == SP_OM) k_load_check<SP_OM><<<grid, 256, 0, s>>>(P, n);
+    else k_load_check<SP_OP><<<grid, 256, 0, s>>>(P, n);
+}
+
+void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, unsigned long long n, cudaStream_t s) {
+    const int grid = (int)(n / 256 + 1 < 4096 ? n / 256 + 1 : 4096);
+    k_philox<<<grid, 256, 0, s>>>(ctr, key, out, n);
+}
+
+void launch_ln(const float* x, float* out, unsigned long long n, cudaStream_t s) {
+    const int grid = (int)(n / 256 + 1 < 4096 ? n / 256 + 1 : 4096);
+    k_ln<<<grid, 256, 0, s>>>(x, out, n);
+}
+
+}  // namespace o2

@@ -1,0 +1,154 @@
+// Shared definitions of the o2pic CUDA library (host runtime + kernels).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "o2pic.h"
+
+namespace o2 {
+
+constexpr int NSP = 3;
+constexpr int SP_E = 0, SP_OM = 1, SP_OP = 2;
+constexpr int MAXPROC = O2PIC_MAXPROC;
+
+// Rate-table grid: 32 points per octave on [2^-10, 2^12] eV (705 points).
+constexpr int GRID_SUB_BITS = 5;
+constexpr int NGRID = 22 * 32 + 1;
+constexpr unsigned GRID_BASE = (127u - 10u) << GRID_SUB_BITS;   // (bits >> 18) at 2^-10
+constexpr float GRID_EMIN = 0.0009765625f;                       // 2^-10
+constexpr float GRID_EMAX = 4096.0f;                             // 2^12
+
+constexpr int BLOCK = 256;              // threads of the particle kernels
+constexpr int ITEMS = 4;                // particles per thread per chunk (one float4)
+constexpr int CHUNK = BLOCK * ITEMS;    // 1024
+constexpr int TILE = 8192;              // particles per tile (look-back unit)
+constexpr int CHUNKS_PER_TILE = TILE / CHUNK;
+constexpr int FLUSH_TILES = 7;          // tiles between deposit flushes (7*8192*2^16 < 2^32)
+constexpr int MAX_TRIES = 32;           // rejection-loop cap
+constexpr uint32_t FIX_ONE = 65536u;    // CIC fixed point per particle
+constexpr int QCAP = BLOCK - 1 + CHUNK; // candidate queue capacity
+constexpr int MAX_NODES = 8193;         // grid limit (smem field and histograms)
+
+enum Kind { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6 };
+enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4 };
+
+// device error bits
+constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE = 4ull, ERR_TIMEOUT = 8ull;
+
+// kernel kinds (timing, tickets)
+enum KernelKind { KK_PUSH_E = 0, KK_PUSH_OM = 1, KK_PUSH_OP = 2, KK_PAIR_SCAN = 3, KK_PAIR = 4,
+                  KK_FIELD = 5, KK_COMPACT = 6, KK_DEPOSIT = 7, NKK = 8 };
+
+// Counters: same layout as the head of o2pic_stats.
+struct DevCounters {
+    unsigned long long events[NSP][MAXPROC];
+    unsigned long long absorbed[NSP][2];
+    unsigned long long born[NSP];
+    unsigned long long neutralized, pair_candidates, particle_steps;
+    unsigned long long warn_emax, warn_tries, warn_pair_gt1;
+    unsigned long long id_overflow;
+    unsigned long long psteps[NSP];
+};
+
+// Births appended by one kernel into species d: births of the electron
+// kernel (e from ionization, O2+ from ionization, O- from attachment) and of
+// the O- kernel (e from detachment) in that canonical order.
+enum BirthSlot { B_E_FROM_E = 0, B_OP_FROM_E = 1, B_OM_FROM_E = 2, B_E_FROM_OM = 3, NB = 4 };
+
+// Device-resident step state; read by every kernel, committed by the field kernel.
+struct DevCtrl {
+    unsigned long long step;               // current step n
+    unsigned long long epoch;              // distinct per step, never reused (look-back flags)
+    unsigned long long slots[NSP];         // array slots in use (live + dead) before this step's births
+    unsigned long long live[NSP];
+    unsigned long long removed[NSP];       // removed this step (absorbed, consumed, neutralized)
+    unsigned long long births[NB];         // this step's births per BirthSlot
+    unsigned long long acc_steps;          // steps summed into Qacc
+    unsigned long long error_flags;
+    unsigned int next_id[NSP];
+    unsigned int cur[NSP];                 // current buffer (ping-pong) per species
+    unsigned int ticket[NKK + NSP];        // tile tickets per kernel kind, + compaction per species
+    unsigned int removals;                 // (17) pairs to remove
+    unsigned int pad;
+    DevCounters cnt;
+};
+
+struct SpeciesBuf {
+    float* x[2];
+    float* vx[2];
+    float* vy[2];
+    float* vz[2];
+    uint32_t* id[2];
+    unsigned long long cap;
+};
+
+// Everything the kernels need; passed by value.
+struct Params {
+    DevCtrl* ctrl;
+    SpeciesBuf sp[NSP];
+    // rate tables (cumulative, FP32), [NGRID][nproc]
+    const float* cum[NSP];
+    int nproc[NSP];
+    int kind[NSP][MAXPROC];
+    float thr[NSP][MAXPROC];
+    float numax[NSP], pmax[NSP];
+    int births_possible[NSP];
+    // (17)
+    const float* Ktab;           // [NGRID] sigma_n g
+    float Kmax_hi;               // max(Ktab) inflated so the prefilter bounds every interpolant
+    int have_neutral;
+    // grid / field
+    int Nc, Ng;
+    float inv_dx, Lf;
+    double dx, c_field, U, two_pi_f, dt;   // c_field = e w dx / (A eps0 2^16)
+    const double* vring;         // electrode voltage U sin(2 pi f t_k) at t_k = k dt, slot k & vring_mask
+    unsigned int vring_mask;
+    float* Ef;                   // [Ng] gather field (FP32)
+    double* phi;                 // [Ng]
+    unsigned long long* Q[NSP];  // committed node charge
+    unsigned long long* Qf[NSP]; // fresh deposit of the species pushed this step
+    unsigned long long* Qb[NSP]; // deposit of this step's births
+    unsigned long long* Qacc[NSP];
+    // per-species constants (FP32, computed once on the host)
+    float dt_s[NSP], qmdt[NSP], kappa[NSP], a_m[NSP], a_M[NSP], sig_birth[NSP];
+    float delta_el, sig_gas, kappa_n, pair_factor;
+    uint32_t seed;
+    // decoupled look-back state: per kernel kind, flag and value words per tile
+    unsigned long long* lb_flag[NKK];
+    unsigned long long* lb_val[NKK];
+    unsigned int max_tiles;
+    // births staging, [tile * TILE + rank] per BirthSlot
+    float4* stage[NB];
+    // (17): per-tile per-cell counts of live ions [2][max_tiles][Nc], per-cell info
+    unsigned int* hist[2];       // 0: O-, 1: O2+
+    unsigned int* cellinfo;      // [Nc][4]: n-, n+, shift r, reserved
+    unsigned int* removal;       // [2 * max_removals]: O- slot, O2+ slot
+    unsigned int max_removals;
+    // compaction trigger
+    float compact_dead_frac;
+};
+
+__host__ __device__ inline unsigned long long ceil_div(unsigned long long a, unsigned long long b) {
+    return (a + b - 1) / b;
+}
+
+// ---------------------------------------------------------------- launchers
+// (defined in the kernel translation units, called by the runtime)
+void launch_push(int species, const Params& P, int grid, cudaStream_t s);
+void launch_pair_scan(const Params& P, cudaStream_t s);
+void launch_pair(const Params& P, int grid, cudaStream_t s);
+void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s);
+void launch_compact(int species, const Params& P, int grid, cudaStream_t s);
+void launch_deposit(int species, const Params& P, int grid, cudaStream_t s);
+void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, unsigned long long n, cudaStream_t s);
+void launch_ln(const float* x, float* out, unsigned long long n, cudaStream_t s);
+void launch_load_check(int species, const Params& P, unsigned long long n, cudaStream_t s);
+void launch_gather(int species, const Params& P, int grid, unsigned long long epoch, unsigned* ticket,
+                   unsigned long long* flag, unsigned long long* val, float* x, float* vx, float* vy, float* vz,
+                   uint32_t* id, unsigned long long cap, unsigned long long* out_count, cudaStream_t s);
+cudaError_t configure_push_smem(size_t max_bytes);
+int push_occupancy(int species, const Params& P, int* blocks_per_sm);
+size_t push_smem_bytes(int species, const Params& P);
+
+}  // namespace o2

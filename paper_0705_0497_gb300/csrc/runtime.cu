@@ -1,0 +1,788 @@
+// Host runtime and C ABI of libo2pic (include/o2pic.h): context and device
+// memory, rate-table construction, particle loading, the per-step launch
+// sequence, readback, timing and error reporting.
+//
+// The rate tables follow the null-collision method of the paper's Sec. 2:
+// per species s and process k, nu_k(E_i) = n_target sigma_k(E_i) g(E_i) on the
+// 705-point grid (32 per octave over [2^-10, 2^12] eV), g = sqrt(2 e E / mu),
+// mu = m_e for electrons (target at rest) and the reduced mass for ions;
+// cumulative sums in process order, nu_max = their maximum over the grid and
+// P_max = 1 - exp(-nu_max dt_s).  Built in FP64, stored in FP32.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace o2 {
+cudaError_t configure_pair_smem(size_t bytes);
+}
+
+using namespace o2;
+
+namespace {
+
+// CODATA 2018 (SI)
+const double QE = 1.602176634e-19;
+const double KB = 1.380649e-23;
+const double EPS0 = 8.8541878128e-12;
+const double TWO_PI = 6.283185307179586476925286766559;
+
+struct HostProc {
+    int kind, target;
+    double thr;
+    std::vector<double> E, s;
+};
+
+double grid_energy(int i) {
+    return std::ldexp(1.0 + (i % 32) / 32.0, i / 32 - 10);
+}
+
+double sigma_at(const HostProc& p, double E) {
+    if (E < p.thr) return 0.0;
+    const size_t n = p.E.size();
+    if (E <= p.E[0]) return p.s[0];
+    if (E >= p.E[n - 1]) return p.s[n - 1];
+    const size_t b = std::upper_bound(p.E.begin(), p.E.end(), E) - p.E.begin();
+    const double Ea = p.E[b - 1], Eb = p.E[b], sa = p.s[b - 1], sb = p.s[b];
+    return sa + (sb - sa) * ((E - Ea) / (Eb - Ea));
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+}  // namespace
+
+struct o2pic_ctx {
+    o2pic_config cfg;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t last = nullptr;
+    Params P;
+    DevCtrl* d_ctrl = nullptr;
+    std::vector<void*> allocs;
+    // host state
+    unsigned long long host_step = 0;
+    unsigned since_check = 0;
+    bool dirty = true;
+    bool have_tables = false;
+    bool loaded[NSP] = {false, false, false};
+    int latched = 0;
+    int grid_push[NSP] = {0, 0, 0};
+    int grid_pair = 0, grid_compact = 0, grid_deposit = 0;
+    unsigned long long launches = 0;
+    // gather (read_particles) state
+    unsigned* d_gticket = nullptr;
+    unsigned long long* d_gflag = nullptr;
+    unsigned long long* d_gval = nullptr;
+    unsigned long long* d_gcount = nullptr;
+    unsigned long long gepoch = 0;
+    // electrode-voltage ring (device) and the highest step index filled
+    double* d_vring = nullptr;
+    // timing
+    bool timing = false;
+    struct Ev { cudaEvent_t a, b; int kind; };
+    std::vector<Ev> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[NKK] = {0};
+    unsigned long long nlaunch[NKK] = {0};
+};
+
+namespace {
+
+int cuda_fail(o2pic_ctx* c, cudaError_t e) {
+    if (e == cudaSuccess) return O2PIC_OK;
+    if (c) c->latched = c->latched ? c->latched : O2PIC_E_CUDA;
+    return O2PIC_E_CUDA;
+}
+
+template <class T>
+cudaError_t ctx_alloc(o2pic_ctx* c, T** p, size_t count) {
+    cudaError_t e = dalloc(p, count);
+    if (e == cudaSuccess) {
+        c->allocs.push_back((void*)*p);
+        e = cudaMemset(*p, 0, sizeof(T) * (count ? count : 1));
+    }
+    return e;
+}
+
+cudaStream_t pick(o2pic_ctx* c, void* s) {
+    cudaStream_t st = s ? (cudaStream_t)s : c->stream;
+    c->last = st;
+    return st;
+}
+
+cudaEvent_t take_event(o2pic_ctx* c) {
+    if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void harvest_timing(o2pic_ctx* c) {
+    for (auto& ev : c->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev.a, ev.b) == cudaSuccess) c->ms[ev.kind] += t;
+        c->pool.push_back(ev.a);
+        c->pool.push_back(ev.b);
+    }
+    c->pending.clear();
+}
+
+// Launch wrapper: optional event pair around the launch.
+template <class F>
+void launch(o2pic_ctx* c, int kind, cudaStream_t s, F&& f) {
+    if (c->timing) {
+        if (c->pending.size() >= 8192) { cudaStreamSynchronize(s); harvest_timing(c); }
+        o2pic_ctx::Ev ev{take_event(c), take_event(c), kind};
+        cudaEventRecord(ev.a, s);
+        f();
+        cudaEventRecord(ev.b, s);
+        c->pending.push_back(ev);
+    } else {
+        f();
+    }
+    c->nlaunch[kind] += 1;
+    c->launches += 1;
+}
+
+int check_flags(o2pic_ctx* c) {
+    unsigned long long flags = 0;
+    cudaError_t e = cudaMemcpy(&flags, &c->d_ctrl->error_flags, sizeof(flags), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    int code = O2PIC_OK;
+    if (flags & ERR_CAPACITY) code = O2PIC_E_CAPACITY;
+    else if (flags & ERR_ID) code = O2PIC_E_ID_OVERFLOW;
+    else if (flags & ERR_NONFINITE) code = O2PIC_E_NONFINITE;
+    else if (flags & ERR_TIMEOUT) code = O2PIC_E_TIMEOUT;
+    if (code && !c->latched) c->latched = code;
+    return c->latched;
+}
+
+int sync_all(o2pic_ctx* c) {
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (c->timing) harvest_timing(c);
+    return check_flags(c);
+}
+
+int validate(const o2pic_config* g) {
+    if (!g) return O2PIC_E_INVALID_ARG;
+    if (!(g->L > 0) || !(g->dt > 0) || !(g->f >= 0) || !(g->p >= 0) || !(g->T_gas > 0) || !(g->weight >= 0) ||
+        !(g->area > 0) || !(g->C_meta >= 0) || !std::isfinite(g->U))
+        return O2PIC_E_INVALID_ARG;
+    if (!(g->m_e > 0) || !(g->m_OM > 0) || !(g->m_OP > 0) || !(g->M_gas > 0)) return O2PIC_E_INVALID_ARG;
+    if (g->n_cells < 1 || g->n_cells + 1 > MAX_NODES || g->ion_subcycle < 1) return O2PIC_E_INVALID_ARG;
+    for (int s = 0; s < NSP; ++s)
+        if (g->capacity[s] > (1ull << 31)) return O2PIC_E_INVALID_ARG;
+    return O2PIC_OK;
+}
+
+void set_constants(o2pic_ctx* c) {
+    const o2pic_config& g = c->cfg;
+    Params& P = c->P;
+    const double mass[NSP] = {g.m_e, g.m_OM, g.m_OP};
+    const int charge[NSP] = {-1, -1, +1};
+    const double dx = g.L / g.n_cells;
+    for (int s = 0; s < NSP; ++s) {
+        const double dts = g.dt * (s == SP_E ? 1.0 : (double)g.ion_subcycle);
+        P.dt_s[s] = (float)dts;
+        P.qmdt[s] = (float)((charge[s] * QE / mass[s]) * dts);
+        const double mu = (s == SP_E) ? mass[s] : mass[s] * g.M_gas / (mass[s] + g.M_gas);
+        P.kappa[s] = (float)(0.5 * mu / QE);
+        P.a_m[s] = (float)(mass[s] / (mass[s] + g.M_gas));
+        P.a_M[s] = (float)(g.M_gas / (mass[s] + g.M_gas));
+        P.sig_birth[s] = (float)std::sqrt(KB * g.T_gas / mass[s]);
+    }
+    P.delta_el = (float)(2.0 * g.m_e / g.M_gas);
+    P.sig_gas = (float)std::sqrt(KB * g.T_gas / g.M_gas);
+    P.inv_dx = (float)(1.0 / dx);
+    P.Lf = (float)g.L;
+    const double mun = g.m_OM * g.m_OP / (g.m_OM + g.m_OP);
+    P.kappa_n = (float)(0.5 * mun / QE);
+    const double dt_ion = g.dt * (double)g.ion_subcycle;
+    P.pair_factor = (float)(g.weight * dt_ion / (g.area * dx));
+    P.seed = g.seed;
+    P.Nc = g.n_cells;
+    P.Ng = g.n_cells + 1;
+    P.dx = dx;
+    P.c_field = QE * g.weight * dx / (g.area * EPS0 * 65536.0);
+    P.U = g.U;
+    P.two_pi_f = TWO_PI * g.f;
+    P.dt = g.dt;
+    P.compact_dead_frac = 1.0f / 16.0f;
+}
+
+constexpr unsigned VRING = 4096;
+
+// U sin(2 pi f t_k), t_k = k dt, for k in [k0, k1], into the device ring.
+int fill_vring(o2pic_ctx* c, unsigned long long k0, unsigned long long k1, cudaStream_t s) {
+    std::vector<double> v;
+    v.reserve((size_t)(k1 - k0 + 1));
+    for (unsigned long long k = k0; k <= k1; ++k) {
+        const double t = (double)k * c->cfg.dt;
+        v.push_back(c->cfg.U * std::sin(TWO_PI * c->cfg.f * t));
+    }
+    size_t i = 0;
+    while (i < v.size()) {
+        const unsigned slot = (unsigned)((k0 + i) & (VRING - 1));
+        const size_t n = std::min<size_t>(v.size() - i, VRING - slot);
+        cudaError_t e = cudaMemcpyAsync(c->d_vring + slot, v.data() + i, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        i += n;
+    }
+    return O2PIC_OK;
+}
+
+int prepare(o2pic_ctx* c, cudaStream_t s) {
+    if (int rc = fill_vring(c, c->host_step, c->host_step, s)) return rc;
+    Params& P = c->P;
+    for (int sp = 0; sp < NSP; ++sp) {
+        cudaMemsetAsync(P.Qf[sp], 0, sizeof(unsigned long long) * P.Ng, s);
+        cudaMemsetAsync(P.Qb[sp], 0, sizeof(unsigned long long) * P.Ng, s);
+    }
+    for (int sp = 0; sp < NSP; ++sp)
+        launch(c, KK_DEPOSIT, s, [&] { launch_deposit(sp, P, c->grid_deposit, s); });
+    launch(c, KK_FIELD, s, [&] { launch_field(P, 1, 7, s); });
+    c->dirty = false;
+    return cuda_fail(c, cudaGetLastError());
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+int o2pic_version(void) { return 1; }
+
+const char* o2pic_strerror(int code) {
+    switch (code) {
+    case O2PIC_OK: return "ok";
+    case O2PIC_E_INVALID_ARG: return "invalid argument";
+    case O2PIC_E_CAPACITY: return "particle capacity exceeded";
+    case O2PIC_E_ID_OVERFLOW: return "particle id overflow (2^32)";
+    case O2PIC_E_NONFINITE: return "non-finite or out-of-range particle";
+    case O2PIC_E_CUDA: return "CUDA error";
+    case O2PIC_E_TIMEOUT: return "bounded device wait gave up";
+    case O2PIC_E_STATE: return "call out of order (tables or particles missing)";
+    default: return "unknown error";
+    }
+}
+
+int o2pic_config_init(o2pic_config* g) {
+    if (!g) return O2PIC_E_INVALID_ARG;
+    std::memset(g, 0, sizeof(*g));
+    const double amu = 1.66053906660e-27;
+    g->L = 0.02; g->f = 13.56e6; g->U = 200.0; g->p = 10.0; g->T_gas = 300.0; g->C_meta = 0.0;
+    g->dt = 1.0 / (13.56e6 * 400.0); g->weight = 2.0e9; g->area = 1.0;
+    g->m_e = 9.1093837015e-31; g->m_OM = 16.0 * amu; g->m_OP = 32.0 * amu; g->M_gas = 32.0 * amu;
+    g->n_cells = 128; g->ion_subcycle = 1; g->seed = 0; g->compact_check = 16;
+    return O2PIC_OK;
+}
+
+int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
+    if (!out) return O2PIC_E_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(cfg);
+    if (rc) return rc;
+    o2pic_ctx* c = new (std::nothrow) o2pic_ctx();
+    if (!c) return O2PIC_E_CUDA;
+    c->cfg = *cfg;
+    if (c->cfg.compact_check == 0) c->cfg.compact_check = 16;
+    c->device = cfg->device;
+    std::memset(&c->P, 0, sizeof(Params));
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete c; return O2PIC_E_CUDA; }
+    c->last = c->stream;
+    set_constants(c);
+    Params& P = c->P;
+    const int Ng = P.Ng, Nc = P.Nc;
+    unsigned long long maxcap = 0;
+    for (int s = 0; s < NSP; ++s) maxcap = std::max<unsigned long long>(maxcap, cfg->capacity[s]);
+    const unsigned long long max_tiles = ceil_div(maxcap, TILE) + 1;
+    P.max_tiles = (unsigned)max_tiles;
+#define TRY(x) do { e = (x); if (e != cudaSuccess) { o2pic_destroy(c); return O2PIC_E_CUDA; } } while (0)
+    TRY(ctx_alloc(c, &c->d_ctrl, 1));
+    P.ctrl = c->d_ctrl;
+    for (int s = 0; s < NSP; ++s) {
+        const unsigned long long cap = ((cfg->capacity[s] + 63) / 64) * 64;
+        P.sp[s].cap = cfg->capacity[s];
+        for (int b = 0; b < 2; ++b) {
+            TRY(ctx_alloc(c, &P.sp[s].x[b], cap));
+            TRY(ctx_alloc(c, &P.sp[s].vx[b], cap));
+            TRY(ctx_alloc(c, &P.sp[s].vy[b], cap));
+            TRY(ctx_alloc(c, &P.sp[s].vz[b], cap));
+            TRY(ctx_alloc(c, &P.sp[s].id[b], cap));
+        }
+        float* cum;
+        TRY(ctx_alloc(c, &cum, (size_t)NGRID * MAXPROC));
+        P.cum[s] = cum;
+        TRY(ctx_alloc(c, &P.Q[s], Ng));
+        TRY(ctx_alloc(c, &P.Qf[s], Ng));
+        TRY(ctx_alloc(c, &P.Qb[s], Ng));
+        TRY(ctx_alloc(c, &P.Qacc[s], Ng));
+    }
+    float* K;
+    TRY(ctx_alloc(c, &K, NGRID));
+    P.Ktab = K;
+    TRY(ctx_alloc(c, &c->d_vring, VRING));
+    P.vring = c->d_vring;
+    P.vring_mask = VRING - 1;
+    TRY(ctx_alloc(c, &P.Ef, Ng));
+    TRY(ctx_alloc(c, &P.phi, Ng));
+    for (int k = 0; k < NKK; ++k) {
+        TRY(ctx_alloc(c, &P.lb_flag[k], max_tiles));
+        TRY(ctx_alloc(c, &P.lb_val[k], 2 * max_tiles));
+    }
+    const unsigned long long tiles_e = ceil_div(cfg->capacity[SP_E], TILE) + 1;
+    const unsigned long long tiles_om = ceil_div(cfg->capacity[SP_OM], TILE) + 1;
+    TRY(ctx_alloc(c, &P.stage[B_E_FROM_E], tiles_e * TILE));
+    TRY(ctx_alloc(c, &P.stage[B_OP_FROM_E], tiles_e * TILE));
+    TRY(ctx_alloc(c, &P.stage[B_OM_FROM_E], tiles_e * TILE));
+    TRY(ctx_alloc(c, &P.stage[B_E_FROM_OM], tiles_om * TILE));
+    const unsigned long long tiles_ion = std::max(ceil_div(cfg->capacity[SP_OM], TILE), ceil_div(cfg->capacity[SP_OP], TILE)) + 1;
+    TRY(ctx_alloc(c, &P.hist[0], tiles_ion * Nc));
+    TRY(ctx_alloc(c, &P.hist[1], tiles_ion * Nc));
+    TRY(ctx_alloc(c, &P.cellinfo, 4 * (size_t)Nc));
+    P.max_removals = (unsigned)std::max<unsigned long long>(1, std::min(cfg->capacity[SP_OM], cfg->capacity[SP_OP]));
+    TRY(ctx_alloc(c, &P.removal, 2 * (size_t)P.max_removals));
+    TRY(ctx_alloc(c, &c->d_gticket, 1));
+    TRY(ctx_alloc(c, &c->d_gflag, max_tiles));
+    TRY(ctx_alloc(c, &c->d_gval, 2 * max_tiles));
+    TRY(ctx_alloc(c, &c->d_gcount, 1));
+    // kernel shared-memory opt-in and launch shapes
+    size_t smax = 0;
+    for (int s = 0; s < NSP; ++s) {
+        P.nproc[s] = MAXPROC;
+        smax = std::max(smax, push_smem_bytes(s, P));
+    }
+    smax = std::max(smax, sizeof(unsigned) * (size_t)Ng);
+    TRY(configure_push_smem(smax));
+    TRY(configure_pair_smem(sizeof(unsigned) * 8 * (size_t)Nc));
+    for (int s = 0; s < NSP; ++s) P.nproc[s] = 0;
+    c->grid_pair = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(ceil_div(tiles_ion, 8), 8ull * c->num_sms));
+    c->grid_compact = 4 * c->num_sms;
+    c->grid_deposit = 4 * c->num_sms;
+    // steady initial control state
+    DevCtrl h;
+    std::memset(&h, 0, sizeof(h));
+    h.epoch = 1;
+    TRY(cudaMemcpy(c->d_ctrl, &h, sizeof(h), cudaMemcpyHostToDevice));
+    TRY(cudaDeviceSynchronize());
+#undef TRY
+    *out = c;
+    return O2PIC_OK;
+}
+
+void o2pic_destroy(o2pic_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (void* p : c->allocs) cudaFree(p);
+    for (auto& ev : c->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+    for (auto e : c->pool) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
+    if (!c || (nproc > 0 && !procs) || nproc < 0) return O2PIC_E_INVALID_ARG;
+    const o2pic_config& g = c->cfg;
+    std::vector<HostProc> sp[NSP];
+    HostProc neutral;
+    bool have_neutral = false;
+    for (int j = 0; j < nproc; ++j) {
+        const o2pic_process& q = procs[j];
+        if (q.n < 1 || q.species < 0 || q.species >= NSP || !q.E_eV || !q.sigma_m2) return O2PIC_E_INVALID_ARG;
+        if (q.kind < O2PIC_ELASTIC || q.kind > O2PIC_NEUTRALIZE) return O2PIC_E_INVALID_ARG;
+        HostProc p;
+        p.kind = q.kind; p.target = q.target; p.thr = q.threshold_eV;
+        p.E.assign(q.E_eV, q.E_eV + q.n);
+        p.s.assign(q.sigma_m2, q.sigma_m2 + q.n);
+        for (int i = 1; i < q.n; ++i) if (!(p.E[i] > p.E[i - 1])) return O2PIC_E_INVALID_ARG;
+        for (int i = 0; i < q.n; ++i) if (!(p.s[i] >= 0) || !std::isfinite(p.s[i])) return O2PIC_E_INVALID_ARG;
+        if (q.kind == O2PIC_NEUTRALIZE) {
+            if (have_neutral) return O2PIC_E_INVALID_ARG;
+            neutral = p; have_neutral = true; continue;
+        }
+        // kinematics exist for: e: elastic, excite, ionize, attach; O-: elastic, detach; O2+: elastic, cx
+        const bool ok = (q.species == SP_E && (q.kind == O2PIC_ELASTIC || q.kind == O2PIC_EXCITE ||
+                                                q.kind == O2PIC_IONIZE || q.kind == O2PIC_ATTACH)) ||
+                        (q.species == SP_OM && (q.kind == O2PIC_ELASTIC || q.kind == O2PIC_DETACH)) ||
+                        (q.species == SP_OP && (q.kind == O2PIC_ELASTIC || q.kind == O2PIC_CX));
+        if (!ok) return O2PIC_E_INVALID_ARG;
+        if ((int)sp[q.species].size() >= MAXPROC) return O2PIC_E_INVALID_ARG;
+        sp[q.species].push_back(p);
+    }
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    Params& P = c->P;
+    const double nO2 = g.p / (KB * g.T_gas);
+    const double nmeta = g.C_meta * nO2;
+    const double mass[NSP] = {g.m_e, g.m_OM, g.m_OP};
+    for (int s = 0; s < NSP; ++s) {
+        const int np = (int)sp[s].size();
+        std::vector<float> cum((size_t)NGRID * std::max(np, 1), 0.0f);
+        const double mu = (s == SP_E) ? mass[s] : mass[s] * g.M_gas / (mass[s] + g.M_gas);
+        double mx = 0.0;
+        for (int i = 0; i < NGRID; ++i) {
+            const double Ei = grid_energy(i);
+            const double gv = std::sqrt(2.0 * QE * Ei / mu);
+            double acc = 0.0;
+            for (int k = 0; k < np; ++k) {
+                const HostProc& pr = sp[s][k];
+                const double ntar = (pr.target == O2PIC_TARGET_O2_META) ? nmeta : nO2;
+                const double nu = ntar * sigma_at(pr, Ei) * gv;
+                acc += nu;
+                cum[(size_t)i * np + k] = (float)acc;
+            }
+            mx = std::max(mx, acc);
+        }
+        const double dts = g.dt * (s == SP_E ? 1.0 : (double)g.ion_subcycle);
+        P.nproc[s] = np;
+        P.numax[s] = (float)mx;
+        P.pmax[s] = (float)(1.0 - std::exp(-mx * dts));
+        bool births = false;
+        for (int k = 0; k < np; ++k) {
+            P.kind[s][k] = sp[s][k].kind;
+            P.thr[s][k] = (float)sp[s][k].thr;
+            if (sp[s][k].kind == O2PIC_IONIZE || sp[s][k].kind == O2PIC_ATTACH || sp[s][k].kind == O2PIC_DETACH)
+                births = true;
+        }
+        P.births_possible[s] = births ? 1 : 0;
+        if (np > 0) {
+            e = cudaMemcpy((void*)P.cum[s], cum.data(), sizeof(float) * cum.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+        }
+    }
+    std::vector<float> K(NGRID, 0.0f);
+    float kmax = 0.0f;
+    if (have_neutral) {
+        const double mun = g.m_OM * g.m_OP / (g.m_OM + g.m_OP);
+        for (int i = 0; i < NGRID; ++i) {
+            const double Ei = grid_energy(i);
+            const double gv = std::sqrt(2.0 * QE * Ei / mun);
+            K[i] = (float)(sigma_at(neutral, Ei) * gv);
+            kmax = std::max(kmax, K[i]);
+        }
+    }
+    P.have_neutral = have_neutral ? 1 : 0;
+    // every interpolated K is below max(K) (1 + 2^-23); the prefilter bound is
+    // inflated by 2^-20 so that it covers them all
+    P.Kmax_hi = (float)((double)kmax * (1.0 + std::ldexp(1.0, -20)));
+    e = cudaMemcpy((void*)P.Ktab, K.data(), sizeof(float) * NGRID, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    for (int s = 0; s < NSP; ++s) {
+        int bps = 0;
+        if (push_occupancy(s, P, &bps) || bps < 1) bps = 1;
+        c->grid_push[s] = bps * c->num_sms;
+    }
+    c->have_tables = true;
+    return O2PIC_OK;
+}
+
+int o2pic_load_particles(o2pic_ctx* c, int species, const float* x, const float* vx, const float* vy,
+                         const float* vz, const uint32_t* id, uint64_t n, int mem_kind, void* stream) {
+    if (!c || species < 0 || species >= NSP) return O2PIC_E_INVALID_ARG;
+    if (n > c->P.sp[species].cap) return O2PIC_E_INVALID_ARG;
+    if (n > 0 && (!x || !vx || !vy || !vz || !id)) return O2PIC_E_INVALID_ARG;
+    if (mem_kind != O2PIC_HOST && mem_kind != O2PIC_DEVICE) return O2PIC_E_INVALID_ARG;
+    unsigned next = 0;
+    if (mem_kind == O2PIC_HOST) {
+        const float Lf = c->P.Lf;
+        for (uint64_t i = 0; i < n; ++i) {
+            if (!(x[i] >= 0.0f && x[i] < Lf) || !std::isfinite(vx[i]) || !std::isfinite(vy[i]) || !std::isfinite(vz[i]))
+                return O2PIC_E_INVALID_ARG;
+            next = std::max(next, id[i] + 1u);
+        }
+    }
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    c->latched = 0;
+    cudaStream_t s = pick(c, stream);
+    DevCtrl h;
+    cudaError_t e = cudaMemcpy(&h, c->d_ctrl, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    const unsigned b = h.cur[species];
+    const SpeciesBuf& B = c->P.sp[species];
+    const cudaMemcpyKind k = (mem_kind == O2PIC_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (n > 0) {
+        e = cudaMemcpyAsync(B.x[b], x, sizeof(float) * n, k, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.vx[b], vx, sizeof(float) * n, k, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.vy[b], vy, sizeof(float) * n, k, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.vz[b], vz, sizeof(float) * n, k, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.id[b], id, sizeof(uint32_t) * n, k, s);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    h.slots[species] = n;
+    h.live[species] = n;
+    h.removed[species] = 0;
+    h.next_id[species] = next;
+    h.error_flags = 0;
+    e = cudaMemcpyAsync(c->d_ctrl, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (mem_kind == O2PIC_DEVICE && n > 0) {
+        launch_load_check(species, c->P, n, s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        unsigned long long flags = 0;
+        e = cudaMemcpy(&flags, &c->d_ctrl->error_flags, sizeof(flags), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        if (flags & ERR_NONFINITE) {
+            const unsigned long long zero = 0;
+            cudaMemcpy(&c->d_ctrl->error_flags, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+            h.slots[species] = 0; h.live[species] = 0;
+            cudaMemcpy(c->d_ctrl, &h, sizeof(h), cudaMemcpyHostToDevice);
+            return O2PIC_E_INVALID_ARG;
+        }
+    } else {
+        e = cudaStreamSynchronize(s);   // the host arrays may be freed once we return
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    c->host_step = h.step;
+    c->loaded[species] = true;
+    c->dirty = true;
+    return O2PIC_OK;
+}
+
+int o2pic_set_step(o2pic_ctx* c, uint64_t step) {
+    if (!c) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    cudaError_t e = cudaMemcpy(&c->d_ctrl->step, &step, sizeof(step), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->host_step = step;
+    c->dirty = true;
+    return O2PIC_OK;
+}
+
+int o2pic_step(o2pic_ctx* c, uint64_t nsteps, void* stream) {
+    if (!c) return O2PIC_E_INVALID_ARG;
+    if (!c->have_tables) return O2PIC_E_STATE;
+    if (c->latched) return c->latched;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    cudaStream_t s = pick(c, stream);
+    Params& P = c->P;
+    if (c->dirty) {
+        int rc = prepare(c, s);
+        if (rc) return rc;
+    }
+    const unsigned S = (unsigned)c->cfg.ion_subcycle;
+    for (uint64_t k = 0; k < nsteps; ++k) {
+        if (k % (VRING / 2) == 0) {
+            const unsigned long long n = std::min<unsigned long long>(nsteps - k, VRING / 2);
+            if (int rc = fill_vring(c, c->host_step + 1, c->host_step + n, s)) return rc;
+        }
+        const bool ion = (c->host_step % S) == 0;
+        launch(c, KK_PUSH_E, s, [&] { launch_push(SP_E, P, c->grid_push[SP_E], s); });
+        if (ion) {
+            launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
+            launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
+            if (P.have_neutral) {
+                launch(c, KK_PAIR_SCAN, s, [&] { launch_pair_scan(P, s); });
+                launch(c, KK_PAIR, s, [&] { launch_pair(P, c->grid_pair, s); });
+            }
+        }
+        launch(c, KK_FIELD, s, [&] { launch_field(P, 0, ion ? 7 : 1, s); });
+        c->host_step += 1;
+        if (++c->since_check >= c->cfg.compact_check) {
+            for (int sp = 0; sp < NSP; ++sp)
+                launch(c, KK_COMPACT, s, [&] { launch_compact(sp, P, c->grid_compact, s); });
+            c->since_check = 0;
+        }
+    }
+    return cuda_fail(c, cudaGetLastError());
+}
+
+int o2pic_synchronize(o2pic_ctx* c) {
+    if (!c) return O2PIC_E_INVALID_ARG;
+    return sync_all(c);
+}
+
+int o2pic_read_particles(o2pic_ctx* c, int species, float* x, float* vx, float* vy, float* vz, uint32_t* id,
+                         uint64_t cap, uint64_t* n, int mem_kind) {
+    if (!c || species < 0 || species >= NSP || !n) return O2PIC_E_INVALID_ARG;
+    if (mem_kind != O2PIC_HOST && mem_kind != O2PIC_DEVICE) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    cudaStream_t s = c->stream;
+    DevCtrl h;
+    cudaError_t e = cudaMemcpy(&h, c->d_ctrl, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    *n = h.live[species];
+    const uint64_t m = std::min<uint64_t>(cap, h.live[species]);
+    if (m == 0 || !x || !vx || !vy || !vz || !id) return rc;
+    float *dx_ = x, *dvx = vx, *dvy = vy, *dvz = vz;
+    uint32_t* did = id;
+    std::vector<void*> tmp;
+    if (mem_kind == O2PIC_HOST) {
+        void* p;
+        for (int k = 0; k < 5; ++k) {
+            e = cudaMalloc(&p, 4 * m);
+            if (e != cudaSuccess) { for (void* q : tmp) cudaFree(q); return cuda_fail(c, e); }
+            tmp.push_back(p);
+        }
+        dx_ = (float*)tmp[0]; dvx = (float*)tmp[1]; dvy = (float*)tmp[2]; dvz = (float*)tmp[3]; did = (uint32_t*)tmp[4];
+    }
+    c->gepoch += 1;
+    cudaMemsetAsync(c->d_gticket, 0, sizeof(unsigned), s);
+    launch_gather(species, c->P, c->grid_compact, (1ull << 60) | c->gepoch, c->d_gticket, c->d_gflag, c->d_gval,
+                  dx_, dvx, dvy, dvz, did, m, c->d_gcount, s);
+    c->launches += 1;
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && mem_kind == O2PIC_HOST) {
+        e = cudaMemcpy(x, dx_, 4 * m, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(vx, dvx, 4 * m, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(vy, dvy, 4 * m, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(vz, dvz, 4 * m, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(id, did, 4 * m, cudaMemcpyDeviceToHost);
+    }
+    for (void* q : tmp) cudaFree(q);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return check_flags(c);
+}
+
+int o2pic_read_field(o2pic_ctx* c, double* phi, float* E) {
+    if (!c) return O2PIC_E_INVALID_ARG;
+    if (c->dirty && c->have_tables) {
+        cudaSetDevice(c->device);
+        int rc = prepare(c, c->stream);
+        if (rc) return rc;
+    }
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    cudaError_t e = cudaSuccess;
+    if (phi) e = cudaMemcpy(phi, c->P.phi, sizeof(double) * c->P.Ng, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(E, c->P.Ef, sizeof(float) * c->P.Ng, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return rc;
+}
+
+int o2pic_read_charge(o2pic_ctx* c, uint64_t* Q, uint64_t* Qacc, uint64_t* acc_steps) {
+    if (!c) return O2PIC_E_INVALID_ARG;
+    if (c->dirty && c->have_tables) {
+        cudaSetDevice(c->device);
+        int rc = prepare(c, c->stream);
+        if (rc) return rc;
+    }
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    const int Ng = c->P.Ng;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < NSP && e == cudaSuccess; ++s) {
+        if (Q) e = cudaMemcpy(Q + (size_t)s * Ng, c->P.Q[s], 8 * (size_t)Ng, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && Qacc) e = cudaMemcpy(Qacc + (size_t)s * Ng, c->P.Qacc[s], 8 * (size_t)Ng, cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess && acc_steps) e = cudaMemcpy(acc_steps, &c->d_ctrl->acc_steps, 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return rc;
+}
+
+int o2pic_read_moments(o2pic_ctx* c, double* density, uint64_t* acc_steps, int reset) {
+    if (!c) return O2PIC_E_INVALID_ARG;
+    const int Ng = c->P.Ng;
+    std::vector<uint64_t> Qa((size_t)NSP * Ng);
+    uint64_t steps = 0;
+    int rc = o2pic_read_charge(c, nullptr, Qa.data(), &steps);
+    if (rc == O2PIC_E_CUDA) return rc;
+    if (density) {
+        const double dx = c->P.dx;
+        for (int s = 0; s < NSP; ++s)
+            for (int j = 0; j < Ng; ++j) {
+                const double vol = c->cfg.area * ((j == 0 || j == Ng - 1) ? 0.5 * dx : dx);
+                density[(size_t)s * Ng + j] =
+                    steps ? (double)Qa[(size_t)s * Ng + j] / (65536.0 * (double)steps) * c->cfg.weight / vol : 0.0;
+            }
+    }
+    if (acc_steps) *acc_steps = steps;
+    if (reset) {
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < NSP && e == cudaSuccess; ++s) e = cudaMemset(c->P.Qacc[s], 0, 8 * (size_t)Ng);
+        const unsigned long long zero = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&c->d_ctrl->acc_steps, &zero, 8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    return rc;
+}
+
+int o2pic_get_stats(o2pic_ctx* c, o2pic_stats* out) {
+    if (!c || !out) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    DevCtrl h;
+    cudaError_t e = cudaMemcpy(&h, c->d_ctrl, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    std::memset(out, 0, sizeof(*out));
+    for (int s = 0; s < NSP; ++s) {
+        for (int k = 0; k < MAXPROC; ++k) out->events[s][k] = h.cnt.events[s][k];
+        out->absorbed[s][0] = h.cnt.absorbed[s][0];
+        out->absorbed[s][1] = h.cnt.absorbed[s][1];
+        out->born[s] = h.cnt.born[s];
+        out->live[s] = h.live[s];
+        out->slots[s] = h.slots[s];
+        out->next_id[s] = h.next_id[s];
+        out->particle_steps_species[s] = h.cnt.psteps[s];
+    }
+    out->neutralized = h.cnt.neutralized;
+    out->pair_candidates = h.cnt.pair_candidates;
+    out->particle_steps = h.cnt.particle_steps;
+    out->warn_emax = h.cnt.warn_emax;
+    out->warn_tries = h.cnt.warn_tries;
+    out->warn_pair_gt1 = h.cnt.warn_pair_gt1;
+    out->id_overflow = h.cnt.id_overflow;
+    out->step = h.step;
+    out->error_flags = h.error_flags;
+    return rc;
+}
+
+int o2pic_set_timing(o2pic_ctx* c, int on) {
+    if (!c) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    c->timing = on != 0;
+    for (int k = 0; k < NKK; ++k) { c->ms[k] = 0; c->nlaunch[k] = 0; }
+    return rc == O2PIC_E_CUDA ? rc : O2PIC_OK;
+}
+
+int o2pic_get_timing(o2pic_ctx* c, double* ms, uint64_t* launches, uint64_t* items, int nkinds) {
+    if (!c || nkinds < 0) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    for (int k = 0; k < nkinds && k < NKK; ++k) {
+        if (ms) ms[k] = c->ms[k];
+        if (launches) launches[k] = c->nlaunch[k];
+        if (items) items[k] = 0;
+    }
+    return rc == O2PIC_E_CUDA ? rc : O2PIC_OK;
+}
+
+uint64_t o2pic_launch_count(o2pic_ctx* c) { return c ? c->launches : 0; }
+
+int o2pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, uint64_t n, void* stream) {
+    if ((!ctr || !key || !out) && n) return O2PIC_E_INVALID_ARG;
+    if (n == 0) return O2PIC_OK;
+    launch_philox(ctr, key, out, n, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? O2PIC_OK : O2PIC_E_CUDA;
+}
+
+int o2pic_ln_f32(const float* x, float* out, uint64_t n, void* stream) {
+    if ((!x || !out) && n) return O2PIC_E_INVALID_ARG;
+    if (n == 0) return O2PIC_OK;
+    launch_ln(x, out, n, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? O2PIC_OK : O2PIC_E_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Tolerance: 1e-5 relative per particle (expected and
+usually found bit-exact, since both sides round the same FP32 operations in
+the same order), identical event counts, integer charge bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0705_0497_gb300 import inputs, xsec
+from helpers import (capacity_for, compare_counters, compare_particles, curand_ref_lib, make_pair, nproc_of)
+
+pytestmark = pytest.mark.gpu
+
+QE, KB, ME, AMU = inputs.QE, inputs.KB, inputs.ME, inputs.AMU
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def test_philox_matches_oracle_and_curand(torch_cuda):
+    import oracle
+    from paper_0705_0497_gb300 import api
+    torch = torch_cuda
+    rng = np.random.default_rng(0)
+    n = 1 << 20
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    dc = torch.from_numpy(ctr.view(np.int32)).cuda()
+    dk = torch.from_numpy(key.view(np.int32)).cuda()
+    out = api.philox(dc, dk).cpu().numpy().view(np.uint32)
+    ref = torch.empty_like(dc)
+    L = curand_ref_lib()
+    assert L.curand_ref_philox(dc.data_ptr(), dk.data_ptr(), ref.data_ptr(), n) == 0
+    assert np.array_equal(out, ref.cpu().numpy().view(np.uint32))
+    for i in range(0, n, n // 64):
+        assert np.array_equal(out[i], oracle.philox(ctr[i], key[i]))
+
+
+def test_ln_series_bitexact_and_bounded(torch_cuda):
+    import oracle
+    from paper_0705_0497_gb300 import api
+    torch = torch_cuda
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.random(200000).astype(np.float32), np.float32([1.0, 0.5, 2.0 ** -46, 0.7071068])])
+    x = x[x > 0]
+    got = api.ln_f32(torch.from_numpy(x).cuda()).cpu().numpy()
+    for i in range(0, len(x), 997):
+        assert got[i] == np.float32(oracle.ln_f32(float(x[i])))
+    ref = np.log(x.astype(np.float64))
+    tol = 2.0 * np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64) + 2.0 ** -24
+    assert np.all(np.abs(got - ref) <= tol)
+    # and within the bound of CUDA's own logf (called through torch)
+    cu = torch.log(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - cu) <= 2 * tol)
+
+
+def test_initial_charge_and_field(torch_cuda):
+    cfg, counts, T, _ = inputs.workload("parity_128")
+    procs = xsec.oxygen_set()
+    g, o, st = make_pair(cfg, counts, T, procs)
+    Qg, _, _ = g.charge()
+    Qo, _, _ = o.charge()
+    assert np.array_equal(Qg, Qo)
+    phig, Eg = g.field()
+    phio, Eo, Ego = o.field()
+    assert np.allclose(phig, phio, rtol=0, atol=1e-11 * np.abs(phio).max())
+    assert np.allclose(Eg, Ego.astype(np.float32), rtol=2e-6, atol=1e-6 * np.abs(Ego).max())
+
+
+def test_parity_100_steps(torch_cuda):
+    """Parity case (2 cm, 128 cells, 2.2e4 particles), 100 coupled steps."""
+    cfg, counts, T, _ = inputs.workload("parity_128")
+    procs = xsec.oxygen_set()
+    g, o, _ = make_pair(cfg, counts, T, procs)
+    for chunk in (1, 9, 40, 50):
+        g.step(chunk)
+        o.step(chunk)
+        compare_particles(g, o)
+        compare_counters(g.stats(), o.counters(), nproc_of(procs))
+        Qg, _, _ = g.charge()
+        Qo, _, _ = o.charge()
+        assert np.array_equal(Qg, Qo)
+    gs = g.stats()
+    assert sum(gs[f"born_{s}"] for s in range(3)) > 0
+    assert gs["step"] == 100
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 1023, 1025, 8191, 8193, 20001])
+def test_parity_ragged_sizes(torch_cuda, n):
+    """Empty, single, ragged and multi-tile particle counts (tiles of 8192,
+    chunks of 1024, 4 particles per thread), with ion subcycling."""
+    cfg, _, T, _ = inputs.workload("parity_128", ion_subcycle=3)
+    counts = (n, n // 3, n)
+    procs = xsec.oxygen_set()
+    g, o, _ = make_pair(cfg, counts, T, procs, capacity=capacity_for(counts, 3.0, 64))
+    g.step(7)
+    o.step(7)
+    compare_particles(g, o)
+    compare_counters(g.stats(), o.counters(), nproc_of(procs))
+
+
+def test_parity_walls_and_edges(torch_cuda):
+    """Particles exactly at x = 0, just below L and at cell boundaries."""
+    cfg, counts, T, _ = inputs.workload("parity_128")
+    st = inputs.initial_state(cfg, (3000, 300, 3000), T)
+    L = np.float32(cfg["L"])
+    dx = cfg["L"] / cfg["n_cells"]
+    for p in st:
+        k = min(len(p["x"]), 200)
+        p["x"][:k:4] = 0.0
+        p["x"][1:k:4] = np.nextafter(L, np.float32(0))
+        p["x"][2:k:4] = np.float32(dx * 17)
+        p["x"][3:k:4] = np.float32(dx * 64)
+    procs = xsec.oxygen_set()
+    g, o, _ = make_pair(cfg, None, None, procs, state=st)
+    g.step(20)
+    o.step(20)
+    compare_particles(g, o)
+    compare_counters(g.stats(), o.counters(), nproc_of(procs))
+
+
+def test_neutralization_parity(torch_cuda):
+    """Many (17) reactions: a large constant rate coefficient, ions at rest in
+    a few cells, the library's pairing against the oracle's, pair for pair."""
+    Nc = 32
+    cfg = inputs.base_config(L=0.02, n_cells=Nc, U=0.0, p=10.0, C_meta=0.0, ion_subcycle=2, weight=2e9, seed=3,
+                             steps_per_cycle=400)
+    dx = cfg["L"] / Nc
+    mu = cfg["m_OM"] * cfg["m_OP"] / (cfg["m_OM"] + cfg["m_OP"])
+    K0 = 1e-4 * cfg["area"] * dx / (cfg["weight"] * cfg["dt"] * 2)
+    procs = [xsec.constant_rate_process(1, xsec.NEUTRALIZE, K0, 1.0, mu, target=xsec.T_ION)]
+    rng = np.random.default_rng(7)
+    st = []
+    for s, n in enumerate((500, 30000, 26000)):
+        x = ((rng.integers(0, Nc, n) + 0.05 + 0.9 * rng.random(n)) * dx).astype(np.float32)
+        v = (rng.standard_normal((3, n)) * (1e5 if s == 0 else 300.0)).astype(np.float32)
+        st.append(dict(x=x, vx=v[0].copy(), vy=v[1].copy(), vz=v[2].copy(), id=np.arange(n, dtype=np.uint32)))
+    g, o, _ = make_pair(cfg, None, None, procs, state=st)
+    for _ in range(3):
+        g.step(2)
+        o.step(2)
+        compare_particles(g, o)
+        compare_counters(g.stats(), o.counters(), nproc_of(procs))
+    assert o.counters()["neutralized"] > 500
+
+
+def test_compaction_keeps_order(torch_cuda):
+    """A strong field empties slots quickly; the periodic stable compaction
+    must keep the array order the method defines."""
+    cfg, counts, T, _ = inputs.workload("parity_128", U=2000.0, ion_subcycle=2)
+    procs = xsec.oxygen_set()
+    g, o, _ = make_pair(cfg, (20000, 5000, 20000), T, procs, compact_check=2)
+    for _ in range(6):
+        g.step(5)
+        o.step(5)
+        compare_particles(g, o)
+    st = g.stats()
+    assert st["slots_0"] < 20000 + st["born_0"]    # compaction happened
+    compare_counters(st, o.counters(), nproc_of(procs))
+
+
+def test_capacity_overflow_is_reported(torch_cuda):
+    from paper_0705_0497_gb300 import api
+    cfg, counts, T, _ = inputs.workload("parity_128", U=600.0)
+    procs = xsec.oxygen_set()
+    st = inputs.initial_state(cfg, counts, T)
+    g = api.Discharge(cfg, (counts[0], counts[1], counts[2]))
+    g.set_processes(procs)
+    g.load_state(st)
+    with pytest.raises(api.O2picError) as ei:
+        g.step(200)
+        g.synchronize()
+    assert ei.value.code == -2
+
+
+def test_invalid_load_rejected(torch_cuda):
+    from paper_0705_0497_gb300 import api
+    cfg, counts, T, _ = inputs.workload("parity_128")
+    g = api.Discharge(cfg, (100, 100, 100))
+    x = np.full(10, cfg["L"] * 1.5, np.float32)
+    z = np.zeros(10, np.float32)
+    with pytest.raises(api.O2picError) as ei:
+        g.load(0, x, z, z, z, np.arange(10))
+    assert ei.value.code == -1
+    import torch
+    with pytest.raises(api.O2picError) as ei:
+        g.load(0, torch.from_numpy(x).cuda(), *(torch.from_numpy(z).cuda() for _ in range(3)),
+               torch.arange(10, dtype=torch.int32).cuda())
+    assert ei.value.code == -1
+
+
+def test_long_run_profiles(torch_cuda):
+    """Parity case over its full 20 RF cycles: cycle-averaged density profiles
+    and the centre electronegativity n_O-/n_e within 2% of the oracle; the
+    deviation of the FP32 path from the FP64 oracle is reported."""
+    import oracle
+    cfg, counts, T, cycles = inputs.workload("parity_128")
+    procs = xsec.oxygen_set()
+    g, o, st = make_pair(cfg, counts, T, procs)
+    o64 = oracle.Oracle(cfg, 64)
+    o64.set_processes(procs)
+    for s, p in enumerate(st):
+        o64.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])
+    spc = cfg["steps_per_cycle"]
+    nsteps = cycles * spc
+    warm = nsteps - 5 * spc
+    g.step(warm)
+    o.step(warm)
+    o64.step(warm)
+    g.moments(reset=True)
+    o.reset_moments()
+    o64.reset_moments()
+    g.step(nsteps - warm)
+    o.step(nsteps - warm)
+    o64.step(nsteps - warm)
+    # same arithmetic on both sides: the whole run stays particle-for-particle equal
+    compare_particles(g, o)
+    dg, ng = g.moments()
+    _, Qa, no = o.charge()
+    _, Qa64, no64 = o64.charge()
+    assert ng == no == no64 == nsteps - warm
+    Ng = cfg["n_cells"] + 1
+    dx = cfg["L"] / cfg["n_cells"]
+    vol = np.full(Ng, dx * cfg["area"])
+    vol[0] = vol[-1] = dx * cfg["area"] / 2
+    do = Qa / (65536.0 * no) * cfg["weight"] / vol
+    d64 = Qa64 / (65536.0 * no64) * cfg["weight"] / vol
+    inner = slice(Ng // 8, Ng - Ng // 8)
+    for s in range(3):
+        scale = do[s].max()
+        if scale == 0:
+            continue
+        err = np.abs(dg[s] - do[s])[inner].max() / scale
+        assert err < 0.02, (s, err)
+        err64 = np.abs(dg[s] - d64[s])[inner].max() / scale
+        print(f"species {s}: max |GPU - oracle32| / max = {err:.3e}, vs FP64 oracle = {err64:.3e}")
+    c = Ng // 2
+    alpha_g = dg[1][c - 4:c + 5].mean() / dg[0][c - 4:c + 5].mean()
+    alpha_o = do[1][c - 4:c + 5].mean() / do[0][c - 4:c + 5].mean()
+    alpha_64 = d64[1][c - 4:c + 5].mean() / d64[0][c - 4:c + 5].mean()
+    print(f"centre electronegativity: GPU {alpha_g:.4f}, oracle32 {alpha_o:.4f}, oracle64 {alpha_64:.4f}")
+    assert abs(alpha_g / alpha_o - 1) < 0.02

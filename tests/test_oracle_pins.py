@@ -199,14 +199,20 @@ def test_poisson_uniform_charge_is_parabola(oracle_mod):
     assert np.allclose(E, Eref, rtol=0, atol=1e-10 * np.abs(Eref).max())
 
 
-def test_poisson_random_charge_vs_dense_and_gauss(oracle_mod):
+def test_poisson_random_charge_vs_dense_thomas_and_gauss(oracle_mod):
+    """The closed-form solve against a dense numpy.linalg.solve of the full
+    system and against the Thomas algorithm (same system, different
+    arithmetic), for potentials and fields; Gauss's law over the gap."""
     rng = np.random.default_rng(3)
-    for N in (1, 2, 3, 17, 128, 513):
+    for N in (1, 2, 3, 17, 128, 513, 2048):
         L, V0, w, A = 0.025, 300.0, 6.25e6, 1.0
         dx = L / N
         R = rng.integers(-2 ** 40, 2 ** 40, N + 1)
         phi, E = oracle_mod.solve_field(N, dx, w, A, V0, R)
-        if N >= 2:
+        phit, Et = oracle_mod.solve_field(N, dx, w, A, V0, R, method="thomas")
+        assert np.allclose(phi, phit, rtol=0, atol=1e-10 * np.abs(phit).max())
+        assert np.allclose(E, Et, rtol=0, atol=1e-8 * np.abs(Et).max())
+        if 2 <= N <= 600:
             ref = _dense_solve(N, dx, w, A, V0, R.astype(np.float64))
             assert np.allclose(phi, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
         # Gauss's law over the whole gap: E_N - E_0 = Q_total / (eps0 A)
