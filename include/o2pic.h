@@ -199,6 +199,20 @@ int o2pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, uint64
  * out[i] = ln(x[i]) for x in (0, 1].  Device pointers. */
 int o2pic_ln_f32(const float* x, float* out, uint64_t n, void* stream);
 
+/* Stable compaction of a caller's particle arrays (the removal part of the
+ * step's births/removal, e.g. of particles absorbed at the electrodes or
+ * consumed by attachment, detachment or neutralization): the particles whose
+ * x is NaN (the library's marker of a removed particle) are dropped, the
+ * others are written to ox.. oid in their input order.  All pointers are
+ * device pointers of the current device; outputs hold n elements and must
+ * not overlap the inputs; *n_out (device) receives the number kept.  The call
+ * allocates its scratch (tile look-back state, 24 B per 8192 particles) with
+ * cudaMalloc, frees it, and returns once the work on `stream` is done.
+ * n <= 2^31.  Errors: INVALID_ARG, CUDA, TIMEOUT. */
+int o2pic_compact_particles(const float* x, const float* vx, const float* vy, const float* vz,
+                            const uint32_t* id, uint64_t n, float* ox, float* ovx, float* ovy, float* ovz,
+                            uint32_t* oid, uint64_t* n_out, void* stream);
+
 const char* o2pic_strerror(int code);
 
 void o2pic_destroy(o2pic_ctx* ctx);

@@ -463,9 +463,10 @@ template <class R> struct Oracle {
             else if (j == N) phi[j] = 0.0;
             else phi[j] = V0 + (double)j * D0 - c * (double)T[j];
         }
-        for (int j = 1; j <= N - 1; ++j) E[j] = (c * (double)(S[j] + S[j - 1]) - 2.0 * D0) / (2.0 * dx);
-        E[0] = (-D0 - c * (double)Rn[0]) / dx;
-        E[N] = (c * (double)S[N - 1] - D0 + c * (double)Rn[N]) / dx;
+        const double inv_dx = 1.0 / dx, inv_2dx = 1.0 / (2.0 * dx);
+        for (int j = 1; j <= N - 1; ++j) E[j] = (c * (double)(S[j] + S[j - 1]) - 2.0 * D0) * inv_2dx;
+        E[0] = (-D0 - c * (double)Rn[0]) * inv_dx;
+        E[N] = (c * (double)S[N - 1] - D0 + c * (double)Rn[N]) * inv_dx;
     }
 
     // The same system by the Thomas algorithm (a = c = -1, b = 2) with the

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("o2pic_launch_count", _u64, [_vp]),
     ("o2pic_philox", _i32, [_vp, _vp, _vp, _u64, _vp]),
     ("o2pic_ln_f32", _i32, [_vp, _vp, _u64, _vp]),
+    ("o2pic_compact_particles", _i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("o2pic_strerror", ctypes.c_char_p, [_i32]),
     ("o2pic_destroy", None, [_vp]),
     ("o2pic_version", _i32, []),
@@ -296,6 +297,26 @@ def philox(ctr, key, stream=None):
     _check(lib().o2pic_philox(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_void_p(key.data_ptr()),
                               ctypes.c_void_p(out.data_ptr()), int(ctr.shape[0]), _stream_ptr(stream)), "o2pic_philox")
     return out
+
+
+def _ptrs(ts):
+    return [ctypes.c_void_p(t.data_ptr()) for t in ts]
+
+
+def compact_particles(x, vx, vy, vz, ids, stream=None, out=None):
+    """Stable removal of the particles with x = NaN from CUDA tensors; returns
+    tensors holding the kept particles in their input order.  `out` = five
+    caller tensors to write into (else new ones)."""
+    import torch
+    n = int(x.numel())
+    outs = out if out is not None else [torch.empty(max(n, 1), dtype=t.dtype, device=t.device)
+                                        for t in (x, vx, vy, vz, ids)]
+    n_out = torch.zeros(1, dtype=torch.int64, device=x.device)
+    _check(lib().o2pic_compact_particles(*_ptrs((x, vx, vy, vz, ids)), n, *_ptrs(outs),
+                                         ctypes.c_void_p(n_out.data_ptr()), _stream_ptr(stream)),
+           "o2pic_compact_particles")
+    m = int(n_out.item())
+    return [o[:m] for o in outs]
 
 
 def ln_f32(x, stream=None):

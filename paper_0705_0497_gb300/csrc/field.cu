@@ -10,8 +10,8 @@
 // exact integer prefix sums:
 //     S_m = sum_{k=1..m} R_k,  T_j = sum_{m<j} S_m,
 //     D_0 = phi_1 - phi_0 = (c T_N - V0) / N,  phi_j = V0 + j D_0 - c T_j,
-//     E_j = (c (S_j + S_{j-1}) - 2 D_0) / (2 dx)           (1 <= j <= N-1),
-//     E_0 = (-D_0 - c R_0) / dx,  E_N = (c S_{N-1} - D_0 + c R_N) / dx
+//     E_j = (c (S_j + S_{j-1}) - 2 D_0) [1/(2 dx)]         (1 <= j <= N-1),
+//     E_0 = (-D_0 - c R_0) [1/dx],  E_N = (c S_{N-1} - D_0 + c R_N) [1/dx]
 // (wall nodes from Gauss's law over the half cell next to the wall).  This is
 // the exact solution of the linear system a Thomas sweep would solve; it
 // needs no serial FP64 recurrence (FP64 throughput on this GPU is low), its
@@ -25,14 +25,19 @@ namespace o2 {
 namespace {
 
 constexpr int FT = 1024;                          // threads of the field block
-constexpr int FPER = (MAX_NODES + FT - 1) / FT;   // nodes per thread (blocked)
 
-// Block-wide inclusive scan of a blocked int64 array (FPER values per thread).
-__device__ __forceinline__ void block_scan_ll(long long (&v)[FPER], long long* ws) {
+// Block-wide inclusive scan of the int64 array a[0..n) in shared memory
+// (blocked: thread t owns [t*per, (t+1)*per)).  ws = 32 words of smem.
+__device__ __forceinline__ void block_scan_smem(long long* a, int n, long long* ws) {
+    const int t = threadIdx.x;
+    const int per = (n + FT - 1) / FT;
+    const int j0 = t * per;
     long long run = 0;
-#pragma unroll
-    for (int i = 0; i < FPER; ++i) { run += v[i]; v[i] = run; }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < per; ++i) {
+        const int j = j0 + i;
+        if (j < n) { run += a[j]; a[j] = run; }
+    }
+    const int lane = t & 31, warp = t >> 5;
     long long x = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -42,92 +47,78 @@ __device__ __forceinline__ void block_scan_ll(long long (&v)[FPER], long long* w
     if (lane == 31) ws[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        long long t = ws[lane];
+        long long v = ws[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
+            const long long y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
         }
-        ws[lane] = t;
+        ws[lane] = v;
     }
     __syncthreads();
     const long long off = (warp == 0 ? 0 : ws[warp - 1]) + (x - run);
-#pragma unroll
-    for (int i = 0; i < FPER; ++i) v[i] += off;
+    for (int i = 0; i < per; ++i) {
+        const int j = j0 + i;
+        if (j < n) a[j] += off;
+    }
     __syncthreads();
 }
 
 // mode 0: end of a step (pushed_mask = species pushed this step);
 // mode 1: after a load (all species freshly deposited into Qf).
+// Dynamic shared memory: R, S, T as int64 [Ng] each.
 __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
+    extern __shared__ long long fsm[];
     __shared__ long long ws[32];
-    __shared__ long long sh_last[4];
     DevCtrl* C = P.ctrl;
     const int N = P.Nc, Ng = P.Ng;
     const int t = threadIdx.x;
-    const int j0 = t * FPER;
+    long long* Rs = fsm;
+    long long* Ss = fsm + Ng;
+    long long* Ts = fsm + 2 * Ng;
 
-    long long R[FPER];
+    // charge commit, moments, net charge (coalesced, all loads before stores)
+    for (int j = t; j < Ng; j += FT) {
+        unsigned long long qf[NSP], qo[NSP], qb[NSP], qa[NSP];
 #pragma unroll
-    for (int i = 0; i < FPER; ++i) {
-        const int j = j0 + i;
-        long long net = 0;
-        if (j < Ng) {
-#pragma unroll
-            for (int s = 0; s < NSP; ++s) {
-                const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
-                unsigned long long q = fresh ? P.Qf[s][j] : P.Q[s][j];
-                q += P.Qb[s][j];
-                P.Q[s][j] = q;
-                P.Qf[s][j] = 0ull;
-                P.Qb[s][j] = 0ull;
-                if (mode == 0) P.Qacc[s][j] += q;
-                net += (s == SP_OP) ? (long long)q : -(long long)q;
-            }
+        for (int s = 0; s < NSP; ++s) {
+            qf[s] = P.Qf[s][j];
+            qo[s] = P.Q[s][j];
+            qb[s] = P.Qb[s][j];
+            qa[s] = (mode == 0) ? P.Qacc[s][j] : 0ull;
         }
-        R[i] = net;
-    }
-    // S_m = sum_{k=1..m} R_k: scan of R with R_0 left out
-    long long Sv[FPER];
+        long long net = 0;
 #pragma unroll
-    for (int i = 0; i < FPER; ++i) Sv[i] = (j0 + i >= 1 && j0 + i < Ng) ? R[i] : 0;
-    block_scan_ll(Sv, ws);
-    // T_j = sum_{m<j} S_m: exclusive scan of S over m = 0..N-1
-    long long Tv[FPER];
-#pragma unroll
-    for (int i = 0; i < FPER; ++i) Tv[i] = (j0 + i < N) ? Sv[i] : 0;
-    block_scan_ll(Tv, ws);     // inclusive: Tv[i] = sum_{m <= j} S_m  => T_{j+1}
-    // values needed across thread boundaries: S_{j-1} for the first node of a
-    // thread, T_j = inclusive(j-1), S_{N-1}, R_N, T_N
-    __shared__ long long sh_Sprev[FT], sh_Tprev[FT];
-    sh_Sprev[t] = Sv[FPER - 1];
-    sh_Tprev[t] = Tv[FPER - 1];
-#pragma unroll
-    for (int i = 0; i < FPER; ++i) {
-        const int j = j0 + i;
-        if (j == N - 1) { sh_last[0] = Sv[i]; sh_last[1] = Tv[i]; }   // S_{N-1}, T_N
-        if (j == N) sh_last[2] = R[i];
+        for (int s = 0; s < NSP; ++s) {
+            const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
+            const unsigned long long q = (fresh ? qf[s] : qo[s]) + qb[s];
+            P.Q[s][j] = q;
+            P.Qf[s][j] = 0ull;
+            P.Qb[s][j] = 0ull;
+            if (mode == 0) P.Qacc[s][j] = qa[s] + q;
+            net += (s == SP_OP) ? (long long)q : -(long long)q;
+        }
+        Rs[j] = net;
+        Ss[j] = (j >= 1) ? net : 0;     // S_m = sum_{k=1..m} R_k
     }
     __syncthreads();
-    const double c = P.c_field, dx = P.dx;
+    block_scan_smem(Ss, Ng, ws);
+    // T_j = sum_{m<j} S_m (exclusive scan of S over m = 0..N-1)
+    for (int j = t; j < Ng; j += FT) Ts[j] = (j >= 1) ? Ss[j - 1] : 0;
+    __syncthreads();
+    block_scan_smem(Ts, Ng, ws);
+    const double c = P.c_field;
     const unsigned long long step = C->step;
     // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load), evaluated
     // on the host in FP64 and staged in a ring indexed by the step
     const double V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
-    const long long TN = sh_last[1];
-    const double D0 = (c * (double)TN - V0) / (double)N;
-    const long long SNm1 = sh_last[0], RN = sh_last[2];
-#pragma unroll
-    for (int i = 0; i < FPER; ++i) {
-        const int j = j0 + i;
-        if (j >= Ng) break;
-        const long long Sprev = (i == 0) ? (t > 0 ? sh_Sprev[t - 1] : 0) : Sv[i - 1];
-        const long long Tj = (i == 0) ? (t > 0 ? sh_Tprev[t - 1] : 0) : Tv[i - 1];
+    const double D0 = (c * (double)Ts[N] - V0) / (double)N;
+    for (int j = t; j < Ng; j += FT) {
         double E;
-        if (j == 0) E = (-D0 - c * (double)R[i]) / dx;
-        else if (j == N) E = (c * (double)SNm1 - D0 + c * (double)RN) / dx;
-        else E = (c * (double)(Sv[i] + Sprev) - 2.0 * D0) / (2.0 * dx);
-        const double phi = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Tj);
+        if (j == 0) E = (-D0 - c * (double)Rs[0]) * P.inv_dx64;
+        else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)Rs[N]) * P.inv_dx64;
+        else E = (c * (double)(Ss[j] + Ss[j - 1]) - 2.0 * D0) * P.inv_2dx64;
+        const double phi = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Ts[j]);
         P.Ef[j] = (float)E;
         P.phi[j] = phi;
     }
@@ -324,7 +315,11 @@ __global__ void k_ln(const float* x, float* out, unsigned long long n) {
 }  // namespace
 
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s) {
-    k_field<<<1, FT, 0, s>>>(P, mode, pushed_mask);
+    k_field<<<1, FT, 3 * sizeof(long long) * (size_t)P.Ng, s>>>(P, mode, pushed_mask);
+}
+
+cudaError_t configure_field_smem(size_t bytes) {
+    return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 void launch_compact(int species, const Params& P, int grid, cudaStream_t s) {

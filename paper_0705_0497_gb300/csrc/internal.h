@@ -102,6 +102,7 @@ struct Params {
     int Nc, Ng;
     float inv_dx, Lf;
     double dx, c_field, U, two_pi_f, dt;   // c_field = e w dx / (A eps0 2^16)
+    double inv_dx64, inv_2dx64;            // 1/dx and 1/(2 dx)
     const double* vring;         // electrode voltage U sin(2 pi f t_k) at t_k = k dt, slot k & vring_mask
     unsigned int vring_mask;
     float* Ef;                   // [Ng] gather field (FP32)
@@ -148,6 +149,8 @@ void launch_gather(int species, const Params& P, int grid, unsigned long long ep
                    unsigned long long* flag, unsigned long long* val, float* x, float* vx, float* vy, float* vz,
                    uint32_t* id, unsigned long long cap, unsigned long long* out_count, cudaStream_t s);
 cudaError_t configure_push_smem(size_t max_bytes);
+cudaError_t configure_field_smem(size_t bytes);
+size_t pair_smem_bytes(int Nc);
 int push_occupancy(int species, const Params& P, int* blocks_per_sm);
 size_t push_smem_bytes(int species, const Params& P);
 

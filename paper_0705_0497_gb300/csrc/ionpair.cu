@@ -11,9 +11,9 @@
 // the number of surviving ions per cell.  k_pair_scan turns these into
 // per-cell exclusive prefixes over tiles (so the rank of an ion in its cell
 // list is prefix + its rank inside the tile) and draws the shifts.  k_pair
-// gives each warp one O- tile: it walks the tile in slot order keeping
-// per-cell counts in shared memory, so every O- learns its rank k in its
-// cell, whether it is paired and the rank q of its partner.  The acceptance
+// gives each block one O- tile, split among its warps; with per-warp cell
+// counts every O- learns its rank k in its cell list, whether it is paired
+// and the rank q of its partner.  The acceptance
 // draw needs only the O- id; since P <= K_max M w dt/(A dx), only the rare
 // draws below that bound need the partner, which the warp then finds by a
 // binary search over the O2+ prefixes and a ballot scan of one O2+ tile.
@@ -115,12 +115,20 @@ __device__ unsigned find_op(const Params& P, const float* XP, unsigned long long
     return 0xFFFFFFFFu;
 }
 
-__global__ void __launch_bounds__(PAIR_WARPS * 32) k_pair(Params P) {
-    extern __shared__ unsigned cnt_all[];    // [PAIR_WARPS][Nc]
+// One block per O- tile.  Pass 1: each warp loads its sub-range of the tile
+// (all loads in flight together), stores each slot's cell (or "dead") in
+// shared memory and counts its ions per cell.  Pass 2: per cell, prefix of
+// the warps' counts, starting from the tile's prefix over earlier tiles.
+// Pass 3: each warp walks its sub-range in slot order from shared memory;
+// an O- learns its rank k in its cell list, whether it is paired, and draws
+// its acceptance number; the rare candidates find their partner.
+__global__ void __launch_bounds__(PAIR_WARPS * 32) k_pair(Params P, int W) {
+    extern __shared__ unsigned pair_smem[];
+    unsigned short* cell16 = reinterpret_cast<unsigned short*>(pair_smem);   // [TILE]
+    unsigned* whist = pair_smem + TILE / 2;                                  // [W][Nc]
     DevCtrl* C = P.ctrl;
     const int Nc = P.Nc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned* cnt = cnt_all + (size_t)warp * Nc;
     const unsigned long long step = C->step;
     const unsigned long long nsm = C->slots[SP_OM], nsp = C->slots[SP_OP];
     const unsigned ntm = (unsigned)ceil_div(nsm, TILE), ntp = (unsigned)ceil_div(nsp, TILE);
@@ -129,35 +137,65 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32) k_pair(Params P) {
     const uint32_t* IDM = P.sp[SP_OM].id[cm];
     const float* XP = P.sp[SP_OP].x[cp];
     const float pf = P.pair_factor;
+    const int sub = TILE / W;
     unsigned gt1 = 0;
+    unsigned* myhist = whist + (size_t)warp * Nc;
 
-    for (unsigned tile = blockIdx.x * PAIR_WARPS + warp; tile < ntm; tile += gridDim.x * PAIR_WARPS) {
-        for (int c = lane; c < Nc; c += 32) cnt[c] = 0u;
-        __syncwarp();
+    for (unsigned tile = blockIdx.x; tile < ntm; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < W * Nc; i += blockDim.x) whist[i] = 0u;
+        __syncthreads();
         const unsigned long long base = (unsigned long long)tile * TILE;
         const unsigned long long end = (base + TILE < nsm) ? base + TILE : nsm;
-        const unsigned* HM = P.hist[0] + (size_t)tile * Nc;
-        for (unsigned long long b = base; b < end; b += 32) {
+        const unsigned long long s0 = base + (unsigned long long)warp * sub;
+        const unsigned long long s1 = (s0 + sub < end) ? s0 + sub : end;
+        // pass 1
+#pragma unroll 4
+        for (unsigned long long b = s0; b < s1; b += 32) {
             const unsigned long long p = b + lane;
-            bool live = false;
-            int c = 0;
-            float fr;
-            if (p < end) {
+            if (p < s1) {
                 const float x = XM[p];
-                if (!is_dead(x)) { live = true; cell_of(x, P.inv_dx, Nc, c, fr); }
+                unsigned short cc = 0xFFFFu;
+                if (!is_dead(x)) {
+                    int c; float fr;
+                    cell_of(x, P.inv_dx, Nc, c, fr);
+                    cc = (unsigned short)c;
+                    atomicAdd(&myhist[c], 1u);
+                }
+                cell16[p - base] = cc;
+            }
+        }
+        __syncthreads();
+        // pass 2
+        const unsigned* HM = P.hist[0] + (size_t)tile * Nc;
+        for (int c = threadIdx.x; c < Nc; c += blockDim.x) {
+            unsigned run = HM[c];
+            for (int w = 0; w < W; ++w) {
+                const unsigned v = whist[(size_t)w * Nc + c];
+                whist[(size_t)w * Nc + c] = run;
+                run += v;
+            }
+        }
+        __syncthreads();
+        // pass 3
+        for (unsigned long long b = s0; b < s1; b += 32) {
+            const unsigned long long p = b + lane;
+            int c = 0;
+            bool live = false;
+            if (p < s1) {
+                const unsigned short cc = cell16[p - base];
+                if (cc != 0xFFFFu) { live = true; c = cc; }
             }
             const unsigned lmask = __ballot_sync(0xffffffffu, live);
-            unsigned k = 0;
             bool cand = false;
             unsigned q = 0, M = 0;
             float u = 0.0f;
             if (live) {
                 const unsigned peers = __match_any_sync(lmask, c);
                 const unsigned lt = peers & ((1u << lane) - 1u);
-                const unsigned before = cnt[c];
-                k = HM[c] + before + __popc(lt);
+                const unsigned before = myhist[c];
+                const unsigned k = before + __popc(lt);
                 __syncwarp(lmask);
-                if (lt == 0u) cnt[c] = before + __popc(peers);
+                if (lt == 0u) myhist[c] = before + __popc(peers);
                 const unsigned nm = P.cellinfo[4 * c], npl = P.cellinfo[4 * c + 1], r = P.cellinfo[4 * c + 2];
                 const unsigned m = nm < npl ? nm : npl;
                 M = nm < npl ? npl : nm;
@@ -217,7 +255,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32) k_pair(Params P) {
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
     if (gt1) atomicAdd(&C->cnt.warn_pair_gt1, (unsigned long long)gt1);
 }
@@ -228,8 +266,20 @@ void launch_pair_scan(const Params& P, cudaStream_t s) {
     k_pair_scan<<<(P.Nc + 31) / 32, SCAN_T, 0, s>>>(P);
 }
 
+// warps per block: the largest of 8, 4, 2, 1 whose per-warp cell counts fit
+int pair_warps(int Nc) {
+    for (int w = PAIR_WARPS; w > 1; w >>= 1)
+        if (2 * TILE + 4 * (size_t)w * Nc <= 200 * 1024) return w;
+    return 1;
+}
+
+size_t pair_smem_bytes(int Nc) {
+    return 2 * (size_t)TILE + 4 * (size_t)pair_warps(Nc) * Nc;
+}
+
 void launch_pair(const Params& P, int grid, cudaStream_t s) {
-    k_pair<<<grid, PAIR_WARPS * 32, sizeof(unsigned) * PAIR_WARPS * (size_t)P.Nc, s>>>(P);
+    const int W = pair_warps(P.Nc);
+    k_pair<<<grid, W * 32, pair_smem_bytes(P.Nc), s>>>(P, W);
 }
 
 cudaError_t configure_pair_smem(size_t bytes) {

@@ -217,6 +217,8 @@ void set_constants(o2pic_ctx* c) {
     P.Ng = g.n_cells + 1;
     P.dx = dx;
     P.c_field = QE * g.weight * dx / (g.area * EPS0 * 65536.0);
+    P.inv_dx64 = 1.0 / dx;
+    P.inv_2dx64 = 1.0 / (2.0 * dx);
     P.U = g.U;
     P.two_pi_f = TWO_PI * g.f;
     P.dt = g.dt;
@@ -370,9 +372,10 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     }
     smax = std::max(smax, sizeof(unsigned) * (size_t)Ng);
     TRY(configure_push_smem(smax));
-    TRY(configure_pair_smem(sizeof(unsigned) * 8 * (size_t)Nc));
+    TRY(configure_pair_smem(pair_smem_bytes(Nc)));
+    TRY(configure_field_smem(3 * sizeof(long long) * (size_t)Ng));
     for (int s = 0; s < NSP; ++s) P.nproc[s] = 0;
-    c->grid_pair = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(ceil_div(tiles_ion, 8), 8ull * c->num_sms));
+    c->grid_pair = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(tiles_ion, 8ull * c->num_sms));
     c->grid_compact = 4 * c->num_sms;
     c->grid_deposit = 4 * c->num_sms;
     // steady initial control state
