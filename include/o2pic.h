@@ -213,6 +213,25 @@ int o2pic_compact_particles(const float* x, const float* vx, const float* vy, co
                             const uint32_t* id, uint64_t n, float* ox, float* ovx, float* ovy, float* ovz,
                             uint32_t* oid, uint64_t* n_out, void* stream);
 
+/* The same compaction for callers that cannot allocate device memory when
+ * they need it: a framework whose caching allocator already holds the free
+ * memory of the device, or a pipeline that cannot accept the synchronization
+ * that cudaFree brings.  No counterpart in the paper: this is a property of
+ * the library, not of the method.  Arguments, results and errors as for
+ * o2pic_compact_particles, except that it calls no allocator: its scratch is
+ * a static device array sized for at most O2PIC_NOALLOC_MAX_PARTICLES
+ * particles (about 96 KB, held on every GPU that loads the library until the
+ * process exits); n beyond that returns INVALID_ARG.  The first call on a
+ * device looks up the array's device address (the current device must be
+ * that device); make that first call before any stream capture.  All calls
+ * on a device share the array, so calls whose GPU work overlaps (e.g. on two
+ * streams at once) race: serialize them.  The call resets what must start at
+ * zero itself and returns once the work on `stream` is done. */
+#define O2PIC_NOALLOC_MAX_PARTICLES (1ull << 25)
+int o2pic_compact_particles_noalloc(const float* x, const float* vx, const float* vy, const float* vz,
+                                    const uint32_t* id, uint64_t n, float* ox, float* ovx, float* ovy, float* ovz,
+                                    uint32_t* oid, uint64_t* n_out, void* stream);
+
 const char* o2pic_strerror(int code);
 
 void o2pic_destroy(o2pic_ctx* ctx);

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("o2pic_philox", _i32, [_vp, _vp, _vp, _u64, _vp]),
     ("o2pic_ln_f32", _i32, [_vp, _vp, _u64, _vp]),
     ("o2pic_compact_particles", _i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("o2pic_compact_particles_noalloc", _i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("o2pic_strerror", ctypes.c_char_p, [_i32]),
     ("o2pic_destroy", None, [_vp]),
     ("o2pic_version", _i32, []),
@@ -303,18 +304,19 @@ def _ptrs(ts):
     return [ctypes.c_void_p(t.data_ptr()) for t in ts]
 
 
-def compact_particles(x, vx, vy, vz, ids, stream=None, out=None):
+def compact_particles(x, vx, vy, vz, ids, stream=None, out=None, noalloc=False):
     """Stable removal of the particles with x = NaN from CUDA tensors; returns
     tensors holding the kept particles in their input order.  `out` = five
-    caller tensors to write into (else new ones)."""
+    caller tensors to write into (else new ones); noalloc=True uses the entry
+    point with static scratch (o2pic_compact_particles_noalloc)."""
     import torch
     n = int(x.numel())
     outs = out if out is not None else [torch.empty(max(n, 1), dtype=t.dtype, device=t.device)
                                         for t in (x, vx, vy, vz, ids)]
     n_out = torch.zeros(1, dtype=torch.int64, device=x.device)
-    _check(lib().o2pic_compact_particles(*_ptrs((x, vx, vy, vz, ids)), n, *_ptrs(outs),
-                                         ctypes.c_void_p(n_out.data_ptr()), _stream_ptr(stream)),
-           "o2pic_compact_particles")
+    f = lib().o2pic_compact_particles_noalloc if noalloc else lib().o2pic_compact_particles
+    _check(f(*_ptrs((x, vx, vy, vz, ids)), n, *_ptrs(outs), ctypes.c_void_p(n_out.data_ptr()), _stream_ptr(stream)),
+           "o2pic_compact_particles" + ("_noalloc" if noalloc else ""))
     m = int(n_out.item())
     return [o[:m] for o in outs]
 
