@@ -540,12 +540,16 @@ template <class R> struct Oracle {
         int i; R w; bool above;
         grid_locate<R>(E, i, w, above);
         if (above) cnt.warn_emax += 1;
+        // null-collision method: the candidate is a null collision unless
+        // u1 nu_max falls below the total rate nu(E); the process is then the
+        // first k with u1 nu_max < sum_{i<=k} nu_i(E) (the last process if
+        // rounding leaves none below it)
         R target = u1 * numax[s];
-        int k = -1;
-        for (int kk = 0; kk < np; ++kk) {
+        if (!(target < cum_at(s, np - 1, i, w))) return true;   // null collision
+        int k = np - 1;
+        for (int kk = 0; kk < np - 1; ++kk) {
             if (target < cum_at(s, kk, i, w)) { k = kk; break; }
         }
-        if (k < 0) return true;                     // null collision
         const Proc& pr = procs[s][k];
         if (E < (R)pr.thr) return true;             // below threshold: null
         cnt.events[s][k] += 1;

@@ -64,27 +64,185 @@ __device__ __forceinline__ void block_scan_smem(long long* a, int n, long long* 
     __syncthreads();
 }
 
+// Births of one step, placed in the order the method defines (source species
+// e then O-, parent order, e before O2+ for an ionization): each warp of a
+// particle kernel staged the births of its slot range [u R, ...) with their
+// count.  The counts are scanned into per-warp offsets in shared memory, and
+// every thread then places single births (found by a binary search over the
+// offsets), so the work spreads over the block however the births cluster.
+__device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP], int d, unsigned long long slot,
+                            unsigned long long id64, float4 b) {
+    const SpeciesBuf& B = P.sp[d];
+    if (slot >= B.cap) { atomicOr(&C->error_flags, ERR_CAPACITY); return; }
+    if (id64 > 0xFFFFFFFFull) atomicOr(&C->error_flags, ERR_ID);
+    const unsigned cb = cur[d];
+    B.x[cb][slot] = b.x;
+    B.vx[cb][slot] = b.y;
+    B.vy[cb][slot] = b.z;
+    B.vz[cb][slot] = b.w;
+    B.id[cb][slot] = (uint32_t)id64;
+    int j; float frac;
+    cell_of(b.x, P.inv_dx, P.Nc, j, frac);
+    const uint32_t r = cic_r(frac);
+    atomicAdd(&P.Qb[d][j], (unsigned long long)(65536u - r));
+    atomicAdd(&P.Qb[d][j + 1], (unsigned long long)r);
+}
+
+// Exclusive block scan of two 32-bit counts packed in 64 bits (FT threads).
+__device__ __forceinline__ unsigned long long block_excl_scan2(unsigned long long v, unsigned long long* ws,
+                                                              unsigned long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long t = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    const unsigned long long excl = (warp == 0 ? 0ull : ws[warp - 1]) + x - v;
+    *total = ws[31];
+    __syncthreads();
+    return excl;
+}
+
+// Offsets of the per-warp counts c1 (and c2) of nu warps into p1[0..nu] (p2).
+__device__ void unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu, unsigned* p1, unsigned* p2,
+                             unsigned long long* ws, unsigned long long* tot) {
+    const int t = threadIdx.x;
+    const unsigned per = (nu + FT - 1) / FT, u0 = t * per, u1 = (u0 + per < nu) ? u0 + per : nu;
+    unsigned long long mine = 0;
+    for (unsigned u = u0; u < u1; ++u) {
+        const unsigned a = c1[u], b = c2 ? c2[u] : 0u;
+        p1[u] = a; p2[u] = b;
+        mine += (unsigned long long)a | ((unsigned long long)b << 32);
+    }
+    unsigned long long all;
+    const unsigned long long ex = block_excl_scan2(mine, ws, &all);
+    unsigned r1 = (unsigned)ex, r2 = (unsigned)(ex >> 32);
+    for (unsigned u = u0; u < u1; ++u) {
+        const unsigned a = p1[u], b = p2[u];
+        p1[u] = r1; p2[u] = r2;
+        r1 += a; r2 += b;
+    }
+    if (t == 0) { p1[nu] = (unsigned)all; p2[nu] = (unsigned)(all >> 32); }
+    *tot = all;
+    __syncthreads();
+}
+
+// The warp that staged birth number b (largest u with p[u] <= b).
+__device__ __forceinline__ unsigned find_unit(const unsigned* p, unsigned nu, unsigned b) {
+    unsigned lo = 0, hi = nu;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (p[mid] <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct CtrlSnap {
+    unsigned long long step, slots[NSP], live[NSP], removed[NSP];
+    unsigned next_id[NSP], cur[NSP], removals;
+};
+
+__device__ void place_births(const Params& P, DevCtrl* C, const CtrlSnap& cs, int pushed_mask, unsigned* p1,
+                             unsigned* p2, unsigned long long* ws, unsigned long long tot[NB]) {
+    const int t = threadIdx.x;
+    for (int k = 0; k < NB; ++k) tot[k] = 0;
+    // electron kernel: ionizations (e + O2+) and attachments (O-)
+    if (P.births_possible[SP_E]) {
+        const unsigned ns = (unsigned)(cs.slots[SP_E] < P.sp[SP_E].cap ? cs.slots[SP_E] : P.sp[SP_E].cap);
+        const unsigned nu = P.push_warps[SP_E], R = warp_range_len(ns, nu);
+        unsigned long long all;
+        unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu, p1, p2, ws, &all);
+        const unsigned n1 = (unsigned)all, n2 = (unsigned)(all >> 32);
+        for (unsigned b = t; b < n1; b += FT) {
+            const unsigned u = find_unit(p1, nu, b);
+            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
+            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + b, (unsigned long long)cs.next_id[SP_E] + b,
+                        P.stage[B_E_FROM_E][sb]);
+            place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + b, (unsigned long long)cs.next_id[SP_OP] + b,
+                        P.stage[B_OP_FROM_E][sb]);
+        }
+        for (unsigned b = t; b < n2; b += FT) {
+            const unsigned u = find_unit(p2, nu, b);
+            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p2[u]);
+            place_birth(P, C, cs.cur, SP_OM, cs.slots[SP_OM] + b, (unsigned long long)cs.next_id[SP_OM] + b,
+                        P.stage[B_OM_FROM_E][sb]);
+        }
+        tot[B_E_FROM_E] = n1;
+        tot[B_OP_FROM_E] = n1;
+        tot[B_OM_FROM_E] = n2;
+        __syncthreads();
+    }
+    // O- kernel (ion steps): detachment electrons, after the electron kernel's
+    if (((pushed_mask >> SP_OM) & 1) && P.births_possible[SP_OM]) {
+        const unsigned ns = (unsigned)(cs.slots[SP_OM] < P.sp[SP_OM].cap ? cs.slots[SP_OM] : P.sp[SP_OM].cap);
+        const unsigned nu = P.push_warps[SP_OM], R = warp_range_len(ns, nu);
+        unsigned long long all;
+        unit_offsets(P.wcount[B_E_FROM_OM], nullptr, nu, p1, p2, ws, &all);
+        const unsigned n = (unsigned)all;
+        const unsigned long long base = tot[B_E_FROM_E];
+        for (unsigned b = t; b < n; b += FT) {
+            const unsigned u = find_unit(p1, nu, b);
+            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
+            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + base + b, (unsigned long long)cs.next_id[SP_E] + base + b,
+                        P.stage[B_E_FROM_OM][sb]);
+        }
+        tot[B_E_FROM_OM] = n;
+    }
+    __threadfence();
+    __syncthreads();
+}
+
 // mode 0: end of a step (pushed_mask = species pushed this step);
 // mode 1: after a load (all species freshly deposited into Qf).
-// Dynamic shared memory: R, S, T as int64 [Ng] each.
+// Dynamic shared memory: S, T as int64 [Ng], then two u32 [max warps + 1].
 __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
     extern __shared__ long long fsm[];
     __shared__ long long ws[32];
+    __shared__ unsigned long long ws2[32];
+    __shared__ CtrlSnap cs;
+    __shared__ long long sh_R0, sh_RN;
     DevCtrl* C = P.ctrl;
     const int N = P.Nc, Ng = P.Ng;
     const int t = threadIdx.x;
-    long long* Rs = fsm;
-    long long* Ss = fsm + Ng;
-    long long* Ts = fsm + 2 * Ng;
+    long long* Ss = fsm;
+    long long* Ts = fsm + Ng;
+    unsigned* p1 = reinterpret_cast<unsigned*>(fsm + 2 * Ng);
+    unsigned* p2 = p1 + (P.max_push_warps + 1);
+
+    // snapshot of the step state, read in parallel
+    if (t < NSP) {
+        cs.slots[t] = C->slots[t]; cs.live[t] = C->live[t]; cs.removed[t] = C->removed[t];
+        cs.next_id[t] = C->next_id[t]; cs.cur[t] = C->cur[t];
+    } else if (t == 32) {
+        cs.step = C->step;
+        cs.removals = C->removals;
+    }
+    __syncthreads();
+    unsigned long long btot[NB];
+    for (int k = 0; k < NB; ++k) btot[k] = 0;
+    if (mode == 0) place_births(P, C, cs, pushed_mask, p1, p2, ws2, btot);
 
     // charge commit, moments, net charge (coalesced, all loads before stores)
     for (int j = t; j < Ng; j += FT) {
         unsigned long long qf[NSP], qo[NSP], qb[NSP], qa[NSP];
 #pragma unroll
         for (int s = 0; s < NSP; ++s) {
-            qf[s] = P.Qf[s][j];
+            qf[s] = __ldcg(&P.Qf[s][j]);
             qo[s] = P.Q[s][j];
-            qb[s] = P.Qb[s][j];
+            qb[s] = __ldcg(&P.Qb[s][j]);
             qa[s] = (mode == 0) ? P.Qacc[s][j] : 0ull;
         }
         long long net = 0;
@@ -98,8 +256,9 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
             if (mode == 0) P.Qacc[s][j] = qa[s] + q;
             net += (s == SP_OP) ? (long long)q : -(long long)q;
         }
-        Rs[j] = net;
-        Ss[j] = (j >= 1) ? net : 0;     // S_m = sum_{k=1..m} R_k
+        Ss[j] = (j >= 1) ? net : 0;     // S_m = sum_{k=1..m} R_k (scanned below)
+        if (j == 0) sh_R0 = net;
+        if (j == N) sh_RN = net;
     }
     __syncthreads();
     block_scan_smem(Ss, Ng, ws);
@@ -108,62 +267,60 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
     __syncthreads();
     block_scan_smem(Ts, Ng, ws);
     const double c = P.c_field;
-    const unsigned long long step = C->step;
+    const unsigned long long step = cs.step;
     // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load), evaluated
     // on the host in FP64 and staged in a ring indexed by the step
     const double V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
     const double D0 = (c * (double)Ts[N] - V0) / (double)N;
+    const long long R0 = sh_R0, RN = sh_RN;
     for (int j = t; j < Ng; j += FT) {
         double E;
-        if (j == 0) E = (-D0 - c * (double)Rs[0]) * P.inv_dx64;
-        else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)Rs[N]) * P.inv_dx64;
+        if (j == 0) E = (-D0 - c * (double)R0) * P.inv_dx64;
+        else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)RN) * P.inv_dx64;
         else E = (c * (double)(Ss[j] + Ss[j - 1]) - 2.0 * D0) * P.inv_2dx64;
         const double phi = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Ts[j]);
         P.Ef[j] = (float)E;
         P.phi[j] = phi;
     }
     if (mode != 0) {
-        if (t == 0) for (int k = 0; k < NKK + NSP; ++k) C->ticket[k] = 0u;
+        if (t < NKK + NSP) C->ticket[t] = 0u;
         return;
     }
 
     // (17) removals: mark both ions of every reacted pair dead
-    const unsigned nrem = (C->removals < P.max_removals) ? C->removals : P.max_removals;
-    const unsigned cm = C->cur[SP_OM], cp = C->cur[SP_OP];
+    const unsigned nrem = (cs.removals < P.max_removals) ? cs.removals : P.max_removals;
     for (unsigned r = t; r < nrem; r += FT) {
-        P.sp[SP_OM].x[cm][P.removal[2 * r]] = dead_marker();
-        P.sp[SP_OP].x[cp][P.removal[2 * r + 1]] = dead_marker();
+        P.sp[SP_OM].x[cs.cur[SP_OM]][P.removal[2 * r]] = dead_marker();
+        P.sp[SP_OP].x[cs.cur[SP_OP]][P.removal[2 * r + 1]] = dead_marker();
     }
-    __syncthreads();
-    if (t == 0) {
-        const unsigned long long bE = C->births[B_E_FROM_E] + C->births[B_E_FROM_OM];
-        const unsigned long long bOP = C->births[B_OP_FROM_E];
-        const unsigned long long bOM = C->births[B_OM_FROM_E];
-        const unsigned long long b[NSP] = {bE, bOM, bOP};
-        for (int s = 0; s < NSP; ++s) {
-            const unsigned long long rem = C->removed[s] + ((s != SP_E) ? (unsigned long long)nrem : 0ull);
-            unsigned long long ns = C->slots[s] + b[s];
-            unsigned long long nl = C->live[s] + b[s] - rem;
-            if (ns > P.sp[s].cap) {   // births beyond the capacity were dropped
-                C->error_flags |= ERR_CAPACITY;
-                nl -= (ns - P.sp[s].cap) < nl ? (ns - P.sp[s].cap) : nl;
-                ns = P.sp[s].cap;
-            }
-            C->slots[s] = ns;
-            C->live[s] = nl;
-            const unsigned long long nid = (unsigned long long)C->next_id[s] + b[s];
-            if (nid > 0xFFFFFFFFull) { C->error_flags |= ERR_ID; C->cnt.id_overflow += 1; }
-            C->next_id[s] = (unsigned)nid;
-            C->cnt.born[s] += b[s];
-            C->removed[s] = 0ull;
+    // commit of the step: one thread per species, then the step counters
+    if (t < NSP) {
+        const int s = t;
+        const unsigned long long bs = (s == SP_E) ? btot[B_E_FROM_E] + btot[B_E_FROM_OM]
+                                                  : (s == SP_OP ? btot[B_OP_FROM_E] : btot[B_OM_FROM_E]);
+        const unsigned long long rem = cs.removed[s] + ((s != SP_E) ? (unsigned long long)nrem : 0ull);
+        unsigned long long ns = cs.slots[s] + bs;
+        unsigned long long nl = cs.live[s] + bs - rem;
+        if (ns > P.sp[s].cap) {   // births beyond the capacity were dropped
+            atomicOr(&C->error_flags, ERR_CAPACITY);
+            nl -= (ns - P.sp[s].cap) < nl ? (ns - P.sp[s].cap) : nl;
+            ns = P.sp[s].cap;
         }
-        C->cnt.neutralized += nrem;
-        for (int k = 0; k < NB; ++k) C->births[k] = 0ull;
-        for (int k = 0; k < NKK + NSP; ++k) C->ticket[k] = 0u;
+        const unsigned long long nid = (unsigned long long)cs.next_id[s] + bs;
+        if (nid > 0xFFFFFFFFull) { atomicOr(&C->error_flags, ERR_ID); atomicAdd(&C->cnt.id_overflow, 1ull); }
+        C->slots[s] = ns;
+        C->live[s] = nl;
+        C->next_id[s] = (unsigned)nid;
+        C->removed[s] = 0ull;
+        if (bs) atomicAdd(&C->cnt.born[s], bs);
+    } else if (t == 32) {
+        if (nrem) atomicAdd(&C->cnt.neutralized, (unsigned long long)nrem);
         C->removals = 0u;
-        C->acc_steps += 1;
+        atomicAdd(&C->acc_steps, 1ull);
         C->step = step + 1;
-        C->epoch += 1;
+        atomicAdd(&C->epoch, 1ull);
+    } else if (t >= 64 && t < 64 + NKK + NSP) {
+        C->ticket[t - 64] = 0u;
     }
 }
 
@@ -314,8 +471,12 @@ __global__ void k_ln(const float* x, float* out, unsigned long long n) {
 
 }  // namespace
 
+size_t field_smem_bytes(const Params& P) {
+    return 2 * sizeof(long long) * (size_t)P.Ng + 2 * sizeof(unsigned) * ((size_t)P.max_push_warps + 1);
+}
+
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s) {
-    k_field<<<1, FT, 3 * sizeof(long long) * (size_t)P.Ng, s>>>(P, mode, pushed_mask);
+    k_field<<<1, FT, field_smem_bytes(P), s>>>(P, mode, pushed_mask);
 }
 
 cudaError_t configure_field_smem(size_t bytes) {

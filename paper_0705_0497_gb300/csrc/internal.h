@@ -22,7 +22,8 @@ constexpr float GRID_EMAX = 4096.0f;                             // 2^12
 constexpr int BLOCK = 256;              // threads of the particle kernels
 constexpr int ITEMS = 4;                // particles per thread per chunk (one float4)
 constexpr int CHUNK = BLOCK * ITEMS;    // 1024
-constexpr int TILE = 8192;              // particles per tile (look-back unit)
+constexpr int TILE = 8192;              // slots per tile (compaction, neutralization histograms)
+constexpr int WTILE = 2048;             // slots per warp work unit of the particle kernels
 constexpr int CHUNKS_PER_TILE = TILE / CHUNK;
 constexpr int FLUSH_TILES = 7;          // tiles between deposit flushes (7*8192*2^16 < 2^32)
 constexpr int MAX_TRIES = 32;           // rejection-loop cap
@@ -119,8 +120,12 @@ struct Params {
     unsigned long long* lb_flag[NKK];
     unsigned long long* lb_val[NKK];
     unsigned int max_tiles;
-    // births staging, [tile * TILE + rank] per BirthSlot
+    // births staging, [wtile * WTILE + rank] per BirthSlot, and the number
+    // staged by each warp work unit (B_OP_FROM_E shares B_E_FROM_E's counts)
     float4* stage[NB];
+    unsigned int* wcount[NB];
+    unsigned int push_warps[NSP];  // warps of each particle kernel launch (units of wcount)
+    unsigned int max_push_warps;   // bound on push_warps (shared memory of the field kernel)
     // (17): per-tile per-cell counts of live ions [2][max_tiles][Nc], per-cell info
     unsigned int* hist[2];       // 0: O-, 1: O2+
     unsigned int* cellinfo;      // [Nc][4]: n-, n+, shift r, reserved
@@ -134,9 +139,17 @@ __host__ __device__ inline unsigned long long ceil_div(unsigned long long a, uns
     return (a + b - 1) / b;
 }
 
+// The particle kernels give warp w of W warps the contiguous slot range
+// [w R, min((w+1) R, n)) with R = this length (128-aligned).
+__host__ __device__ inline unsigned warp_range_len(unsigned n, unsigned W) {
+    const unsigned per = (n + W - 1) / W;
+    return ((per + 127u) / 128u) * 128u;
+}
+
 // ---------------------------------------------------------------- launchers
 // (defined in the kernel translation units, called by the runtime)
 void launch_push(int species, const Params& P, int grid, cudaStream_t s);
+void launch_pair_hist(const Params& P, int grid, cudaStream_t s);
 void launch_pair_scan(const Params& P, cudaStream_t s);
 void launch_pair(const Params& P, int grid, cudaStream_t s);
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s);
@@ -151,6 +164,7 @@ void launch_gather(int species, const Params& P, int grid, unsigned long long ep
 cudaError_t configure_push_smem(size_t max_bytes);
 cudaError_t configure_field_smem(size_t bytes);
 size_t pair_smem_bytes(int Nc);
+size_t field_smem_bytes(const Params& P);
 int push_occupancy(int species, const Params& P, int* blocks_per_sm);
 size_t push_smem_bytes(int species, const Params& P);
 

@@ -7,8 +7,8 @@
 // tie), i < m, is paired with member (i + r_c) mod M of the longer one.  A
 // pair reacts with probability P = M w sigma_n(E_rel) g dt_ion / (A dx).
 //
-// GPU form: the push kernels of both ion species leave, per 8192-slot tile,
-// the number of surviving ions per cell.  k_pair_scan turns these into
+// GPU form: k_pair_hist counts, per 8192-slot tile, the surviving ions per
+// cell of both species.  k_pair_scan turns these into
 // per-cell exclusive prefixes over tiles (so the rank of an ion in its cell
 // list is prefix + its rank inside the tile) and draws the shifts.  k_pair
 // gives each block one O- tile, split among its warps; with per-warp cell
@@ -24,6 +24,42 @@ namespace o2 {
 namespace {
 
 constexpr int SCAN_T = 1024;   // 32 cells x 32 tile groups
+constexpr int HIST_T = 512;
+
+// Per 8192-slot tile of each ion species, the number of live ions per cell
+// (post-push positions): hist[sp][tile][cell].  Blocks take tiles of O-
+// first, then of O2+.
+__global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P) {
+    extern __shared__ unsigned hsm[];
+    DevCtrl* C = P.ctrl;
+    const int Nc = P.Nc;
+    const unsigned long long nsm = C->slots[SP_OM], nsp = C->slots[SP_OP];
+    const unsigned ntm = (unsigned)ceil_div(nsm, TILE), ntp = (unsigned)ceil_div(nsp, TILE);
+    for (unsigned g = blockIdx.x; g < ntm + ntp; g += gridDim.x) {
+        const int sp = (g < ntm) ? 0 : 1;
+        const unsigned tile = (g < ntm) ? g : g - ntm;
+        const int S = sp == 0 ? SP_OM : SP_OP;
+        const unsigned long long n = sp == 0 ? nsm : nsp;
+        const float* X = P.sp[S].x[C->cur[S]];
+        for (int c = threadIdx.x; c < Nc; c += HIST_T) hsm[c] = 0u;
+        __syncthreads();
+        const unsigned long long base = (unsigned long long)tile * TILE;
+        const unsigned long long end = (base + TILE < n) ? base + TILE : n;
+#pragma unroll 4
+        for (unsigned long long i = base + threadIdx.x; i < end; i += HIST_T) {
+            const float x = X[i];
+            if (!is_dead(x)) {
+                int c; float fr;
+                cell_of(x, P.inv_dx, Nc, c, fr);
+                atomicAdd(&hsm[c], 1u);
+            }
+        }
+        __syncthreads();
+        unsigned* H = P.hist[sp] + (size_t)tile * Nc;
+        for (int c = threadIdx.x; c < Nc; c += HIST_T) H[c] = hsm[c];
+        __syncthreads();
+    }
+}
 
 __global__ void __launch_bounds__(SCAN_T) k_pair_scan(Params P) {
     __shared__ unsigned part[32][33];
@@ -261,6 +297,10 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32) k_pair(Params P, int W) {
 }
 
 }  // namespace
+
+void launch_pair_hist(const Params& P, int grid, cudaStream_t s) {
+    k_pair_hist<<<grid, HIST_T, sizeof(unsigned) * (size_t)P.Nc, s>>>(P);
+}
 
 void launch_pair_scan(const Params& P, cudaStream_t s) {
     k_pair_scan<<<(P.Nc + 31) / 32, SCAN_T, 0, s>>>(P);

@@ -7,19 +7,32 @@
 //   * SoA FP32 arrays x, vx, vy, vz + u32 id, updated IN PLACE: a particle
 //     keeps its slot, removed particles are marked (x = NaN) and dropped by a
 //     periodic stable compaction, births are appended after the last slot.
-//     The common path reads x, vx, vy, vz, id (20 B) and writes x, vx (8 B).
-//   * a persistent grid; 8192-particle tiles claimed in increasing order by
-//     an atomic ticket; each thread owns 4 consecutive particles per 1024-
-//     particle chunk (one 16-byte vector per array);
-//   * gather field, rate tables and a fixed-point deposit histogram live in
-//     shared memory; the histogram is flushed with 64-bit atomics;
+//     The common path reads x, vx, id (12 B) and writes x, vx (8 B); vy, vz
+//     are read only for collision candidates.
+//   * a persistent grid; each warp owns one contiguous, 128-aligned slot range
+//     and walks it in rounds of 128 (lane l takes slots l, l+32, l+64, l+96:
+//     every load and store is one coalesced 128-byte line per array).  No
+//     block-wide barrier between the set-up and the final flush.
+//   * the gather field and the deposit live in shared memory; the deposit is
+//     one 64-bit atomic per particle holding (count, sum of CIC weights) per
+//     cell, turned into node charges when the block flushes;
 //   * one Philox block per particle per step decides "collision candidate";
-//     candidates go to a shared-memory queue in slot order and are processed
-//     256 at a time by the whole block (no warp-divergent rare branch);
-//   * births are staged per tile and placed after the tile's decoupled
-//     look-back (prefix of earlier tiles' births), which keeps the order the
-//     method defines (parent order) without a second pass.
+//     candidates are queued per warp in slot order and filtered 32 at a time
+//     (electrons: energy against the total rate); only real collisions reach
+//     the out-of-line kinematics, again 32 at a time;
+//   * births are ranked with warp ballots and staged at the warp's range;
+//     the end-of-step kernel places them in parent order.
 #include "common.cuh"
+
+// Launch shape of the particle kernels (tuned per build; see the design notes):
+// minimum resident blocks per SM (caps registers) and unrolling of the four
+// particles a lane handles per round.
+#ifndef O2PIC_PUSH_MIN_BLOCKS
+#define O2PIC_PUSH_MIN_BLOCKS 2
+#endif
+#ifndef O2PIC_PUSH_UNROLL
+#define O2PIC_PUSH_UNROLL 4
+#endif
 
 namespace o2 {
 
@@ -30,12 +43,13 @@ template <> struct SpeciesTraits<SP_E> { static constexpr uint32_t tag = TAG_E; 
 template <> struct SpeciesTraits<SP_OM> { static constexpr uint32_t tag = TAG_OM; static constexpr int kk = KK_PUSH_OM; };
 template <> struct SpeciesTraits<SP_OP> { static constexpr uint32_t tag = TAG_OP; static constexpr int kk = KK_PUSH_OP; };
 
+constexpr int WARPS = BLOCK / 32;           // 8
+constexpr int ROUND = 128;                  // slots per warp round (4 per lane)
+constexpr int QW = 32 - 1 + ROUND + 1;      // per-warp candidate queue (160 entries)
+constexpr int Q2 = 64;                      // per-warp real-collision queue (31 + 32 max)
+constexpr int PUSH_UNROLL = O2PIC_PUSH_UNROLL;
+
 struct PushShared {
-    unsigned ws[32];
-    unsigned tile;
-    unsigned qn;
-    unsigned long long excl;
-    int ok;
     unsigned events[MAXPROC];
     unsigned absorbed[2];
     unsigned removed;
@@ -45,20 +59,23 @@ struct PushShared {
 };
 
 struct SmemLayout {
-    size_t ef, hist, chist, cum, qslot, qw, total;
+    size_t ef, hist, qslot, qw, qslot2, qw2, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int Ng, int Nc, int nproc, bool ion) {
+// shared memory: counters, gather field, deposit (count, rsum) per cell, and
+// per warp a candidate queue and a real-collision queue
+__host__ __device__ inline SmemLayout smem_layout(int Ng, int nproc) {
+    (void)nproc;
     SmemLayout L;
     size_t o = align16(sizeof(PushShared));
     L.ef = o; o = align16(o + sizeof(float) * Ng);
-    L.hist = o; o = align16(o + sizeof(unsigned) * Ng);
-    L.chist = o; o = align16(o + (ion ? sizeof(unsigned) * Nc : 0));
-    L.cum = o; o = align16(o + sizeof(float) * NGRID * (nproc > 0 ? nproc : 1));
-    L.qw = o; o = align16(o + sizeof(uint4) * QCAP);
-    L.qslot = o; o = align16(o + sizeof(unsigned) * QCAP);
+    L.hist = o; o = align16(o + sizeof(unsigned long long) * Ng);
+    L.qw = o; o = align16(o + sizeof(uint4) * WARPS * QW);
+    L.qslot = o; o = align16(o + sizeof(unsigned) * WARPS * QW);
+    L.qw2 = o; o = align16(o + sizeof(uint4) * WARPS * Q2);
+    L.qslot2 = o; o = align16(o + sizeof(unsigned) * WARPS * Q2);
     L.total = o;
     return L;
 }
@@ -67,7 +84,7 @@ __host__ __device__ inline SmemLayout smem_layout(int Ng, int Nc, int nproc, boo
 // order of the oracle.  Returns the event index (-1 = null collision).
 // bkind: 0 none, 1 ionization (two births), 2 attachment / detachment (one).
 template <int S>
-__device__ __forceinline__ int collide(const Params& P, const float* cum, int np, unsigned long long step,
+__device__ __noinline__ int collide(const Params& P, const float* cum, int np, unsigned long long step,
                                        uint32_t id, uint4 w0, float x, float& vx, float& vy, float& vz,
                                        bool& alive, int& bkind, float4& b1, float4& b2,
                                        unsigned& warn_tries, unsigned& warn_emax) {
@@ -86,12 +103,15 @@ __device__ __forceinline__ int collide(const Params& P, const float* cum, int np
     int i; float w; bool above;
     grid_locate(E, i, w, above);
     if (above) ++warn_emax;
+    // null collision unless u1 nu_max falls below the total rate; then the
+    // first process whose cumulative rate exceeds it (the last one if
+    // rounding leaves none)
     const float target = u1 * P.numax[S];
-    int k = -1;
-    for (int kk = 0; kk < np; ++kk) {
+    if (!(target < grid_interp(cum, np, np - 1, i, w))) return -1;
+    int k = np - 1;
+    for (int kk = 0; kk < np - 1; ++kk) {
         if (target < grid_interp(cum, np, kk, i, w)) { k = kk; break; }
     }
-    if (k < 0) return -1;
     const float thr = P.thr[S][k];
     if (E < thr) return -1;
     const int kind = P.kind[S][k];
@@ -162,12 +182,12 @@ __device__ __forceinline__ void deposit_add(unsigned* hist, float x, float inv_d
     atomicAdd(&hist[j + 1], r);
 }
 
-__device__ __forceinline__ void deposit_sub(unsigned* hist, float x, float inv_dx, int Nc) {
+__device__ __forceinline__ void deposit_sub_global(unsigned long long* Q, float x, float inv_dx, int Nc) {
     int j; float frac;
     cell_of(x, inv_dx, Nc, j, frac);
     const uint32_t r = cic_r(frac);
-    atomicSub(&hist[j], 65536u - r);
-    atomicSub(&hist[j + 1], r);
+    atomicAdd(&Q[j], 0ull - (unsigned long long)(65536u - r));
+    atomicAdd(&Q[j + 1], 0ull - (unsigned long long)r);
 }
 
 // deposit of a birth straight into the global accumulator (rare)
@@ -189,297 +209,229 @@ __device__ __forceinline__ void flush_hist(unsigned* hist, unsigned long long* Q
     }
 }
 
-// Write one birth into species d at slot `slot` with id `id`.
-__device__ __forceinline__ void place_birth(const Params& P, int d, unsigned long long slot, unsigned long long id64,
-                                            float4 b, unsigned long long* err) {
-    const SpeciesBuf& B = P.sp[d];
-    if (slot >= B.cap) { atomicOr(err, ERR_CAPACITY); return; }
-    if (id64 > 0xFFFFFFFFull) { atomicOr(err, ERR_ID); }
-    const unsigned cb = P.ctrl->cur[d];
-    B.x[cb][slot] = b.x;
-    B.vx[cb][slot] = b.y;
-    B.vy[cb][slot] = b.z;
-    B.vz[cb][slot] = b.w;
-    B.id[cb][slot] = (uint32_t)id64;
-    deposit_global(P.Qb[d], b.x, P.inv_dx, P.Nc);
+// Stage-A filter of an electron candidate: is it a real collision?  The
+// same arithmetic as the start of collide(): energy of the particle, the
+// total rate on the table grid and the comparison with u1 nu_max.
+__device__ __forceinline__ bool electron_is_real(const Params& P, const float* __restrict__ cum, int np, uint4 w0,
+                                                 float vx, float vy, float vz) {
+    const float u1 = uniform(w0.y);
+    const float E = P.kappa[SP_E] * dot3(vx, vy, vz, vx, vy, vz);
+    int i; float w; bool above;
+    grid_locate(E, i, w, above);
+    return (u1 * P.numax[SP_E]) < grid_interp(cum, np, np - 1, i, w);
 }
 
 template <int S>
-__global__ void __launch_bounds__(BLOCK) k_push(Params P) {
+__global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr bool ION = (S != SP_E);
-    constexpr int KKIND = SpeciesTraits<S>::kk;
     const int np = P.nproc[S];
-    const SmemLayout L = smem_layout(P.Ng, P.Nc, np, ION);
+    const SmemLayout L = smem_layout(P.Ng, np);
     PushShared& sh = *reinterpret_cast<PushShared*>(smem);
     float* Es = reinterpret_cast<float*>(smem + L.ef);
-    unsigned* hist = reinterpret_cast<unsigned*>(smem + L.hist);
-    unsigned* chist = reinterpret_cast<unsigned*>(smem + L.chist);
-    float* cum = reinterpret_cast<float*>(smem + L.cum);
-    uint4* qw = reinterpret_cast<uint4*>(smem + L.qw);
-    unsigned* qslot = reinterpret_cast<unsigned*>(smem + L.qslot);
-    const int tid = threadIdx.x;
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(smem + L.hist);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint4* q1w = reinterpret_cast<uint4*>(smem + L.qw) + warp * QW;
+    unsigned* q1s = reinterpret_cast<unsigned*>(smem + L.qslot) + warp * QW;
+    uint4* q2w = reinterpret_cast<uint4*>(smem + L.qw2) + warp * Q2;
+    unsigned* q2s = reinterpret_cast<unsigned*>(smem + L.qslot2) + warp * Q2;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const float* __restrict__ cum = P.cum[S];
 
     DevCtrl* C = P.ctrl;
     const unsigned long long step = C->step;
-    const unsigned long long epoch = C->epoch;
     const unsigned cb = C->cur[S];
-    const unsigned long long nslots = (C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap;
-    const unsigned ntiles = (unsigned)ceil_div(nslots, TILE);
+    const unsigned nslots = (unsigned)((C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap);
     float* __restrict__ X = P.sp[S].x[cb];
     float* __restrict__ VX = P.sp[S].vx[cb];
-    float* __restrict__ VY = P.sp[S].vy[cb];
-    float* __restrict__ VZ = P.sp[S].vz[cb];
+    const float* __restrict__ VY = P.sp[S].vy[cb];
+    const float* __restrict__ VZ = P.sp[S].vz[cb];
     const uint32_t* __restrict__ ID = P.sp[S].id[cb];
-    const bool track_cells = ION && P.have_neutral;
     const float qmdt = P.qmdt[S], dts = P.dt_s[S], inv_dx = P.inv_dx, Lf = P.Lf, pmax = P.pmax[S];
     const int Nc = P.Nc, Ng = P.Ng;
     const uint32_t seed = P.seed, tag = SpeciesTraits<S>::tag;
+    const uint32_t step_lo = (uint32_t)step, step_hi = (uint32_t)(step >> 32);
+    const bool births = P.births_possible[S] != 0;
+    unsigned* cnt1 = (S == SP_E) ? P.wcount[B_E_FROM_E] : nullptr;
+    unsigned* cnt2 = (S == SP_E) ? P.wcount[B_OM_FROM_E] : (S == SP_OM ? P.wcount[B_E_FROM_OM] : nullptr);
 
-    for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0u; }
-    for (int i = tid; i < NGRID * np; i += BLOCK) cum[i] = P.cum[S][i];
+    for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0ull; }
     if (tid < MAXPROC) sh.events[tid] = 0u;
     if (tid == 0) {
         sh.absorbed[0] = sh.absorbed[1] = 0u;
         sh.removed = 0u; sh.psteps = 0u; sh.warn_emax = 0u; sh.warn_tries = 0u; sh.nonfinite = 0u;
     }
-    // birth destinations (slots and ids already committed before this step)
-    unsigned long long dst_slot0 = 0, dst_id0 = 0, dst2_slot0 = 0, dst2_id0 = 0;
-    if (S == SP_E) {
-        dst_slot0 = C->slots[SP_E];             // e from ionization
-        dst_id0 = C->next_id[SP_E];
-        dst2_slot0 = C->slots[SP_OM];           // O- from attachment
-        dst2_id0 = C->next_id[SP_OM];
-    } else if (S == SP_OM) {
-        const unsigned long long before = C->births[B_E_FROM_E];
-        dst_slot0 = C->slots[SP_E] + before;    // e from detachment, after the e-kernel's births
-        dst_id0 = (unsigned long long)C->next_id[SP_E] + before;
-    }
-    const unsigned long long op_slot0 = C->slots[SP_OP];
-    const unsigned long long op_id0 = C->next_id[SP_OP];
     __syncthreads();
 
-    unsigned tiles_since_flush = 0;
-    for (;;) {
-        if (tid == 0) sh.tile = atomicAdd(&C->ticket[KKIND], 1u);
-        __syncthreads();
-        const unsigned tile = sh.tile;
-        __syncthreads();
-        if (tile >= ntiles) break;
+    // this warp's contiguous slot range
+    const unsigned W = gridDim.x * WARPS;
+    const unsigned gw = blockIdx.x * WARPS + warp;
+    const unsigned R = warp_range_len(nslots, W);
+    const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
+    const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
 
-        const unsigned long long base = (unsigned long long)tile * TILE;
-        const unsigned long long end = (base + TILE < nslots) ? base + TILE : nslots;
-        if (track_cells) for (int c = tid; c < Nc; c += BLOCK) chist[c] = 0u;
-        unsigned qn = 0;            // uniform across the block
-        unsigned nb1 = 0, nb2 = 0;  // births staged in this tile (uniform)
-        if (tid == 0) sh.qn = 0;
-        __syncthreads();
+    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nremoved = 0, nnf = 0, wtries = 0, wemax = 0;
+    unsigned q1n = 0, q2n = 0, nb1 = 0, nb2 = 0;   // warp-uniform
 
-        // -------- process a batch of queued candidates (entries [0, n))
-        auto run_batch = [&](unsigned n) {
-            bool has = (unsigned)tid < n;
-            int bkind = 0;
-            float4 b1 = make_float4(0, 0, 0, 0), b2 = b1;
-            if (has) {
-                const unsigned slot = qslot[tid];
-                const uint4 w0 = qw[tid];
-                const float x = X[slot];
-                float vx = VX[slot], vy = VY[slot], vz = VZ[slot];
-                const uint32_t id = ID[slot];
-                bool alive;
-                unsigned wt = 0, we = 0;
-                const int k = collide<S>(P, cum, np, step, id, w0, x, vx, vy, vz, alive, bkind, b1, b2, wt, we);
-                if (wt) atomicAdd(&sh.warn_tries, wt);
-                if (we) atomicAdd(&sh.warn_emax, we);
-                if (k >= 0) {
-                    atomicAdd(&sh.events[k], 1u);
-                    if (alive) {
-                        VX[slot] = vx; VY[slot] = vy; VZ[slot] = vz;
-                    } else {
-                        X[slot] = dead_marker();
-                        deposit_sub(hist, x, inv_dx, Nc);
-                        if (track_cells) { int j; float fr; cell_of(x, inv_dx, Nc, j, fr); atomicSub(&chist[j], 1u); }
-                        atomicAdd(&sh.removed, 1u);
-                    }
+    // stage B: kinematics of up to 32 real collisions (q2), one per lane
+    auto run_real = [&](unsigned n) {
+        int bkind = 0;
+        float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
+        if ((unsigned)lane < n) {
+            const unsigned slot = q2s[lane];
+            const uint4 w0 = q2w[lane];
+            const float x = X[slot];
+            float vx = VX[slot], vy = VY[slot], vz = VZ[slot];
+            const uint32_t id = ID[slot];
+            bool alive;
+            const int k = collide<S>(P, cum, np, step, id, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
+            if (k >= 0) {
+                atomicAdd(&sh.events[k], 1u);
+                if (alive) {
+                    VX[slot] = vx; P.sp[S].vy[cb][slot] = vy; P.sp[S].vz[cb][slot] = vz;
+                } else {
+                    X[slot] = dead_marker();
+                    deposit_sub_global(P.Qf[S], x, inv_dx, Nc);   // its deposit may be flushed already
+                    ++nremoved;
                 }
             }
-            if (P.births_possible[S]) {
-                // ranks of this batch's births (parent order), then stage them
-                const unsigned f1 = (bkind == 1) ? 1u : 0u;
-                const unsigned f2 = (bkind == 2) ? 1u : 0u;
-                unsigned t1, t2;
-                const unsigned packed = block_excl_scan<BLOCK>(f1 | (f2 << 16), sh.ws, &t1);
-                t2 = t1 >> 16; t1 &= 0xFFFFu;
-                const unsigned r1 = packed & 0xFFFFu, r2 = packed >> 16;
-                const unsigned long long sbase = (unsigned long long)tile * TILE;
-                if (S == SP_E) {
-                    if (f1) {
-                        P.stage[B_E_FROM_E][sbase + nb1 + r1] = b1;
-                        P.stage[B_OP_FROM_E][sbase + nb1 + r1] = b2;
-                    }
-                    if (f2) P.stage[B_OM_FROM_E][sbase + nb2 + r2] = b1;
-                } else if (S == SP_OM) {
-                    if (f2) P.stage[B_E_FROM_OM][sbase + nb2 + r2] = b1;
+        }
+        if (births) {
+            const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1);
+            const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2);
+            if (S == SP_E) {
+                if (bkind == 1) {
+                    const unsigned r = nb1 + __popc(m1 & lt_mask);
+                    P.stage[B_E_FROM_E][r0 + r] = b1;
+                    P.stage[B_OP_FROM_E][r0 + r] = b2;
+                } else if (bkind == 2) {
+                    P.stage[B_OM_FROM_E][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
                 }
-                nb1 += t1; nb2 += t2;
+            } else if (S == SP_OM) {
+                if (bkind == 2) P.stage[B_E_FROM_OM][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
             }
-            __syncthreads();
-        };
+            nb1 += __popc(m1);
+            nb2 += __popc(m2);
+        }
+        __syncwarp();
+    };
+    auto push_real = [&](bool real, unsigned slot, uint4 w0) {
+        const unsigned m = __ballot_sync(0xffffffffu, real);
+        if (real) {
+            const unsigned q = q2n + __popc(m & lt_mask);
+            q2s[q] = slot; q2w[q] = w0;
+        }
+        q2n += __popc(m);
+        __syncwarp();
+        if (q2n >= 32u) {
+            run_real(32u);
+            const unsigned rest = q2n - 32u;     // < 32: lane q moves entry 32 + q
+            if ((unsigned)lane < rest) { const unsigned s0 = q2s[32 + lane]; const uint4 w1 = q2w[32 + lane]; q2s[lane] = s0; q2w[lane] = w1; }
+            q2n = rest;
+            __syncwarp();
+        }
+    };
+    // stage A: up to 32 candidates (q1), one per lane
+    auto run_cand = [&](unsigned n) {
+        bool real = false;
+        unsigned slot = 0;
+        uint4 w0 = make_uint4(0u, 0u, 0u, 0u);
+        if ((unsigned)lane < n) {
+            slot = q1s[lane];
+            w0 = q1w[lane];
+            if (S == SP_E) real = electron_is_real(P, cum, np, w0, VX[slot], VY[slot], VZ[slot]);
+            else real = true;    // ion candidates are rare: straight to stage B
+        }
+        push_real(real, slot, w0);
+    };
 
-        for (int c = 0; c < CHUNKS_PER_TILE; ++c) {
-            const unsigned long long cb0 = base + (unsigned long long)c * CHUNK;
-            if (cb0 >= end) break;
-            const unsigned long long i0 = cb0 + 4ull * tid;
-            float x[4], vx[4], vy[4], vz[4];
-            uint32_t id[4];
-            const bool full = (i0 + 3 < end);
-            if (full) {
-                const float4 a = *reinterpret_cast<const float4*>(X + i0);
-                const float4 b = *reinterpret_cast<const float4*>(VX + i0);
-                const float4 cc = *reinterpret_cast<const float4*>(VY + i0);
-                const float4 d = *reinterpret_cast<const float4*>(VZ + i0);
-                const uint4 e = *reinterpret_cast<const uint4*>(ID + i0);
-                x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-                vx[0] = b.x; vx[1] = b.y; vx[2] = b.z; vx[3] = b.w;
-                vy[0] = cc.x; vy[1] = cc.y; vy[2] = cc.z; vy[3] = cc.w;
-                vz[0] = d.x; vz[1] = d.y; vz[2] = d.z; vz[3] = d.w;
-                id[0] = e.x; id[1] = e.y; id[2] = e.z; id[3] = e.w;
-            } else {
+    for (unsigned g0 = r0; g0 < r1; g0 += ROUND) {
+        const bool full = g0 + ROUND <= r1;
+        // all loads of the round first (independent, in flight together)
+        float xs[4], vxs[4];
+        uint32_t ids[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (i0 + k < end) {
-                        x[k] = X[i0 + k]; vx[k] = VX[i0 + k]; vy[k] = VY[i0 + k]; vz[k] = VZ[i0 + k]; id[k] = ID[i0 + k];
-                    } else {
-                        x[k] = dead_marker(); vx[k] = vy[k] = vz[k] = 0.0f; id[k] = 0u;
-                    }
-                }
-            }
-            unsigned cand = 0u;
-            uint4 wv[4];
-            unsigned nabs0 = 0, nabs1 = 0, nps = 0, nnf = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                wv[k] = make_uint4(0, 0, 0, 0);
-                if (is_dead(x[k])) continue;
+        for (int k = 0; k < 4; ++k) {
+            const unsigned i = g0 + 32u * k + lane;
+            const bool inr = full || i < r1;
+            xs[k] = inr ? X[i] : dead_marker();
+            vxs[k] = inr ? VX[i] : 0.0f;
+            ids[k] = inr ? ID[i] : 0u;
+        }
+#pragma unroll PUSH_UNROLL
+        for (int k = 0; k < 4; ++k) {
+            const unsigned i = g0 + 32u * k + lane;
+            float x = xs[k];
+            bool cand = false;
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (!is_dead(x)) {
+                float vx = vxs[k];
                 int j; float frac;
-                cell_of(x[k], inv_dx, Nc, j, frac);
+                cell_of(x, inv_dx, Nc, j, frac);
                 const float Ep = fmaf(frac, Es[j + 1] - Es[j], Es[j]);
-                vx[k] = fmaf(qmdt, Ep, vx[k]);
-                x[k] = fmaf(vx[k], dts, x[k]);
-                ++nps;
-                if (x[k] < 0.0f) { ++nabs0; x[k] = dead_marker(); continue; }
-                if (x[k] >= Lf) { ++nabs1; x[k] = dead_marker(); continue; }
-                if (!(x[k] >= 0.0f) || !isfinite(vx[k])) { ++nnf; x[k] = dead_marker(); continue; }
-                int j2; float f2;
-                cell_of(x[k], inv_dx, Nc, j2, f2);
-                const uint32_t r = cic_r(f2);
-                atomicAdd(&hist[j2], 65536u - r);
-                atomicAdd(&hist[j2 + 1], r);
-                if (track_cells) atomicAdd(&chist[j2], 1u);
-                if (np > 0) {
-                    const uint4 w = philox4x32_10(make_uint4((uint32_t)step, tag, 0u, (uint32_t)(step >> 32)),
-                                                  make_uint2(id[k], seed));
-                    if (uniform(w.x) < pmax) { cand |= 1u << k; wv[k] = w; }
+                vx = fmaf(qmdt, Ep, vx);
+                x = fmaf(vx, dts, x);
+                ++psteps;
+                if (x < 0.0f) { ++nabs0; ++nremoved; x = dead_marker(); }
+                else if (x >= Lf) { ++nabs1; ++nremoved; x = dead_marker(); }
+                else if (!(x >= 0.0f) || !isfinite(vx)) { ++nnf; ++nremoved; x = dead_marker(); }
+                else {
+                    // CIC deposit as (count, sum of r) per cell: node c gets
+                    // 2^16 count_c - rsum_c, node c+1 gets rsum_c
+                    int j2; float f2;
+                    cell_of(x, inv_dx, Nc, j2, f2);
+                    atomicAdd(&hist[j2], (1ull << 40) + (unsigned long long)cic_r(f2));
+                    if (np > 0) {
+                        w = philox4x32_10(make_uint4(step_lo, tag, 0u, step_hi), make_uint2(ids[k], seed));
+                        cand = uniform(w.x) < pmax;
+                    }
                 }
+                X[i] = x;
+                VX[i] = vx;
             }
-            if (full) {
-                *reinterpret_cast<float4*>(X + i0) = make_float4(x[0], x[1], x[2], x[3]);
-                *reinterpret_cast<float4*>(VX + i0) = make_float4(vx[0], vx[1], vx[2], vx[3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (i0 + k < end) { X[i0 + k] = x[k]; VX[i0 + k] = vx[k]; }
-            }
-            if (nabs0) atomicAdd(&sh.absorbed[0], nabs0);
-            if (nabs1) atomicAdd(&sh.absorbed[1], nabs1);
-            if (nabs0 + nabs1 + nnf) atomicAdd(&sh.removed, nabs0 + nabs1 + nnf);
-            if (nps) atomicAdd(&sh.psteps, nps);
-            if (nnf) atomicAdd(&sh.nonfinite, nnf);
-
-            // enqueue candidates in slot order
-            unsigned total;
-            const unsigned off = block_excl_scan<BLOCK>(__popc(cand), sh.ws, &total);
+            const unsigned cm = __ballot_sync(0xffffffffu, cand);
             if (cand) {
-                unsigned q = qn + off;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (cand & (1u << k)) { qslot[q] = (unsigned)(i0 + k); qw[q] = wv[k]; ++q; }
+                const unsigned q = q1n + __popc(cm & lt_mask);
+                q1s[q] = i; q1w[q] = w;
             }
-            qn += total;
-            __syncthreads();
-            while (qn >= (unsigned)BLOCK) {
-                run_batch(BLOCK);
-                // move the remaining entries to the front; entry q is read
-                // (from BLOCK + q) and written (to q) by the same thread, one
-                // pass after it read that slot, so no cross-thread hazard
-                const unsigned rest = qn - BLOCK;
-                for (unsigned q = tid; q < rest; q += BLOCK) {
-                    const unsigned s0 = qslot[BLOCK + q];
-                    const uint4 w0 = qw[BLOCK + q];
-                    qslot[q] = s0; qw[q] = w0;
-                }
-                qn = rest;
-                __syncthreads();
+            q1n += __popc(cm);
+        }
+        __syncwarp();
+        while (q1n >= 32u) {
+            run_cand(32u);
+            const unsigned rest = q1n - 32u;
+            for (unsigned q = lane; q < rest; q += 32u) {
+                const unsigned s0 = q1s[32 + q];
+                const uint4 w1 = q1w[32 + q];
+                q1s[q] = s0; q1w[q] = w1;
             }
+            q1n = rest;
+            __syncwarp();
         }
-        if (qn > 0) run_batch(qn);
-
-        // -------- births: prefix over earlier tiles, then place them
-        if (P.births_possible[S]) {
-            if (tid == 0) {
-                bool ok;
-                sh.excl = lookback(P.lb_flag[KKIND], P.lb_val[KKIND], tile, pack2(nb1, nb2), epoch,
-                                   &C->error_flags, &ok);
-                sh.ok = ok ? 1 : 0;
-                if (ok && tile == ntiles - 1) {
-                    const unsigned long long incl = add2(sh.excl, pack2(nb1, nb2));
-                    const unsigned tot1 = (unsigned)incl, tot2 = (unsigned)(incl >> 32);
-                    if (S == SP_E) {
-                        C->births[B_E_FROM_E] = tot1;
-                        C->births[B_OP_FROM_E] = tot1;
-                        C->births[B_OM_FROM_E] = tot2;
-                    } else if (S == SP_OM) {
-                        C->births[B_E_FROM_OM] = tot2;
-                    }
-                }
-            }
-            __syncthreads();
-            if (sh.ok) {
-                const unsigned e1 = (unsigned)sh.excl, e2 = (unsigned)(sh.excl >> 32);
-                const unsigned long long sbase = (unsigned long long)tile * TILE;
-                if (S == SP_E) {
-                    for (unsigned r = tid; r < nb1; r += BLOCK) {
-                        const unsigned long long k = (unsigned long long)e1 + r;
-                        place_birth(P, SP_E, dst_slot0 + k, dst_id0 + k, P.stage[B_E_FROM_E][sbase + r], &C->error_flags);
-                        place_birth(P, SP_OP, op_slot0 + k, op_id0 + k, P.stage[B_OP_FROM_E][sbase + r], &C->error_flags);
-                    }
-                    for (unsigned r = tid; r < nb2; r += BLOCK) {
-                        const unsigned long long k = (unsigned long long)e2 + r;
-                        place_birth(P, SP_OM, dst2_slot0 + k, dst2_id0 + k, P.stage[B_OM_FROM_E][sbase + r], &C->error_flags);
-                    }
-                } else if (S == SP_OM) {
-                    for (unsigned r = tid; r < nb2; r += BLOCK) {
-                        const unsigned long long k = (unsigned long long)e2 + r;
-                        place_birth(P, SP_E, dst_slot0 + k, dst_id0 + k, P.stage[B_E_FROM_OM][sbase + r], &C->error_flags);
-                    }
-                }
-            }
-        }
-        // -------- per-tile cell counts of the surviving ions, for (17)
-        if (track_cells) {
-            __syncthreads();
-            unsigned* H = P.hist[S == SP_OM ? 0 : 1] + (size_t)tile * Nc;
-            for (int c = tid; c < Nc; c += BLOCK) H[c] = chist[c];
-        }
-        if (++tiles_since_flush == FLUSH_TILES) {
-            __syncthreads();
-            flush_hist(hist, P.Qf[S], Ng);
-            tiles_since_flush = 0;
-        }
-        __syncthreads();
     }
+    if (q1n > 0) run_cand(q1n);
+    if (q2n > 0) run_real(q2n);
+    if (births && lane == 0) {
+        if (cnt1) cnt1[gw] = nb1;
+        if (cnt2) cnt2[gw] = nb2;
+    }
+    // per-thread counters into the block's; the block's deposit and counters
+    // into the global accumulators
+    if (psteps) atomicAdd(&sh.psteps, psteps);
+    if (nabs0) atomicAdd(&sh.absorbed[0], nabs0);
+    if (nabs1) atomicAdd(&sh.absorbed[1], nabs1);
+    if (nremoved) atomicAdd(&sh.removed, nremoved);
+    if (nnf) atomicAdd(&sh.nonfinite, nnf);
+    if (wtries) atomicAdd(&sh.warn_tries, wtries);
+    if (wemax) atomicAdd(&sh.warn_emax, wemax);
     __syncthreads();
-    flush_hist(hist, P.Qf[S], Ng);
+    for (int c = tid; c < Nc; c += BLOCK) {
+        const unsigned long long v = hist[c];
+        if (v) {
+            const unsigned long long count = v >> 40, rsum = v & ((1ull << 40) - 1);
+            atomicAdd(&P.Qf[S][c], (count << 16) - rsum);
+            if (rsum) atomicAdd(&P.Qf[S][c + 1], rsum);
+        }
+    }
     if (tid < np && sh.events[tid]) atomicAdd(&C->cnt.events[S][tid], (unsigned long long)sh.events[tid]);
     if (tid == 0) {
         if (sh.absorbed[0]) atomicAdd(&C->cnt.absorbed[S][0], (unsigned long long)sh.absorbed[0]);
@@ -531,7 +483,7 @@ __global__ void __launch_bounds__(BLOCK) k_deposit(Params P) {
 }  // namespace
 
 size_t push_smem_bytes(int species, const Params& P) {
-    return smem_layout(P.Ng, P.Nc, P.nproc[species], species != SP_E).total;
+    return smem_layout(P.Ng, P.nproc[species]).total;
 }
 
 void launch_push(int species, const Params& P, int grid, cudaStream_t s) {

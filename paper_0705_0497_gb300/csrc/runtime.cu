@@ -22,6 +22,10 @@ namespace o2 {
 cudaError_t configure_pair_smem(size_t bytes);
 }
 
+// particle kernels run at most this many blocks per SM (bounds the per-warp
+// birth counts the field kernel scans in shared memory)
+constexpr int MAX_PUSH_BLOCKS_PER_SM = 4;
+
 using namespace o2;
 
 namespace {
@@ -348,12 +352,18 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
         TRY(ctx_alloc(c, &P.lb_flag[k], max_tiles));
         TRY(ctx_alloc(c, &P.lb_val[k], 2 * max_tiles));
     }
-    const unsigned long long tiles_e = ceil_div(cfg->capacity[SP_E], TILE) + 1;
-    const unsigned long long tiles_om = ceil_div(cfg->capacity[SP_OM], TILE) + 1;
-    TRY(ctx_alloc(c, &P.stage[B_E_FROM_E], tiles_e * TILE));
-    TRY(ctx_alloc(c, &P.stage[B_OP_FROM_E], tiles_e * TILE));
-    TRY(ctx_alloc(c, &P.stage[B_OM_FROM_E], tiles_e * TILE));
-    TRY(ctx_alloc(c, &P.stage[B_E_FROM_OM], tiles_om * TILE));
+    const unsigned long long units_e = ceil_div(cfg->capacity[SP_E], WTILE) + 1;
+    const unsigned long long units_om = ceil_div(cfg->capacity[SP_OM], WTILE) + 1;
+    TRY(ctx_alloc(c, &P.stage[B_E_FROM_E], units_e * WTILE));
+    TRY(ctx_alloc(c, &P.stage[B_OP_FROM_E], units_e * WTILE));
+    TRY(ctx_alloc(c, &P.stage[B_OM_FROM_E], units_e * WTILE));
+    TRY(ctx_alloc(c, &P.stage[B_E_FROM_OM], units_om * WTILE));
+    const size_t max_warps = (size_t)c->num_sms * MAX_PUSH_BLOCKS_PER_SM * (BLOCK / 32);
+    P.max_push_warps = (unsigned)max_warps;
+    TRY(ctx_alloc(c, &P.wcount[B_E_FROM_E], max_warps));
+    P.wcount[B_OP_FROM_E] = P.wcount[B_E_FROM_E];
+    TRY(ctx_alloc(c, &P.wcount[B_OM_FROM_E], max_warps));
+    TRY(ctx_alloc(c, &P.wcount[B_E_FROM_OM], max_warps));
     const unsigned long long tiles_ion = std::max(ceil_div(cfg->capacity[SP_OM], TILE), ceil_div(cfg->capacity[SP_OP], TILE)) + 1;
     TRY(ctx_alloc(c, &P.hist[0], tiles_ion * Nc));
     TRY(ctx_alloc(c, &P.hist[1], tiles_ion * Nc));
@@ -373,7 +383,7 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     smax = std::max(smax, sizeof(unsigned) * (size_t)Ng);
     TRY(configure_push_smem(smax));
     TRY(configure_pair_smem(pair_smem_bytes(Nc)));
-    TRY(configure_field_smem(3 * sizeof(long long) * (size_t)Ng));
+    TRY(configure_field_smem(field_smem_bytes(P)));
     for (int s = 0; s < NSP; ++s) P.nproc[s] = 0;
     c->grid_pair = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(tiles_ion, 8ull * c->num_sms));
     c->grid_compact = 4 * c->num_sms;
@@ -492,7 +502,9 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
     for (int s = 0; s < NSP; ++s) {
         int bps = 0;
         if (push_occupancy(s, P, &bps) || bps < 1) bps = 1;
+        if (bps > MAX_PUSH_BLOCKS_PER_SM) bps = MAX_PUSH_BLOCKS_PER_SM;
         c->grid_push[s] = bps * c->num_sms;
+        P.push_warps[s] = (unsigned)c->grid_push[s] * (BLOCK / 32);
     }
     c->have_tables = true;
     return O2PIC_OK;
@@ -597,6 +609,7 @@ int o2pic_step(o2pic_ctx* c, uint64_t nsteps, void* stream) {
             launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
             launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
             if (P.have_neutral) {
+                launch(c, KK_PAIR_SCAN, s, [&] { launch_pair_hist(P, c->grid_compact, s); });
                 launch(c, KK_PAIR_SCAN, s, [&] { launch_pair_scan(P, s); });
                 launch(c, KK_PAIR, s, [&] { launch_pair(P, c->grid_pair, s); });
             }
