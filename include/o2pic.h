@@ -183,8 +183,9 @@ int o2pic_set_step(o2pic_ctx* ctx, uint64_t step);
 
 /* Kernel timing with CUDA events on the launching stream: on != 0 records an
  * event pair around every launch; o2pic_get_timing returns, per kernel kind
- * (0 push e, 1 push O-, 2 push O2+, 3 pair scan, 4 pair, 5 field, 6 compact,
- * 7 deposit), the summed milliseconds, launches and particles processed. */
+ * (0 push e, 1 push O-, 2 push O2+, 3 pair histograms, 4 pair, 5 field,
+ * 6 compact, 7 deposit, 8 collisions e, 9 collisions O-, 10 collisions O2+),
+ * the summed milliseconds and launches; items is reserved (zeros). */
 int o2pic_set_timing(o2pic_ctx* ctx, int on);
 int o2pic_get_timing(o2pic_ctx* ctx, double* ms, uint64_t* launches, uint64_t* items, int nkinds);
 

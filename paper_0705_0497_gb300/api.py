@@ -16,7 +16,8 @@ NSP = 3
 MAXPROC = 16
 E, OM, OP = 0, 1, 2
 HOST, DEVICE = 0, 1
-KERNEL_KINDS = ("push_e", "push_om", "push_op", "pair_scan", "pair", "field", "compact", "deposit")
+KERNEL_KINDS = ("push_e", "push_om", "push_op", "pair_hist", "pair", "field", "compact", "deposit",
+                "cand_e", "cand_om", "cand_op")
 
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "ID_OVERFLOW", -4: "NONFINITE", -5: "CUDA", -6: "TIMEOUT",

@@ -6,9 +6,10 @@
 //     -phi_{j-1} + 2 phi_j - phi_{j+1} = rho_j dx^2 / eps0,
 // phi_0 = U sin(2 pi f t) (driven electrode at x = 0), phi_N = 0 (grounded).
 // With the net fixed-point charge R_j (2^16 per macro-particle, exact int64)
-// and c = e w dx / (A eps0 2^16), the system is solved in closed form by two
-// exact integer prefix sums:
-//     S_m = sum_{k=1..m} R_k,  T_j = sum_{m<j} S_m,
+// and c = e w dx / (A eps0 2^16), the system is solved in closed form by
+// exact integer prefix sums (one block scan of the pair S, U):
+//     S_m = sum_{k=1..m} R_k,  U_m = sum_{k=1..m} k R_k,
+//     T_j = sum_{m<j} S_m = j S_{j-1} - U_{j-1},
 //     D_0 = phi_1 - phi_0 = (c T_N - V0) / N,  phi_j = V0 + j D_0 - c T_j,
 //     E_j = (c (S_j + S_{j-1}) - 2 D_0) [1/(2 dx)]         (1 <= j <= N-1),
 //     E_0 = (-D_0 - c R_0) [1/dx],  E_N = (c S_{N-1} - D_0 + c R_N) [1/dx]
@@ -205,20 +206,61 @@ __device__ void place_births(const Params& P, DevCtrl* C, const CtrlSnap& cs, in
     __syncthreads();
 }
 
+// Block-wide inclusive scans of two int64 arrays a, b [0..n) in shared memory
+// at once (blocked: thread t owns [t*per, (t+1)*per)).
+__device__ __forceinline__ void block_scan_smem_pair(long long* a, long long* b, int n, long long* ws) {
+    const int t = threadIdx.x;
+    const int per = (n + FT - 1) / FT;
+    const int j0 = t * per;
+    long long ra = 0, rb = 0;
+    for (int i = 0; i < per; ++i) {
+        const int j = j0 + i;
+        if (j < n) { ra += a[j]; a[j] = ra; rb += b[j]; b[j] = rb; }
+    }
+    const int lane = t & 31, warp = t >> 5;
+    long long xa = ra, xb = rb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long ya = __shfl_up_sync(0xffffffffu, xa, o);
+        const long long yb = __shfl_up_sync(0xffffffffu, xb, o);
+        if (lane >= o) { xa += ya; xb += yb; }
+    }
+    if (lane == 31) { ws[warp] = xa; ws[32 + warp] = xb; }
+    __syncthreads();
+    if (warp == 0) {
+        long long va = ws[lane], vb = ws[32 + lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long ya = __shfl_up_sync(0xffffffffu, va, o);
+            const long long yb = __shfl_up_sync(0xffffffffu, vb, o);
+            if (lane >= o) { va += ya; vb += yb; }
+        }
+        ws[lane] = va; ws[32 + lane] = vb;
+    }
+    __syncthreads();
+    const long long offa = (warp == 0 ? 0 : ws[warp - 1]) + (xa - ra);
+    const long long offb = (warp == 0 ? 0 : ws[32 + warp - 1]) + (xb - rb);
+    for (int i = 0; i < per; ++i) {
+        const int j = j0 + i;
+        if (j < n) { a[j] += offa; b[j] += offb; }
+    }
+    __syncthreads();
+}
+
 // mode 0: end of a step (pushed_mask = species pushed this step);
 // mode 1: after a load (all species freshly deposited into Qf).
-// Dynamic shared memory: S, T as int64 [Ng], then two u32 [max warps + 1].
+// Dynamic shared memory: S, U as int64 [Ng], then two u32 [max warps + 1].
 __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
     extern __shared__ long long fsm[];
-    __shared__ long long ws[32];
+    __shared__ long long ws[64];
     __shared__ unsigned long long ws2[32];
     __shared__ CtrlSnap cs;
     __shared__ long long sh_R0, sh_RN;
     DevCtrl* C = P.ctrl;
     const int N = P.Nc, Ng = P.Ng;
     const int t = threadIdx.x;
-    long long* Ss = fsm;
-    long long* Ts = fsm + Ng;
+    long long* Ss = fsm;          // S_j = sum_{k=1..j} R_k
+    long long* Us = fsm + Ng;     // U_j = sum_{k=1..j} k R_k   (T_j = j S_{j-1} - U_{j-1})
     unsigned* p1 = reinterpret_cast<unsigned*>(fsm + 2 * Ng);
     unsigned* p2 = p1 + (P.max_push_warps + 1);
 
@@ -256,32 +298,40 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
             if (mode == 0) P.Qacc[s][j] = qa[s] + q;
             net += (s == SP_OP) ? (long long)q : -(long long)q;
         }
-        Ss[j] = (j >= 1) ? net : 0;     // S_m = sum_{k=1..m} R_k (scanned below)
+        Ss[j] = (j >= 1) ? net : 0;                    // scanned below
+        Us[j] = (j >= 1) ? (long long)j * net : 0;
         if (j == 0) sh_R0 = net;
         if (j == N) sh_RN = net;
     }
     __syncthreads();
-    block_scan_smem(Ss, Ng, ws);
-    // T_j = sum_{m<j} S_m (exclusive scan of S over m = 0..N-1)
-    for (int j = t; j < Ng; j += FT) Ts[j] = (j >= 1) ? Ss[j - 1] : 0;
-    __syncthreads();
-    block_scan_smem(Ts, Ng, ws);
+    block_scan_smem_pair(Ss, Us, Ng, ws);
     const double c = P.c_field;
     const unsigned long long step = cs.step;
     // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load), evaluated
-    // on the host in FP64 and staged in a ring indexed by the step
-    const double V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
-    const double D0 = (c * (double)Ts[N] - V0) / (double)N;
+    // on the host in FP64 and staged in a ring indexed by the step.  D0 once
+    // per block: FP64 throughput on this GPU is low.
+    __shared__ double sh_V0, sh_D0;
+    if (t == 0) {
+        const double v = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
+        const long long TN = (long long)N * Ss[N - 1] - Us[N - 1];
+        sh_V0 = v;
+        sh_D0 = (c * (double)TN - v) / (double)N;
+    }
+    __syncthreads();
+    const double V0 = sh_V0, D0 = sh_D0;
     const long long R0 = sh_R0, RN = sh_RN;
     for (int j = t; j < Ng; j += FT) {
         double E;
         if (j == 0) E = (-D0 - c * (double)R0) * P.inv_dx64;
         else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)RN) * P.inv_dx64;
         else E = (c * (double)(Ss[j] + Ss[j - 1]) - 2.0 * D0) * P.inv_2dx64;
-        const double phi = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Ts[j]);
+        const long long Tj = (j >= 1) ? (long long)j * Ss[j - 1] - Us[j - 1] : 0;
+        const double phi = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Tj);
         P.Ef[j] = (float)E;
         P.phi[j] = phi;
     }
+    // per-cell ion totals of (17): zero for the next ion step
+    for (int c = t; c < 2 * P.Nc; c += FT) P.ptot[c] = 0u;
     if (mode != 0) {
         if (t < NKK + NSP) C->ticket[t] = 0u;
         return;

@@ -38,8 +38,9 @@ enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT
 constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE = 4ull, ERR_TIMEOUT = 8ull;
 
 // kernel kinds (timing, tickets)
-enum KernelKind { KK_PUSH_E = 0, KK_PUSH_OM = 1, KK_PUSH_OP = 2, KK_PAIR_SCAN = 3, KK_PAIR = 4,
-                  KK_FIELD = 5, KK_COMPACT = 6, KK_DEPOSIT = 7, NKK = 8 };
+enum KernelKind { KK_PUSH_E = 0, KK_PUSH_OM = 1, KK_PUSH_OP = 2, KK_PAIR_HIST = 3, KK_PAIR = 4,
+                  KK_FIELD = 5, KK_COMPACT = 6, KK_DEPOSIT = 7, KK_CAND_E = 8, KK_CAND_OM = 9, KK_CAND_OP = 10,
+                  NKK = 11 };
 
 // Counters: same layout as the head of o2pic_stats.
 struct DevCounters {
@@ -125,10 +126,12 @@ struct Params {
     float4* stage[NB];
     unsigned int* wcount[NB];
     unsigned int push_warps[NSP];  // warps of each particle kernel launch (units of wcount)
+    uint4* cand[NSP];              // collision candidates {slot, w1, w2, w3} at each warp's range
+    unsigned int* ccount[NSP];     // candidates per warp
     unsigned int max_push_warps;   // bound on push_warps (shared memory of the field kernel)
     // (17): per-tile per-cell counts of live ions [2][max_tiles][Nc], per-cell info
     unsigned int* hist[2];       // 0: O-, 1: O2+
-    unsigned int* cellinfo;      // [Nc][4]: n-, n+, shift r, reserved
+    unsigned int* ptot;          // [2][Nc]: live O-, O2+ per cell (cleared by the end-of-step kernel)
     unsigned int* removal;       // [2 * max_removals]: O- slot, O2+ slot
     unsigned int max_removals;
     // compaction trigger
@@ -149,8 +152,9 @@ __host__ __device__ inline unsigned warp_range_len(unsigned n, unsigned W) {
 // ---------------------------------------------------------------- launchers
 // (defined in the kernel translation units, called by the runtime)
 void launch_push(int species, const Params& P, int grid, cudaStream_t s);
+void launch_cand(int species, const Params& P, int grid, cudaStream_t s);
 void launch_pair_hist(const Params& P, int grid, cudaStream_t s);
-void launch_pair_scan(const Params& P, cudaStream_t s);
+cudaError_t configure_pair_hist_smem(int Nc);
 void launch_pair(const Params& P, int grid, cudaStream_t s);
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s);
 void launch_compact(int species, const Params& P, int grid, cudaStream_t s);
@@ -163,7 +167,6 @@ void launch_gather(int species, const Params& P, int grid, unsigned long long ep
                    uint32_t* id, unsigned long long cap, unsigned long long* out_count, cudaStream_t s);
 cudaError_t configure_push_smem(size_t max_bytes);
 cudaError_t configure_field_smem(size_t bytes);
-size_t pair_smem_bytes(int Nc);
 size_t field_smem_bytes(const Params& P);
 int push_occupancy(int species, const Params& P, int* blocks_per_sm);
 size_t push_smem_bytes(int species, const Params& P);

@@ -7,32 +7,48 @@
 // tie), i < m, is paired with member (i + r_c) mod M of the longer one.  A
 // pair reacts with probability P = M w sigma_n(E_rel) g dt_ion / (A dx).
 //
-// GPU form: k_pair_hist counts, per 8192-slot tile, the surviving ions per
-// cell of both species.  k_pair_scan turns these into
-// per-cell exclusive prefixes over tiles (so the rank of an ion in its cell
-// list is prefix + its rank inside the tile) and draws the shifts.  k_pair
-// gives each block one O- tile, split among its warps; with per-warp cell
-// counts every O- learns its rank k in its cell list, whether it is paired
-// and the rank q of its partner.  The acceptance
-// draw needs only the O- id; since P <= K_max M w dt/(A dx), only the rare
-// draws below that bound need the partner, which the warp then finds by a
-// binary search over the O2+ prefixes and a ballot scan of one O2+ tile.
+// GPU form.  The acceptance draw u of a pair needs only the O- id, and
+// P <= K_max M pf (pf = w dt_ion / (A dx)), so an O- can react only if
+// u < K_max M pf; at the method's weights and time steps that bound is
+// ~1e-6 and only a handful of O- per step pass it.  So:
+//   * k_pair_hist counts, per 8192-slot tile of each ion species, the live
+//     ions per cell, and adds them into per-cell totals n-, n+;
+//   * k_pair streams x and id of the O- once, draws u and flags the O- below
+//     the bound (M from the totals);
+//   * for a flagged O- the whole block finds its rank k in the cell list
+//     (counts of the earlier tiles + same-cell slots before it in its tile),
+//     the partner rank q, the O2+ tile holding rank q (block scan of that
+//     cell's per-tile counts) and the partner's slot there (block scan of the
+//     hits in slot order), each step with all of the block's loads in flight;
+//     one thread then does the reaction test with the exact P.
+// Reactions only append (O- slot, O2+ slot) to the removal list and take the
+// pair out of the fresh deposit; both are order-independent, so flagged ions
+// may be resolved in any order.
 #include "common.cuh"
 
 namespace o2 {
 
 namespace {
 
-constexpr int SCAN_T = 1024;   // 32 cells x 32 tile groups
-constexpr int HIST_T = 512;
+constexpr int HIST_T = 512;                  // threads of k_pair_hist
+constexpr int HIST_PER = TILE / HIST_T;      // 16 slots per thread
+constexpr int PAIR_T = 256;                  // threads of k_pair
+constexpr int PER_T = TILE / PAIR_T;         // 32 slots of a tile per thread
+constexpr int LCAP = 256;                    // flagged O- listed per tile before the slow path
+constexpr unsigned short CELL_DEAD = 0x7FFFu, CELL_FLAG = 0x8000u;
+static_assert(PER_T == 32, "one 32-bit hit mask per thread");
+static_assert(MAX_NODES - 1 < CELL_DEAD, "cell index fits 15 bits");
 
-// Per 8192-slot tile of each ion species, the number of live ions per cell
-// (post-push positions): hist[sp][tile][cell].  Blocks take tiles of O-
-// first, then of O2+.
+// Per tile of each ion species, the live ions per cell (post-push
+// positions): hist[sp][tile][cell]; and the per-cell totals ptot[sp][cell]
+// (zero on entry; the end-of-step kernel clears them).  Blocks take tiles of
+// O- first, then of O2+, and add their totals once at the end.
 __global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P) {
-    extern __shared__ unsigned hsm[];
+    extern __shared__ unsigned hsm[];   // [Nc] tile counts, [2][Nc] block totals
     DevCtrl* C = P.ctrl;
     const int Nc = P.Nc;
+    unsigned* bt = hsm + Nc;
+    for (int c = threadIdx.x; c < 2 * Nc; c += HIST_T) bt[c] = 0u;
     const unsigned long long nsm = C->slots[SP_OM], nsp = C->slots[SP_OP];
     const unsigned ntm = (unsigned)ceil_div(nsm, TILE), ntp = (unsigned)ceil_div(nsp, TILE);
     for (unsigned g = blockIdx.x; g < ntm + ntp; g += gridDim.x) {
@@ -40,255 +56,240 @@ __global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P) {
         const unsigned tile = (g < ntm) ? g : g - ntm;
         const int S = sp == 0 ? SP_OM : SP_OP;
         const unsigned long long n = sp == 0 ? nsm : nsp;
-        const float* X = P.sp[S].x[C->cur[S]];
+        const float* __restrict__ X = P.sp[S].x[C->cur[S]];
         for (int c = threadIdx.x; c < Nc; c += HIST_T) hsm[c] = 0u;
-        __syncthreads();
         const unsigned long long base = (unsigned long long)tile * TILE;
-        const unsigned long long end = (base + TILE < n) ? base + TILE : n;
-#pragma unroll 4
-        for (unsigned long long i = base + threadIdx.x; i < end; i += HIST_T) {
-            const float x = X[i];
-            if (!is_dead(x)) {
+        float xs[HIST_PER];
+#pragma unroll
+        for (int i = 0; i < HIST_PER; ++i) {
+            const unsigned long long p = base + (unsigned long long)i * HIST_T + threadIdx.x;
+            xs[i] = (p < n) ? X[p] : dead_marker();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < HIST_PER; ++i) {
+            if (!is_dead(xs[i])) {
                 int c; float fr;
-                cell_of(x, P.inv_dx, Nc, c, fr);
+                cell_of(xs[i], P.inv_dx, Nc, c, fr);
                 atomicAdd(&hsm[c], 1u);
             }
         }
         __syncthreads();
         unsigned* H = P.hist[sp] + (size_t)tile * Nc;
-        for (int c = threadIdx.x; c < Nc; c += HIST_T) H[c] = hsm[c];
+        for (int c = threadIdx.x; c < Nc; c += HIST_T) {
+            const unsigned v = hsm[c];
+            H[c] = v;
+            bt[sp * Nc + c] += v;
+        }
         __syncthreads();
     }
+    for (int c = threadIdx.x; c < 2 * Nc; c += HIST_T)
+        if (bt[c]) atomicAdd(&P.ptot[c], bt[c]);
 }
 
-__global__ void __launch_bounds__(SCAN_T) k_pair_scan(Params P) {
-    __shared__ unsigned part[32][33];
-    __shared__ unsigned tot[2][32];
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* ws) {
+    unsigned total;
+    (void)block_excl_scan<PAIR_T>(v, ws, &total);
+    return total;
+}
+
+// Resolve one flagged O- (tile position pos, cell in cell16[pos]).  Every
+// thread of the block calls it; all return at the same point except at the
+// very end.  sh = 2 words of shared memory for the partner tile search.
+__device__ void resolve_one(const Params& P, unsigned pos, unsigned tile, unsigned long long base,
+                            const unsigned short* cell16, unsigned* ws, unsigned* sh, unsigned long long step,
+                            unsigned long long nsp, unsigned ntp, unsigned cm, unsigned cp, unsigned& gt1) {
     DevCtrl* C = P.ctrl;
     const int Nc = P.Nc;
-    const int cl = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int c = blockIdx.x * 32 + cl;
-    for (int sp = 0; sp < 2; ++sp) {
-        const unsigned long long ns = C->slots[sp == 0 ? SP_OM : SP_OP];
-        const unsigned ntiles = (unsigned)ceil_div(ns, TILE);
-        const unsigned per = (ntiles + 31) / 32;
-        const unsigned t0 = g * per, t1 = (t0 + per < ntiles) ? t0 + per : ntiles;
-        unsigned* H = P.hist[sp];
-        unsigned sum = 0;
-        if (c < Nc)
-            for (unsigned t = t0; t < t1; ++t) sum += H[(size_t)t * Nc + c];
-        part[g][cl] = sum;
-        __syncthreads();
-        unsigned before = 0;
-        for (int k = 0; k < g; ++k) before += part[k][cl];
-        if (g == 31) tot[sp][cl] = before + sum;
-        __syncthreads();
-        if (c < Nc) {
-            unsigned run = before;
-            for (unsigned t = t0; t < t1; ++t) {
-                const unsigned v = H[(size_t)t * Nc + c];
-                H[(size_t)t * Nc + c] = run;
-                run += v;
-            }
-        }
-        __syncthreads();
+    const int tid = threadIdx.x;
+    const unsigned c = cell16[pos] & CELL_DEAD;
+    // rank k of the O- in its cell list
+    unsigned cnt = 0;
+    const unsigned* H0 = P.hist[0];
+    for (unsigned t = tid; t < tile; t += PAIR_T) cnt += H0[(size_t)t * Nc + c];
+#pragma unroll 8
+    for (int i = 0; i < PER_T; ++i) {
+        const unsigned q = (unsigned)i * PAIR_T + tid;
+        if (q < pos && (cell16[q] & CELL_DEAD) == c) ++cnt;
     }
-    if (g == 0 && c < Nc) {
-        const unsigned nm = tot[0][cl], npl = tot[1][cl];
-        const unsigned m = nm < npl ? nm : npl, M = nm < npl ? npl : nm;
-        unsigned r = 0;
-        if (m > 0) {
-            const unsigned long long step = C->step;
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)step, TAG_SHIFT, 0u, (uint32_t)(step >> 32)),
-                                          make_uint2((uint32_t)c, P.seed));
-            r = w.x % M;
-            atomicAdd(&C->cnt.pair_candidates, (unsigned long long)m);
+    const unsigned k = block_sum(cnt, ws);
+    const unsigned nm = P.ptot[c], npl = P.ptot[Nc + c];
+    const unsigned m = nm < npl ? nm : npl, M = nm < npl ? npl : nm;
+    if (m == 0 || k >= nm) return;   // block-uniform
+    const uint4 wr = philox4x32_10(make_uint4((uint32_t)step, TAG_SHIFT, 0u, (uint32_t)(step >> 32)),
+                                   make_uint2(c, P.seed));
+    const unsigned r = wr.x % M;
+    unsigned q;
+    if (nm <= npl) {
+        q = k + r; if (q >= M) q -= M;
+    } else {
+        unsigned i = k + (M - r); if (i >= M) i -= M;   // the O2+ of rank i has this O- as partner
+        if (i >= m) return;                              // block-uniform
+        q = i;
+    }
+    // O2+ tile holding rank q: thread t sums a contiguous group of tiles
+    const unsigned* H1 = P.hist[1];
+    const unsigned per = (ntp + PAIR_T - 1) / PAIR_T;
+    const unsigned t0 = (unsigned)tid * per, t1 = (t0 + per < ntp) ? t0 + per : ntp;
+    unsigned gs = 0;
+    for (unsigned t = t0; t < t1; ++t) gs += H1[(size_t)t * Nc + c];
+    unsigned gtot;
+    const unsigned gex = block_excl_scan<PAIR_T>(gs, ws, &gtot);
+    if (q >= gtot) return;   // block-uniform (inconsistent counts; never expected)
+    if (gex <= q && q < gex + gs) {
+        unsigned run = gex, t = t0;
+        for (; t < t1; ++t) {
+            const unsigned v = H1[(size_t)t * Nc + c];
+            if (q < run + v) break;
+            run += v;
         }
-        P.cellinfo[4 * c + 0] = nm;
-        P.cellinfo[4 * c + 1] = npl;
-        P.cellinfo[4 * c + 2] = r;
+        sh[0] = t;
+        sh[1] = q - run;
+    }
+    __syncthreads();
+    const unsigned lo = sh[0], want = sh[1];
+    __syncthreads();
+    // the partner's slot: rank `want` among the tile's live O2+ of cell c
+    const float* XP = P.sp[SP_OP].x[cp];
+    const unsigned long long bb = (unsigned long long)lo * TILE + (unsigned long long)tid * PER_T;
+    float xs[PER_T];
+#pragma unroll
+    for (int i = 0; i < PER_T; ++i) xs[i] = (bb + i < nsp) ? XP[bb + i] : dead_marker();
+    unsigned mask = 0;
+#pragma unroll
+    for (int i = 0; i < PER_T; ++i) {
+        if (!is_dead(xs[i])) {
+            int j; float fr;
+            cell_of(xs[i], P.inv_dx, Nc, j, fr);
+            if ((unsigned)j == c) mask |= 1u << i;
+        }
+    }
+    const unsigned h = __popc(mask);
+    unsigned htot;
+    const unsigned excl = block_excl_scan<PAIR_T>(h, ws, &htot);
+    if (want < excl || want >= excl + h) return;
+    unsigned bits = mask;
+    for (unsigned t = 0; t < want - excl; ++t) bits &= bits - 1u;
+    const unsigned b_slot = (unsigned)(bb + (unsigned)(__ffs(bits) - 1));
+    // reaction test with the exact probability
+    const unsigned long long p = base + pos;
+    const SpeciesBuf& SM = P.sp[SP_OM];
+    const SpeciesBuf& SPp = P.sp[SP_OP];
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)step, TAG_PAIR, 0u, (uint32_t)(step >> 32)),
+                                  make_uint2(SM.id[cm][p], P.seed));
+    const float u = uniform(w.x);
+    const float gx = SM.vx[cm][p] - SPp.vx[cp][b_slot];
+    const float gy = SM.vy[cm][p] - SPp.vy[cp][b_slot];
+    const float gz = SM.vz[cm][p] - SPp.vz[cp][b_slot];
+    const float E = P.kappa_n * dot3(gx, gy, gz, gx, gy, gz);
+    int gi; float gw; bool above;
+    grid_locate(E, gi, gw, above);
+    if (above) atomicAdd(&C->cnt.warn_emax, 1ull);
+    const float K = grid_interp(P.Ktab, 1, 0, gi, gw);
+    const float Pp = K * (P.pair_factor * (float)M);
+    if (Pp > 1.0f) ++gt1;
+    if (u < Pp) {
+        const unsigned idx = atomicAdd(&C->removals, 1u);
+        if (idx < P.max_removals) {
+            P.removal[2 * idx] = (unsigned)p;
+            P.removal[2 * idx + 1] = b_slot;
+        }
+        // take both out of the fresh deposit
+        int j; float f;
+        cell_of(SM.x[cm][p], P.inv_dx, Nc, j, f);
+        uint32_t rr = cic_r(f);
+        atomicAdd(&P.Qf[SP_OM][j], 0ull - (unsigned long long)(65536u - rr));
+        atomicAdd(&P.Qf[SP_OM][j + 1], 0ull - (unsigned long long)rr);
+        cell_of(XP[b_slot], P.inv_dx, Nc, j, f);
+        rr = cic_r(f);
+        atomicAdd(&P.Qf[SP_OP][j], 0ull - (unsigned long long)(65536u - rr));
+        atomicAdd(&P.Qf[SP_OP][j + 1], 0ull - (unsigned long long)rr);
     }
 }
 
-constexpr int PAIR_WARPS = 8;
-
-// Slot of the O2+ with rank q in cell c (cell list in slot order).
-__device__ unsigned find_op(const Params& P, const float* XP, unsigned long long nsl, unsigned ntiles, int c,
-                            unsigned q, int lane) {
-    const int Nc = P.Nc;
-    const unsigned* H = P.hist[1];
-    // largest tile t with prefix(t, c) <= q
-    unsigned lo = 0, hi = ntiles;   // answer in [lo, hi)
-    while (hi - lo > 1) {
-        const unsigned mid = (lo + hi) >> 1;
-        if (H[(size_t)mid * Nc + c] <= q) lo = mid; else hi = mid;
-    }
-    const unsigned want = q - H[(size_t)lo * Nc + c];
-    const unsigned long long base = (unsigned long long)lo * TILE;
-    const unsigned long long end = (base + TILE < nsl) ? base + TILE : nsl;
-    unsigned seen = 0;
-    for (unsigned long long b = base; b < end; b += 32) {
-        const unsigned long long p = b + lane;
-        bool hit = false;
-        if (p < end) {
-            const float x = XP[p];
-            if (!is_dead(x)) {
-                int j; float fr;
-                cell_of(x, P.inv_dx, Nc, j, fr);
-                hit = (j == c);
-            }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        const unsigned cnt = __popc(bal);
-        if (seen + cnt > want) {
-            // the (want - seen)-th set bit
-            unsigned bits = bal;
-            for (unsigned k = 0; k < want - seen; ++k) bits &= bits - 1;
-            return (unsigned)(b + (__ffs(bits) - 1));
-        }
-        seen += cnt;
-    }
-    return 0xFFFFFFFFu;
-}
-
-// One block per O- tile.  Pass 1: each warp loads its sub-range of the tile
-// (all loads in flight together), stores each slot's cell (or "dead") in
-// shared memory and counts its ions per cell.  Pass 2: per cell, prefix of
-// the warps' counts, starting from the tile's prefix over earlier tiles.
-// Pass 3: each warp walks its sub-range in slot order from shared memory;
-// an O- learns its rank k in its cell list, whether it is paired, and draws
-// its acceptance number; the rare candidates find their partner.
-__global__ void __launch_bounds__(PAIR_WARPS * 32) k_pair(Params P, int W) {
-    extern __shared__ unsigned pair_smem[];
-    unsigned short* cell16 = reinterpret_cast<unsigned short*>(pair_smem);   // [TILE]
-    unsigned* whist = pair_smem + TILE / 2;                                  // [W][Nc]
+// One block per O- tile (grid-stride): the streaming pass, then the flagged
+// O- of the tile.  Block 0 also adds sum_c min(n-, n+) to the pair counter.
+__global__ void __launch_bounds__(PAIR_T) k_pair(Params P) {
+    __shared__ unsigned short cell16[TILE];
+    __shared__ unsigned short list[LCAP];
+    __shared__ unsigned ws[32];
+    __shared__ unsigned sh[2];
+    __shared__ unsigned nflag;
     DevCtrl* C = P.ctrl;
     const int Nc = P.Nc;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
     const unsigned long long step = C->step;
     const unsigned long long nsm = C->slots[SP_OM], nsp = C->slots[SP_OP];
     const unsigned ntm = (unsigned)ceil_div(nsm, TILE), ntp = (unsigned)ceil_div(nsp, TILE);
     const unsigned cm = C->cur[SP_OM], cp = C->cur[SP_OP];
-    const float* XM = P.sp[SP_OM].x[cm];
-    const uint32_t* IDM = P.sp[SP_OM].id[cm];
-    const float* XP = P.sp[SP_OP].x[cp];
-    const float pf = P.pair_factor;
-    const int sub = TILE / W;
+    const float* __restrict__ XM = P.sp[SP_OM].x[cm];
+    const uint32_t* __restrict__ IDM = P.sp[SP_OM].id[cm];
+    const unsigned* __restrict__ tot = P.ptot;
+    const uint4 ctr = make_uint4((uint32_t)step, TAG_PAIR, 0u, (uint32_t)(step >> 32));
     unsigned gt1 = 0;
-    unsigned* myhist = whist + (size_t)warp * Nc;
+
+    if (blockIdx.x == 0) {
+        unsigned pairs = 0;   // at most 2^32 ions in all
+        for (int c = tid; c < Nc; c += PAIR_T) {
+            const unsigned a = tot[c], b = tot[Nc + c];
+            pairs += a < b ? a : b;
+        }
+        const unsigned s = block_sum(pairs, ws);
+        if (tid == 0 && s) atomicAdd(&C->cnt.pair_candidates, (unsigned long long)s);
+    }
 
     for (unsigned tile = blockIdx.x; tile < ntm; tile += gridDim.x) {
-        for (int i = threadIdx.x; i < W * Nc; i += blockDim.x) whist[i] = 0u;
-        __syncthreads();
         const unsigned long long base = (unsigned long long)tile * TILE;
-        const unsigned long long end = (base + TILE < nsm) ? base + TILE : nsm;
-        const unsigned long long s0 = base + (unsigned long long)warp * sub;
-        const unsigned long long s1 = (s0 + sub < end) ? s0 + sub : end;
-        // pass 1
-#pragma unroll 4
-        for (unsigned long long b = s0; b < s1; b += 32) {
-            const unsigned long long p = b + lane;
-            if (p < s1) {
-                const float x = XM[p];
-                unsigned short cc = 0xFFFFu;
-                if (!is_dead(x)) {
+        if (tid == 0) nflag = 0u;
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < PER_T; h += 16) {
+            float xs[16];
+            uint32_t ids[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const unsigned long long p = base + (unsigned long long)(h + i) * PAIR_T + tid;
+                const bool in = p < nsm;
+                xs[i] = in ? XM[p] : dead_marker();
+                ids[i] = in ? IDM[p] : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const unsigned pos = (unsigned)(h + i) * PAIR_T + tid;
+                unsigned short cc = CELL_DEAD;
+                if (!is_dead(xs[i])) {
                     int c; float fr;
-                    cell_of(x, P.inv_dx, Nc, c, fr);
+                    cell_of(xs[i], P.inv_dx, Nc, c, fr);
+                    const unsigned a = __ldg(&tot[c]), b = __ldg(&tot[Nc + c]);
+                    const unsigned M = a < b ? b : a;
+                    const float u = uniform(philox4x32_10(ctr, make_uint2(ids[i], P.seed)).x);
                     cc = (unsigned short)c;
-                    atomicAdd(&myhist[c], 1u);
+                    if (u < P.Kmax_hi * (P.pair_factor * (float)M)) {
+                        cc |= CELL_FLAG;
+                        const unsigned idx = atomicAdd(&nflag, 1u);
+                        if (idx < LCAP) list[idx] = (unsigned short)pos;
+                    }
                 }
-                cell16[p - base] = cc;
+                cell16[pos] = cc;
             }
         }
         __syncthreads();
-        // pass 2
-        const unsigned* HM = P.hist[0] + (size_t)tile * Nc;
-        for (int c = threadIdx.x; c < Nc; c += blockDim.x) {
-            unsigned run = HM[c];
-            for (int w = 0; w < W; ++w) {
-                const unsigned v = whist[(size_t)w * Nc + c];
-                whist[(size_t)w * Nc + c] = run;
-                run += v;
-            }
-        }
-        __syncthreads();
-        // pass 3
-        for (unsigned long long b = s0; b < s1; b += 32) {
-            const unsigned long long p = b + lane;
-            int c = 0;
-            bool live = false;
-            if (p < s1) {
-                const unsigned short cc = cell16[p - base];
-                if (cc != 0xFFFFu) { live = true; c = cc; }
-            }
-            const unsigned lmask = __ballot_sync(0xffffffffu, live);
-            bool cand = false;
-            unsigned q = 0, M = 0;
-            float u = 0.0f;
-            if (live) {
-                const unsigned peers = __match_any_sync(lmask, c);
-                const unsigned lt = peers & ((1u << lane) - 1u);
-                const unsigned before = myhist[c];
-                const unsigned k = before + __popc(lt);
-                __syncwarp(lmask);
-                if (lt == 0u) myhist[c] = before + __popc(peers);
-                const unsigned nm = P.cellinfo[4 * c], npl = P.cellinfo[4 * c + 1], r = P.cellinfo[4 * c + 2];
-                const unsigned m = nm < npl ? nm : npl;
-                M = nm < npl ? npl : nm;
-                bool paired = false;
-                if (m > 0) {
-                    if (nm <= npl) { q = (unsigned)(((unsigned long long)k + r) % M); paired = true; }
-                    else {
-                        const unsigned i = (unsigned)(((unsigned long long)k + M - r) % M);
-                        if (i < m) { q = i; paired = true; }
-                    }
-                }
-                if (paired) {
-                    const uint4 w = philox4x32_10(make_uint4((uint32_t)step, TAG_PAIR, 0u, (uint32_t)(step >> 32)),
-                                                  make_uint2(IDM[p], P.seed));
-                    u = uniform(w.x);
-                    cand = u < P.Kmax_hi * (pf * (float)M);
-                }
-            }
-            __syncwarp();
-            unsigned cmask = __ballot_sync(0xffffffffu, cand);
-            while (cmask) {
-                const int owner = __ffs(cmask) - 1;
-                cmask &= cmask - 1;
-                const int oc = __shfl_sync(0xffffffffu, c, owner);
-                const unsigned oq = __shfl_sync(0xffffffffu, q, owner);
-                const unsigned b_slot = find_op(P, XP, nsp, ntp, oc, oq, lane);
-                if (lane == owner && b_slot != 0xFFFFFFFFu) {
-                    const SpeciesBuf& SM = P.sp[SP_OM];
-                    const SpeciesBuf& SPp = P.sp[SP_OP];
-                    const float gx = SM.vx[cm][p] - SPp.vx[cp][b_slot];
-                    const float gy = SM.vy[cm][p] - SPp.vy[cp][b_slot];
-                    const float gz = SM.vz[cm][p] - SPp.vz[cp][b_slot];
-                    const float E = P.kappa_n * dot3(gx, gy, gz, gx, gy, gz);
-                    int gi; float gw; bool above;
-                    grid_locate(E, gi, gw, above);
-                    if (above) atomicAdd(&C->cnt.warn_emax, 1ull);
-                    const float K = grid_interp(P.Ktab, 1, 0, gi, gw);
-                    const float Pp = K * (pf * (float)M);
-                    if (Pp > 1.0f) ++gt1;
-                    if (u < Pp) {
-                        const unsigned idx = atomicAdd(&C->removals, 1u);
-                        if (idx < P.max_removals) {
-                            P.removal[2 * idx] = (unsigned)p;
-                            P.removal[2 * idx + 1] = b_slot;
-                        }
-                        // take both out of the fresh deposit
-                        int j; float f;
-                        cell_of(XM[p], P.inv_dx, Nc, j, f);
-                        uint32_t rr = cic_r(f);
-                        atomicAdd(&P.Qf[SP_OM][j], 0ull - (unsigned long long)(65536u - rr));
-                        atomicAdd(&P.Qf[SP_OM][j + 1], 0ull - (unsigned long long)rr);
-                        cell_of(XP[b_slot], P.inv_dx, Nc, j, f);
-                        rr = cic_r(f);
-                        atomicAdd(&P.Qf[SP_OP][j], 0ull - (unsigned long long)(65536u - rr));
-                        atomicAdd(&P.Qf[SP_OP][j + 1], 0ull - (unsigned long long)rr);
-                    }
-                }
+        const unsigned nf = nflag;
+        if (nf > 0 && nf <= LCAP) {
+            for (unsigned j = 0; j < nf; ++j)
+                resolve_one(P, list[j], tile, base, cell16, ws, sh, step, nsp, ntp, cm, cp, gt1);
+        } else if (nf > LCAP) {
+            // many flagged ions: list them segment by segment from the flags
+            for (int seg = 0; seg < PER_T; ++seg) {
+                const unsigned pos = (unsigned)seg * PAIR_T + tid;
+                const bool f = (cell16[pos] & CELL_FLAG) != 0;
+                unsigned ns;
+                const unsigned idx = block_excl_scan<PAIR_T>(f ? 1u : 0u, ws, &ns);
+                if (f) list[idx] = (unsigned short)pos;
+                __syncthreads();
+                for (unsigned j = 0; j < ns; ++j)
+                    resolve_one(P, list[j], tile, base, cell16, ws, sh, step, nsp, ntp, cm, cp, gt1);
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -298,32 +299,19 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32) k_pair(Params P, int W) {
 
 }  // namespace
 
+size_t pair_hist_smem_bytes(int Nc) { return 3 * sizeof(unsigned) * (size_t)Nc; }
+
+cudaError_t configure_pair_hist_smem(int Nc) {
+    return cudaFuncSetAttribute(k_pair_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pair_hist_smem_bytes(Nc));
+}
+
 void launch_pair_hist(const Params& P, int grid, cudaStream_t s) {
-    k_pair_hist<<<grid, HIST_T, sizeof(unsigned) * (size_t)P.Nc, s>>>(P);
-}
-
-void launch_pair_scan(const Params& P, cudaStream_t s) {
-    k_pair_scan<<<(P.Nc + 31) / 32, SCAN_T, 0, s>>>(P);
-}
-
-// warps per block: the largest of 8, 4, 2, 1 whose per-warp cell counts fit
-int pair_warps(int Nc) {
-    for (int w = PAIR_WARPS; w > 1; w >>= 1)
-        if (2 * TILE + 4 * (size_t)w * Nc <= 200 * 1024) return w;
-    return 1;
-}
-
-size_t pair_smem_bytes(int Nc) {
-    return 2 * (size_t)TILE + 4 * (size_t)pair_warps(Nc) * Nc;
+    k_pair_hist<<<grid, HIST_T, pair_hist_smem_bytes(P.Nc), s>>>(P);
 }
 
 void launch_pair(const Params& P, int grid, cudaStream_t s) {
-    const int W = pair_warps(P.Nc);
-    k_pair<<<grid, W * 32, pair_smem_bytes(P.Nc), s>>>(P, W);
-}
-
-cudaError_t configure_pair_smem(size_t bytes) {
-    return cudaFuncSetAttribute(k_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_pair<<<grid, PAIR_T, 0, s>>>(P);
 }
 
 }  // namespace o2

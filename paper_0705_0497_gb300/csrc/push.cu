@@ -45,40 +45,17 @@ template <> struct SpeciesTraits<SP_OP> { static constexpr uint32_t tag = TAG_OP
 
 constexpr int WARPS = BLOCK / 32;           // 8
 constexpr int ROUND = 128;                  // slots per warp round (4 per lane)
-constexpr int QW = 32 - 1 + ROUND + 1;      // per-warp candidate queue (160 entries)
 constexpr int Q2 = 64;                      // per-warp real-collision queue (31 + 32 max)
 constexpr int PUSH_UNROLL = O2PIC_PUSH_UNROLL;
 
 struct PushShared {
-    unsigned events[MAXPROC];
     unsigned absorbed[2];
     unsigned removed;
     unsigned psteps;
-    unsigned warn_emax, warn_tries;
     unsigned nonfinite;
 };
 
-struct SmemLayout {
-    size_t ef, hist, qslot, qw, qslot2, qw2, total;
-};
-
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
-
-// shared memory: counters, gather field, deposit (count, rsum) per cell, and
-// per warp a candidate queue and a real-collision queue
-__host__ __device__ inline SmemLayout smem_layout(int Ng, int nproc) {
-    (void)nproc;
-    SmemLayout L;
-    size_t o = align16(sizeof(PushShared));
-    L.ef = o; o = align16(o + sizeof(float) * Ng);
-    L.hist = o; o = align16(o + sizeof(unsigned long long) * Ng);
-    L.qw = o; o = align16(o + sizeof(uint4) * WARPS * QW);
-    L.qslot = o; o = align16(o + sizeof(unsigned) * WARPS * QW);
-    L.qw2 = o; o = align16(o + sizeof(uint4) * WARPS * Q2);
-    L.qslot2 = o; o = align16(o + sizeof(unsigned) * WARPS * Q2);
-    L.total = o;
-    return L;
-}
 
 // One candidate through process selection and kinematics, exactly in the
 // order of the oracle.  Returns the event index (-1 = null collision).
@@ -225,17 +202,12 @@ template <int S>
 __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int np = P.nproc[S];
-    const SmemLayout L = smem_layout(P.Ng, np);
     PushShared& sh = *reinterpret_cast<PushShared*>(smem);
-    float* Es = reinterpret_cast<float*>(smem + L.ef);
-    unsigned long long* hist = reinterpret_cast<unsigned long long*>(smem + L.hist);
+    float* Es = reinterpret_cast<float*>(smem + align16(sizeof(PushShared)));
+    unsigned long long* hist =
+        reinterpret_cast<unsigned long long*>(smem + align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint4* q1w = reinterpret_cast<uint4*>(smem + L.qw) + warp * QW;
-    unsigned* q1s = reinterpret_cast<unsigned*>(smem + L.qslot) + warp * QW;
-    uint4* q2w = reinterpret_cast<uint4*>(smem + L.qw2) + warp * Q2;
-    unsigned* q2s = reinterpret_cast<unsigned*>(smem + L.qslot2) + warp * Q2;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const float* __restrict__ cum = P.cum[S];
 
     DevCtrl* C = P.ctrl;
     const unsigned long long step = C->step;
@@ -243,23 +215,15 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
     const unsigned nslots = (unsigned)((C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap);
     float* __restrict__ X = P.sp[S].x[cb];
     float* __restrict__ VX = P.sp[S].vx[cb];
-    const float* __restrict__ VY = P.sp[S].vy[cb];
-    const float* __restrict__ VZ = P.sp[S].vz[cb];
     const uint32_t* __restrict__ ID = P.sp[S].id[cb];
+    uint4* __restrict__ CAND = P.cand[S];
     const float qmdt = P.qmdt[S], dts = P.dt_s[S], inv_dx = P.inv_dx, Lf = P.Lf, pmax = P.pmax[S];
     const int Nc = P.Nc, Ng = P.Ng;
     const uint32_t seed = P.seed, tag = SpeciesTraits<S>::tag;
     const uint32_t step_lo = (uint32_t)step, step_hi = (uint32_t)(step >> 32);
-    const bool births = P.births_possible[S] != 0;
-    unsigned* cnt1 = (S == SP_E) ? P.wcount[B_E_FROM_E] : nullptr;
-    unsigned* cnt2 = (S == SP_E) ? P.wcount[B_OM_FROM_E] : (S == SP_OM ? P.wcount[B_E_FROM_OM] : nullptr);
 
     for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0ull; }
-    if (tid < MAXPROC) sh.events[tid] = 0u;
-    if (tid == 0) {
-        sh.absorbed[0] = sh.absorbed[1] = 0u;
-        sh.removed = 0u; sh.psteps = 0u; sh.warn_emax = 0u; sh.warn_tries = 0u; sh.nonfinite = 0u;
-    }
+    if (tid == 0) { sh.absorbed[0] = sh.absorbed[1] = 0u; sh.removed = 0u; sh.psteps = 0u; sh.nonfinite = 0u; }
     __syncthreads();
 
     // this warp's contiguous slot range
@@ -269,84 +233,10 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
     const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
     const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
 
-    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nremoved = 0, nnf = 0, wtries = 0, wemax = 0;
-    unsigned q1n = 0, q2n = 0, nb1 = 0, nb2 = 0;   // warp-uniform
-
-    // stage B: kinematics of up to 32 real collisions (q2), one per lane
-    auto run_real = [&](unsigned n) {
-        int bkind = 0;
-        float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
-        if ((unsigned)lane < n) {
-            const unsigned slot = q2s[lane];
-            const uint4 w0 = q2w[lane];
-            const float x = X[slot];
-            float vx = VX[slot], vy = VY[slot], vz = VZ[slot];
-            const uint32_t id = ID[slot];
-            bool alive;
-            const int k = collide<S>(P, cum, np, step, id, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
-            if (k >= 0) {
-                atomicAdd(&sh.events[k], 1u);
-                if (alive) {
-                    VX[slot] = vx; P.sp[S].vy[cb][slot] = vy; P.sp[S].vz[cb][slot] = vz;
-                } else {
-                    X[slot] = dead_marker();
-                    deposit_sub_global(P.Qf[S], x, inv_dx, Nc);   // its deposit may be flushed already
-                    ++nremoved;
-                }
-            }
-        }
-        if (births) {
-            const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1);
-            const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2);
-            if (S == SP_E) {
-                if (bkind == 1) {
-                    const unsigned r = nb1 + __popc(m1 & lt_mask);
-                    P.stage[B_E_FROM_E][r0 + r] = b1;
-                    P.stage[B_OP_FROM_E][r0 + r] = b2;
-                } else if (bkind == 2) {
-                    P.stage[B_OM_FROM_E][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
-                }
-            } else if (S == SP_OM) {
-                if (bkind == 2) P.stage[B_E_FROM_OM][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
-            }
-            nb1 += __popc(m1);
-            nb2 += __popc(m2);
-        }
-        __syncwarp();
-    };
-    auto push_real = [&](bool real, unsigned slot, uint4 w0) {
-        const unsigned m = __ballot_sync(0xffffffffu, real);
-        if (real) {
-            const unsigned q = q2n + __popc(m & lt_mask);
-            q2s[q] = slot; q2w[q] = w0;
-        }
-        q2n += __popc(m);
-        __syncwarp();
-        if (q2n >= 32u) {
-            run_real(32u);
-            const unsigned rest = q2n - 32u;     // < 32: lane q moves entry 32 + q
-            if ((unsigned)lane < rest) { const unsigned s0 = q2s[32 + lane]; const uint4 w1 = q2w[32 + lane]; q2s[lane] = s0; q2w[lane] = w1; }
-            q2n = rest;
-            __syncwarp();
-        }
-    };
-    // stage A: up to 32 candidates (q1), one per lane
-    auto run_cand = [&](unsigned n) {
-        bool real = false;
-        unsigned slot = 0;
-        uint4 w0 = make_uint4(0u, 0u, 0u, 0u);
-        if ((unsigned)lane < n) {
-            slot = q1s[lane];
-            w0 = q1w[lane];
-            if (S == SP_E) real = electron_is_real(P, cum, np, w0, VX[slot], VY[slot], VZ[slot]);
-            else real = true;    // ion candidates are rare: straight to stage B
-        }
-        push_real(real, slot, w0);
-    };
-
+    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0;
+    unsigned ncand = 0;   // warp-uniform: candidates of this warp so far
     for (unsigned g0 = r0; g0 < r1; g0 += ROUND) {
         const bool full = g0 + ROUND <= r1;
-        // all loads of the round first (independent, in flight together)
         float xs[4], vxs[4];
         uint32_t ids[4];
 #pragma unroll
@@ -371,9 +261,9 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
                 vx = fmaf(qmdt, Ep, vx);
                 x = fmaf(vx, dts, x);
                 ++psteps;
-                if (x < 0.0f) { ++nabs0; ++nremoved; x = dead_marker(); }
-                else if (x >= Lf) { ++nabs1; ++nremoved; x = dead_marker(); }
-                else if (!(x >= 0.0f) || !isfinite(vx)) { ++nnf; ++nremoved; x = dead_marker(); }
+                if (x < 0.0f) { ++nabs0; x = dead_marker(); }
+                else if (x >= Lf) { ++nabs1; x = dead_marker(); }
+                else if (!(x >= 0.0f) || !isfinite(vx)) { ++nnf; x = dead_marker(); }
                 else {
                     // CIC deposit as (count, sum of r) per cell: node c gets
                     // 2^16 count_c - rsum_c, node c+1 gets rsum_c
@@ -388,41 +278,18 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
                 X[i] = x;
                 VX[i] = vx;
             }
+            // candidates go to the warp's list in slot order: {slot, w1, w2, w3}
             const unsigned cm = __ballot_sync(0xffffffffu, cand);
-            if (cand) {
-                const unsigned q = q1n + __popc(cm & lt_mask);
-                q1s[q] = i; q1w[q] = w;
-            }
-            q1n += __popc(cm);
-        }
-        __syncwarp();
-        while (q1n >= 32u) {
-            run_cand(32u);
-            const unsigned rest = q1n - 32u;
-            for (unsigned q = lane; q < rest; q += 32u) {
-                const unsigned s0 = q1s[32 + q];
-                const uint4 w1 = q1w[32 + q];
-                q1s[q] = s0; q1w[q] = w1;
-            }
-            q1n = rest;
-            __syncwarp();
+            if (cand) CAND[r0 + ncand + __popc(cm & lt_mask)] = make_uint4(i, w.y, w.z, w.w);
+            ncand += __popc(cm);
         }
     }
-    if (q1n > 0) run_cand(q1n);
-    if (q2n > 0) run_real(q2n);
-    if (births && lane == 0) {
-        if (cnt1) cnt1[gw] = nb1;
-        if (cnt2) cnt2[gw] = nb2;
-    }
-    // per-thread counters into the block's; the block's deposit and counters
-    // into the global accumulators
+    if (lane == 0) P.ccount[S][gw] = ncand;
     if (psteps) atomicAdd(&sh.psteps, psteps);
     if (nabs0) atomicAdd(&sh.absorbed[0], nabs0);
     if (nabs1) atomicAdd(&sh.absorbed[1], nabs1);
-    if (nremoved) atomicAdd(&sh.removed, nremoved);
+    if (nabs0 + nabs1 + nnf) atomicAdd(&sh.removed, nabs0 + nabs1 + nnf);
     if (nnf) atomicAdd(&sh.nonfinite, nnf);
-    if (wtries) atomicAdd(&sh.warn_tries, wtries);
-    if (wemax) atomicAdd(&sh.warn_emax, wemax);
     __syncthreads();
     for (int c = tid; c < Nc; c += BLOCK) {
         const unsigned long long v = hist[c];
@@ -432,7 +299,6 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
             if (rsum) atomicAdd(&P.Qf[S][c + 1], rsum);
         }
     }
-    if (tid < np && sh.events[tid]) atomicAdd(&C->cnt.events[S][tid], (unsigned long long)sh.events[tid]);
     if (tid == 0) {
         if (sh.absorbed[0]) atomicAdd(&C->cnt.absorbed[S][0], (unsigned long long)sh.absorbed[0]);
         if (sh.absorbed[1]) atomicAdd(&C->cnt.absorbed[S][1], (unsigned long long)sh.absorbed[1]);
@@ -441,9 +307,168 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
             atomicAdd(&C->cnt.particle_steps, (unsigned long long)sh.psteps);
             atomicAdd(&C->cnt.psteps[S], (unsigned long long)sh.psteps);
         }
-        if (sh.warn_emax) atomicAdd(&C->cnt.warn_emax, (unsigned long long)sh.warn_emax);
-        if (sh.warn_tries) atomicAdd(&C->cnt.warn_tries, (unsigned long long)sh.warn_tries);
         if (sh.nonfinite) atomicOr(&C->error_flags, ERR_NONFINITE);
+    }
+}
+
+// Collision candidates of one species for this step: one warp per warp of
+// the particle kernel, walking that warp's candidate list in slot order.
+// Electrons are first filtered 32 at a time (energy against the total rate);
+// the real collisions, and all ion candidates, go through the out-of-line
+// kinematics 32 at a time.  Births are ranked with ballots and staged at the
+// particle warp's slot range with their count.
+template <int S>
+__global__ void __launch_bounds__(BLOCK) k_cand(Params P) {
+    __shared__ unsigned events[MAXPROC];
+    __shared__ unsigned sh_removed, sh_wtries, sh_wemax;
+    __shared__ uint4 q2w_all[WARPS][Q2];
+    __shared__ unsigned q2s_all[WARPS][Q2];
+    __shared__ float4 q2v_all[WARPS][Q2];     // x, vx, vy, vz of the queued particle
+    const int np = P.nproc[S];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    uint4* q2w = q2w_all[warp];
+    unsigned* q2s = q2s_all[warp];
+    float4* q2v = q2v_all[warp];
+    const float* __restrict__ cum = P.cum[S];
+    if (tid < MAXPROC) events[tid] = 0u;
+    if (tid == 0) { sh_removed = 0u; sh_wtries = 0u; sh_wemax = 0u; }
+    __syncthreads();
+
+    DevCtrl* C = P.ctrl;
+    const unsigned long long step = C->step;
+    const unsigned cb = C->cur[S];
+    const unsigned nslots = (unsigned)((C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap);
+    float* __restrict__ X = P.sp[S].x[cb];
+    float* __restrict__ VX = P.sp[S].vx[cb];
+    float* __restrict__ VY = P.sp[S].vy[cb];
+    float* __restrict__ VZ = P.sp[S].vz[cb];
+    const uint32_t* __restrict__ ID = P.sp[S].id[cb];
+    const uint4* __restrict__ CAND = P.cand[S];
+    const float inv_dx = P.inv_dx;
+    const int Nc = P.Nc;
+    const bool births = P.births_possible[S] != 0;
+    unsigned* cnt1 = (S == SP_E) ? P.wcount[B_E_FROM_E] : nullptr;
+    unsigned* cnt2 = (S == SP_E) ? P.wcount[B_OM_FROM_E] : (S == SP_OM ? P.wcount[B_E_FROM_OM] : nullptr);
+    const unsigned W = P.push_warps[S];
+    const unsigned R = warp_range_len(nslots, W);
+    unsigned wtries = 0, wemax = 0, nremoved = 0;
+
+    for (unsigned gw = blockIdx.x * WARPS + warp; gw < W; gw += gridDim.x * WARPS) {
+        const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
+        const unsigned n = P.ccount[S][gw];
+        unsigned q2n = 0, nb1 = 0, nb2 = 0;   // warp-uniform
+
+        // kinematics of lane's particle (has = lane holds one), births ranked
+        auto run_real = [&](bool has, unsigned slot, uint4 w0, float x, float vx, float vy, float vz) {
+            int bkind = 0;
+            float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
+            if (has) {
+                const uint32_t id = ID[slot];
+                bool alive;
+                const int k = collide<S>(P, cum, np, step, id, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
+                if (k >= 0) {
+                    atomicAdd(&events[k], 1u);
+                    if (alive) {
+                        VX[slot] = vx; VY[slot] = vy; VZ[slot] = vz;
+                    } else {
+                        X[slot] = dead_marker();
+                        deposit_sub_global(P.Qf[S], x, inv_dx, Nc);
+                        ++nremoved;
+                    }
+                }
+            }
+            if (births) {
+                const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1);
+                const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2);
+                if (S == SP_E) {
+                    if (bkind == 1) {
+                        const unsigned r = nb1 + __popc(m1 & lt_mask);
+                        P.stage[B_E_FROM_E][r0 + r] = b1;
+                        P.stage[B_OP_FROM_E][r0 + r] = b2;
+                    } else if (bkind == 2) {
+                        P.stage[B_OM_FROM_E][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
+                    }
+                } else if (S == SP_OM) {
+                    if (bkind == 2) P.stage[B_E_FROM_OM][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
+                }
+                nb1 += __popc(m1);
+                nb2 += __popc(m2);
+            }
+            __syncwarp();
+        };
+
+        auto run_queue = [&](unsigned m) {
+            const bool has = (unsigned)lane < m;
+            const float4 v = has ? q2v[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            run_real(has, has ? q2s[lane] : 0u, has ? q2w[lane] : make_uint4(0u, 0u, 0u, 0u), v.x, v.y, v.z, v.w);
+        };
+        // 128 candidates per pass, four per lane, all their loads in flight together
+        for (unsigned c0 = 0; c0 < n; c0 += 128) {
+            unsigned slot[4];
+            uint4 w0[4];
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned ci = c0 + 32u * k + lane;
+                if (ci < n) {
+                    const uint4 e = CAND[r0 + ci];
+                    slot[k] = e.x;
+                    w0[k] = make_uint4(0u, e.y, e.z, e.w);   // word 0 was the candidate draw
+                } else {
+                    slot[k] = 0xFFFFFFFFu;
+                    w0[k] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned sl = slot[k];
+                v[k] = (sl != 0xFFFFFFFFu) ? make_float4(X[sl], VX[sl], VY[sl], VZ[sl]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (c0 + 32u * k >= n) break;          // warp-uniform
+                const bool in = slot[k] != 0xFFFFFFFFu;
+                if (S != SP_E) {
+                    // ion candidates all need the target sample: straight on
+                    run_real(in, in ? slot[k] : 0u, w0[k], v[k].x, v[k].y, v[k].z, v[k].w);
+                    continue;
+                }
+                const bool real = in && electron_is_real(P, cum, np, w0[k], v[k].y, v[k].z, v[k].w);
+                const unsigned m = __ballot_sync(0xffffffffu, real);
+                if (real) {
+                    const unsigned q = q2n + __popc(m & lt_mask);
+                    q2s[q] = slot[k]; q2w[q] = w0[k]; q2v[q] = v[k];
+                }
+                q2n += __popc(m);
+                __syncwarp();
+                if (q2n >= 32u) {
+                    run_queue(32u);
+                    const unsigned rest = q2n - 32u;    // < 32: lane q moves entry 32 + q
+                    if ((unsigned)lane < rest) {
+                        const unsigned s0 = q2s[32 + lane]; const uint4 w1 = q2w[32 + lane]; const float4 v1 = q2v[32 + lane];
+                        q2s[lane] = s0; q2w[lane] = w1; q2v[lane] = v1;
+                    }
+                    q2n = rest;
+                    __syncwarp();
+                }
+            }
+        }
+        if (q2n > 0) run_queue(q2n);
+        if (births && lane == 0) {
+            if (cnt1) cnt1[gw] = nb1;
+            if (cnt2) cnt2[gw] = nb2;
+        }
+    }
+    if (nremoved) atomicAdd(&sh_removed, nremoved);
+    if (wtries) atomicAdd(&sh_wtries, wtries);
+    if (wemax) atomicAdd(&sh_wemax, wemax);
+    __syncthreads();
+    if (tid < np && events[tid]) atomicAdd(&C->cnt.events[S][tid], (unsigned long long)events[tid]);
+    if (tid == 0) {
+        if (sh_removed) atomicAdd(&C->removed[S], (unsigned long long)sh_removed);
+        if (sh_wtries) atomicAdd(&C->cnt.warn_tries, (unsigned long long)sh_wtries);
+        if (sh_wemax) atomicAdd(&C->cnt.warn_emax, (unsigned long long)sh_wemax);
     }
 }
 
@@ -483,7 +508,8 @@ __global__ void __launch_bounds__(BLOCK) k_deposit(Params P) {
 }  // namespace
 
 size_t push_smem_bytes(int species, const Params& P) {
-    return smem_layout(P.Ng, P.nproc[species]).total;
+    (void)species;
+    return align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng) + sizeof(unsigned long long) * P.Ng;
 }
 
 void launch_push(int species, const Params& P, int grid, cudaStream_t s) {
@@ -491,6 +517,12 @@ void launch_push(int species, const Params& P, int grid, cudaStream_t s) {
     if (species == SP_E) k_push<SP_E><<<grid, BLOCK, sm, s>>>(P);
     else if (species == SP_OM) k_push<SP_OM><<<grid, BLOCK, sm, s>>>(P);
     else k_push<SP_OP><<<grid, BLOCK, sm, s>>>(P);
+}
+
+void launch_cand(int species, const Params& P, int grid, cudaStream_t s) {
+    if (species == SP_E) k_cand<SP_E><<<grid, BLOCK, 0, s>>>(P);
+    else if (species == SP_OM) k_cand<SP_OM><<<grid, BLOCK, 0, s>>>(P);
+    else k_cand<SP_OP><<<grid, BLOCK, 0, s>>>(P);
 }
 
 void launch_deposit(int species, const Params& P, int grid, cudaStream_t s) {

@@ -19,12 +19,11 @@
 #include "internal.h"
 
 namespace o2 {
-cudaError_t configure_pair_smem(size_t bytes);
 }
 
 // particle kernels run at most this many blocks per SM (bounds the per-warp
 // birth counts the field kernel scans in shared memory)
-constexpr int MAX_PUSH_BLOCKS_PER_SM = 4;
+constexpr int MAX_PUSH_BLOCKS_PER_SM = 8;
 
 using namespace o2;
 
@@ -364,10 +363,14 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     P.wcount[B_OP_FROM_E] = P.wcount[B_E_FROM_E];
     TRY(ctx_alloc(c, &P.wcount[B_OM_FROM_E], max_warps));
     TRY(ctx_alloc(c, &P.wcount[B_E_FROM_OM], max_warps));
+    for (int s = 0; s < NSP; ++s) {
+        TRY(ctx_alloc(c, &P.cand[s], cfg->capacity[s] + 128));
+        TRY(ctx_alloc(c, &P.ccount[s], max_warps));
+    }
     const unsigned long long tiles_ion = std::max(ceil_div(cfg->capacity[SP_OM], TILE), ceil_div(cfg->capacity[SP_OP], TILE)) + 1;
     TRY(ctx_alloc(c, &P.hist[0], tiles_ion * Nc));
     TRY(ctx_alloc(c, &P.hist[1], tiles_ion * Nc));
-    TRY(ctx_alloc(c, &P.cellinfo, 4 * (size_t)Nc));
+    TRY(ctx_alloc(c, &P.ptot, 2 * (size_t)Nc));
     P.max_removals = (unsigned)std::max<unsigned long long>(1, std::min(cfg->capacity[SP_OM], cfg->capacity[SP_OP]));
     TRY(ctx_alloc(c, &P.removal, 2 * (size_t)P.max_removals));
     TRY(ctx_alloc(c, &c->d_gticket, 1));
@@ -382,8 +385,8 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     }
     smax = std::max(smax, sizeof(unsigned) * (size_t)Ng);
     TRY(configure_push_smem(smax));
-    TRY(configure_pair_smem(pair_smem_bytes(Nc)));
     TRY(configure_field_smem(field_smem_bytes(P)));
+    TRY(configure_pair_hist_smem(Nc));
     for (int s = 0; s < NSP; ++s) P.nproc[s] = 0;
     c->grid_pair = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(tiles_ion, 8ull * c->num_sms));
     c->grid_compact = 4 * c->num_sms;
@@ -605,12 +608,14 @@ int o2pic_step(o2pic_ctx* c, uint64_t nsteps, void* stream) {
         }
         const bool ion = (c->host_step % S) == 0;
         launch(c, KK_PUSH_E, s, [&] { launch_push(SP_E, P, c->grid_push[SP_E], s); });
+        if (P.nproc[SP_E]) launch(c, KK_CAND_E, s, [&] { launch_cand(SP_E, P, c->grid_push[SP_E], s); });
         if (ion) {
             launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
+            if (P.nproc[SP_OM]) launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
             launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
+            if (P.nproc[SP_OP]) launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
             if (P.have_neutral) {
-                launch(c, KK_PAIR_SCAN, s, [&] { launch_pair_hist(P, c->grid_compact, s); });
-                launch(c, KK_PAIR_SCAN, s, [&] { launch_pair_scan(P, s); });
+                launch(c, KK_PAIR_HIST, s, [&] { launch_pair_hist(P, c->grid_compact, s); });
                 launch(c, KK_PAIR, s, [&] { launch_pair(P, c->grid_pair, s); });
             }
         }

@@ -124,9 +124,11 @@ def test_parity_walls_and_edges(torch_cuda):
     compare_counters(g.stats(), o.counters(), nproc_of(procs))
 
 
-def test_neutralization_parity(torch_cuda):
+@pytest.mark.parametrize("n_om,n_op", [(30000, 26000), (26000, 30000), (9000, 8192)])
+def test_neutralization_parity(torch_cuda, n_om, n_op):
     """Many (17) reactions: a large constant rate coefficient, ions at rest in
-    a few cells, the library's pairing against the oracle's, pair for pair."""
+    a few cells, the library's pairing against the oracle's, pair for pair.
+    Cases with more O- than O2+ per cell, fewer, and ragged tiles."""
     Nc = 32
     cfg = inputs.base_config(L=0.02, n_cells=Nc, U=0.0, p=10.0, C_meta=0.0, ion_subcycle=2, weight=2e9, seed=3,
                              steps_per_cycle=400)
@@ -136,7 +138,7 @@ def test_neutralization_parity(torch_cuda):
     procs = [xsec.constant_rate_process(1, xsec.NEUTRALIZE, K0, 1.0, mu, target=xsec.T_ION)]
     rng = np.random.default_rng(7)
     st = []
-    for s, n in enumerate((500, 30000, 26000)):
+    for s, n in enumerate((500, n_om, n_op)):
         x = ((rng.integers(0, Nc, n) + 0.05 + 0.9 * rng.random(n)) * dx).astype(np.float32)
         v = (rng.standard_normal((3, n)) * (1e5 if s == 0 else 300.0)).astype(np.float32)
         st.append(dict(x=x, vx=v[0].copy(), vy=v[1].copy(), vz=v[2].copy(), id=np.arange(n, dtype=np.uint32)))
@@ -146,7 +148,7 @@ def test_neutralization_parity(torch_cuda):
         o.step(2)
         compare_particles(g, o)
         compare_counters(g.stats(), o.counters(), nproc_of(procs))
-    assert o.counters()["neutralized"] > 500
+    assert o.counters()["neutralized"] > 0.01 * min(n_om, n_op)
 
 
 def test_compaction_keeps_order(torch_cuda):
