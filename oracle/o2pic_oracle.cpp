@@ -26,8 +26,9 @@
 //   * Eq. 1 (associative detachment) and the Landau-Zener sigma_n enter as
 //     cross-section data;
 //   * ion-ion neutralization (17) as a binary, cell-local (DSMC-like) process.
-// Where the paper is silent the readings listed in the design notes are used
-// (leapfrog, CIC, Thomas, isotropic scattering, birth velocities, pairing).
+// Where the paper is silent a reading is taken and stated beside the code
+// that implements it (leapfrog, CIC, the Poisson discretization, isotropic
+// scattering, birth velocities, pairing).
 //
 // Parity status of each function is stated next to it.  All functions here
 // are pinned by tests under tests/ (closed forms, invariants, brute force);

@@ -71,8 +71,11 @@ __device__ __forceinline__ void block_scan_smem(long long* a, int n, long long* 
 // count.  The counts are scanned into per-warp offsets in shared memory, and
 // every thread then places single births (found by a binary search over the
 // offsets), so the work spreads over the block however the births cluster.
+// A birth's CIC charge goes to the shared-memory accumulator bq[species][node]
+// (32-bit: at most 65535 births per species and step, checked by the caller),
+// or, above that, straight to the global Qb.
 __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP], int d, unsigned long long slot,
-                            unsigned long long id64, float4 b) {
+                            unsigned long long id64, float4 b, unsigned* bq) {
     const SpeciesBuf& B = P.sp[d];
     if (slot >= B.cap) { atomicOr(&C->error_flags, ERR_CAPACITY); return; }
     if (id64 > 0xFFFFFFFFull) atomicOr(&C->error_flags, ERR_ID);
@@ -85,8 +88,13 @@ __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP]
     int j; float frac;
     cell_of(b.x, P.inv_dx, P.Nc, j, frac);
     const uint32_t r = cic_r(frac);
-    atomicAdd(&P.Qb[d][j], (unsigned long long)(65536u - r));
-    atomicAdd(&P.Qb[d][j + 1], (unsigned long long)r);
+    if (bq) {
+        atomicAdd(&bq[d * P.Ng + j], 65536u - r);
+        atomicAdd(&bq[d * P.Ng + j + 1], r);
+    } else {
+        atomicAdd(&P.Qb[d][j], (unsigned long long)(65536u - r));
+        atomicAdd(&P.Qb[d][j + 1], (unsigned long long)r);
+    }
 }
 
 // Exclusive block scan of two 32-bit counts packed in 64 bits (FT threads).
@@ -118,8 +126,8 @@ __device__ __forceinline__ unsigned long long block_excl_scan2(unsigned long lon
 }
 
 // Offsets of the per-warp counts c1 (and c2) of nu warps into p1[0..nu] (p2).
-__device__ void unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu, unsigned* p1, unsigned* p2,
-                             unsigned long long* ws, unsigned long long* tot) {
+__device__ unsigned long long unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu, unsigned* p1,
+                                           unsigned* p2, unsigned long long* ws) {
     const int t = threadIdx.x;
     const unsigned per = (nu + FT - 1) / FT, u0 = t * per, u1 = (u0 + per < nu) ? u0 + per : nu;
     unsigned long long mine = 0;
@@ -137,8 +145,22 @@ __device__ void unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu
         r1 += a; r2 += b;
     }
     if (t == 0) { p1[nu] = (unsigned)all; p2[nu] = (unsigned)(all >> 32); }
-    *tot = all;
     __syncthreads();
+    return all;
+}
+
+// Start moving a line into this SM's L1 (the loads that follow hit it).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Prefetch a thread's share of the per-warp counts of unit_offsets.
+__device__ __forceinline__ void prefetch_units(const unsigned* c1, const unsigned* c2, unsigned nu) {
+    const unsigned per = (nu + FT - 1) / FT, u0 = threadIdx.x * per, u1 = (u0 + per < nu) ? u0 + per : nu;
+    for (unsigned u = u0; u < u1; u += 32) {   // 32 counts per 128-byte line
+        prefetch_l1(c1 + u);
+        if (c2) prefetch_l1(c2 + u);
+    }
 }
 
 // The warp that staged birth number b (largest u with p[u] <= b).
@@ -155,56 +177,6 @@ struct CtrlSnap {
     unsigned long long step, slots[NSP], live[NSP], removed[NSP];
     unsigned next_id[NSP], cur[NSP], removals;
 };
-
-__device__ void place_births(const Params& P, DevCtrl* C, const CtrlSnap& cs, int pushed_mask, unsigned* p1,
-                             unsigned* p2, unsigned long long* ws, unsigned long long tot[NB]) {
-    const int t = threadIdx.x;
-    for (int k = 0; k < NB; ++k) tot[k] = 0;
-    // electron kernel: ionizations (e + O2+) and attachments (O-)
-    if (P.births_possible[SP_E]) {
-        const unsigned ns = (unsigned)(cs.slots[SP_E] < P.sp[SP_E].cap ? cs.slots[SP_E] : P.sp[SP_E].cap);
-        const unsigned nu = P.push_warps[SP_E], R = warp_range_len(ns, nu);
-        unsigned long long all;
-        unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu, p1, p2, ws, &all);
-        const unsigned n1 = (unsigned)all, n2 = (unsigned)(all >> 32);
-        for (unsigned b = t; b < n1; b += FT) {
-            const unsigned u = find_unit(p1, nu, b);
-            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
-            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + b, (unsigned long long)cs.next_id[SP_E] + b,
-                        P.stage[B_E_FROM_E][sb]);
-            place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + b, (unsigned long long)cs.next_id[SP_OP] + b,
-                        P.stage[B_OP_FROM_E][sb]);
-        }
-        for (unsigned b = t; b < n2; b += FT) {
-            const unsigned u = find_unit(p2, nu, b);
-            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p2[u]);
-            place_birth(P, C, cs.cur, SP_OM, cs.slots[SP_OM] + b, (unsigned long long)cs.next_id[SP_OM] + b,
-                        P.stage[B_OM_FROM_E][sb]);
-        }
-        tot[B_E_FROM_E] = n1;
-        tot[B_OP_FROM_E] = n1;
-        tot[B_OM_FROM_E] = n2;
-        __syncthreads();
-    }
-    // O- kernel (ion steps): detachment electrons, after the electron kernel's
-    if (((pushed_mask >> SP_OM) & 1) && P.births_possible[SP_OM]) {
-        const unsigned ns = (unsigned)(cs.slots[SP_OM] < P.sp[SP_OM].cap ? cs.slots[SP_OM] : P.sp[SP_OM].cap);
-        const unsigned nu = P.push_warps[SP_OM], R = warp_range_len(ns, nu);
-        unsigned long long all;
-        unit_offsets(P.wcount[B_E_FROM_OM], nullptr, nu, p1, p2, ws, &all);
-        const unsigned n = (unsigned)all;
-        const unsigned long long base = tot[B_E_FROM_E];
-        for (unsigned b = t; b < n; b += FT) {
-            const unsigned u = find_unit(p1, nu, b);
-            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
-            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + base + b, (unsigned long long)cs.next_id[SP_E] + base + b,
-                        P.stage[B_E_FROM_OM][sb]);
-        }
-        tot[B_E_FROM_OM] = n;
-    }
-    __threadfence();
-    __syncthreads();
-}
 
 // Block-wide inclusive scans of two int64 arrays a, b [0..n) in shared memory
 // at once (blocked: thread t owns [t*per, (t+1)*per)).
@@ -249,89 +221,169 @@ __device__ __forceinline__ void block_scan_smem_pair(long long* a, long long* b,
 
 // mode 0: end of a step (pushed_mask = species pushed this step);
 // mode 1: after a load (all species freshly deposited into Qf).
-// Dynamic shared memory: S, U as int64 [Ng], then two u32 [max warps + 1].
+// Dynamic shared memory: S, U as int64 [Ng] (before the charge commit the
+// same bytes hold the births' 32-bit charge bq[3][Ng]), then two u32
+// [max warps + 1].  Every load that does not depend on another is issued at
+// the start: the step state, the charges of the thread's nodes, the per-warp
+// birth counts and U sin(2 pi f t).
 __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
     extern __shared__ long long fsm[];
     __shared__ long long ws[64];
     __shared__ unsigned long long ws2[32];
     __shared__ CtrlSnap cs;
     __shared__ long long sh_R0, sh_RN;
+    __shared__ double sh_V0, sh_D0;
     DevCtrl* C = P.ctrl;
     const int N = P.Nc, Ng = P.Ng;
     const int t = threadIdx.x;
     long long* Ss = fsm;          // S_j = sum_{k=1..j} R_k
     long long* Us = fsm + Ng;     // U_j = sum_{k=1..j} k R_k   (T_j = j S_{j-1} - U_{j-1})
+    unsigned* bq = reinterpret_cast<unsigned*>(fsm);
     unsigned* p1 = reinterpret_cast<unsigned*>(fsm + 2 * Ng);
     unsigned* p2 = p1 + (P.max_push_warps + 1);
+    const bool births_e = mode == 0 && P.births_possible[SP_E];
+    const bool births_om = mode == 0 && ((pushed_mask >> SP_OM) & 1) && P.births_possible[SP_OM];
 
-    // snapshot of the step state, read in parallel
+    // ---- loads: the step state and U sin(2 pi f t) now; the charges and the
+    // birth counts into L1, read where they are used
     if (t < NSP) {
         cs.slots[t] = C->slots[t]; cs.live[t] = C->live[t]; cs.removed[t] = C->removed[t];
         cs.next_id[t] = C->next_id[t]; cs.cur[t] = C->cur[t];
     } else if (t == 32) {
-        cs.step = C->step;
+        const unsigned long long step = C->step;
+        cs.step = step;
         cs.removals = C->removals;
+        sh_V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
     }
+    for (int j = t * 16; j < Ng; j += FT * 16) {   // 16 u64 per 128-byte line
+#pragma unroll
+        for (int s = 0; s < NSP; ++s) {
+            prefetch_l1(&P.Qf[s][j]);
+            prefetch_l1(&P.Q[s][j]);
+            if (mode == 0) prefetch_l1(&P.Qacc[s][j]);
+        }
+    }
+    if (births_e) prefetch_units(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], P.push_warps[SP_E]);
+    if (births_om) prefetch_units(P.wcount[B_E_FROM_OM], nullptr, P.push_warps[SP_OM]);
+    for (int i = t; i < NSP * Ng; i += FT) bq[i] = 0u;
     __syncthreads();
+
+    // ---- births
     unsigned long long btot[NB];
     for (int k = 0; k < NB; ++k) btot[k] = 0;
-    if (mode == 0) place_births(P, C, cs, pushed_mask, p1, p2, ws2, btot);
+    bool bq_used = true;
+    if (births_e) {
+        const unsigned ns = (unsigned)(cs.slots[SP_E] < P.sp[SP_E].cap ? cs.slots[SP_E] : P.sp[SP_E].cap);
+        const unsigned nu = P.push_warps[SP_E], R = warp_range_len(ns, nu);
+        const unsigned long long all = unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu, p1, p2, ws2);
+        const unsigned n1 = (unsigned)all, n2 = (unsigned)(all >> 32);
+        unsigned* acc = (n1 < 65536u && n2 < 65536u) ? bq : nullptr;
+        bq_used = acc != nullptr;
+        for (unsigned b = t; b < n1; b += FT) {
+            const unsigned u = find_unit(p1, nu, b);
+            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
+            const float4 be = P.stage[B_E_FROM_E][sb], bo = P.stage[B_OP_FROM_E][sb];
+            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + b, (unsigned long long)cs.next_id[SP_E] + b, be, acc);
+            place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + b, (unsigned long long)cs.next_id[SP_OP] + b, bo, acc);
+        }
+        for (unsigned b = t; b < n2; b += FT) {
+            const unsigned u = find_unit(p2, nu, b);
+            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p2[u]);
+            place_birth(P, C, cs.cur, SP_OM, cs.slots[SP_OM] + b, (unsigned long long)cs.next_id[SP_OM] + b,
+                        P.stage[B_OM_FROM_E][sb], acc);
+        }
+        btot[B_E_FROM_E] = n1;
+        btot[B_OP_FROM_E] = n1;
+        btot[B_OM_FROM_E] = n2;
+        __syncthreads();
+    }
+    // O- kernel (ion steps): detachment electrons, after the electron kernel's
+    if (births_om) {
+        const unsigned ns = (unsigned)(cs.slots[SP_OM] < P.sp[SP_OM].cap ? cs.slots[SP_OM] : P.sp[SP_OM].cap);
+        const unsigned nu = P.push_warps[SP_OM], R = warp_range_len(ns, nu);
+        const unsigned n = (unsigned)unit_offsets(P.wcount[B_E_FROM_OM], nullptr, nu, p1, p2, ws2);
+        const unsigned long long base = btot[B_E_FROM_E];
+        unsigned* acc = (bq_used && base + n < 65536u) ? bq : nullptr;
+        for (unsigned b = t; b < n; b += FT) {
+            const unsigned u = find_unit(p1, nu, b);
+            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
+            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + base + b, (unsigned long long)cs.next_id[SP_E] + base + b,
+                        P.stage[B_E_FROM_OM][sb], acc);
+        }
+        btot[B_E_FROM_OM] = n;
+        if (!acc) bq_used = false;
+        __syncthreads();
+    }
+    // births that went to the global accumulator (a step with > 65535 births)
+    const bool qb_global = __syncthreads_or(!bq_used);
+    if (qb_global) __threadfence();
+    __syncthreads();
 
-    // charge commit, moments, net charge (coalesced, all loads before stores)
-    for (int j = t; j < Ng; j += FT) {
-        unsigned long long qf[NSP], qo[NSP], qb[NSP], qa[NSP];
+    // ---- charge commit, moments, net charge.  bq shares its bytes with S and
+    // U: every bq value is read (and net kept in registers) before S, U are
+    // written.
+    constexpr int JK = (MAX_NODES + FT - 1) / FT;
+    long long netr[JK];
 #pragma unroll
-        for (int s = 0; s < NSP; ++s) {
-            qf[s] = __ldcg(&P.Qf[s][j]);
-            qo[s] = P.Q[s][j];
-            qb[s] = __ldcg(&P.Qb[s][j]);
-            qa[s] = (mode == 0) ? P.Qacc[s][j] : 0ull;
-        }
-        long long net = 0;
+    for (int k = 0; k < JK; ++k) {
+        const int j = t + k * FT;
+        netr[k] = 0;
+        if (j < Ng) {
+            long long net = 0;
 #pragma unroll
-        for (int s = 0; s < NSP; ++s) {
-            const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
-            const unsigned long long q = (fresh ? qf[s] : qo[s]) + qb[s];
-            P.Q[s][j] = q;
-            P.Qf[s][j] = 0ull;
-            P.Qb[s][j] = 0ull;
-            if (mode == 0) P.Qacc[s][j] = qa[s] + q;
-            net += (s == SP_OP) ? (long long)q : -(long long)q;
+            for (int s = 0; s < NSP; ++s) {
+                const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
+                unsigned long long q = (fresh ? P.Qf[s][j] : P.Q[s][j]) + bq[s * Ng + j];
+                if (qb_global) { q += __ldcg(&P.Qb[s][j]); P.Qb[s][j] = 0ull; }
+                P.Q[s][j] = q;
+                P.Qf[s][j] = 0ull;
+                if (mode == 0) P.Qacc[s][j] += q;
+                net += (s == SP_OP) ? (long long)q : -(long long)q;
+            }
+            netr[k] = net;
         }
-        Ss[j] = (j >= 1) ? net : 0;                    // scanned below
-        Us[j] = (j >= 1) ? (long long)j * net : 0;
-        if (j == 0) sh_R0 = net;
-        if (j == N) sh_RN = net;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < JK; ++k) {
+        const int j = t + k * FT;
+        if (j < Ng) {
+            Ss[j] = (j >= 1) ? netr[k] : 0;                    // scanned below
+            Us[j] = (j >= 1) ? (long long)j * netr[k] : 0;
+            if (j == 0) sh_R0 = netr[k];
+            if (j == N) sh_RN = netr[k];
+        }
     }
     __syncthreads();
     block_scan_smem_pair(Ss, Us, Ng, ws);
     const double c = P.c_field;
-    const unsigned long long step = cs.step;
     // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load), evaluated
     // on the host in FP64 and staged in a ring indexed by the step.  D0 once
     // per block: FP64 throughput on this GPU is low.
-    __shared__ double sh_V0, sh_D0;
     if (t == 0) {
-        const double v = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
         const long long TN = (long long)N * Ss[N - 1] - Us[N - 1];
-        sh_V0 = v;
-        sh_D0 = (c * (double)TN - v) / (double)N;
+        const double D0 = (c * (double)TN - sh_V0) / (double)N;
+        sh_D0 = D0;
+        P.fVD[0] = sh_V0;
+        P.fVD[1] = D0;
     }
     __syncthreads();
-    const double V0 = sh_V0, D0 = sh_D0;
+    // E on the nodes (what the next push gathers).  The potential needs as
+    // much FP64 work again and only diagnostics read it: S, U, V0 and D0 are
+    // kept so that k_phi evaluates it with the same expressions on request.
+    const double D0 = sh_D0, D2 = 2.0 * sh_D0;   // 2 D0 is exact
     const long long R0 = sh_R0, RN = sh_RN;
     for (int j = t; j < Ng; j += FT) {
         double E;
         if (j == 0) E = (-D0 - c * (double)R0) * P.inv_dx64;
         else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)RN) * P.inv_dx64;
-        else E = (c * (double)(Ss[j] + Ss[j - 1]) - 2.0 * D0) * P.inv_2dx64;
-        const long long Tj = (j >= 1) ? (long long)j * Ss[j - 1] - Us[j - 1] : 0;
-        const double phi = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Tj);
+        else E = (c * (double)(Ss[j] + Ss[j - 1]) - D2) * P.inv_2dx64;
         P.Ef[j] = (float)E;
-        P.phi[j] = phi;
+        P.fS[j] = Ss[j];
+        P.fU[j] = Us[j];
     }
     // per-cell ion totals of (17): zero for the next ion step
-    for (int c = t; c < 2 * P.Nc; c += FT) P.ptot[c] = 0u;
+    for (int k = t; k < 2 * N; k += FT) P.ptot[k] = 0u;
     if (mode != 0) {
         if (t < NKK + NSP) C->ticket[t] = 0u;
         return;
@@ -367,7 +419,7 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
         if (nrem) atomicAdd(&C->cnt.neutralized, (unsigned long long)nrem);
         C->removals = 0u;
         atomicAdd(&C->acc_steps, 1ull);
-        C->step = step + 1;
+        C->step = cs.step + 1;
         atomicAdd(&C->epoch, 1ull);
     } else if (t >= 64 && t < 64 + NKK + NSP) {
         C->ticket[t - 64] = 0u;
@@ -523,6 +575,22 @@ __global__ void k_ln(const float* x, float* out, unsigned long long n) {
 
 size_t field_smem_bytes(const Params& P) {
     return 2 * sizeof(long long) * (size_t)P.Ng + 2 * sizeof(unsigned) * ((size_t)P.max_push_warps + 1);
+}
+
+// The potential of the last field solve: phi_0 = V0, phi_N = 0,
+// phi_j = V0 + j D0 - c T_j with T_j = j S_{j-1} - U_{j-1} (FP64, the
+// expressions of the closed-form solve).
+__global__ void k_phi(Params P) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = P.Nc;
+    if (j > N) return;
+    const double V0 = P.fVD[0], D0 = P.fVD[1], c = P.c_field;
+    const long long Tj = (j >= 1) ? (long long)j * P.fS[j - 1] - P.fU[j - 1] : 0;
+    P.phi[j] = (j == 0) ? V0 : (j == N ? 0.0 : V0 + (double)j * D0 - c * (double)Tj);
+}
+
+void launch_phi(const Params& P, cudaStream_t s) {
+    k_phi<<<(P.Ng + 255) / 256, 256, 0, s>>>(P);
 }
 
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s) {

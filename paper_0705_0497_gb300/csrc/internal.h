@@ -108,7 +108,10 @@ struct Params {
     const double* vring;         // electrode voltage U sin(2 pi f t_k) at t_k = k dt, slot k & vring_mask
     unsigned int vring_mask;
     float* Ef;                   // [Ng] gather field (FP32)
-    double* phi;                 // [Ng]
+    double* phi;                 // [Ng], evaluated on request from fS, fU, fVD
+    long long* fS;               // [Ng] S_j of the last field solve (exact prefix sums)
+    long long* fU;               // [Ng] U_j of the last field solve
+    double* fVD;                 // [2] V0, D0 of the last field solve
     unsigned long long* Q[NSP];  // committed node charge
     unsigned long long* Qf[NSP]; // fresh deposit of the species pushed this step
     unsigned long long* Qb[NSP]; // deposit of this step's births
@@ -157,6 +160,7 @@ void launch_pair_hist(const Params& P, int grid, cudaStream_t s);
 cudaError_t configure_pair_hist_smem(int Nc);
 void launch_pair(const Params& P, int grid, cudaStream_t s);
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s);
+void launch_phi(const Params& P, cudaStream_t s);
 void launch_compact(int species, const Params& P, int grid, cudaStream_t s);
 void launch_deposit(int species, const Params& P, int grid, cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, unsigned long long n, cudaStream_t s);

@@ -24,11 +24,11 @@
 //     the end-of-step kernel places them in parent order.
 #include "common.cuh"
 
-// Launch shape of the particle kernels (tuned per build; see the design notes):
-// minimum resident blocks per SM (caps registers) and unrolling of the four
-// particles a lane handles per round.
+// Launch shape of the particle kernels: minimum resident blocks per SM (caps
+// the registers; 4 timed fastest of 2, 3, 4 on the 512-cell, 1.6e7-particle
+// workload) and unrolling of the four particles a lane handles per round.
 #ifndef O2PIC_PUSH_MIN_BLOCKS
-#define O2PIC_PUSH_MIN_BLOCKS 2
+#define O2PIC_PUSH_MIN_BLOCKS 4
 #endif
 #ifndef O2PIC_PUSH_UNROLL
 #define O2PIC_PUSH_UNROLL 4
@@ -83,11 +83,37 @@ __device__ __noinline__ int collide(const Params& P, const float* cum, int np, u
     // null collision unless u1 nu_max falls below the total rate; then the
     // first process whose cumulative rate exceeds it (the last one if
     // rounding leaves none)
+    // the cumulative rates are read four processes at a time (loads in
+    // flight together); each value is grid_interp(cum, np, kk, i, w)
     const float target = u1 * P.numax[S];
-    if (!(target < grid_interp(cum, np, np - 1, i, w))) return -1;
+    const bool last = i >= NGRID - 1;
+    const float* row = cum + (size_t)(last ? NGRID - 1 : i) * np;
+    auto interp = [&](float a, float b) { return last ? a : fmaf(w, b - a, a); };
+    const float ta = row[np - 1], tb = last ? 0.0f : row[2 * np - 1];
+    float a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        a[j] = (j < np - 1) ? row[j] : 0.0f;
+        b[j] = (j < np - 1 && !last) ? row[np + j] : 0.0f;
+    }
+    if (!(target < interp(ta, tb))) return -1;
     int k = np - 1;
-    for (int kk = 0; kk < np - 1; ++kk) {
-        if (target < grid_interp(cum, np, kk, i, w)) { k = kk; break; }
+    for (int k0 = 0; k0 < np - 1; k0 += 4) {
+        if (k0 > 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int kk = k0 + j;
+                a[j] = (kk < np - 1) ? row[kk] : 0.0f;
+                b[j] = (kk < np - 1 && !last) ? row[np + kk] : 0.0f;
+            }
+        }
+        int f = -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kk = k0 + j;
+            if (f < 0 && kk < np - 1 && target < interp(a[j], b[j])) f = kk;
+        }
+        if (f >= 0) { k = f; break; }
     }
     const float thr = P.thr[S][k];
     if (E < thr) return -1;
@@ -364,7 +390,7 @@ __global__ void __launch_bounds__(BLOCK) k_cand(Params P) {
             int bkind = 0;
             float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
             if (has) {
-                const uint32_t id = ID[slot];
+                const uint32_t id = w0.x;   // word 0 (the candidate draw) is spent: it carries the id
                 bool alive;
                 const int k = collide<S>(P, cum, np, step, id, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
                 if (k >= 0) {
@@ -414,7 +440,7 @@ __global__ void __launch_bounds__(BLOCK) k_cand(Params P) {
                 if (ci < n) {
                     const uint4 e = CAND[r0 + ci];
                     slot[k] = e.x;
-                    w0[k] = make_uint4(0u, e.y, e.z, e.w);   // word 0 was the candidate draw
+                    w0[k] = make_uint4(0u, e.y, e.z, e.w);
                 } else {
                     slot[k] = 0xFFFFFFFFu;
                     w0[k] = make_uint4(0u, 0u, 0u, 0u);
@@ -423,7 +449,9 @@ __global__ void __launch_bounds__(BLOCK) k_cand(Params P) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const unsigned sl = slot[k];
-                v[k] = (sl != 0xFFFFFFFFu) ? make_float4(X[sl], VX[sl], VY[sl], VZ[sl]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool in = sl != 0xFFFFFFFFu;
+                v[k] = in ? make_float4(X[sl], VX[sl], VY[sl], VZ[sl]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                w0[k].x = in ? ID[sl] : 0u;
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {

@@ -347,6 +347,9 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     P.vring_mask = VRING - 1;
     TRY(ctx_alloc(c, &P.Ef, Ng));
     TRY(ctx_alloc(c, &P.phi, Ng));
+    TRY(ctx_alloc(c, &P.fS, Ng));
+    TRY(ctx_alloc(c, &P.fU, Ng));
+    TRY(ctx_alloc(c, &P.fVD, 2));
     for (int k = 0; k < NKK; ++k) {
         TRY(ctx_alloc(c, &P.lb_flag[k], max_tiles));
         TRY(ctx_alloc(c, &P.lb_val[k], 2 * max_tiles));
@@ -685,9 +688,14 @@ int o2pic_read_field(o2pic_ctx* c, double* phi, float* E) {
         int rc = prepare(c, c->stream);
         if (rc) return rc;
     }
+    cudaError_t e = cudaSuccess;
+    if (phi) {
+        e = cudaSetDevice(c->device);
+        if (e == cudaSuccess) { launch_phi(c->P, c->last); e = cudaGetLastError(); }
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
     int rc = sync_all(c);
     if (rc == O2PIC_E_CUDA) return rc;
-    cudaError_t e = cudaSuccess;
     if (phi) e = cudaMemcpy(phi, c->P.phi, sizeof(double) * c->P.Ng, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && E) e = cudaMemcpy(E, c->P.Ef, sizeof(float) * c->P.Ng, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e);
