@@ -233,6 +233,55 @@ int o2pic_compact_particles_noalloc(const float* x, const float* vx, const float
                                     const uint32_t* id, uint64_t n, float* ox, float* ovx, float* ovy, float* ovz,
                                     uint32_t* oid, uint64_t* n_out, void* stream);
 
+/* ---- Launch shape and batched stepping (many discharges, one graph) ----
+ *
+ * A parameter sweep (voltages, pressures, particle counts) runs many small
+ * discharges; each is one context.  A batch advances all of them together:
+ * one CUDA graph holds steps_per_launch time steps of every context, each
+ * context on its own branch, so their kernels run concurrently (the
+ * single-block field solves of different discharges on different SMs).  The
+ * method is unchanged: every context gives exactly the results of
+ * o2pic_step, whatever the batch and the launch shape. */
+
+/* Blocks of the particle kernels (push and collisions) per species, in
+ * [1, 8 * SMs]; results do not depend on them.  Defaults (set by
+ * o2pic_set_processes): as many as fit the GPU at once. */
+int o2pic_set_launch_shape(o2pic_ctx* ctx, const int32_t push_blocks[3]);
+int o2pic_get_launch_shape(o2pic_ctx* ctx, int32_t push_blocks[3]);
+
+typedef struct o2pic_batch o2pic_batch;   /* opaque, library-owned */
+
+/* Captures the graph.  ctxs: n >= 1 contexts on one device, each with
+ * processes set and particles loaded (borrowed: they must outlive the batch
+ * and are not to be stepped alone while it exists).  steps_per_launch in
+ * [1, 2048], a multiple of every context's ion_subcycle and compact_check.
+ * Errors: INVALID_ARG, STATE (a context without tables), CUDA. */
+int o2pic_batch_create(o2pic_ctx* const* ctxs, int32_t n, uint64_t steps_per_launch, o2pic_batch** out);
+
+/* Enqueues `launches` replays of the graph (launches * steps_per_launch
+ * steps of every context) on the batch's own stream; asynchronous. */
+int o2pic_batch_step(o2pic_batch* b, uint64_t launches);
+
+/* Waits for the batch and returns the first error latched by any context. */
+int o2pic_batch_synchronize(o2pic_batch* b);
+
+/* Autotuner: tries launch-shape policies (particle-kernel blocks from a
+ * target number of particles per warp, and the default full-GPU shape),
+ * times one graph replay of each on the real batch (these replays are real
+ * steps of the discharges: 7 policies x steps_per_launch steps), keeps the
+ * fastest and re-captures the graph.  The shapes stay set on the contexts,
+ * so a batch created afterwards with another steps_per_launch uses them. */
+#define O2PIC_TUNE_MAX 8
+typedef struct {
+    int32_t n;                                   /* policies tried */
+    int32_t particles_per_warp[O2PIC_TUNE_MAX];  /* 0 = default full-GPU shape */
+    double ms[O2PIC_TUNE_MAX];                   /* one replay, CUDA events */
+    int32_t chosen;                              /* index of the policy kept */
+} o2pic_tune_report;
+int o2pic_batch_autotune(o2pic_batch* b, o2pic_tune_report* report);
+
+void o2pic_batch_destroy(o2pic_batch* b);
+
 const char* o2pic_strerror(int code);
 
 void o2pic_destroy(o2pic_ctx* ctx);

@@ -44,6 +44,14 @@ class Process(ctypes.Structure):
                 ("E_eV", ctypes.POINTER(ctypes.c_double)), ("sigma_m2", ctypes.POINTER(ctypes.c_double))]
 
 
+TUNE_MAX = 8
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("particles_per_warp", ctypes.c_int32 * TUNE_MAX),
+                ("ms", ctypes.c_double * TUNE_MAX), ("chosen", ctypes.c_int32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("events", (ctypes.c_uint64 * MAXPROC) * NSP), ("absorbed", (ctypes.c_uint64 * 2) * NSP),
                 ("born", ctypes.c_uint64 * NSP), ("neutralized", ctypes.c_uint64),
@@ -96,6 +104,13 @@ SIGNATURES = [
     ("o2pic_ln_f32", _i32, [_vp, _vp, _u64, _vp]),
     ("o2pic_compact_particles", _i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("o2pic_compact_particles_noalloc", _i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("o2pic_set_launch_shape", _i32, [_vp, _P(ctypes.c_int32)]),
+    ("o2pic_get_launch_shape", _i32, [_vp, _P(ctypes.c_int32)]),
+    ("o2pic_batch_create", _i32, [_P(_vp), ctypes.c_int32, _u64, _P(_vp)]),
+    ("o2pic_batch_step", _i32, [_vp, _u64]),
+    ("o2pic_batch_synchronize", _i32, [_vp]),
+    ("o2pic_batch_autotune", _i32, [_vp, _vp]),
+    ("o2pic_batch_destroy", None, [_vp]),
     ("o2pic_strerror", ctypes.c_char_p, [_i32]),
     ("o2pic_destroy", None, [_vp]),
     ("o2pic_version", _i32, []),
@@ -288,6 +303,15 @@ class Discharge:
                                       None, k), "o2pic_get_timing")
         return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(KERNEL_KINDS)}
 
+    def set_launch_shape(self, push_blocks):
+        arr = (ctypes.c_int32 * NSP)(*[int(b) for b in push_blocks])
+        _check(lib().o2pic_set_launch_shape(self.h, arr), "o2pic_set_launch_shape")
+
+    def launch_shape(self):
+        arr = (ctypes.c_int32 * NSP)()
+        _check(lib().o2pic_get_launch_shape(self.h, arr), "o2pic_get_launch_shape")
+        return tuple(arr)
+
     def launch_count(self):
         return int(lib().o2pic_launch_count(self.h))
 
@@ -328,3 +352,39 @@ def ln_f32(x, stream=None):
     _check(lib().o2pic_ln_f32(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(x.numel()),
                               _stream_ptr(stream)), "o2pic_ln_f32")
     return out
+
+
+class Batch:
+    """Many discharges (Discharge objects, borrowed) advanced together by one
+    CUDA graph of `steps_per_launch` steps each (o2pic_batch_*)."""
+
+    def __init__(self, discharges, steps_per_launch):
+        self.discharges = list(discharges)
+        self.K = int(steps_per_launch)
+        arr = (ctypes.c_void_p * len(self.discharges))(*[d.h for d in self.discharges])
+        h = ctypes.c_void_p()
+        _check(lib().o2pic_batch_create(arr, len(self.discharges), self.K, ctypes.byref(h)), "o2pic_batch_create")
+        self.h = h
+
+    def step(self, launches=1):
+        _check(lib().o2pic_batch_step(self.h, int(launches)), "o2pic_batch_step")
+
+    def synchronize(self):
+        _check(lib().o2pic_batch_synchronize(self.h), "o2pic_batch_synchronize")
+
+    def autotune(self):
+        r = TuneReport()
+        _check(lib().o2pic_batch_autotune(self.h, ctypes.byref(r)), "o2pic_batch_autotune")
+        return {"particles_per_warp": [int(r.particles_per_warp[i]) for i in range(r.n)],
+                "ms": [float(r.ms[i]) for i in range(r.n)], "chosen": int(r.chosen)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().o2pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -83,6 +83,7 @@ struct o2pic_ctx {
     int grid_push[NSP] = {0, 0, 0};
     int grid_pair = 0, grid_compact = 0, grid_deposit = 0;
     unsigned long long launches = 0;
+    unsigned long long gen = 0;        // bumped by every call that invalidates a captured graph
     // gather (read_particles) state
     unsigned* d_gticket = nullptr;
     unsigned long long* d_gflag = nullptr;
@@ -261,6 +262,37 @@ int prepare(o2pic_ctx* c, cudaStream_t s) {
     launch(c, KK_FIELD, s, [&] { launch_field(P, 1, 7, s); });
     c->dirty = false;
     return cuda_fail(c, cudaGetLastError());
+}
+
+// The kernel sequence of nsteps time steps on stream s (the electrode
+// voltages of those steps must be in the ring already): electrons every step,
+// ions and (17) on ion steps, the end-of-step kernel, and every compact_check
+// steps a compaction check per species.  Host state advances with it.
+void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
+    Params& P = c->P;
+    const unsigned S = (unsigned)c->cfg.ion_subcycle;
+    for (uint64_t k = 0; k < nsteps; ++k) {
+        const bool ion = (c->host_step % S) == 0;
+        launch(c, KK_PUSH_E, s, [&] { launch_push(SP_E, P, c->grid_push[SP_E], s); });
+        if (P.nproc[SP_E]) launch(c, KK_CAND_E, s, [&] { launch_cand(SP_E, P, c->grid_push[SP_E], s); });
+        if (ion) {
+            launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
+            if (P.nproc[SP_OM]) launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
+            launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
+            if (P.nproc[SP_OP]) launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
+            if (P.have_neutral) {
+                launch(c, KK_PAIR_HIST, s, [&] { launch_pair_hist(P, c->grid_compact, s); });
+                launch(c, KK_PAIR, s, [&] { launch_pair(P, c->grid_pair, s); });
+            }
+        }
+        launch(c, KK_FIELD, s, [&] { launch_field(P, 0, ion ? 7 : 1, s); });
+        c->host_step += 1;
+        if (++c->since_check >= c->cfg.compact_check) {
+            for (int sp = 0; sp < NSP; ++sp)
+                launch(c, KK_COMPACT, s, [&] { launch_compact(sp, P, c->grid_compact, s); });
+            c->since_check = 0;
+        }
+    }
 }
 
 }  // namespace
@@ -513,6 +545,7 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
         P.push_warps[s] = (unsigned)c->grid_push[s] * (BLOCK / 32);
     }
     c->have_tables = true;
+    c->gen += 1;
     return O2PIC_OK;
 }
 
@@ -577,6 +610,7 @@ int o2pic_load_particles(o2pic_ctx* c, int species, const float* x, const float*
     c->host_step = h.step;
     c->loaded[species] = true;
     c->dirty = true;
+    c->gen += 1;
     return O2PIC_OK;
 }
 
@@ -588,6 +622,7 @@ int o2pic_set_step(o2pic_ctx* c, uint64_t step) {
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->host_step = step;
     c->dirty = true;
+    c->gen += 1;
     return O2PIC_OK;
 }
 
@@ -603,32 +638,10 @@ int o2pic_step(o2pic_ctx* c, uint64_t nsteps, void* stream) {
         int rc = prepare(c, s);
         if (rc) return rc;
     }
-    const unsigned S = (unsigned)c->cfg.ion_subcycle;
-    for (uint64_t k = 0; k < nsteps; ++k) {
-        if (k % (VRING / 2) == 0) {
-            const unsigned long long n = std::min<unsigned long long>(nsteps - k, VRING / 2);
-            if (int rc = fill_vring(c, c->host_step + 1, c->host_step + n, s)) return rc;
-        }
-        const bool ion = (c->host_step % S) == 0;
-        launch(c, KK_PUSH_E, s, [&] { launch_push(SP_E, P, c->grid_push[SP_E], s); });
-        if (P.nproc[SP_E]) launch(c, KK_CAND_E, s, [&] { launch_cand(SP_E, P, c->grid_push[SP_E], s); });
-        if (ion) {
-            launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
-            if (P.nproc[SP_OM]) launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
-            launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
-            if (P.nproc[SP_OP]) launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
-            if (P.have_neutral) {
-                launch(c, KK_PAIR_HIST, s, [&] { launch_pair_hist(P, c->grid_compact, s); });
-                launch(c, KK_PAIR, s, [&] { launch_pair(P, c->grid_pair, s); });
-            }
-        }
-        launch(c, KK_FIELD, s, [&] { launch_field(P, 0, ion ? 7 : 1, s); });
-        c->host_step += 1;
-        if (++c->since_check >= c->cfg.compact_check) {
-            for (int sp = 0; sp < NSP; ++sp)
-                launch(c, KK_COMPACT, s, [&] { launch_compact(sp, P, c->grid_compact, s); });
-            c->since_check = 0;
-        }
+    for (uint64_t k = 0; k < nsteps; k += VRING / 2) {
+        const unsigned long long n = std::min<unsigned long long>(nsteps - k, VRING / 2);
+        if (int rc = fill_vring(c, c->host_step + 1, c->host_step + n, s)) return rc;
+        enqueue_steps(c, n, s);
     }
     return cuda_fail(c, cudaGetLastError());
 }
@@ -814,4 +827,266 @@ int o2pic_ln_f32(const float* x, float* out, uint64_t n, void* stream) {
     return cudaGetLastError() == cudaSuccess ? O2PIC_OK : O2PIC_E_CUDA;
 }
 
+// ============================================================ batched stepping
 }  // extern "C"
+
+struct o2pic_batch {
+    std::vector<o2pic_ctx*> ctx;
+    uint64_t K = 0;                       // steps per graph replay
+    int device = 0;
+    cudaStream_t stream = nullptr;        // origin stream: ring fills and graph launches
+    std::vector<cudaStream_t> branch;     // one capture branch per context
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned long long> launches_per_replay;
+    std::vector<unsigned long long> phase_step;   // host_step of each context at capture
+    std::vector<unsigned long long> gen;          // generation of each context at capture
+};
+
+namespace {
+
+void batch_release_graph(o2pic_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Records K steps of every context into a graph, one branch per context.
+// Nothing runs; the contexts' host counters are restored afterwards.
+int batch_capture(o2pic_batch* b) {
+    batch_release_graph(b);
+    const size_t n = b->ctx.size();
+    std::vector<unsigned long long> hs(n), launches(n), nl(n * NKK);
+    std::vector<unsigned> sc(n);
+    for (size_t i = 0; i < n; ++i) {
+        o2pic_ctx* c = b->ctx[i];
+        hs[i] = c->host_step; sc[i] = c->since_check; launches[i] = c->launches;
+        for (int k = 0; k < NKK; ++k) nl[i * NKK + k] = c->nlaunch[k];
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return O2PIC_E_CUDA;
+    cudaEventRecord(b->fork, b->stream);
+    for (size_t i = 0; i < n; ++i) {
+        cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+        enqueue_steps(b->ctx[i], b->K, b->branch[i]);
+        cudaEventRecord(b->join[i], b->branch[i]);
+        cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+    for (size_t i = 0; i < n; ++i) {
+        o2pic_ctx* c = b->ctx[i];
+        b->launches_per_replay[i] = c->launches - launches[i];
+        b->phase_step[i] = hs[i];
+        b->gen[i] = c->gen;
+        c->host_step = hs[i]; c->since_check = sc[i]; c->launches = launches[i];
+        for (int k = 0; k < NKK; ++k) c->nlaunch[k] = nl[i * NKK + k];
+    }
+    if (ec != cudaSuccess || e != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return O2PIC_E_CUDA; }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) { batch_release_graph(b); cudaGetLastError(); return O2PIC_E_CUDA; }
+    return O2PIC_OK;
+}
+
+// Live-slot count of each species of a context (device control block).
+int ctx_slots(o2pic_ctx* c, unsigned long long slots[NSP]) {
+    DevCtrl h;
+    if (cudaMemcpy(&h, c->d_ctrl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(c, cudaErrorUnknown);
+    for (int s = 0; s < NSP; ++s) slots[s] = h.slots[s];
+    return O2PIC_OK;
+}
+
+int default_push_blocks(o2pic_ctx* c, int s) {
+    int bps = 0;
+    if (push_occupancy(s, c->P, &bps) || bps < 1) bps = 1;
+    if (bps > MAX_PUSH_BLOCKS_PER_SM) bps = MAX_PUSH_BLOCKS_PER_SM;
+    return bps * c->num_sms;
+}
+
+}  // namespace
+
+extern "C" {
+
+int o2pic_set_launch_shape(o2pic_ctx* c, const int32_t push_blocks[3]) {
+    if (!c || !push_blocks) return O2PIC_E_INVALID_ARG;
+    if (!c->have_tables) return O2PIC_E_STATE;
+    for (int s = 0; s < NSP; ++s)
+        if (push_blocks[s] < 1 || push_blocks[s] > MAX_PUSH_BLOCKS_PER_SM * c->num_sms) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    for (int s = 0; s < NSP; ++s) {
+        c->grid_push[s] = push_blocks[s];
+        c->P.push_warps[s] = (unsigned)push_blocks[s] * (BLOCK / 32);
+    }
+    c->gen += 1;
+    return O2PIC_OK;
+}
+
+int o2pic_get_launch_shape(o2pic_ctx* c, int32_t push_blocks[3]) {
+    if (!c || !push_blocks) return O2PIC_E_INVALID_ARG;
+    for (int s = 0; s < NSP; ++s) push_blocks[s] = c->grid_push[s];
+    return O2PIC_OK;
+}
+
+int o2pic_batch_create(o2pic_ctx* const* ctxs, int32_t n, uint64_t K, o2pic_batch** out) {
+    if (!out) return O2PIC_E_INVALID_ARG;
+    *out = nullptr;
+    if (!ctxs || n < 1 || K < 1 || K > VRING / 2) return O2PIC_E_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        o2pic_ctx* c = ctxs[i];
+        if (!c || c->device != ctxs[0]->device) return O2PIC_E_INVALID_ARG;
+        if (K % (uint64_t)c->cfg.ion_subcycle || K % (uint64_t)c->cfg.compact_check) return O2PIC_E_INVALID_ARG;
+        if (!c->have_tables) return O2PIC_E_STATE;
+        if (c->latched) return c->latched;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return O2PIC_E_INVALID_ARG;
+    }
+    if (cudaSetDevice(ctxs[0]->device) != cudaSuccess) return O2PIC_E_CUDA;
+    o2pic_batch* b = new (std::nothrow) o2pic_batch;
+    if (!b) return O2PIC_E_CUDA;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->K = K;
+    b->device = ctxs[0]->device;
+    b->branch.assign(n, nullptr);
+    b->join.assign(n, nullptr);
+    b->launches_per_replay.assign(n, 0);
+    b->phase_step.assign(n, 0);
+    b->gen.assign(n, 0);
+    bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreate(&b->t0) == cudaSuccess && cudaEventCreate(&b->t1) == cudaSuccess;
+    for (int i = 0; ok && i < n; ++i)
+        ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { o2pic_batch_destroy(b); return O2PIC_E_CUDA; }
+    // initial deposit and field of contexts not yet stepped; timing off (no
+    // event records inside the graph)
+    for (o2pic_ctx* c : b->ctx) {
+        int rc = sync_all(c);
+        if (rc) { o2pic_batch_destroy(b); return rc; }
+        if (c->timing) o2pic_set_timing(c, 0);
+        if (c->dirty) {
+            rc = prepare(c, b->stream);
+            if (!rc) rc = cuda_fail(c, cudaStreamSynchronize(b->stream));
+            if (rc) { o2pic_batch_destroy(b); return rc; }
+        }
+    }
+    int rc = batch_capture(b);
+    if (rc) { o2pic_batch_destroy(b); return rc; }
+    *out = b;
+    return O2PIC_OK;
+}
+
+int o2pic_batch_step(o2pic_batch* b, uint64_t launches) {
+    if (!b || !b->exec) return O2PIC_E_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return O2PIC_E_CUDA;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        o2pic_ctx* c = b->ctx[i];
+        if (c->latched) return c->latched;
+        // the graph holds the kernel sequence of its capture phase, with the
+        // context's tables, launch shape and particle buffers of that time
+        if ((c->host_step - b->phase_step[i]) % b->K || c->gen != b->gen[i] || c->dirty) return O2PIC_E_STATE;
+    }
+    for (uint64_t r = 0; r < launches; ++r) {
+        for (o2pic_ctx* c : b->ctx)
+            if (int rc = fill_vring(c, c->host_step + 1, c->host_step + b->K, b->stream)) return rc;
+        if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return O2PIC_E_CUDA;
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            o2pic_ctx* c = b->ctx[i];
+            c->host_step += b->K;
+            c->launches += b->launches_per_replay[i];
+            c->last = b->stream;
+        }
+    }
+    return O2PIC_OK;
+}
+
+int o2pic_batch_synchronize(o2pic_batch* b) {
+    if (!b) return O2PIC_E_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return O2PIC_E_CUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return O2PIC_E_CUDA;
+    int first = O2PIC_OK;
+    for (o2pic_ctx* c : b->ctx) {
+        const int rc = check_flags(c);
+        if (rc && !first) first = rc;
+    }
+    return first;
+}
+
+int o2pic_batch_autotune(o2pic_batch* b, o2pic_tune_report* report) {
+    if (!b) return O2PIC_E_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return O2PIC_E_CUDA;
+    if (int rc = o2pic_batch_synchronize(b)) return rc;
+    static const int32_t policies[] = {0, 256, 512, 1024, 2048, 4096, 8192};
+    const int np = (int)(sizeof(policies) / sizeof(policies[0]));
+    o2pic_tune_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    const size_t n = b->ctx.size();
+    std::vector<std::vector<int32_t>> shapes(np, std::vector<int32_t>(3 * n));
+    for (size_t i = 0; i < n; ++i) {
+        o2pic_ctx* c = b->ctx[i];
+        unsigned long long slots[NSP];
+        if (int rc = ctx_slots(c, slots)) return rc;
+        for (int p = 0; p < np; ++p)
+            for (int s = 0; s < NSP; ++s) {
+                long long g;
+                if (policies[p] == 0) g = default_push_blocks(c, s);
+                else g = (long long)((slots[s] + (unsigned long long)policies[p] * (BLOCK / 32) - 1) /
+                                     ((unsigned long long)policies[p] * (BLOCK / 32)));
+                g = std::max<long long>(1, std::min<long long>(g, (long long)MAX_PUSH_BLOCKS_PER_SM * c->num_sms));
+                shapes[p][3 * i + s] = (int32_t)g;
+            }
+    }
+    int best = 0;
+    double best_ms = 0.0;
+    for (int p = 0; p < np; ++p) {
+        for (size_t i = 0; i < n; ++i)
+            if (int rc = o2pic_set_launch_shape(b->ctx[i], &shapes[p][3 * i])) return rc;
+        if (int rc = batch_capture(b)) return rc;
+        if (cudaGraphUpload(b->exec, b->stream) != cudaSuccess) return O2PIC_E_CUDA;
+        for (o2pic_ctx* c : b->ctx)
+            if (int rc = fill_vring(c, c->host_step + 1, c->host_step + b->K, b->stream)) return rc;
+        cudaEventRecord(b->t0, b->stream);
+        if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return O2PIC_E_CUDA;
+        cudaEventRecord(b->t1, b->stream);
+        for (size_t i = 0; i < n; ++i) {
+            b->ctx[i]->host_step += b->K;
+            b->ctx[i]->launches += b->launches_per_replay[i];
+        }
+        if (int rc = o2pic_batch_synchronize(b)) return rc;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, b->t0, b->t1);
+        if (rep.n < O2PIC_TUNE_MAX) {
+            rep.particles_per_warp[rep.n] = policies[p];
+            rep.ms[rep.n] = ms;
+            rep.n += 1;
+        }
+        if (p == 0 || ms < best_ms) { best = p; best_ms = ms; }
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (int rc = o2pic_set_launch_shape(b->ctx[i], &shapes[best][3 * i])) return rc;
+    if (int rc = batch_capture(b)) return rc;
+    rep.chosen = best;
+    if (report) *report = rep;
+    return O2PIC_OK;
+}
+
+void o2pic_batch_destroy(o2pic_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_release_graph(b);
+    for (cudaStream_t s : b->branch) if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"
+

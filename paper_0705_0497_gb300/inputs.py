@@ -75,6 +75,28 @@ def workload(name, scale=1.0, **over):
     return cfg, counts, w["T_eV"], w["cycles"]
 
 
+def batch_sweep(n=64, seed=0, scale=1.0, count_range=(1.0e5, 2.0e6)):
+    """A parameter sweep of `n` discharges for the batched stepper: U uniform
+    on [100, 500] V, p log-uniform on [5, 50] Pa, and one particle count N per
+    discharge, log-uniform on `count_range` (times `scale`), loaded
+    quasi-neutral as N e + N O- + 2N O2+.  Fixed: L = 2.5 cm, 256 cells,
+    metastable fraction 5%, 1000 steps per RF cycle, ions subcycled x10;
+    weight n0 L / N with n0 = 1e15 m^-3; seed of discharge i = seed + i.
+    Returns a list of (cfg, counts, T_eV)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo, hi = count_range
+    out = []
+    for i in range(n):
+        U = float(rng.uniform(100.0, 500.0))
+        p = float(math.exp(rng.uniform(math.log(5.0), math.log(50.0))))
+        N = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))) * scale))
+        N = max(N, 1)
+        cfg = base_config(L=0.025, n_cells=256, steps_per_cycle=1000, U=U, p=p, C_meta=0.05,
+                          ion_subcycle=10, weight=1.0e15 * 0.025 / N, seed=seed + i)
+        out.append((cfg, (N, N, 2 * N), (3.0, 0.026, 0.026)))
+    return out
+
+
 def species_mass(cfg, s):
     return (cfg["m_e"], cfg["m_OM"], cfg["m_OP"])[s]
 

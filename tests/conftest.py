@@ -17,3 +17,11 @@ def oracle_mod():
     import oracle
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def torch_cuda():
+    """torch with a CUDA device (GPU tests only)."""
+    import torch
+    assert torch.cuda.is_available()
+    return torch

@@ -15,13 +15,6 @@ pytestmark = pytest.mark.gpu
 QE, KB, ME, AMU = inputs.QE, inputs.KB, inputs.ME, inputs.AMU
 
 
-@pytest.fixture(scope="module")
-def torch_cuda():
-    import torch
-    assert torch.cuda.is_available()
-    return torch
-
-
 def test_philox_matches_oracle_and_curand(torch_cuda):
     import oracle
     from paper_0705_0497_gb300 import api
