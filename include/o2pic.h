@@ -164,6 +164,20 @@ int o2pic_read_particles(o2pic_ctx* ctx, int species, float* x, float* vx, float
  * FP32 copy the gather uses); either pointer may be NULL.  Host memory. */
 int o2pic_read_field(o2pic_ctx* ctx, double* phi, float* E);
 
+/* Current densities through the gap (Fig. 5 of the paper) of the steps
+ * first_step .. first_step+n-1, out[5 i + k] [A/m^2]:
+ *   k = 0, 1, 2: conduction current of e, O-, O2+, gap-averaged,
+ *                J_s = q_s w sum_p v_x,p^{n+1/2} / (A L) over the particles
+ *                pushed in the step (the ions' last push on steps without
+ *                one), summed exactly in fixed point (trunc(256 v_x));
+ *   k = 3: displacement current eps0 (V(t^{n+1}) - V(t^n)) / (L dt) of the
+ *          prescribed electrode voltage V = U sin(2 pi f t) (the gap
+ *          average of eps0 dE/dt);
+ *   k = 4: total current density (k = 0..3 summed), uniform across the gap.
+ * The device keeps the last 8191 completed steps since the last load or
+ * set_step; steps outside that window return INVALID_ARG.  Host memory. */
+int o2pic_read_currents(o2pic_ctx* ctx, uint64_t first_step, uint64_t n, double* out);
+
 /* Fixed-point node charges (2^16 per macro-particle, CIC) of the current
  * particles, Q[3][n_cells+1], and their sum over the steps since the last
  * reset, Qacc[3][n_cells+1] (either may be NULL); *acc_steps = steps summed.

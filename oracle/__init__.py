@@ -67,6 +67,7 @@ def lib():
         L.oracle_read_charge.argtypes = [vp, vp, vp]
         L.oracle_reset_moments.argtypes = [vp]
         L.oracle_counters.argtypes = [vp, vp, i32]
+        L.oracle_currents.argtypes = [vp, u64, u64, vp]
         L.oracle_table.argtypes = [vp, i32, vp, vp, vp, vp]
         L.oracle_neutral_table.argtypes = [vp, vp]
         L.oracle_update_particle.argtypes = [vp, i32, u64, vp, vp, u32, vp, vp]
@@ -183,6 +184,15 @@ class Oracle:
         buf = np.zeros(n, np.uint64)
         lib().oracle_counters(self.h, _ptr(buf), n)
         return dict(zip(COUNTER_NAMES, (int(v) for v in buf)))
+
+    def current_sums(self, step0, n):
+        """Conduction-current sums [n][3] (int64) of steps step0 .. step0+n-1:
+        sum over the particles pushed in the step of trunc(256 v_x^{n+1/2})."""
+        out = np.zeros((n, 3), np.int64)
+        rc = lib().oracle_currents(self.h, step0, n, _ptr(out))
+        if rc != 0:
+            raise ValueError("steps not recorded since the last load")
+        return out
 
     def table(self, species):
         G = ngrid()

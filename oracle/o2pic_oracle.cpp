@@ -298,6 +298,13 @@ template <class R> struct Oracle {
     std::vector<Proc> procs[NSP];
     std::vector<R> cum[NSP];          // [NGRID][nproc] cumulative rate, precision R
     std::vector<double> nu64[NSP];    // [NGRID][nproc] per-process rate, FP64
+    // Conduction-current sums (Fig. 5 of the paper): for step n and species s,
+    // J_sum = sum over the particles pushed in step n of trunc(256 v_x^{n+1/2})
+    // (exact int64; the current density is q_s e w J_sum / (256 A L)).  On a
+    // step that does not push the ions their entries repeat the last value.
+    std::vector<int64_t> jhist;       // [steps since jbase][NSP]
+    uint64_t jbase = 0;
+    int64_t jacc[NSP] = {0, 0, 0};
     R numax[NSP], Pmax[NSP];
     double numax64[NSP];
     bool have_neutral;
@@ -517,6 +524,7 @@ template <class R> struct Oracle {
         vx = fma_(qmdt[s], Ep, vx);
         x = fma_(vx, dt_s[s], x);
         cnt.particle_steps += 1;
+        jacc[s] += (int64_t)(vx * (R)256);   // exact scaling by 2^8, then truncation
         // absorbing electrodes
         if (x < (R)0) { cnt.absorbed[s][0] += 1; return false; }
         if (x >= Lr) { cnt.absorbed[s][1] += 1; return false; }
@@ -704,6 +712,7 @@ template <class R> struct Oracle {
         uint64_t n = step;
         bool ion_step = (n % (uint64_t)cfg.ion_subcycle) == 0;
         std::vector<Birth4> births[NSP];
+        for (int s = 0; s < NSP; ++s) jacc[s] = 0;
         process_species(SP_E, n, births);
         if (ion_step) {
             process_species(SP_OM, n, births);
@@ -716,6 +725,12 @@ template <class R> struct Oracle {
         for (int s = 0; s < NSP; ++s)
             for (int j = 0; j < Ng; ++j) Qacc[s][j] += Q[s][j];
         acc_steps += 1;
+        if (jhist.empty()) jbase = n;
+        const size_t prev = jhist.size();
+        for (int s = 0; s < NSP; ++s) {
+            const bool pushed = (s == SP_E) || ion_step;
+            jhist.push_back(pushed ? jacc[s] : (prev ? jhist[prev - NSP + s] : 0));
+        }
         step = n + 1;
     }
 };
@@ -789,6 +804,7 @@ int oracle_load(void* p, int s, const float* x, const float* vx, const float* vy
         }
         O.next_id[s] = mx;
         O.field_valid = false;
+        O.jhist.clear();
     });
     return 0;
 }
@@ -807,8 +823,22 @@ int oracle_step(void* p, uint64_t nsteps) {
 
 int oracle_set_step(void* p, uint64_t step) {
     Handle* h = (Handle*)p;
-    DISPATCH(h, { O.step = step; O.field_valid = false; });
+    DISPATCH(h, { O.step = step; O.field_valid = false; O.jhist.clear(); });
     return 0;
+}
+
+// Conduction-current sums of steps step0 .. step0+n-1 (out[3 i + s]); -1 if
+// a step was not recorded since the last load / set_step.
+int oracle_currents(void* p, uint64_t step0, uint64_t n, int64_t* out) {
+    Handle* h = (Handle*)p; int rc = 0;
+    DISPATCH(h, {
+        const uint64_t have = O.jhist.size() / NSP;
+        if (n > 0 && (O.jhist.empty() || step0 < O.jbase || step0 + n > O.jbase + have)) rc = -1;
+        else
+            for (uint64_t i = 0; i < n; ++i)
+                for (int s = 0; s < NSP; ++s) out[3 * i + s] = O.jhist[(step0 - O.jbase + i) * NSP + s];
+    });
+    return rc;
 }
 
 uint64_t oracle_get_step(void* p) {

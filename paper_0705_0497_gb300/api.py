@@ -94,6 +94,7 @@ SIGNATURES = [
     ("o2pic_read_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _P(_u64), _i32]),
     ("o2pic_read_field", _i32, [_vp, _vp, _vp]),
     ("o2pic_read_charge", _i32, [_vp, _vp, _vp, _P(_u64)]),
+    ("o2pic_read_currents", _i32, [_vp, _u64, _u64, _vp]),
     ("o2pic_read_moments", _i32, [_vp, _vp, _P(_u64), _i32]),
     ("o2pic_get_stats", _i32, [_vp, _P(Stats)]),
     ("o2pic_set_step", _i32, [_vp, _u64]),
@@ -268,6 +269,14 @@ class Discharge:
         _check(lib().o2pic_read_field(self.h, phi.ctypes.data_as(ctypes.c_void_p), Ef.ctypes.data_as(ctypes.c_void_p)),
                "o2pic_read_field")
         return phi, Ef
+
+    def currents(self, first_step, n):
+        """Current densities [n][5] in A/m^2 of steps first_step ..: conduction
+        current of e, O-, O2+, displacement current, total (o2pic_read_currents)."""
+        out = np.zeros((n, 5))
+        _check(lib().o2pic_read_currents(self.h, int(first_step), int(n), out.ctypes.data_as(ctypes.c_void_p)),
+               "o2pic_read_currents")
+        return out
 
     def charge(self):
         Q = np.zeros((NSP, self.Ng), np.uint64)

@@ -384,6 +384,18 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
     }
     // per-cell ion totals of (17): zero for the next ion step
     for (int k = t; k < 2 * N; k += FT) P.ptot[k] = 0u;
+    // conduction-current sums: after a load the ring restarts; at the end of
+    // step n the ions' entries of a step without an ion push repeat those of
+    // step n-1, and the slot of step n+1 is cleared for its pushes
+    if (mode != 0) {
+        for (int k = t; k < JRING * NSP; k += FT) P.jring[k] = 0ull;
+    } else if (t >= 96 && t < 96 + NSP) {
+        const int sp = t - 96;
+        const unsigned long long n = cs.step;
+        if (sp != SP_E && !((pushed_mask >> sp) & 1))
+            P.jring[(n & (JRING - 1)) * NSP + sp] = P.jring[((n - 1) & (JRING - 1)) * NSP + sp];
+        P.jring[((n + 1) & (JRING - 1)) * NSP + sp] = 0ull;
+    }
     if (mode != 0) {
         if (t < NKK + NSP) C->ticket[t] = 0u;
         return;

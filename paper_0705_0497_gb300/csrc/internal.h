@@ -30,6 +30,7 @@ constexpr int MAX_TRIES = 32;           // rejection-loop cap
 constexpr uint32_t FIX_ONE = 65536u;    // CIC fixed point per particle
 constexpr int QCAP = BLOCK - 1 + CHUNK; // candidate queue capacity
 constexpr int MAX_NODES = 8193;         // grid limit (smem field and histograms)
+constexpr int JRING = 8192;             // steps of conduction-current sums kept on the device
 
 enum Kind { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6 };
 enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4 };
@@ -112,6 +113,7 @@ struct Params {
     long long* fS;               // [Ng] S_j of the last field solve (exact prefix sums)
     long long* fU;               // [Ng] U_j of the last field solve
     double* fVD;                 // [2] V0, D0 of the last field solve
+    unsigned long long* jring;   // [JRING][NSP] conduction-current sums (int64 mod 2^64), slot = step % JRING
     unsigned long long* Q[NSP];  // committed node charge
     unsigned long long* Qf[NSP]; // fresh deposit of the species pushed this step
     unsigned long long* Qb[NSP]; // deposit of this step's births

@@ -49,6 +49,7 @@ constexpr int Q2 = 64;                      // per-warp real-collision queue (31
 constexpr int PUSH_UNROLL = O2PIC_PUSH_UNROLL;
 
 struct PushShared {
+    unsigned long long jsum;     // block's sum of trunc(256 v_x^{n+1/2})
     unsigned absorbed[2];
     unsigned removed;
     unsigned psteps;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
     const uint32_t step_lo = (uint32_t)step, step_hi = (uint32_t)(step >> 32);
 
     for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0ull; }
-    if (tid == 0) { sh.absorbed[0] = sh.absorbed[1] = 0u; sh.removed = 0u; sh.psteps = 0u; sh.nonfinite = 0u; }
+    if (tid == 0) { sh.absorbed[0] = sh.absorbed[1] = 0u; sh.removed = 0u; sh.psteps = 0u; sh.nonfinite = 0u; sh.jsum = 0ull; }
     __syncthreads();
 
     // this warp's contiguous slot range
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
     const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
 
     unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0;
+    long long jacc = 0;   // conduction current: sum of trunc(256 v_x^{n+1/2}) (exact)
     unsigned ncand = 0;   // warp-uniform: candidates of this warp so far
     for (unsigned g0 = r0; g0 < r1; g0 += ROUND) {
         const bool full = g0 + ROUND <= r1;
@@ -287,6 +289,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
                 vx = fmaf(qmdt, Ep, vx);
                 x = fmaf(vx, dts, x);
                 ++psteps;
+                jacc += (long long)(vx * 256.0f);   // exact scaling by 2^8, then truncation
                 if (x < 0.0f) { ++nabs0; x = dead_marker(); }
                 else if (x >= Lf) { ++nabs1; x = dead_marker(); }
                 else if (!(x >= 0.0f) || !isfinite(vx)) { ++nnf; x = dead_marker(); }
@@ -311,6 +314,9 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
         }
     }
     if (lane == 0) P.ccount[S][gw] = ncand;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) jacc += __shfl_down_sync(0xffffffffu, jacc, o);
+    if (lane == 0 && jacc) atomicAdd(&sh.jsum, (unsigned long long)jacc);
     if (psteps) atomicAdd(&sh.psteps, psteps);
     if (nabs0) atomicAdd(&sh.absorbed[0], nabs0);
     if (nabs1) atomicAdd(&sh.absorbed[1], nabs1);
@@ -334,6 +340,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
             atomicAdd(&C->cnt.psteps[S], (unsigned long long)sh.psteps);
         }
         if (sh.nonfinite) atomicOr(&C->error_flags, ERR_NONFINITE);
+        if (sh.jsum) atomicAdd(&P.jring[(step & (JRING - 1)) * NSP + S], sh.jsum);
     }
 }
 

@@ -84,6 +84,7 @@ struct o2pic_ctx {
     int grid_pair = 0, grid_compact = 0, grid_deposit = 0;
     unsigned long long launches = 0;
     unsigned long long gen = 0;        // bumped by every call that invalidates a captured graph
+    unsigned long long ring_start = 0; // first step recorded in the current-sum ring
     // gather (read_particles) state
     unsigned* d_gticket = nullptr;
     unsigned long long* d_gflag = nullptr;
@@ -260,6 +261,7 @@ int prepare(o2pic_ctx* c, cudaStream_t s) {
     for (int sp = 0; sp < NSP; ++sp)
         launch(c, KK_DEPOSIT, s, [&] { launch_deposit(sp, P, c->grid_deposit, s); });
     launch(c, KK_FIELD, s, [&] { launch_field(P, 1, 7, s); });
+    c->ring_start = c->host_step;
     c->dirty = false;
     return cuda_fail(c, cudaGetLastError());
 }
@@ -382,6 +384,7 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     TRY(ctx_alloc(c, &P.fS, Ng));
     TRY(ctx_alloc(c, &P.fU, Ng));
     TRY(ctx_alloc(c, &P.fVD, 2));
+    TRY(ctx_alloc(c, &P.jring, (size_t)JRING * NSP));
     for (int k = 0; k < NKK; ++k) {
         TRY(ctx_alloc(c, &P.lb_flag[k], max_tiles));
         TRY(ctx_alloc(c, &P.lb_val[k], 2 * max_tiles));
@@ -712,6 +715,38 @@ int o2pic_read_field(o2pic_ctx* c, double* phi, float* E) {
     if (phi) e = cudaMemcpy(phi, c->P.phi, sizeof(double) * c->P.Ng, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && E) e = cudaMemcpy(E, c->P.Ef, sizeof(float) * c->P.Ng, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e);
+    return rc;
+}
+
+int o2pic_read_currents(o2pic_ctx* c, uint64_t first, uint64_t n, double* out) {
+    if (!c || (n && !out)) return O2PIC_E_INVALID_ARG;
+    if (n == 0) return O2PIC_OK;
+    const unsigned long long done = c->host_step;   // steps < done are complete
+    if (c->dirty || first < c->ring_start || first + n > done || done - first > JRING - 1)
+        return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    std::vector<unsigned long long> raw(JRING * NSP);
+    cudaError_t e = cudaMemcpy(raw.data(), c->P.jring, sizeof(unsigned long long) * raw.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    const o2pic_config& g = c->cfg;
+    const int charge[NSP] = {-1, -1, +1};
+    const double unit = QE * g.weight / (256.0 * g.area * g.L);
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t k = first + i;
+        double tot = 0.0;
+        for (int s = 0; s < NSP; ++s) {
+            const long long sum = (long long)raw[(k & (JRING - 1)) * NSP + s];
+            const double J = (double)charge[s] * unit * (double)sum;
+            out[5 * i + s] = J;
+            tot += J;
+        }
+        const double v0 = g.U * std::sin(TWO_PI * g.f * ((double)k * g.dt));
+        const double v1 = g.U * std::sin(TWO_PI * g.f * ((double)(k + 1) * g.dt));
+        const double Jd = EPS0 * (v1 - v0) / (g.L * g.dt);
+        out[5 * i + 3] = Jd;
+        out[5 * i + 4] = tot + Jd;
+    }
     return rc;
 }
 

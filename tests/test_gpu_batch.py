@@ -36,6 +36,9 @@ def _same(a, b):
         assert sa[k] == sb[k], (k, sa[k], sb[k])
     fa, fb = a.field(), b.field()
     assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+    n = sa["step"]
+    k = min(n, 40)
+    assert np.array_equal(a.currents(n - k, k), b.currents(n - k, k))
 
 
 def test_batch_equals_single_runs(torch_cuda):

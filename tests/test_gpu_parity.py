@@ -240,3 +240,46 @@ def test_long_run_profiles(torch_cuda):
     alpha_64 = d64[1][c - 4:c + 5].mean() / d64[0][c - 4:c + 5].mean()
     print(f"centre electronegativity: GPU {alpha_g:.4f}, oracle32 {alpha_o:.4f}, oracle64 {alpha_64:.4f}")
     assert abs(alpha_g / alpha_o - 1) < 0.02
+
+
+def _expected_currents(cfg, sums, first):
+    """Current densities from the oracle's exact sums, with the library's
+    FP64 expressions (conduction: q_s e w sum / (256 A L); displacement:
+    eps0 (V(t_{n+1}) - V(t_n)) / (L dt) with V = U sin(2 pi f t))."""
+    EPS0 = inputs.EPS0
+    unit = QE * cfg["weight"] / (256.0 * cfg["area"] * cfg["L"])
+    out = np.zeros((len(sums), 5))
+    for i, row in enumerate(sums):
+        k = first + i
+        tot = 0.0
+        for s, q in enumerate((-1, -1, 1)):
+            out[i, s] = (float(q) * unit) * float(row[s])
+            tot += out[i, s]
+        v0 = cfg["U"] * math.sin(2.0 * math.pi * cfg["f"] * (k * cfg["dt"]))
+        v1 = cfg["U"] * math.sin(2.0 * math.pi * cfg["f"] * ((k + 1) * cfg["dt"]))
+        out[i, 3] = EPS0 * (v1 - v0) / (cfg["L"] * cfg["dt"])
+        out[i, 4] = tot + out[i, 3]
+    return out
+
+
+@pytest.mark.parametrize("S", [1, 3])
+def test_current_densities_match_oracle(torch_cuda, S):
+    """Fig. 5 diagnostics: per-step conduction-current sums of every species
+    bit-exact with the oracle (ions repeating between their pushes when
+    subcycled), the displacement current from the prescribed voltage, and
+    the total."""
+    cfg, counts, T, _ = inputs.workload("parity_128", ion_subcycle=S)
+    procs = xsec.oxygen_set()
+    g, o, _ = make_pair(cfg, counts, T, procs)
+    g.step(60)
+    o.step(60)
+    J = g.currents(0, 60)
+    E = _expected_currents(cfg, o.current_sums(0, 60), 0)
+    assert np.array_equal(J[:, :3], E[:, :3])
+    assert np.allclose(J[:, 3:], E[:, 3:], rtol=1e-12, atol=0)
+    if S > 1:
+        assert J[1, 1] == J[0, 1] and J[1, 2] == J[0, 2]
+    # window: the last 8191 steps since the load
+    from paper_0705_0497_gb300 import api
+    with pytest.raises(api.O2picError):
+        g.currents(55, 10)

@@ -648,3 +648,65 @@ def test_ion_elastic_relaxation_closed_form(oracle_mod):
         Em = 0.5 * m * (q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2).mean() / QE
         ref = ET + (E0 - ET) * (1 - P * k) ** n
         assert Em == pytest.approx(ref, rel=0.02)
+
+
+# ---------------------------------------------------------------- currents
+# The conduction-current sums behind the paper's Fig. 5: per step and species,
+# sum over the pushed particles of trunc(256 v_x^{n+1/2}).
+
+def _drift_oracle(oracle_mod, precision, S=1, U=0.0):
+    """Zero weight (no self-field): E = U sin(2 pi f t) / L is uniform (zero
+    for U = 0, so the push keeps every velocity); one O- process that never
+    fires keeps the tables valid without collisions."""
+    cfg = _cfg(weight=0.0, U=U, ion_subcycle=S)
+    o = oracle_mod.Oracle(cfg, precision)
+    nO2 = cfg["p"] / (KB * cfg["T_gas"])
+    o.set_processes([xsec.constant_rate_process(1, xsec.ELASTIC, 1e-30, nO2, 16 * AMU)])
+    return o, cfg
+
+
+def test_current_sum_uniform_drift(oracle_mod):
+    """N particles of one velocity v0 and no field: every step's sum is exactly
+    N trunc(256 v0); with the ions pushed every second step their sums repeat
+    on the steps between (the last push's current)."""
+    o, cfg = _drift_oracle(oracle_mod, 32, S=2)
+    L = cfg["L"]
+    v0 = {0: 1.5e5, 1: -3.2e3, 2: 1.7e3}
+    N = {0: 1000, 1: 300, 2: 500}
+    for s in range(3):
+        x = (0.4 + 0.2 * np.arange(N[s]) / N[s]) * L
+        v = np.full(N[s], v0[s], np.float32)
+        z = np.zeros(N[s], np.float32)
+        o.load(s, x.astype(np.float32), v, z, z, np.arange(N[s], dtype=np.uint32))
+    o.step(6)
+    sums = o.current_sums(0, 6)
+    for s in range(3):
+        expect = N[s] * math.trunc(256.0 * float(np.float32(v0[s])))
+        assert (sums[:, s] == expect).all(), (s, sums[:, s], expect)
+    with pytest.raises(ValueError):
+        o.current_sums(0, 7)
+
+
+def test_current_sum_is_the_displacement_rate(oracle_mod):
+    """sum_p (x^{n+1} - x^n) = dt sum_p v_x^{n+1/2}: the particles' total
+    displacement over a step (from the oracle's positions, summed here in
+    FP64) equals dt times the current sum / 256, within the truncation of the
+    fixed point (dt / 256 per particle) and the FP32 rounding of each x.  A
+    driving voltage makes v^{n+1/2} differ from v^{n-1/2}, so the identity
+    also fixes which velocity the sum takes."""
+    o, cfg = _drift_oracle(oracle_mod, 32, U=200.0)
+    L, dt = cfg["L"], cfg["dt"]
+    rng = np.random.default_rng(21)
+    n = 4000
+    x = (0.3 + 0.4 * rng.random(n)) * L
+    v = rng.standard_normal((3, n)) * 2e5
+    o.load(0, x.astype(np.float32), v[0].astype(np.float32), v[1].astype(np.float32), v[2].astype(np.float32),
+           np.arange(n, dtype=np.uint32))
+    for step in range(6):
+        x0 = o.particles(0)["x"].astype(np.float64)
+        o.step(1)
+        x1 = o.particles(0)["x"].astype(np.float64)
+        disp = float(np.sum(x1 - x0))
+        js = int(o.current_sums(step, 1)[0, 0])
+        bound = n * (dt / 256.0) + n * np.spacing(np.float32(L))
+        assert abs(disp - dt * js / 256.0) <= bound, (step, disp, dt * js / 256.0, bound)
