@@ -5,8 +5,11 @@ metastable fraction 5%, 1000 steps per RF cycle, ions subcycled x10,
 4e6 e + 4e6 O- + 8e6 O2+ (quasi-neutral load), synthetic seeded inputs.
 One bench step = one RF cycle (1000 time steps: every step pushes the
 electrons, every 10th also the ions and runs the O-/O2+ neutralization; each
-step ends with the deposit and the Poisson solve).  The particle arrays
-(320 MB) exceed the 129 MB L2, so no flush is needed between steps.
+step ends with the deposit and the Poisson solve), run as one replay of the
+library's step graph (o2pic_batch_* with a single discharge).  The particle
+arrays (320 MB) exceed the 129 MB L2, so no flush is needed between steps.
+`--workload batch_sweep_64` runs the 64-discharge sweep of the batched
+stepper instead (its own JSON line).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
@@ -245,16 +248,21 @@ def bench_gpu(args, world, rank, local):
     cfg, counts, T, cycles = inputs.workload(WORKLOAD, seed=rank)
     spc = cfg["steps_per_cycle"]
     st = inputs.initial_state(cfg, counts, T, seed=rank)
-    g = api.Discharge(cfg, capacity(counts), device=local)
+    # compaction check every 20 steps: a multiple-of-both divisor of the
+    # 1000-step cycle and the 10-step ion subcycle, so one RF cycle is one
+    # replay of the library's step graph
+    g = api.Discharge(cfg, capacity(counts), device=local, compact_check=20)
     g.set_processes(xsec.oxygen_set())
     g.load_state(st)
     del st
     stream = torch.cuda.Stream(device=local)
-    g.step(args.warmup * spc, stream)
-    g.synchronize()
+    b = api.Batch([g], steps_per_launch=spc)
+    b.step(args.warmup)
+    b.synchronize()
     live0 = [g.count(s) for s in range(3)]
 
-    # ---- timed region A: K RF cycles, device-resident, CUDA events on the stream
+    # ---- timed region A: K RF cycles, device-resident: K replays of the
+    # one-cycle graph on the batch's stream, timed by CUDA events on it
     s0 = g.stats()
     l0 = g.launch_count()
     clocks = ClockSampler(local)
@@ -262,21 +270,16 @@ def bench_gpu(args, world, rank, local):
     time.sleep(0.5)
     barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        g.step(spc, stream)
-    ev1.record(stream)
-    g.synchronize()
+    ms = b.timed_step(args.steps)
+    b.synchronize()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
     s1 = g.stats()
     launches = g.launch_count() - l0
     ps = s1["particle_steps"] - s0["particle_steps"]
     live1 = [g.count(s) for s in range(3)]
+    b.close()
 
     # ---- timed region B: the same loop with an event pair around every launch
     kb = max(1, min(args.steps, 10))

@@ -276,6 +276,10 @@ int o2pic_batch_create(o2pic_ctx* const* ctxs, int32_t n, uint64_t steps_per_lau
  * steps of every context) on the batch's own stream; asynchronous. */
 int o2pic_batch_step(o2pic_batch* b, uint64_t launches);
 
+/* The batch's own CUDA stream (cudaStream_t), on which o2pic_batch_step
+ * enqueues its work: a caller may record events on it to time replays. */
+void* o2pic_batch_stream(o2pic_batch* b);
+
 /* Waits for the batch and returns the first error latched by any context. */
 int o2pic_batch_synchronize(o2pic_batch* b);
 
@@ -295,6 +299,32 @@ typedef struct {
 int o2pic_batch_autotune(o2pic_batch* b, o2pic_tune_report* report);
 
 void o2pic_batch_destroy(o2pic_batch* b);
+
+/* ---- Learned warm start: a small MLP trained on converged runs ----------
+ *
+ * Maps normalized discharge parameters (U, p, L, C) to cycle-averaged
+ * log-density profiles; the profiles load the initial particles of a new run
+ * so that it needs fewer RF cycles to converge.  No counterpart in the
+ * paper.  widths[0] inputs ... widths[n-1] outputs (2 <= n <= 16, each in
+ * [1, 8192]); tanh on hidden layers, linear output, bf16 weights with an fp32
+ * master copy, fp32 accumulation, deterministic results.  Parameters
+ * (host, fp32): for each layer W[in][out] row-major, then b[out].  Initial
+ * weights Glorot-uniform from SplitMix64(seed), biases 0.  X, Y, T, grad and
+ * loss are device pointers; X [B][in], Y and T [B][out] row-major. */
+typedef struct o2pic_mlp o2pic_mlp;
+int o2pic_mlp_create(const int32_t* widths, int32_t n_widths, uint64_t seed, o2pic_mlp** out);
+uint64_t o2pic_mlp_num_params(o2pic_mlp* m);
+int o2pic_mlp_set_params(o2pic_mlp* m, const float* host_params);   /* also resets the Adam state */
+int o2pic_mlp_get_params(o2pic_mlp* m, float* host_params);
+int o2pic_mlp_forward(o2pic_mlp* m, const float* X, float* Y, int32_t B, void* stream);
+/* loss = mean over B x out of (Y - T)^2; grad (may be NULL) = its gradient
+ * in the parameter layout. */
+int o2pic_mlp_gradients(o2pic_mlp* m, const float* X, const float* T, int32_t B, float* grad, float* loss,
+                        void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the same loss. */
+int o2pic_mlp_train_step(o2pic_mlp* m, const float* X, const float* T, int32_t B, float lr, float* loss,
+                         void* stream);
+void o2pic_mlp_destroy(o2pic_mlp* m);
 
 const char* o2pic_strerror(int code);
 

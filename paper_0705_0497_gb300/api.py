@@ -110,8 +110,17 @@ SIGNATURES = [
     ("o2pic_batch_create", _i32, [_P(_vp), ctypes.c_int32, _u64, _P(_vp)]),
     ("o2pic_batch_step", _i32, [_vp, _u64]),
     ("o2pic_batch_synchronize", _i32, [_vp]),
+    ("o2pic_batch_stream", _vp, [_vp]),
     ("o2pic_batch_autotune", _i32, [_vp, _vp]),
     ("o2pic_batch_destroy", None, [_vp]),
+    ("o2pic_mlp_create", _i32, [_P(ctypes.c_int32), ctypes.c_int32, _u64, _P(_vp)]),
+    ("o2pic_mlp_num_params", _u64, [_vp]),
+    ("o2pic_mlp_set_params", _i32, [_vp, _vp]),
+    ("o2pic_mlp_get_params", _i32, [_vp, _vp]),
+    ("o2pic_mlp_forward", _i32, [_vp, _vp, _vp, ctypes.c_int32, _vp]),
+    ("o2pic_mlp_gradients", _i32, [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
+    ("o2pic_mlp_train_step", _i32, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp, _vp]),
+    ("o2pic_mlp_destroy", None, [_vp]),
     ("o2pic_strerror", ctypes.c_char_p, [_i32]),
     ("o2pic_destroy", None, [_vp]),
     ("o2pic_version", _i32, []),
@@ -381,6 +390,24 @@ class Batch:
     def synchronize(self):
         _check(lib().o2pic_batch_synchronize(self.h), "o2pic_batch_synchronize")
 
+    def stream(self):
+        """The batch's CUDA stream as a torch stream (for events)."""
+        import torch
+        return torch.cuda.ExternalStream(lib().o2pic_batch_stream(self.h))
+
+    def timed_step(self, launches):
+        """step(launches) bracketed by CUDA events on the batch's stream;
+        returns the elapsed milliseconds."""
+        import torch
+        s = self.stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        self.step(launches)
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
     def autotune(self):
         r = TuneReport()
         _check(lib().o2pic_batch_autotune(self.h, ctypes.byref(r)), "o2pic_batch_autotune")
@@ -390,6 +417,68 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().o2pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The warm-start MLP (o2pic_mlp_*): bf16 weights, fp32 accumulation; the
+    tensors passed in are CUDA float32 tensors."""
+
+    def __init__(self, widths, seed=0):
+        self.widths = [int(w) for w in widths]
+        arr = (ctypes.c_int32 * len(self.widths))(*self.widths)
+        h = ctypes.c_void_p()
+        _check(lib().o2pic_mlp_create(arr, len(self.widths), int(seed), ctypes.byref(h)), "o2pic_mlp_create")
+        self.h = h
+        self.n = int(lib().o2pic_mlp_num_params(self.h))
+
+    def params(self):
+        out = np.zeros(self.n, np.float32)
+        _check(lib().o2pic_mlp_get_params(self.h, out.ctypes.data_as(ctypes.c_void_p)), "o2pic_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.n
+        _check(lib().o2pic_mlp_set_params(self.h, p.ctypes.data_as(ctypes.c_void_p)), "o2pic_mlp_set_params")
+
+    def forward(self, X, stream=None):
+        import torch
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], self.widths[-1]), dtype=torch.float32, device=X.device)
+        _check(lib().o2pic_mlp_forward(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                       int(X.shape[0]), _stream_ptr(stream)), "o2pic_mlp_forward")
+        return Y
+
+    def gradients(self, X, T, stream=None):
+        import torch
+        X, T = X.contiguous(), T.contiguous()
+        g = torch.empty(self.n, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib().o2pic_mlp_gradients(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                         int(X.shape[0]), ctypes.c_void_p(g.data_ptr()),
+                                         ctypes.c_void_p(loss.data_ptr()), _stream_ptr(stream)),
+               "o2pic_mlp_gradients")
+        return g, loss
+
+    def train_step(self, X, T, lr, loss=None, stream=None):
+        import torch
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib().o2pic_mlp_train_step(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                          int(X.shape[0]), float(lr), ctypes.c_void_p(loss.data_ptr()),
+                                          _stream_ptr(stream)), "o2pic_mlp_train_step")
+        return loss
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().o2pic_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1039,6 +1039,8 @@ int o2pic_batch_step(o2pic_batch* b, uint64_t launches) {
     return O2PIC_OK;
 }
 
+void* o2pic_batch_stream(o2pic_batch* b) { return b ? (void*)b->stream : nullptr; }
+
 int o2pic_batch_synchronize(o2pic_batch* b) {
     if (!b) return O2PIC_E_INVALID_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return O2PIC_E_CUDA;
