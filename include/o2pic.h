@@ -53,9 +53,11 @@ enum { O2PIC_E = 0, O2PIC_OM = 1, O2PIC_OP = 2 };
  *   CX         (9): O2+ + O2 charge exchange (ion takes the target velocity)
  *   NEUTRALIZE (17): O- + O2+ -> neutrals, binary, cell-local (give it with
  *              species O-, target ION; sigma is the neutralization cross
- *              section, e.g. the Landau-Zener form of the paper) */
+ *              section, e.g. the Landau-Zener form of the paper)
+ *   RECOMBINE  (16): e + O2+ -> O + O, binary and cell-local like (17), on
+ *              ion steps before (17) (species e, target ION) */
 enum { O2PIC_ELASTIC = 0, O2PIC_EXCITE = 1, O2PIC_IONIZE = 2, O2PIC_ATTACH = 3,
-       O2PIC_DETACH = 4, O2PIC_CX = 5, O2PIC_NEUTRALIZE = 6 };
+       O2PIC_DETACH = 4, O2PIC_CX = 5, O2PIC_NEUTRALIZE = 6, O2PIC_RECOMBINE = 7 };
 
 /* Targets: ground-state O2 (density p/kT), metastable O2(a1Dg) (density
  * C_meta p/kT, Sec. 2), or the other ion species (neutralization only). */
@@ -119,6 +121,7 @@ typedef struct {
     uint64_t next_id[O2PIC_NSPECIES];
     uint64_t error_flags;
     uint64_t particle_steps_species[O2PIC_NSPECIES];  /* particles pushed, per species */
+    uint64_t recombined, rec_candidates;              /* (16): pairs removed, pairs tested */
 } o2pic_stats;
 
 /* Fills `cfg` with the defaults (parity-case geometry, T_gas = 300 K, O, O2
@@ -134,7 +137,7 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out);
  * on 32 points per octave over [2^-10, 2^12] eV (FP64, stored FP32 as
  * cumulative sums), nu_max and P_max = 1 - exp(-nu_max dt_s) (null-collision
  * method, Sec. 2), and the (17) rate-coefficient table; copies them to the
- * device.  At most O2PIC_MAXPROC processes per species, one NEUTRALIZE.
+ * device.  At most O2PIC_MAXPROC processes per species, one NEUTRALIZE, one RECOMBINE.
  * Errors: INVALID_ARG. */
 int o2pic_set_processes(o2pic_ctx* ctx, const o2pic_process* procs, int nproc);
 
@@ -198,7 +201,7 @@ int o2pic_set_step(o2pic_ctx* ctx, uint64_t step);
 /* Kernel timing with CUDA events on the launching stream: on != 0 records an
  * event pair around every launch; o2pic_get_timing returns, per kernel kind
  * (0 push e, 1 push O-, 2 push O2+, 3 pair histograms, 4 pair, 5 field,
- * 6 compact, 7 deposit, 8 collisions e, 9 collisions O-, 10 collisions O2+),
+ * 6 compact, 7 deposit, 8 collisions e, 9 collisions O-, 10 collisions O2+, 11 (16) pairing),
  * the summed milliseconds and launches; items is reserved (zeros). */
 int o2pic_set_timing(o2pic_ctx* ctx, int on);
 int o2pic_get_timing(o2pic_ctx* ctx, double* ms, uint64_t* launches, uint64_t* items, int nkinds);

@@ -37,7 +37,7 @@ COUNTER_NAMES = ([f"events_{s}_{k}" for s in range(NSP) for k in range(MAXPROC)]
                  [f"absorbed_{s}_{w}" for s in range(NSP) for w in range(2)] +
                  [f"born_{s}" for s in range(NSP)] +
                  ["neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries",
-                  "warn_pair_gt1", "id_overflow"])
+                  "warn_pair_gt1", "id_overflow", "recombined", "rec_candidates"])
 
 
 def lib():

@@ -53,7 +53,8 @@ const double EPS0 = 8.8541878128e-12;  // vacuum permittivity [F/m]
 const double TWO_PI = 6.283185307179586476925286766559;
 
 enum { SP_E = 0, SP_OM = 1, SP_OP = 2, NSP = 3 };
-enum { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6 };
+enum { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6,
+       K_RECOMBINE = 7 };
 enum { T_O2 = 0, T_O2_META = 1, T_ION = 2 };
 
 // Energy grid of the rate tables: 32 points per octave on [2^-10, 2^12] eV.
@@ -66,7 +67,7 @@ const int MAX_TRIES = 32;                        // rejection-loop cap
 const double FIX_ONE = 65536.0;                  // CIC fixed point: 2^16 per particle
 
 // RNG stream tags (counter word 1).
-enum { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4 };
+enum { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6 };
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
@@ -283,6 +284,8 @@ struct Counters {
     uint64_t warn_tries;           // rejection loop exhausted
     uint64_t warn_pair_gt1;        // neutralization probability > 1
     uint64_t id_overflow;
+    uint64_t recombined;           // pairs removed by (16)
+    uint64_t rec_candidates;       // pairs tested by (16)
 };
 
 template <class R> struct Oracle {
@@ -310,6 +313,10 @@ template <class R> struct Oracle {
     bool have_neutral;
     Proc neutral;
     std::vector<R> Ktab;              // [NGRID] sigma_n g
+    bool have_recomb;
+    Proc recomb;
+    std::vector<R> Ktab_r;            // [NGRID] sigma_r g  (16)
+    R kappa_r;
     // state
     Particles<R> sp[NSP];
     uint32_t next_id[NSP];
@@ -350,7 +357,10 @@ template <class R> struct Oracle {
         kappa_n = (R)(0.5 * mun / QE);
         double dt_ion = cfg.dt * (double)cfg.ion_subcycle;
         pair_factor = (R)(cfg.weight * dt_ion / (cfg.area * dx));
+        const double mur = cfg.m_e * cfg.m_OP / (cfg.m_e + cfg.m_OP);
+        kappa_r = (R)(0.5 * mur / QE);
         have_neutral = false;
+        have_recomb = false;
         step = 0; acc_steps = 0;
         phi.assign(Ng, 0.0); Efield.assign(Ng, 0.0); Eg.assign(Ng, (R)0);
         std::memset(&cnt, 0, sizeof(cnt));
@@ -364,6 +374,7 @@ template <class R> struct Oracle {
     int set_processes(const oracle_process* p, int n) {
         for (int s = 0; s < NSP; ++s) { procs[s].clear(); cum[s].clear(); nu64[s].clear(); }
         have_neutral = false;
+        have_recomb = false;
         for (int j = 0; j < n; ++j) {
             const oracle_process& q = p[j];
             if (q.n < 1 || q.species < 0 || q.species >= NSP) return -1;
@@ -371,6 +382,10 @@ template <class R> struct Oracle {
             pr.E.assign(q.E_eV, q.E_eV + q.n); pr.s.assign(q.sigma_m2, q.sigma_m2 + q.n);
             for (int i = 1; i < q.n; ++i) if (!(pr.E[i] > pr.E[i - 1])) return -1;
             if (q.kind == K_NEUTRALIZE) { neutral = pr; have_neutral = true; continue; }
+            if (q.kind == K_RECOMBINE) {
+                if (q.species != SP_E) return -1;
+                recomb = pr; have_recomb = true; continue;
+            }
             if ((int)procs[q.species].size() >= MAXPROC) return -1;
             procs[q.species].push_back(pr);
         }
@@ -406,6 +421,15 @@ template <class R> struct Oracle {
                 double Ei = grid_energy(i);
                 double g = std::sqrt(2.0 * QE * Ei / mun);
                 Ktab[i] = (R)(sigma_at(neutral.E, neutral.s, neutral.thr, Ei) * g);
+            }
+        }
+        Ktab_r.assign(NGRID, (R)0);
+        if (have_recomb) {
+            double mur = cfg.m_e * cfg.m_OP / (cfg.m_e + cfg.m_OP);
+            for (int i = 0; i < NGRID; ++i) {
+                double Ei = grid_energy(i);
+                double g = std::sqrt(2.0 * QE * Ei / mur);
+                Ktab_r[i] = (R)(sigma_at(recomb.E, recomb.s, recomb.thr, Ei) * g);
             }
         }
         return 0;
@@ -640,51 +664,67 @@ template <class R> struct Oracle {
         P = out;
     }
 
-    // ---- (17) O- + O2+ -> neutrals, cell-binned binary process.
-    // In each cell j, list the O- and the O2+ in array order; with
-    // m = min(n-, n+), M = max(n-, n+) and a cell shift r_j drawn per cell and
-    // step, the i-th member of the shorter list (i < m) is paired with member
-    // (i + r_j) mod M of the longer list (O- counts as shorter on a tie).  A
-    // pair reacts with probability P = M w sigma_n(E_rel) g dt_ion / (A dx),
-    // which gives n- n+ w <sigma g> dt / (A dx) reactions per cell and step.
-    void neutralize(uint64_t n) {
-        if (!have_neutral) return;
+    // ---- cell-binned binary processes between species A and B (the
+    // reading of (17), also used for (16)).  In each cell j, list the A and
+    // the B particles in array order; with m = min(nA, nB), M = max(nA, nB)
+    // and a cell shift r_j drawn per cell and step, the i-th member of the
+    // shorter list (i < m) is paired with member (i + r_j) mod M of the
+    // longer list (A counts as shorter on a tie).  A pair reacts with
+    // probability P = M w sigma(E_rel) g dt_ion / (A dx), which gives
+    // nA nB w <sigma g> dt / (A dx) reactions per cell and step; both
+    // particles are removed.  The acceptance number comes from the A
+    // particle's stream.
+    void pair_process(uint64_t n, int A, int B, const std::vector<R>& K_tab, R kap, uint32_t tag_shift,
+                      uint32_t tag_pair, uint64_t& tested, uint64_t& reacted) {
         int Nc = cfg.n_cells;
-        std::vector<std::vector<size_t>> LM(Nc), LP(Nc);
-        for (size_t i = 0; i < sp[SP_OM].size(); ++i) { int j; R fr; cell_of(sp[SP_OM].x[i], j, fr); LM[j].push_back(i); }
-        for (size_t i = 0; i < sp[SP_OP].size(); ++i) { int j; R fr; cell_of(sp[SP_OP].x[i], j, fr); LP[j].push_back(i); }
-        std::vector<char> deadM(sp[SP_OM].size(), 0), deadP(sp[SP_OP].size(), 0);
+        std::vector<std::vector<size_t>> LA(Nc), LB(Nc);
+        for (size_t i = 0; i < sp[A].size(); ++i) { int j; R fr; cell_of(sp[A].x[i], j, fr); LA[j].push_back(i); }
+        for (size_t i = 0; i < sp[B].size(); ++i) { int j; R fr; cell_of(sp[B].x[i], j, fr); LB[j].push_back(i); }
+        std::vector<char> deadA(sp[A].size(), 0), deadB(sp[B].size(), 0);
         for (int c = 0; c < Nc; ++c) {
-            size_t nm = LM[c].size(), npl = LP[c].size();
-            size_t m = std::min(nm, npl), M = std::max(nm, npl);
+            size_t na = LA[c].size(), nb = LB[c].size();
+            size_t m = std::min(na, nb), M = std::max(na, nb);
             if (m == 0) continue;
-            Stream sh((uint32_t)c, cfg.seed, n, TAG_SHIFT);
+            Stream sh((uint32_t)c, cfg.seed, n, tag_shift);
             uint32_t r = (uint32_t)(sh.next() % (uint32_t)M);
-            bool minus_short = (nm <= npl);
+            bool a_short = (na <= nb);
             for (size_t i = 0; i < m; ++i) {
                 size_t partner = (i + r) % M;
-                size_t a = minus_short ? LM[c][i] : LM[c][partner];
-                size_t b = minus_short ? LP[c][partner] : LP[c][i];
-                uint32_t ida = sp[SP_OM].id[a];
-                Stream st(ida, cfg.seed, n, TAG_PAIR);
+                size_t a = a_short ? LA[c][i] : LA[c][partner];
+                size_t b = a_short ? LB[c][partner] : LB[c][i];
+                Stream st(sp[A].id[a], cfg.seed, n, tag_pair);
                 R u = uniform<R>(st.next());
-                R gx = sp[SP_OM].vx[a] - sp[SP_OP].vx[b];
-                R gy = sp[SP_OM].vy[a] - sp[SP_OP].vy[b];
-                R gz = sp[SP_OM].vz[a] - sp[SP_OP].vz[b];
-                R E = kappa_n * dot3<R>(gx, gy, gz, gx, gy, gz);
+                R gx = sp[A].vx[a] - sp[B].vx[b];
+                R gy = sp[A].vy[a] - sp[B].vy[b];
+                R gz = sp[A].vz[a] - sp[B].vz[b];
+                R E = kap * dot3<R>(gx, gy, gz, gx, gy, gz);
                 int gi; R gw; bool above;
                 grid_locate<R>(E, gi, gw, above);
                 if (above) cnt.warn_emax += 1;
-                R K = grid_interp<R>(Ktab, 1, 0, gi, gw);
+                R K = grid_interp<R>(K_tab, 1, 0, gi, gw);
                 R P = K * (pair_factor * (R)M);
-                cnt.pair_candidates += 1;
+                tested += 1;
                 if (P > (R)1) cnt.warn_pair_gt1 += 1;
-                if (u < P) { deadM[a] = 1; deadP[b] = 1; cnt.neutralized += 1; }
+                if (u < P) { deadA[a] = 1; deadB[b] = 1; reacted += 1; }
             }
         }
-        filter(sp[SP_OM], deadM);
-        filter(sp[SP_OP], deadP);
+        filter(sp[A], deadA);
+        filter(sp[B], deadB);
     }
+
+    // (17) O- + O2+ -> O + O2
+    void neutralize(uint64_t n) {
+        if (!have_neutral) return;
+        pair_process(n, SP_OM, SP_OP, Ktab, kappa_n, TAG_SHIFT, TAG_PAIR, cnt.pair_candidates, cnt.neutralized);
+    }
+
+    // (16) e + O2+ -> O + O, on ion steps before (17) (reading: the paper
+    // gives no order; the two then never claim the same O2+)
+    void recombine(uint64_t n) {
+        if (!have_recomb) return;
+        pair_process(n, SP_E, SP_OP, Ktab_r, kappa_r, TAG_SHIFT_REC, TAG_REC, cnt.rec_candidates, cnt.recombined);
+    }
+
     static void filter(Particles<R>& P, const std::vector<char>& dead) {
         Particles<R> out;
         for (size_t i = 0; i < P.size(); ++i)
@@ -717,6 +757,7 @@ template <class R> struct Oracle {
         if (ion_step) {
             process_species(SP_OM, n, births);
             process_species(SP_OP, n, births);
+            recombine(n);
             neutralize(n);
         }
         append_births(births);

@@ -17,7 +17,7 @@ MAXPROC = 16
 E, OM, OP = 0, 1, 2
 HOST, DEVICE = 0, 1
 KERNEL_KINDS = ("push_e", "push_om", "push_op", "pair_hist", "pair", "field", "compact", "deposit",
-                "cand_e", "cand_om", "cand_op")
+                "cand_e", "cand_om", "cand_op", "recomb")
 
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "ID_OVERFLOW", -4: "NONFINITE", -5: "CUDA", -6: "TIMEOUT",
@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("warn_emax", ctypes.c_uint64), ("warn_tries", ctypes.c_uint64), ("warn_pair_gt1", ctypes.c_uint64),
                 ("id_overflow", ctypes.c_uint64), ("step", ctypes.c_uint64), ("live", ctypes.c_uint64 * NSP),
                 ("slots", ctypes.c_uint64 * NSP), ("next_id", ctypes.c_uint64 * NSP),
-                ("error_flags", ctypes.c_uint64), ("particle_steps_species", ctypes.c_uint64 * NSP)]
+                ("error_flags", ctypes.c_uint64), ("particle_steps_species", ctypes.c_uint64 * NSP),
+                ("recombined", ctypes.c_uint64), ("rec_candidates", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {}
@@ -74,7 +75,7 @@ class Stats(ctypes.Structure):
             d[f"next_id_{s}"] = int(self.next_id[s])
             d[f"particle_steps_{s}"] = int(self.particle_steps_species[s])
         for n in ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
-                  "id_overflow", "step", "error_flags"):
+                  "id_overflow", "step", "error_flags", "recombined", "rec_candidates"):
             d[n] = int(getattr(self, n))
         return d
 

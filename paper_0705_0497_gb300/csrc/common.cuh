@@ -188,6 +188,16 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* ws, un
     return warp_excl + x - v;
 }
 
+// -------------------------------------------- programmatic dependent launch
+// The step kernels are launched with programmatic stream serialization: a
+// kernel may be scheduled while its predecessor in the stream still runs.
+// pdl_wait() returns once the predecessor has completed and its writes are
+// visible (immediately for a normal launch), so every such kernel calls it
+// before it reads anything a predecessor wrote.  pdl_trigger() lets the
+// successor be scheduled once every block of this grid has issued it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------- decoupled look-back
 // Per tile: a flag word = (epoch << 2) | state (1 = aggregate published,
 // 2 = inclusive prefix published) and two value words (val[2t] = aggregate,

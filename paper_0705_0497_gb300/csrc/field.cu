@@ -27,44 +27,6 @@ namespace {
 
 constexpr int FT = 1024;                          // threads of the field block
 
-// Block-wide inclusive scan of the int64 array a[0..n) in shared memory
-// (blocked: thread t owns [t*per, (t+1)*per)).  ws = 32 words of smem.
-__device__ __forceinline__ void block_scan_smem(long long* a, int n, long long* ws) {
-    const int t = threadIdx.x;
-    const int per = (n + FT - 1) / FT;
-    const int j0 = t * per;
-    long long run = 0;
-    for (int i = 0; i < per; ++i) {
-        const int j = j0 + i;
-        if (j < n) { run += a[j]; a[j] = run; }
-    }
-    const int lane = t & 31, warp = t >> 5;
-    long long x = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        long long v = ws[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        ws[lane] = v;
-    }
-    __syncthreads();
-    const long long off = (warp == 0 ? 0 : ws[warp - 1]) + (x - run);
-    for (int i = 0; i < per; ++i) {
-        const int j = j0 + i;
-        if (j < n) a[j] += off;
-    }
-    __syncthreads();
-}
-
 // Births of one step, placed in the order the method defines (source species
 // e then O-, parent order, e before O2+ for an ionization): each warp of a
 // particle kernel staged the births of its slot range [u R, ...) with their
@@ -228,6 +190,8 @@ __device__ __forceinline__ void block_scan_smem_pair(long long* a, long long* b,
 // birth counts and U sin(2 pi f t).
 __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
     extern __shared__ long long fsm[];
+    pdl_wait();
+    pdl_trigger();   // one block on one SM: the next step's push may take the others
     __shared__ long long ws[64];
     __shared__ unsigned long long ws2[32];
     __shared__ CtrlSnap cs;
@@ -319,6 +283,47 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
     if (qb_global) __threadfence();
     __syncthreads();
 
+    // ---- commit of the step (early: its stores overlap the field solve,
+    // which reads only the snapshot).  Removals of (17) first.
+    if (mode == 0) {
+        // (17) removals: mark both ions of every reacted pair dead
+        const unsigned nrem = (cs.removals < P.max_removals) ? cs.removals : P.max_removals;
+        for (unsigned r = t; r < nrem; r += FT) {
+            P.sp[SP_OM].x[cs.cur[SP_OM]][P.removal[2 * r]] = dead_marker();
+            P.sp[SP_OP].x[cs.cur[SP_OP]][P.removal[2 * r + 1]] = dead_marker();
+        }
+        // commit of the step: one thread per species, then the step counters
+        if (t < NSP) {
+            const int s = t;
+            const unsigned long long bs = (s == SP_E) ? btot[B_E_FROM_E] + btot[B_E_FROM_OM]
+                                                      : (s == SP_OP ? btot[B_OP_FROM_E] : btot[B_OM_FROM_E]);
+            const unsigned long long rem = cs.removed[s] + ((s != SP_E) ? (unsigned long long)nrem : 0ull);
+            unsigned long long ns = cs.slots[s] + bs;
+            unsigned long long nl = cs.live[s] + bs - rem;
+            if (ns > P.sp[s].cap) {   // births beyond the capacity were dropped
+                atomicOr(&C->error_flags, ERR_CAPACITY);
+                nl -= (ns - P.sp[s].cap) < nl ? (ns - P.sp[s].cap) : nl;
+                ns = P.sp[s].cap;
+            }
+            const unsigned long long nid = (unsigned long long)cs.next_id[s] + bs;
+            if (nid > 0xFFFFFFFFull) { atomicOr(&C->error_flags, ERR_ID); atomicAdd(&C->cnt.id_overflow, 1ull); }
+            C->slots[s] = ns;
+            C->live[s] = nl;
+            C->next_id[s] = (unsigned)nid;
+            C->removed[s] = 0ull;
+            if (bs) atomicAdd(&C->cnt.born[s], bs);
+        } else if (t == 32) {
+            if (nrem) atomicAdd(&C->cnt.neutralized, (unsigned long long)nrem);
+            C->removals = 0u;
+            C->rremovals = 0u;
+            atomicAdd(&C->acc_steps, 1ull);
+            C->step = cs.step + 1;
+            atomicAdd(&C->epoch, 1ull);
+        } else if (t >= 64 && t < 64 + NKK + NSP) {
+            C->ticket[t - 64] = 0u;
+        }
+    }
+
     // ---- charge commit, moments, net charge.  bq shares its bytes with S and
     // U: every bq value is read (and net kept in registers) before S, U are
     // written.
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
         P.fU[j] = Us[j];
     }
     // per-cell ion totals of (17): zero for the next ion step
-    for (int k = t; k < 2 * N; k += FT) P.ptot[k] = 0u;
+    for (int k = t; k < 2 * N; k += FT) { P.ptot[k] = 0u; P.rtot[k] = 0u; }
     // conduction-current sums: after a load the ring restarts; at the end of
     // step n the ions' entries of a step without an ion push repeat those of
     // step n-1, and the slot of step n+1 is cleared for its pushes
@@ -396,46 +401,7 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
             P.jring[(n & (JRING - 1)) * NSP + sp] = P.jring[((n - 1) & (JRING - 1)) * NSP + sp];
         P.jring[((n + 1) & (JRING - 1)) * NSP + sp] = 0ull;
     }
-    if (mode != 0) {
-        if (t < NKK + NSP) C->ticket[t] = 0u;
-        return;
-    }
-
-    // (17) removals: mark both ions of every reacted pair dead
-    const unsigned nrem = (cs.removals < P.max_removals) ? cs.removals : P.max_removals;
-    for (unsigned r = t; r < nrem; r += FT) {
-        P.sp[SP_OM].x[cs.cur[SP_OM]][P.removal[2 * r]] = dead_marker();
-        P.sp[SP_OP].x[cs.cur[SP_OP]][P.removal[2 * r + 1]] = dead_marker();
-    }
-    // commit of the step: one thread per species, then the step counters
-    if (t < NSP) {
-        const int s = t;
-        const unsigned long long bs = (s == SP_E) ? btot[B_E_FROM_E] + btot[B_E_FROM_OM]
-                                                  : (s == SP_OP ? btot[B_OP_FROM_E] : btot[B_OM_FROM_E]);
-        const unsigned long long rem = cs.removed[s] + ((s != SP_E) ? (unsigned long long)nrem : 0ull);
-        unsigned long long ns = cs.slots[s] + bs;
-        unsigned long long nl = cs.live[s] + bs - rem;
-        if (ns > P.sp[s].cap) {   // births beyond the capacity were dropped
-            atomicOr(&C->error_flags, ERR_CAPACITY);
-            nl -= (ns - P.sp[s].cap) < nl ? (ns - P.sp[s].cap) : nl;
-            ns = P.sp[s].cap;
-        }
-        const unsigned long long nid = (unsigned long long)cs.next_id[s] + bs;
-        if (nid > 0xFFFFFFFFull) { atomicOr(&C->error_flags, ERR_ID); atomicAdd(&C->cnt.id_overflow, 1ull); }
-        C->slots[s] = ns;
-        C->live[s] = nl;
-        C->next_id[s] = (unsigned)nid;
-        C->removed[s] = 0ull;
-        if (bs) atomicAdd(&C->cnt.born[s], bs);
-    } else if (t == 32) {
-        if (nrem) atomicAdd(&C->cnt.neutralized, (unsigned long long)nrem);
-        C->removals = 0u;
-        atomicAdd(&C->acc_steps, 1ull);
-        C->step = cs.step + 1;
-        atomicAdd(&C->epoch, 1ull);
-    } else if (t >= 64 && t < 64 + NKK + NSP) {
-        C->ticket[t - 64] = 0u;
-    }
+    if (mode != 0 && t < NKK + NSP) C->ticket[t] = 0u;
 }
 
 // Stable compaction of the live slots of one species into the other buffer
@@ -448,6 +414,7 @@ __global__ void __launch_bounds__(BLOCK) k_compact(Params P, int mode, unsigned 
                                                    unsigned long long* val_arg, float* ox, float* ovx, float* ovy,
                                                    float* ovz, uint32_t* oid, unsigned long long ocap,
                                                    unsigned long long* out_count) {
+    pdl_wait();
     __shared__ unsigned ws[32];
     __shared__ unsigned sh_tile;
     __shared__ unsigned long long sh_excl;
@@ -606,7 +573,7 @@ void launch_phi(const Params& P, cudaStream_t s) {
 }
 
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s) {
-    k_field<<<1, FT, field_smem_bytes(P), s>>>(P, mode, pushed_mask);
+    launch_pdl(k_field, 1, FT, field_smem_bytes(P), s, P, mode, pushed_mask);
 }
 
 cudaError_t configure_field_smem(size_t bytes) {
@@ -614,9 +581,10 @@ cudaError_t configure_field_smem(size_t bytes) {
 }
 
 void launch_compact(int species, const Params& P, int grid, cudaStream_t s) {
-    if (species == SP_E) k_compact<SP_E><<<grid, BLOCK, 0, s>>>(P, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
-    else if (species == SP_OM) k_compact<SP_OM><<<grid, BLOCK, 0, s>>>(P, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
-    else k_compact<SP_OP><<<grid, BLOCK, 0, s>>>(P, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+    auto k = species == SP_E ? k_compact<SP_E> : (species == SP_OM ? k_compact<SP_OM> : k_compact<SP_OP>);
+    launch_pdl(k, grid, BLOCK, 0, s, P, 0, 0ull, (unsigned*)nullptr, (unsigned long long*)nullptr,
+               (unsigned long long*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr,
+               (uint32_t*)nullptr, 0ull, (unsigned long long*)nullptr);
 }
 
 void launch_gather(int species, const Params& P, int grid, unsigned long long epoch, unsigned* ticket,

@@ -2,11 +2,30 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "o2pic.h"
 
 namespace o2 {
+
+// Launch with programmatic stream serialization (see pdl_wait in common.cuh).
+template <typename... Params_, typename... Args>
+inline void launch_pdl(void (*kernel)(Params_...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 
 constexpr int NSP = 3;
 constexpr int SP_E = 0, SP_OM = 1, SP_OP = 2;
@@ -33,7 +52,7 @@ constexpr int MAX_NODES = 8193;         // grid limit (smem field and histograms
 constexpr int JRING = 8192;             // steps of conduction-current sums kept on the device
 
 enum Kind { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6 };
-enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4 };
+enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6 };
 
 // device error bits
 constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE = 4ull, ERR_TIMEOUT = 8ull;
@@ -41,7 +60,7 @@ constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE =
 // kernel kinds (timing, tickets)
 enum KernelKind { KK_PUSH_E = 0, KK_PUSH_OM = 1, KK_PUSH_OP = 2, KK_PAIR_HIST = 3, KK_PAIR = 4,
                   KK_FIELD = 5, KK_COMPACT = 6, KK_DEPOSIT = 7, KK_CAND_E = 8, KK_CAND_OM = 9, KK_CAND_OP = 10,
-                  NKK = 11 };
+                  KK_REC = 11, NKK = 12 };
 
 // Counters: same layout as the head of o2pic_stats.
 struct DevCounters {
@@ -52,6 +71,7 @@ struct DevCounters {
     unsigned long long warn_emax, warn_tries, warn_pair_gt1;
     unsigned long long id_overflow;
     unsigned long long psteps[NSP];
+    unsigned long long recombined, rec_candidates;
 };
 
 // Births appended by one kernel into species d: births of the electron
@@ -73,7 +93,7 @@ struct DevCtrl {
     unsigned int cur[NSP];                 // current buffer (ping-pong) per species
     unsigned int ticket[NKK + NSP];        // tile tickets per kernel kind, + compaction per species
     unsigned int removals;                 // (17) pairs to remove
-    unsigned int pad;
+    unsigned int rremovals;                // (16) pairs to remove
     DevCounters cnt;
 };
 
@@ -139,8 +159,33 @@ struct Params {
     unsigned int* ptot;          // [2][Nc]: live O-, O2+ per cell (cleared by the end-of-step kernel)
     unsigned int* removal;       // [2 * max_removals]: O- slot, O2+ slot
     unsigned int max_removals;
+    // (16): per-tile per-cell counts of live e and O2+, per-cell totals, pairs
+    const float* Ktab_r;         // [NGRID] sigma_r g
+    float Kmax_r_hi, kappa_r;
+    int have_recomb;
+    unsigned int* rhist[2];      // 0: e, 1: O2+
+    unsigned int* rtot;          // [2][Nc] (cleared by the end-of-step kernel)
+    unsigned int* rremoval;      // [2 * max_rremovals]: e slot, O2+ slot
+    unsigned int max_rremovals;
     // compaction trigger
     float compact_dead_frac;
+};
+
+// A cell-binned binary process between species A and B (the reading of
+// (17), also used for (16)): A's id draws the acceptance number; reacted
+// pairs go to a removal list (A slot, B slot).
+struct PairSpec {
+    int A, B;
+    unsigned int* histA;         // [tiles of A][Nc] live A per cell
+    unsigned int* histB;
+    unsigned int* tot;           // [2][Nc]: A, B per cell
+    const float* K;              // [NGRID] sigma g
+    float Kmax_hi, kappa;
+    uint32_t tag_pair, tag_shift;
+    unsigned int* removal;
+    unsigned int* nremovals;     // device counter of listed pairs
+    unsigned int max_removals;
+    unsigned long long* tested;  // device counter of pairs tested
 };
 
 __host__ __device__ inline unsigned long long ceil_div(unsigned long long a, unsigned long long b) {
@@ -158,9 +203,10 @@ __host__ __device__ inline unsigned warp_range_len(unsigned n, unsigned W) {
 // (defined in the kernel translation units, called by the runtime)
 void launch_push(int species, const Params& P, int grid, cudaStream_t s);
 void launch_cand(int species, const Params& P, int grid, cudaStream_t s);
-void launch_pair_hist(const Params& P, int grid, cudaStream_t s);
+void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t s);
 cudaError_t configure_pair_hist_smem(int Nc);
-void launch_pair(const Params& P, int grid, cudaStream_t s);
+void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s);
+void launch_pair_apply(const Params& P, const PairSpec& S, cudaStream_t s);
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s);
 void launch_phi(const Params& P, cudaStream_t s);
 void launch_compact(int species, const Params& P, int grid, cudaStream_t s);

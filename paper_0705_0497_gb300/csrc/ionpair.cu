@@ -24,6 +24,10 @@
 // Reactions only append (O- slot, O2+ slot) to the removal list and take the
 // pair out of the fresh deposit; both are order-independent, so flagged ions
 // may be resolved in any order.
+//
+// The kernels take the two species, tables and lists as a PairSpec: the same
+// code runs (16) e + O2+ -> O + O (A = e) before (17) (A = O-); the (16)
+// removals are applied by k_pair_apply before (17) counts its ions.
 #include "common.cuh"
 
 namespace o2 {
@@ -43,19 +47,20 @@ static_assert(MAX_NODES - 1 < CELL_DEAD, "cell index fits 15 bits");
 // positions): hist[sp][tile][cell]; and the per-cell totals ptot[sp][cell]
 // (zero on entry; the end-of-step kernel clears them).  Blocks take tiles of
 // O- first, then of O2+, and add their totals once at the end.
-__global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P) {
+__global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P, PairSpec Sp) {
     extern __shared__ unsigned hsm[];   // [Nc] tile counts, [2][Nc] block totals
+    pdl_wait();
     DevCtrl* C = P.ctrl;
     const int Nc = P.Nc;
     unsigned* bt = hsm + Nc;
     for (int c = threadIdx.x; c < 2 * Nc; c += HIST_T) bt[c] = 0u;
-    const unsigned long long nsm = C->slots[SP_OM], nsp = C->slots[SP_OP];
-    const unsigned ntm = (unsigned)ceil_div(nsm, TILE), ntp = (unsigned)ceil_div(nsp, TILE);
-    for (unsigned g = blockIdx.x; g < ntm + ntp; g += gridDim.x) {
-        const int sp = (g < ntm) ? 0 : 1;
-        const unsigned tile = (g < ntm) ? g : g - ntm;
-        const int S = sp == 0 ? SP_OM : SP_OP;
-        const unsigned long long n = sp == 0 ? nsm : nsp;
+    const unsigned long long nsa = C->slots[Sp.A], nsb = C->slots[Sp.B];
+    const unsigned nta = (unsigned)ceil_div(nsa, TILE), ntb = (unsigned)ceil_div(nsb, TILE);
+    for (unsigned g = blockIdx.x; g < nta + ntb; g += gridDim.x) {
+        const int sp = (g < nta) ? 0 : 1;
+        const unsigned tile = (g < nta) ? g : g - nta;
+        const int S = sp == 0 ? Sp.A : Sp.B;
+        const unsigned long long n = sp == 0 ? nsa : nsb;
         const float* __restrict__ X = P.sp[S].x[C->cur[S]];
         for (int c = threadIdx.x; c < Nc; c += HIST_T) hsm[c] = 0u;
         const unsigned long long base = (unsigned long long)tile * TILE;
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P) {
             }
         }
         __syncthreads();
-        unsigned* H = P.hist[sp] + (size_t)tile * Nc;
+        unsigned* H = (sp == 0 ? Sp.histA : Sp.histB) + (size_t)tile * Nc;
         for (int c = threadIdx.x; c < Nc; c += HIST_T) {
             const unsigned v = hsm[c];
             H[c] = v;
@@ -83,8 +88,9 @@ __global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P) {
         }
         __syncthreads();
     }
+    pdl_trigger();
     for (int c = threadIdx.x; c < 2 * Nc; c += HIST_T)
-        if (bt[c]) atomicAdd(&P.ptot[c], bt[c]);
+        if (bt[c]) atomicAdd(&Sp.tot[c], bt[c]);
 }
 
 __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* ws) {
@@ -96,7 +102,7 @@ __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* ws) {
 // Resolve one flagged O- (tile position pos, cell in cell16[pos]).  Every
 // thread of the block calls it; all return at the same point except at the
 // very end.  sh = 2 words of shared memory for the partner tile search.
-__device__ void resolve_one(const Params& P, unsigned pos, unsigned tile, unsigned long long base,
+__device__ void resolve_one(const Params& P, const PairSpec& Sp, unsigned pos, unsigned tile, unsigned long long base,
                             const unsigned short* cell16, unsigned* ws, unsigned* sh, unsigned long long step,
                             unsigned long long nsp, unsigned ntp, unsigned cm, unsigned cp, unsigned& gt1) {
     DevCtrl* C = P.ctrl;
@@ -105,7 +111,7 @@ __device__ void resolve_one(const Params& P, unsigned pos, unsigned tile, unsign
     const unsigned c = cell16[pos] & CELL_DEAD;
     // rank k of the O- in its cell list
     unsigned cnt = 0;
-    const unsigned* H0 = P.hist[0];
+    const unsigned* H0 = Sp.histA;
     for (unsigned t = tid; t < tile; t += PAIR_T) cnt += H0[(size_t)t * Nc + c];
 #pragma unroll 8
     for (int i = 0; i < PER_T; ++i) {
@@ -113,10 +119,10 @@ __device__ void resolve_one(const Params& P, unsigned pos, unsigned tile, unsign
         if (q < pos && (cell16[q] & CELL_DEAD) == c) ++cnt;
     }
     const unsigned k = block_sum(cnt, ws);
-    const unsigned nm = P.ptot[c], npl = P.ptot[Nc + c];
+    const unsigned nm = Sp.tot[c], npl = Sp.tot[Nc + c];
     const unsigned m = nm < npl ? nm : npl, M = nm < npl ? npl : nm;
     if (m == 0 || k >= nm) return;   // block-uniform
-    const uint4 wr = philox4x32_10(make_uint4((uint32_t)step, TAG_SHIFT, 0u, (uint32_t)(step >> 32)),
+    const uint4 wr = philox4x32_10(make_uint4((uint32_t)step, Sp.tag_shift, 0u, (uint32_t)(step >> 32)),
                                    make_uint2(c, P.seed));
     const unsigned r = wr.x % M;
     unsigned q;
@@ -128,7 +134,7 @@ __device__ void resolve_one(const Params& P, unsigned pos, unsigned tile, unsign
         q = i;
     }
     // O2+ tile holding rank q: thread t sums a contiguous group of tiles
-    const unsigned* H1 = P.hist[1];
+    const unsigned* H1 = Sp.histB;
     const unsigned per = (ntp + PAIR_T - 1) / PAIR_T;
     const unsigned t0 = (unsigned)tid * per, t1 = (t0 + per < ntp) ? t0 + per : ntp;
     unsigned gs = 0;
@@ -150,7 +156,7 @@ __device__ void resolve_one(const Params& P, unsigned pos, unsigned tile, unsign
     const unsigned lo = sh[0], want = sh[1];
     __syncthreads();
     // the partner's slot: rank `want` among the tile's live O2+ of cell c
-    const float* XP = P.sp[SP_OP].x[cp];
+    const float* XP = P.sp[Sp.B].x[cp];
     const unsigned long long bb = (unsigned long long)lo * TILE + (unsigned long long)tid * PER_T;
     float xs[PER_T];
 #pragma unroll
@@ -173,43 +179,44 @@ __device__ void resolve_one(const Params& P, unsigned pos, unsigned tile, unsign
     const unsigned b_slot = (unsigned)(bb + (unsigned)(__ffs(bits) - 1));
     // reaction test with the exact probability
     const unsigned long long p = base + pos;
-    const SpeciesBuf& SM = P.sp[SP_OM];
-    const SpeciesBuf& SPp = P.sp[SP_OP];
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)step, TAG_PAIR, 0u, (uint32_t)(step >> 32)),
+    const SpeciesBuf& SM = P.sp[Sp.A];
+    const SpeciesBuf& SPp = P.sp[Sp.B];
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)step, Sp.tag_pair, 0u, (uint32_t)(step >> 32)),
                                   make_uint2(SM.id[cm][p], P.seed));
     const float u = uniform(w.x);
     const float gx = SM.vx[cm][p] - SPp.vx[cp][b_slot];
     const float gy = SM.vy[cm][p] - SPp.vy[cp][b_slot];
     const float gz = SM.vz[cm][p] - SPp.vz[cp][b_slot];
-    const float E = P.kappa_n * dot3(gx, gy, gz, gx, gy, gz);
+    const float E = Sp.kappa * dot3(gx, gy, gz, gx, gy, gz);
     int gi; float gw; bool above;
     grid_locate(E, gi, gw, above);
     if (above) atomicAdd(&C->cnt.warn_emax, 1ull);
-    const float K = grid_interp(P.Ktab, 1, 0, gi, gw);
+    const float K = grid_interp(Sp.K, 1, 0, gi, gw);
     const float Pp = K * (P.pair_factor * (float)M);
     if (Pp > 1.0f) ++gt1;
     if (u < Pp) {
-        const unsigned idx = atomicAdd(&C->removals, 1u);
-        if (idx < P.max_removals) {
-            P.removal[2 * idx] = (unsigned)p;
-            P.removal[2 * idx + 1] = b_slot;
+        const unsigned idx = atomicAdd(Sp.nremovals, 1u);
+        if (idx < Sp.max_removals) {
+            Sp.removal[2 * idx] = (unsigned)p;
+            Sp.removal[2 * idx + 1] = b_slot;
         }
         // take both out of the fresh deposit
         int j; float f;
         cell_of(SM.x[cm][p], P.inv_dx, Nc, j, f);
         uint32_t rr = cic_r(f);
-        atomicAdd(&P.Qf[SP_OM][j], 0ull - (unsigned long long)(65536u - rr));
-        atomicAdd(&P.Qf[SP_OM][j + 1], 0ull - (unsigned long long)rr);
+        atomicAdd(&P.Qf[Sp.A][j], 0ull - (unsigned long long)(65536u - rr));
+        atomicAdd(&P.Qf[Sp.A][j + 1], 0ull - (unsigned long long)rr);
         cell_of(XP[b_slot], P.inv_dx, Nc, j, f);
         rr = cic_r(f);
-        atomicAdd(&P.Qf[SP_OP][j], 0ull - (unsigned long long)(65536u - rr));
-        atomicAdd(&P.Qf[SP_OP][j + 1], 0ull - (unsigned long long)rr);
+        atomicAdd(&P.Qf[Sp.B][j], 0ull - (unsigned long long)(65536u - rr));
+        atomicAdd(&P.Qf[Sp.B][j + 1], 0ull - (unsigned long long)rr);
     }
 }
 
 // One block per O- tile (grid-stride): the streaming pass, then the flagged
 // O- of the tile.  Block 0 also adds sum_c min(n-, n+) to the pair counter.
-__global__ void __launch_bounds__(PAIR_T) k_pair(Params P) {
+__global__ void __launch_bounds__(PAIR_T) k_pair(Params P, PairSpec Sp) {
+    pdl_wait();
     __shared__ unsigned short cell16[TILE];
     __shared__ unsigned short list[LCAP];
     __shared__ unsigned ws[32];
@@ -219,13 +226,13 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P) {
     const int Nc = P.Nc;
     const int tid = threadIdx.x;
     const unsigned long long step = C->step;
-    const unsigned long long nsm = C->slots[SP_OM], nsp = C->slots[SP_OP];
+    const unsigned long long nsm = C->slots[Sp.A], nsp = C->slots[Sp.B];
     const unsigned ntm = (unsigned)ceil_div(nsm, TILE), ntp = (unsigned)ceil_div(nsp, TILE);
-    const unsigned cm = C->cur[SP_OM], cp = C->cur[SP_OP];
-    const float* __restrict__ XM = P.sp[SP_OM].x[cm];
-    const uint32_t* __restrict__ IDM = P.sp[SP_OM].id[cm];
-    const unsigned* __restrict__ tot = P.ptot;
-    const uint4 ctr = make_uint4((uint32_t)step, TAG_PAIR, 0u, (uint32_t)(step >> 32));
+    const unsigned cm = C->cur[Sp.A], cp = C->cur[Sp.B];
+    const float* __restrict__ XM = P.sp[Sp.A].x[cm];
+    const uint32_t* __restrict__ IDM = P.sp[Sp.A].id[cm];
+    const unsigned* __restrict__ tot = Sp.tot;
+    const uint4 ctr = make_uint4((uint32_t)step, Sp.tag_pair, 0u, (uint32_t)(step >> 32));
     unsigned gt1 = 0;
 
     if (blockIdx.x == 0) {
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P) {
             pairs += a < b ? a : b;
         }
         const unsigned s = block_sum(pairs, ws);
-        if (tid == 0 && s) atomicAdd(&C->cnt.pair_candidates, (unsigned long long)s);
+        if (tid == 0 && s) atomicAdd(Sp.tested, (unsigned long long)s);
     }
 
     for (unsigned tile = blockIdx.x; tile < ntm; tile += gridDim.x) {
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P) {
                     const unsigned M = a < b ? b : a;
                     const float u = uniform(philox4x32_10(ctr, make_uint2(ids[i], P.seed)).x);
                     cc = (unsigned short)c;
-                    if (u < P.Kmax_hi * (P.pair_factor * (float)M)) {
+                    if (u < Sp.Kmax_hi * (P.pair_factor * (float)M)) {
                         cc |= CELL_FLAG;
                         const unsigned idx = atomicAdd(&nflag, 1u);
                         if (idx < LCAP) list[idx] = (unsigned short)pos;
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P) {
         const unsigned nf = nflag;
         if (nf > 0 && nf <= LCAP) {
             for (unsigned j = 0; j < nf; ++j)
-                resolve_one(P, list[j], tile, base, cell16, ws, sh, step, nsp, ntp, cm, cp, gt1);
+                resolve_one(P, Sp, list[j], tile, base, cell16, ws, sh, step, nsp, ntp, cm, cp, gt1);
         } else if (nf > LCAP) {
             // many flagged ions: list them segment by segment from the flags
             for (int seg = 0; seg < PER_T; ++seg) {
@@ -288,13 +295,34 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P) {
                 if (f) list[idx] = (unsigned short)pos;
                 __syncthreads();
                 for (unsigned j = 0; j < ns; ++j)
-                    resolve_one(P, list[j], tile, base, cell16, ws, sh, step, nsp, ntp, cm, cp, gt1);
+                    resolve_one(P, Sp, list[j], tile, base, cell16, ws, sh, step, nsp, ntp, cm, cp, gt1);
                 __syncthreads();
             }
         }
         __syncthreads();
     }
+    pdl_trigger();
     if (gt1) atomicAdd(&C->cnt.warn_pair_gt1, (unsigned long long)gt1);
+}
+
+// The removals of a pair process that runs before another (16 before 17):
+// mark both particles of every listed pair dead, count them, clear the list.
+__global__ void k_pair_apply(Params P, PairSpec Sp, unsigned long long* reacted) {
+    pdl_wait();
+    DevCtrl* C = P.ctrl;
+    const unsigned listed = *Sp.nremovals;
+    const unsigned n = listed < Sp.max_removals ? listed : Sp.max_removals;
+    const unsigned ca = C->cur[Sp.A], cb = C->cur[Sp.B];
+    for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        P.sp[Sp.A].x[ca][Sp.removal[2 * r]] = dead_marker();
+        P.sp[Sp.B].x[cb][Sp.removal[2 * r + 1]] = dead_marker();
+    }
+    pdl_trigger();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n) {
+        atomicAdd(&C->removed[Sp.A], (unsigned long long)n);
+        atomicAdd(&C->removed[Sp.B], (unsigned long long)n);
+        atomicAdd(reacted, (unsigned long long)n);
+    }
 }
 
 }  // namespace
@@ -306,12 +334,17 @@ cudaError_t configure_pair_hist_smem(int Nc) {
                                 (int)pair_hist_smem_bytes(Nc));
 }
 
-void launch_pair_hist(const Params& P, int grid, cudaStream_t s) {
-    k_pair_hist<<<grid, HIST_T, pair_hist_smem_bytes(P.Nc), s>>>(P);
+void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t s) {
+    launch_pdl(k_pair_hist, grid, HIST_T, pair_hist_smem_bytes(P.Nc), s, P, S);
 }
 
-void launch_pair(const Params& P, int grid, cudaStream_t s) {
-    k_pair<<<grid, PAIR_T, 0, s>>>(P);
+void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s) {
+    launch_pdl(k_pair, grid, PAIR_T, 0, s, P, S);
+}
+
+// the list counter is cleared by the end-of-step kernel
+void launch_pair_apply(const Params& P, const PairSpec& S, cudaStream_t s) {
+    launch_pdl(k_pair_apply, 8, 256, 0, s, P, S, &P.ctrl->cnt.recombined);
 }
 
 }  // namespace o2

@@ -33,15 +33,20 @@
 #ifndef O2PIC_PUSH_UNROLL
 #define O2PIC_PUSH_UNROLL 4
 #endif
+// Minimum resident blocks per SM of the collision kernel (caps its registers;
+// 2 timed fastest of 1-4 on the same workload).
+#ifndef O2PIC_CAND_MIN_BLOCKS
+#define O2PIC_CAND_MIN_BLOCKS 2
+#endif
 
 namespace o2 {
 
 namespace {
 
 template <int S> struct SpeciesTraits;
-template <> struct SpeciesTraits<SP_E> { static constexpr uint32_t tag = TAG_E; static constexpr int kk = KK_PUSH_E; };
-template <> struct SpeciesTraits<SP_OM> { static constexpr uint32_t tag = TAG_OM; static constexpr int kk = KK_PUSH_OM; };
-template <> struct SpeciesTraits<SP_OP> { static constexpr uint32_t tag = TAG_OP; static constexpr int kk = KK_PUSH_OP; };
+template <> struct SpeciesTraits<SP_E> { static constexpr uint32_t tag = TAG_E; };
+template <> struct SpeciesTraits<SP_OM> { static constexpr uint32_t tag = TAG_OM; };
+template <> struct SpeciesTraits<SP_OP> { static constexpr uint32_t tag = TAG_OP; };
 
 constexpr int WARPS = BLOCK / 32;           // 8
 constexpr int ROUND = 128;                  // slots per warp round (4 per lane)
@@ -194,15 +199,6 @@ __device__ __forceinline__ void deposit_sub_global(unsigned long long* Q, float 
     atomicAdd(&Q[j + 1], 0ull - (unsigned long long)r);
 }
 
-// deposit of a birth straight into the global accumulator (rare)
-__device__ __forceinline__ void deposit_global(unsigned long long* Q, float x, float inv_dx, int Nc) {
-    int j; float frac;
-    cell_of(x, inv_dx, Nc, j, frac);
-    const uint32_t r = cic_r(frac);
-    atomicAdd(&Q[j], (unsigned long long)(65536u - r));
-    atomicAdd(&Q[j + 1], (unsigned long long)r);
-}
-
 __device__ __forceinline__ void flush_hist(unsigned* hist, unsigned long long* Q, int Ng) {
     for (int j = threadIdx.x; j < Ng; j += BLOCK) {
         const unsigned v = hist[j];
@@ -228,6 +224,7 @@ __device__ __forceinline__ bool electron_is_real(const Params& P, const float* _
 template <int S>
 __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
+    pdl_wait();
     const int np = P.nproc[S];
     PushShared& sh = *reinterpret_cast<PushShared*>(smem);
     float* Es = reinterpret_cast<float*>(smem + align16(sizeof(PushShared)));
@@ -313,6 +310,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
             ncand += __popc(cm);
         }
     }
+    pdl_trigger();
     if (lane == 0) P.ccount[S][gw] = ncand;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) jacc += __shfl_down_sync(0xffffffffu, jacc, o);
@@ -351,7 +349,8 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
 // kinematics 32 at a time.  Births are ranked with ballots and staged at the
 // particle warp's slot range with their count.
 template <int S>
-__global__ void __launch_bounds__(BLOCK) k_cand(Params P) {
+__global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand(Params P) {
+    pdl_wait();
     __shared__ unsigned events[MAXPROC];
     __shared__ unsigned sh_removed, sh_wtries, sh_wemax;
     __shared__ uint4 q2w_all[WARPS][Q2];
@@ -495,6 +494,7 @@ __global__ void __launch_bounds__(BLOCK) k_cand(Params P) {
             if (cnt2) cnt2[gw] = nb2;
         }
     }
+    pdl_trigger();
     if (nremoved) atomicAdd(&sh_removed, nremoved);
     if (wtries) atomicAdd(&sh_wtries, wtries);
     if (wemax) atomicAdd(&sh_wemax, wemax);
@@ -549,15 +549,15 @@ size_t push_smem_bytes(int species, const Params& P) {
 
 void launch_push(int species, const Params& P, int grid, cudaStream_t s) {
     const size_t sm = push_smem_bytes(species, P);
-    if (species == SP_E) k_push<SP_E><<<grid, BLOCK, sm, s>>>(P);
-    else if (species == SP_OM) k_push<SP_OM><<<grid, BLOCK, sm, s>>>(P);
-    else k_push<SP_OP><<<grid, BLOCK, sm, s>>>(P);
+    if (species == SP_E) launch_pdl(k_push<SP_E>, grid, BLOCK, sm, s, P);
+    else if (species == SP_OM) launch_pdl(k_push<SP_OM>, grid, BLOCK, sm, s, P);
+    else launch_pdl(k_push<SP_OP>, grid, BLOCK, sm, s, P);
 }
 
 void launch_cand(int species, const Params& P, int grid, cudaStream_t s) {
-    if (species == SP_E) k_cand<SP_E><<<grid, BLOCK, 0, s>>>(P);
-    else if (species == SP_OM) k_cand<SP_OM><<<grid, BLOCK, 0, s>>>(P);
-    else k_cand<SP_OP><<<grid, BLOCK, 0, s>>>(P);
+    if (species == SP_E) launch_pdl(k_cand<SP_E>, grid, BLOCK, 0, s, P);
+    else if (species == SP_OM) launch_pdl(k_cand<SP_OM>, grid, BLOCK, 0, s, P);
+    else launch_pdl(k_cand<SP_OP>, grid, BLOCK, 0, s, P);
 }
 
 void launch_deposit(int species, const Params& P, int grid, cudaStream_t s) {

@@ -81,7 +81,7 @@ struct o2pic_ctx {
     bool loaded[NSP] = {false, false, false};
     int latched = 0;
     int grid_push[NSP] = {0, 0, 0};
-    int grid_pair = 0, grid_compact = 0, grid_deposit = 0;
+    int grid_pair = 0, grid_pair_e = 0, grid_compact = 0, grid_deposit = 0;
     unsigned long long launches = 0;
     unsigned long long gen = 0;        // bumped by every call that invalidates a captured graph
     unsigned long long ring_start = 0; // first step recorded in the current-sum ring
@@ -215,6 +215,8 @@ void set_constants(o2pic_ctx* c) {
     P.Lf = (float)g.L;
     const double mun = g.m_OM * g.m_OP / (g.m_OM + g.m_OP);
     P.kappa_n = (float)(0.5 * mun / QE);
+    const double mur = g.m_e * g.m_OP / (g.m_e + g.m_OP);
+    P.kappa_r = (float)(0.5 * mur / QE);
     const double dt_ion = g.dt * (double)g.ion_subcycle;
     P.pair_factor = (float)(g.weight * dt_ion / (g.area * dx));
     P.seed = g.seed;
@@ -282,9 +284,20 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
             if (P.nproc[SP_OM]) launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
             launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
             if (P.nproc[SP_OP]) launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
+            if (P.have_recomb) {
+                const PairSpec R{SP_E, SP_OP, P.rhist[0], P.rhist[1], P.rtot, P.Ktab_r, P.Kmax_r_hi, P.kappa_r,
+                                 TAG_REC, TAG_SHIFT_REC, P.rremoval, &c->d_ctrl->rremovals, P.max_rremovals,
+                                 &c->d_ctrl->cnt.rec_candidates};
+                launch(c, KK_REC, s, [&] { launch_pair_hist(P, R, c->grid_compact, s); });
+                launch(c, KK_REC, s, [&] { launch_pair(P, R, c->grid_pair_e, s); });
+                launch(c, KK_REC, s, [&] { launch_pair_apply(P, R, s); });
+            }
             if (P.have_neutral) {
-                launch(c, KK_PAIR_HIST, s, [&] { launch_pair_hist(P, c->grid_compact, s); });
-                launch(c, KK_PAIR, s, [&] { launch_pair(P, c->grid_pair, s); });
+                const PairSpec N{SP_OM, SP_OP, P.hist[0], P.hist[1], P.ptot, P.Ktab, P.Kmax_hi, P.kappa_n,
+                                 TAG_PAIR, TAG_SHIFT, P.removal, &c->d_ctrl->removals, P.max_removals,
+                                 &c->d_ctrl->cnt.pair_candidates};
+                launch(c, KK_PAIR_HIST, s, [&] { launch_pair_hist(P, N, c->grid_compact, s); });
+                launch(c, KK_PAIR, s, [&] { launch_pair(P, N, c->grid_pair, s); });
             }
         }
         launch(c, KK_FIELD, s, [&] { launch_field(P, 0, ion ? 7 : 1, s); });
@@ -376,6 +389,9 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     float* K;
     TRY(ctx_alloc(c, &K, NGRID));
     P.Ktab = K;
+    float* Kr;
+    TRY(ctx_alloc(c, &Kr, NGRID));
+    P.Ktab_r = Kr;
     TRY(ctx_alloc(c, &c->d_vring, VRING));
     P.vring = c->d_vring;
     P.vring_mask = VRING - 1;
@@ -408,6 +424,12 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     const unsigned long long tiles_ion = std::max(ceil_div(cfg->capacity[SP_OM], TILE), ceil_div(cfg->capacity[SP_OP], TILE)) + 1;
     TRY(ctx_alloc(c, &P.hist[0], tiles_ion * Nc));
     TRY(ctx_alloc(c, &P.hist[1], tiles_ion * Nc));
+    // (16): e and O2+ tiles, totals, pair list
+    TRY(ctx_alloc(c, &P.rhist[0], (ceil_div(cfg->capacity[SP_E], TILE) + 1) * Nc));
+    TRY(ctx_alloc(c, &P.rhist[1], (ceil_div(cfg->capacity[SP_OP], TILE) + 1) * Nc));
+    TRY(ctx_alloc(c, &P.rtot, 2 * (size_t)Nc));
+    P.max_rremovals = (unsigned)std::max<unsigned long long>(1, std::min(cfg->capacity[SP_E], cfg->capacity[SP_OP]));
+    TRY(ctx_alloc(c, &P.rremoval, 2 * (size_t)P.max_rremovals));
     TRY(ctx_alloc(c, &P.ptot, 2 * (size_t)Nc));
     P.max_removals = (unsigned)std::max<unsigned long long>(1, std::min(cfg->capacity[SP_OM], cfg->capacity[SP_OP]));
     TRY(ctx_alloc(c, &P.removal, 2 * (size_t)P.max_removals));
@@ -427,6 +449,8 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     TRY(configure_pair_hist_smem(Nc));
     for (int s = 0; s < NSP; ++s) P.nproc[s] = 0;
     c->grid_pair = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(tiles_ion, 8ull * c->num_sms));
+    c->grid_pair_e = (int)std::max<unsigned long long>(
+        1, std::min<unsigned long long>(ceil_div(cfg->capacity[SP_E], TILE) + 1, 8ull * c->num_sms));
     c->grid_compact = 4 * c->num_sms;
     c->grid_deposit = 4 * c->num_sms;
     // steady initial control state
@@ -455,12 +479,12 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
     if (!c || (nproc > 0 && !procs) || nproc < 0) return O2PIC_E_INVALID_ARG;
     const o2pic_config& g = c->cfg;
     std::vector<HostProc> sp[NSP];
-    HostProc neutral;
-    bool have_neutral = false;
+    HostProc neutral, recomb;
+    bool have_neutral = false, have_recomb = false;
     for (int j = 0; j < nproc; ++j) {
         const o2pic_process& q = procs[j];
         if (q.n < 1 || q.species < 0 || q.species >= NSP || !q.E_eV || !q.sigma_m2) return O2PIC_E_INVALID_ARG;
-        if (q.kind < O2PIC_ELASTIC || q.kind > O2PIC_NEUTRALIZE) return O2PIC_E_INVALID_ARG;
+        if (q.kind < O2PIC_ELASTIC || q.kind > O2PIC_RECOMBINE) return O2PIC_E_INVALID_ARG;
         HostProc p;
         p.kind = q.kind; p.target = q.target; p.thr = q.threshold_eV;
         p.E.assign(q.E_eV, q.E_eV + q.n);
@@ -470,6 +494,10 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
         if (q.kind == O2PIC_NEUTRALIZE) {
             if (have_neutral) return O2PIC_E_INVALID_ARG;
             neutral = p; have_neutral = true; continue;
+        }
+        if (q.kind == O2PIC_RECOMBINE) {
+            if (have_recomb || q.species != SP_E) return O2PIC_E_INVALID_ARG;
+            recomb = p; have_recomb = true; continue;
         }
         // kinematics exist for: e: elastic, excite, ionize, attach; O-: elastic, detach; O2+: elastic, cx
         const bool ok = (q.species == SP_E && (q.kind == O2PIC_ELASTIC || q.kind == O2PIC_EXCITE ||
@@ -539,6 +567,22 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
     // inflated by 2^-20 so that it covers them all
     P.Kmax_hi = (float)((double)kmax * (1.0 + std::ldexp(1.0, -20)));
     e = cudaMemcpy((void*)P.Ktab, K.data(), sizeof(float) * NGRID, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    // (16): the same table form with the e-O2+ reduced mass
+    std::vector<float> Kr(NGRID, 0.0f);
+    float krmax = 0.0f;
+    if (have_recomb) {
+        const double mur = g.m_e * g.m_OP / (g.m_e + g.m_OP);
+        for (int i = 0; i < NGRID; ++i) {
+            const double Ei = grid_energy(i);
+            const double gv = std::sqrt(2.0 * QE * Ei / mur);
+            Kr[i] = (float)(sigma_at(recomb, Ei) * gv);
+            krmax = std::max(krmax, Kr[i]);
+        }
+    }
+    P.have_recomb = have_recomb ? 1 : 0;
+    P.Kmax_r_hi = (float)((double)krmax * (1.0 + std::ldexp(1.0, -20)));
+    e = cudaMemcpy((void*)P.Ktab_r, Kr.data(), sizeof(float) * NGRID, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e);
     for (int s = 0; s < NSP; ++s) {
         int bps = 0;
@@ -636,7 +680,6 @@ int o2pic_step(o2pic_ctx* c, uint64_t nsteps, void* stream) {
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e);
     cudaStream_t s = pick(c, stream);
-    Params& P = c->P;
     if (c->dirty) {
         int rc = prepare(c, s);
         if (rc) return rc;
@@ -822,6 +865,8 @@ int o2pic_get_stats(o2pic_ctx* c, o2pic_stats* out) {
     out->warn_tries = h.cnt.warn_tries;
     out->warn_pair_gt1 = h.cnt.warn_pair_gt1;
     out->id_overflow = h.cnt.id_overflow;
+    out->recombined = h.cnt.recombined;
+    out->rec_candidates = h.cnt.rec_candidates;
     out->step = h.step;
     out->error_flags = h.error_flags;
     return rc;

@@ -30,8 +30,8 @@ from .inputs import EPS0, QE
 # species
 E, OM, OP = 0, 1, 2
 # process kinds (same numbering as the C ABI)
-ELASTIC, EXCITE, IONIZE, ATTACH, DETACH, CX, NEUTRALIZE = range(7)
-KIND_NAMES = ("elastic", "excite", "ionize", "attach", "detach", "cx", "neutralize")
+ELASTIC, EXCITE, IONIZE, ATTACH, DETACH, CX, NEUTRALIZE, RECOMBINE = range(8)
+KIND_NAMES = ("elastic", "excite", "ionize", "attach", "detach", "cx", "neutralize", "recombine")
 # targets
 T_O2, T_O2_META, T_ION = 0, 1, 2
 
@@ -164,9 +164,25 @@ def neutralization_process(R_x_m=1.0e-9):
     return _proc(OM, NEUTRALIZE, T_ION, 0.0, GRID, sigma_n(GRID, R_x_m), "(17) neutralization")
 
 
-def oxygen_set(include_ad=True, R_x_m=1.0e-9):
-    """The full 3-species set used by the workloads."""
-    return electron_processes() + om_processes(include_ad) + op_processes() + [neutralization_process(R_x_m)]
+def sigma_r(E_eV):
+    """(16) e + O2+ -> O + O dissociative recombination: placeholder
+    sigma_r = 3.4e-19 m^2 (1 eV / E), i.e. a rate coefficient sigma_r g of
+    2e-13 m^3/s at 1 eV that grows as E^-1/2 towards low energies.  The
+    paper lists (16) in Table 1 without its cross section."""
+    return 3.4e-19 / np.asarray(E_eV, dtype=np.float64)
+
+
+def recombination_process():
+    """(16) e + O2+ -> O + O, binary and cell-local like (17), on the grid."""
+    return _proc(E, RECOMBINE, T_ION, 0.0, GRID, sigma_r(GRID), "(16) recombination")
+
+
+def oxygen_set(include_ad=True, R_x_m=1.0e-9, include_rec=False):
+    """The full 3-species set used by the workloads ((16) on request)."""
+    out = electron_processes() + om_processes(include_ad) + op_processes() + [neutralization_process(R_x_m)]
+    if include_rec:
+        out.append(recombination_process())
+    return out
 
 
 def constant_rate_process(species, kind, nu0, n_target, mu, target=T_O2, thr=0.0):

@@ -1,0 +1,92 @@
+"""Parity at the benchmark's full size (scale_512: 512 cells, 4e6 e + 4e6 O-
++ 8e6 O2+), with the launch shape and step graph bench.py times, on outputs
+the oracle can compute one by one:
+
+* sampled particles: given the GPU's field E^n and a particle's state at
+  step n, the oracle's single-particle update (push, absorb, MCC) must give
+  exactly the GPU's state of that particle (by id) at n+1, or its removal;
+* the node charge of all particles after the step, against the oracle's
+  deposit of the GPU's particles (exact integers);
+* the field, against the oracle's closed-form solve of the GPU's charge.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SAMPLE = 20000
+
+
+def _index(ids):
+    order = np.argsort(ids, kind="stable")
+    return ids[order], order
+
+
+def _check_species(o, g_before, g_after, s, step, E, rng):
+    a, b = g_before, g_after
+    n = len(a["id"])
+    pick = rng.choice(n, size=min(SAMPLE, n), replace=False)
+    bid, border = _index(b["id"])
+    Ef = E.astype(np.float64)
+    same = gone = 0
+    for i in pick:
+        pid = int(a["id"][i])
+        alive, st, _ = o.update_particle(s, step, Ef, [a["x"][i], a["vx"][i], a["vy"][i], a["vz"][i]], pid)
+        k = np.searchsorted(bid, pid)
+        present = k < len(bid) and bid[k] == pid
+        if not alive:
+            assert not present, (s, pid)
+            gone += 1
+            continue
+        if not present:
+            # an ion removed by (17) after its push; only possible on ion steps
+            assert s != 0, (s, pid)
+            gone += 1
+            continue
+        j = border[k]
+        got = np.array([b["x"][j], b["vx"][j], b["vy"][j], b["vz"][j]], np.float64)
+        assert np.array_equal(got, np.asarray(st, np.float32).astype(np.float64)), (s, pid, got, st)
+        same += 1
+    return same, gone
+
+
+def test_scale_512_sampled_particles_charge_and_field(torch_cuda):
+    import oracle
+    from paper_0705_0497_gb300 import api, inputs, xsec
+    cfg, counts, T, _ = inputs.workload("scale_512")
+    procs = xsec.oxygen_set()
+    g = api.Discharge(cfg, tuple(int(n * 1.5) + (1 << 20) for n in counts), compact_check=20)
+    g.set_processes(procs)
+    g.load_state(inputs.initial_state(cfg, counts, T))
+    b = api.Batch([g], steps_per_launch=20)
+    b.step(2)                       # steps 0..39 through the step graph
+    b.synchronize()
+    b.close()
+    o = oracle.Oracle(cfg, 32)
+    o.set_processes(procs)
+    rng = np.random.default_rng(12)
+    g.step(1)                       # ion step 40
+    for step, species in ((41, (0,)), (50, (0, 1, 2))):
+        while g.stats()["step"] < step:
+            g.step(1)
+        before = [g.particles(s) for s in range(3)]
+        _, E = g.field()
+        g.step(1)
+        after = [g.particles(s) for s in range(3)]
+        for s in species:
+            same, gone = _check_species(o, before[s], after[s], s, step, E, rng)
+            assert same > 0.9 * min(SAMPLE, len(before[s]["id"])), (s, same, gone)
+        # charge of all particles after the step, and the field it gives
+        Q, _, _ = g.charge()
+        for s in range(3):
+            assert np.array_equal(Q[s], oracle.deposit(cfg["n_cells"], cfg["L"], after[s]["x"])), s
+        Rnet = Q[2].astype(np.int64) - Q[0].astype(np.int64) - Q[1].astype(np.int64)
+        t = (step + 1) * cfg["dt"]
+        V0 = cfg["U"] * math.sin(2.0 * math.pi * cfg["f"] * t)
+        phi64, E64 = oracle.solve_field(cfg["n_cells"], cfg["L"] / cfg["n_cells"], cfg["weight"], cfg["area"], V0, Rnet)
+        phi, E1 = g.field()
+        assert np.array_equal(E1, E64.astype(np.float32))
+        assert np.array_equal(phi, phi64)
+    g.close()

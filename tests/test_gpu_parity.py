@@ -283,3 +283,47 @@ def test_current_densities_match_oracle(torch_cuda, S):
     from paper_0705_0497_gb300 import api
     with pytest.raises(api.O2picError):
         g.currents(55, 10)
+
+
+@pytest.mark.parametrize("n_e,n_op", [(30000, 26000), (20000, 30000)])
+def test_recombination_parity(torch_cuda, n_e, n_op):
+    """(16) e + O2+ with a large constant rate coefficient, run before (17)
+    on the same ion steps: the library's pairing against the oracle's, pair
+    for pair, and both counters.  (A small weight keeps the space-charge
+    field negligible; the acceptance probability does not depend on it.)"""
+    Nc = 32
+    cfg = inputs.base_config(L=0.02, n_cells=Nc, U=0.0, p=10.0, C_meta=0.0, ion_subcycle=2, weight=1e3, seed=5,
+                             steps_per_cycle=400)
+    dx = cfg["L"] / Nc
+    mur = cfg["m_e"] * cfg["m_OP"] / (cfg["m_e"] + cfg["m_OP"])
+    mun = cfg["m_OM"] * cfg["m_OP"] / (cfg["m_OM"] + cfg["m_OP"])
+    K0 = 1e-4 * cfg["area"] * dx / (cfg["weight"] * cfg["dt"] * 2)
+    procs = [xsec.constant_rate_process(0, xsec.RECOMBINE, K0, 1.0, mur, target=xsec.T_ION),
+             xsec.constant_rate_process(1, xsec.NEUTRALIZE, K0, 1.0, mun, target=xsec.T_ION)]
+    rng = np.random.default_rng(9)
+    st = []
+    for s, n in enumerate((n_e, 8000, n_op)):
+        x = ((rng.integers(0, Nc, n) + 0.05 + 0.9 * rng.random(n)) * dx).astype(np.float32)
+        v = (rng.standard_normal((3, n)) * (3e4 if s == 0 else 300.0)).astype(np.float32)
+        st.append(dict(x=x, vx=v[0].copy(), vy=v[1].copy(), vz=v[2].copy(), id=np.arange(n, dtype=np.uint32)))
+    g, o, _ = make_pair(cfg, None, None, procs, state=st)
+    for _ in range(3):
+        g.step(2)
+        o.step(2)
+        compare_particles(g, o)
+        compare_counters(g.stats(), o.counters(), nproc_of(procs))
+    c = o.counters()
+    assert c["recombined"] > 0.01 * min(n_e, n_op) and c["neutralized"] > 0
+
+
+def test_oxygen_set_with_recombination_100_steps(torch_cuda):
+    """The full process set with (16) added: 100 steps of the parity case,
+    per particle and every counter."""
+    cfg, counts, T, _ = inputs.workload("parity_128", ion_subcycle=2)
+    procs = xsec.oxygen_set(include_rec=True)
+    g, o, _ = make_pair(cfg, counts, T, procs)
+    g.step(100)
+    o.step(100)
+    compare_particles(g, o)
+    compare_counters(g.stats(), o.counters(), nproc_of(procs))
+    assert o.counters()["rec_candidates"] > 0

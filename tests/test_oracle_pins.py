@@ -710,3 +710,61 @@ def test_current_sum_is_the_displacement_rate(oracle_mod):
         js = int(o.current_sums(step, 1)[0, 0])
         bound = n * (dt / 256.0) + n * np.spacing(np.float32(L))
         assert abs(disp - dt * js / 256.0) <= bound, (step, disp, dt * js / 256.0, bound)
+
+
+# ------------------------------------------------------------- (16) pairing
+def test_recombination_expected_count_and_order(oracle_mod):
+    """Cell-binned (16) e + O2+ with a constant rate coefficient K: the
+    expected number of reactions per ion step is sum_cells n_e n_+ w K dt /
+    (A dx), electrons and ions removed in pairs.  With (16) and (17) both
+    certain and more electrons than O2+ in every cell, (16) runs first and
+    takes every O2+, so (17) finds none."""
+    Nc = 16
+    # a tiny weight: P_pair is fixed by K w, and the electrons feel no field
+    cfg = _cfg(n_cells=Nc, weight=1.0e-3, ion_subcycle=1)
+    dx = cfg["L"] / Nc
+    K0 = 2.0e-4 * cfg["area"] * dx / (cfg["weight"] * cfg["dt"])   # P_pair = 2e-4 M
+    mur = cfg["m_e"] * cfg["m_OP"] / (cfg["m_e"] + cfg["m_OP"])
+    pr = xsec.constant_rate_process(0, xsec.RECOMBINE, K0, 1.0, mur, target=xsec.T_ION)
+    rng = np.random.default_rng(16)
+    z = lambda n: np.zeros(n, np.float32)
+
+    def cells(counts):
+        x = np.concatenate([(c + 0.1 + 0.8 * rng.random(counts[c])) * dx for c in range(Nc)]).astype(np.float32)
+        rng.shuffle(x)
+        return x
+
+    expected, got = 0.0, 0
+    for trial in range(4):
+        cfg["seed"] = 200 + trial
+        o = oracle_mod.Oracle(cfg, 32)
+        o.set_processes([pr])
+        ne = rng.integers(200, 1200, Nc)
+        npl = rng.integers(200, 1200, Nc)
+        xe, xp = cells(ne), cells(npl)
+        # electrons and ions at rest at the same places: no net charge, no field
+        o.load(0, xe, z(len(xe)), z(len(xe)), z(len(xe)), np.arange(len(xe), dtype=np.uint32))
+        _empty(o, (1,))
+        o.load(2, xp, z(len(xp)), z(len(xp)), z(len(xp)), np.arange(len(xp), dtype=np.uint32))
+        o.step(1)
+        c = o.counters()
+        got += c["recombined"]
+        expected += float((ne * npl).sum()) * cfg["weight"] * K0 * cfg["dt"] / (cfg["area"] * dx)
+        assert c["rec_candidates"] == int(np.minimum(ne, npl).sum())
+        assert o.count(0) == len(xe) - c["recombined"] and o.count(2) == len(xp) - c["recombined"]
+    assert 2000 < expected < 20000
+    assert abs(got - expected) < 5 * math.sqrt(expected)
+    # order: both processes certain (P = M K w dt/(A dx) >= 1)
+    Kbig = 2.0 * cfg["area"] * dx / (cfg["weight"] * cfg["dt"])
+    mun = cfg["m_OM"] * cfg["m_OP"] / (cfg["m_OM"] + cfg["m_OP"])
+    o = oracle_mod.Oracle(cfg, 32)
+    o.set_processes([xsec.constant_rate_process(0, xsec.RECOMBINE, Kbig, 1.0, mur, target=xsec.T_ION),
+                     xsec.constant_rate_process(1, xsec.NEUTRALIZE, Kbig, 1.0, mun, target=xsec.T_ION)])
+    ne, nm, npl = np.full(Nc, 300), np.full(Nc, 100), np.full(Nc, 200)
+    for s, n in ((0, ne), (1, nm), (2, npl)):
+        x = cells(n)
+        o.load(s, x, z(len(x)), z(len(x)), z(len(x)), np.arange(len(x), dtype=np.uint32))
+    o.step(1)
+    c = o.counters()
+    assert c["recombined"] == int(npl.sum()) and c["neutralized"] == 0
+    assert o.count(2) == 0 and o.count(1) == int(nm.sum()) and o.count(0) == int((ne - npl).sum())
