@@ -253,12 +253,16 @@ int o2pic_compact_particles_noalloc(const float* x, const float* vx, const float
 /* ---- Launch shape and batched stepping (many discharges, one graph) ----
  *
  * A parameter sweep (voltages, pressures, particle counts) runs many small
- * discharges; each is one context.  A batch advances all of them together:
- * one CUDA graph holds steps_per_launch time steps of every context, each
- * context on its own branch, so their kernels run concurrently (the
- * single-block field solves of different discharges on different SMs).  The
+ * discharges; each is one context.  A batch advances all of them together
+ * with one CUDA graph of steps_per_launch time steps.  When the contexts
+ * share the step schedule (ion subcycle, compaction period and their phase)
+ * the graph holds one batched launch per kernel and step for all of them:
+ * each block of a batched grid works for one discharge (a block map), so a
+ * sweep of small discharges needs a handful of launches per step instead of
+ * a handful per discharge.  Otherwise (or with the environment variable
+ * O2PIC_BATCH_BRANCHES=1) each context gets its own graph branch.  The
  * method is unchanged: every context gives exactly the results of
- * o2pic_step, whatever the batch and the launch shape. */
+ * o2pic_step, whatever the batch, the mode and the launch shape. */
 
 /* Blocks of the particle kernels (push and collisions) per species, in
  * [1, 8 * SMs]; results do not depend on them.  Defaults (set by

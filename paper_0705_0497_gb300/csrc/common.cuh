@@ -198,6 +198,15 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* ws, un
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Copy of one discharge's parameters into shared memory (batched launches).
+__device__ __forceinline__ void load_params(Params& dst, const Params* src) {
+    static_assert(sizeof(Params) % 8 == 0, "Params copied as 64-bit words");
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+    for (unsigned i = threadIdx.x; i < sizeof(Params) / 8; i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
 // ------------------------------------------------------- decoupled look-back
 // Per tile: a flag word = (epoch << 2) | state (1 = aggregate published,
 // 2 = inclusive prefix published) and two value words (val[2t] = aggregate,

@@ -136,7 +136,7 @@ __device__ __forceinline__ unsigned find_unit(const unsigned* p, unsigned nu, un
 }
 
 struct CtrlSnap {
-    unsigned long long step, slots[NSP], live[NSP], removed[NSP];
+    unsigned long long step, epoch, acc_steps, slots[NSP], live[NSP], removed[NSP];
     unsigned next_id[NSP], cur[NSP], removals;
 };
 
@@ -188,10 +188,8 @@ __device__ __forceinline__ void block_scan_smem_pair(long long* a, long long* b,
 // [max warps + 1].  Every load that does not depend on another is issued at
 // the start: the step state, the charges of the thread's nodes, the per-warp
 // birth counts and U sin(2 pi f t).
-__global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
+__device__ __forceinline__ void field_body(const Params& P, int mode, int pushed_mask) {
     extern __shared__ long long fsm[];
-    pdl_wait();
-    pdl_trigger();   // one block on one SM: the next step's push may take the others
     __shared__ long long ws[64];
     __shared__ unsigned long long ws2[32];
     __shared__ CtrlSnap cs;
@@ -216,6 +214,8 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
     } else if (t == 32) {
         const unsigned long long step = C->step;
         cs.step = step;
+        cs.epoch = C->epoch;
+        cs.acc_steps = C->acc_steps;
         cs.removals = C->removals;
         sh_V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
     }
@@ -314,11 +314,12 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
             if (bs) atomicAdd(&C->cnt.born[s], bs);
         } else if (t == 32) {
             if (nrem) atomicAdd(&C->cnt.neutralized, (unsigned long long)nrem);
+            // this block is the only writer of the step state: plain stores
             C->removals = 0u;
             C->rremovals = 0u;
-            atomicAdd(&C->acc_steps, 1ull);
+            C->acc_steps = cs.acc_steps + 1;
             C->step = cs.step + 1;
-            atomicAdd(&C->epoch, 1ull);
+            C->epoch = cs.epoch + 1;
         } else if (t >= 64 && t < 64 + NKK + NSP) {
             C->ticket[t - 64] = 0u;
         }
@@ -409,12 +410,11 @@ __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mas
 // of the live particles into caller buffers (mode 1).  Tiles of TILE slots in
 // increasing order, decoupled look-back on the live counts.
 template <int S>
-__global__ void __launch_bounds__(BLOCK) k_compact(Params P, int mode, unsigned long long epoch_arg,
-                                                   unsigned* ticket_arg, unsigned long long* flag_arg,
-                                                   unsigned long long* val_arg, float* ox, float* ovx, float* ovy,
-                                                   float* ovz, uint32_t* oid, unsigned long long ocap,
-                                                   unsigned long long* out_count) {
-    pdl_wait();
+__device__ __forceinline__ void compact_body(const Params& P, int mode, unsigned long long epoch_arg,
+                                             unsigned* ticket_arg, unsigned long long* flag_arg,
+                                             unsigned long long* val_arg, float* ox, float* ovx, float* ovy,
+                                             float* ovz, uint32_t* oid, unsigned long long ocap,
+                                             unsigned long long* out_count) {
     __shared__ unsigned ws[32];
     __shared__ unsigned sh_tile;
     __shared__ unsigned long long sh_excl;
@@ -513,6 +513,40 @@ __global__ void __launch_bounds__(BLOCK) k_compact(Params P, int mode, unsigned 
 
 // Validation of freshly loaded particles (x in [0, L), finite velocities)
 // and the largest id (+1) for the species' next id.
+__global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
+    pdl_wait();
+    pdl_trigger();   // one block on one SM: the next step's push may take the others
+    field_body(P, mode, pushed_mask);
+}
+
+// batched: block d is the end-of-step kernel of discharge d
+__global__ void __launch_bounds__(FT) k_field_b(const Params* __restrict__ all, int mode, int pushed_mask) {
+    __shared__ Params sP;
+    pdl_wait();
+    pdl_trigger();
+    load_params(sP, all + blockIdx.x);
+    field_body(sP, mode, pushed_mask);
+}
+
+template <int S>
+__global__ void __launch_bounds__(BLOCK) k_compact(Params P, int mode, unsigned long long epoch_arg, unsigned* ticket_arg,
+                                                   unsigned long long* flag_arg, unsigned long long* val_arg, float* ox,
+                                                   float* ovx, float* ovy, float* ovz, uint32_t* oid,
+                                                   unsigned long long ocap, unsigned long long* out_count) {
+    pdl_wait();
+    compact_body<S>(P, mode, epoch_arg, ticket_arg, flag_arg, val_arg, ox, ovx, ovy, ovz, oid, ocap, out_count);
+}
+
+// batched compaction check (mode 0): the blocks of map[b].x claim that
+// discharge's tiles by its own ticket
+template <int S>
+__global__ void __launch_bounds__(BLOCK) k_compact_b(const Params* __restrict__ all, const uint4* __restrict__ map) {
+    __shared__ Params sP;
+    pdl_wait();
+    load_params(sP, all + map[blockIdx.x].x);
+    compact_body<S>(sP, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+}
+
 template <int S>
 __global__ void k_load_check(Params P, unsigned long long n) {
     DevCtrl* C = P.ctrl;
@@ -572,12 +606,23 @@ void launch_phi(const Params& P, cudaStream_t s) {
     k_phi<<<(P.Ng + 255) / 256, 256, 0, s>>>(P);
 }
 
+void launch_field_batched(const Params* all, int n, size_t smem, int mode, int pushed_mask, cudaStream_t s) {
+    launch_pdl(k_field_b, n, FT, smem, s, all, mode, pushed_mask);
+}
+
+void launch_compact_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s) {
+    auto k = species == SP_E ? k_compact_b<SP_E> : (species == SP_OM ? k_compact_b<SP_OM> : k_compact_b<SP_OP>);
+    launch_pdl(k, nblocks, BLOCK, 0, s, all, map);
+}
+
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s) {
     launch_pdl(k_field, 1, FT, field_smem_bytes(P), s, P, mode, pushed_mask);
 }
 
 cudaError_t configure_field_smem(size_t bytes) {
-    return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_field_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
 }
 
 void launch_compact(int species, const Params& P, int grid, cudaStream_t s) {

@@ -9,6 +9,12 @@
 
 namespace o2 {
 
+// Programmatic stream serialization is on except while a graph with one
+// branch per discharge is captured: there, the early-launched blocks of many
+// branches could hold pieces of every SM while single-block kernels of other
+// branches wait for a whole one.
+extern thread_local bool pdl_enabled;
+
 // Launch with programmatic stream serialization (see pdl_wait in common.cuh).
 template <typename... Params_, typename... Args>
 inline void launch_pdl(void (*kernel)(Params_...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
@@ -20,7 +26,7 @@ inline void launch_pdl(void (*kernel)(Params_...), dim3 grid, dim3 block, size_t
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
@@ -186,6 +192,8 @@ struct PairSpec {
     unsigned int* nremovals;     // device counter of listed pairs
     unsigned int max_removals;
     unsigned long long* tested;  // device counter of pairs tested
+    unsigned long long* reacted; // device counter of pairs removed (the apply kernel's)
+    int active;                  // 0: the discharge has no such process (batched launches skip it)
 };
 
 __host__ __device__ inline unsigned long long ceil_div(unsigned long long a, unsigned long long b) {
@@ -207,6 +215,15 @@ void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t
 cudaError_t configure_pair_hist_smem(int Nc);
 void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s);
 void launch_pair_apply(const Params& P, const PairSpec& S, cudaStream_t s);
+// batched launches (one grid for many discharges; map[b] = discharge, block, blocks)
+void launch_push_batched(int species, const Params* all, const uint4* map, int nblocks, size_t smem, cudaStream_t s);
+void launch_cand_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s);
+void launch_field_batched(const Params* all, int n, size_t smem, int mode, int pushed_mask, cudaStream_t s);
+void launch_compact_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s);
+void launch_pair_hist_batched(const Params* all, const PairSpec* specs, const uint4* map, int nblocks, size_t smem,
+                              cudaStream_t s);
+void launch_pair_batched(const Params* all, const PairSpec* specs, const uint4* map, int nblocks, cudaStream_t s);
+void launch_pair_apply_batched(const Params* all, const PairSpec* specs, int n, cudaStream_t s);
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s);
 void launch_phi(const Params& P, cudaStream_t s);
 void launch_compact(int species, const Params& P, int grid, cudaStream_t s);

@@ -47,16 +47,15 @@ static_assert(MAX_NODES - 1 < CELL_DEAD, "cell index fits 15 bits");
 // positions): hist[sp][tile][cell]; and the per-cell totals ptot[sp][cell]
 // (zero on entry; the end-of-step kernel clears them).  Blocks take tiles of
 // O- first, then of O2+, and add their totals once at the end.
-__global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P, PairSpec Sp) {
+__device__ __forceinline__ void pair_hist_body(const Params& P, const PairSpec& Sp, unsigned blk, unsigned nblk) {
     extern __shared__ unsigned hsm[];   // [Nc] tile counts, [2][Nc] block totals
-    pdl_wait();
     DevCtrl* C = P.ctrl;
     const int Nc = P.Nc;
     unsigned* bt = hsm + Nc;
     for (int c = threadIdx.x; c < 2 * Nc; c += HIST_T) bt[c] = 0u;
     const unsigned long long nsa = C->slots[Sp.A], nsb = C->slots[Sp.B];
     const unsigned nta = (unsigned)ceil_div(nsa, TILE), ntb = (unsigned)ceil_div(nsb, TILE);
-    for (unsigned g = blockIdx.x; g < nta + ntb; g += gridDim.x) {
+    for (unsigned g = blk; g < nta + ntb; g += nblk) {
         const int sp = (g < nta) ? 0 : 1;
         const unsigned tile = (g < nta) ? g : g - nta;
         const int S = sp == 0 ? Sp.A : Sp.B;
@@ -215,8 +214,7 @@ __device__ void resolve_one(const Params& P, const PairSpec& Sp, unsigned pos, u
 
 // One block per O- tile (grid-stride): the streaming pass, then the flagged
 // O- of the tile.  Block 0 also adds sum_c min(n-, n+) to the pair counter.
-__global__ void __launch_bounds__(PAIR_T) k_pair(Params P, PairSpec Sp) {
-    pdl_wait();
+__device__ __forceinline__ void pair_body(const Params& P, const PairSpec& Sp, unsigned blk, unsigned nblk) {
     __shared__ unsigned short cell16[TILE];
     __shared__ unsigned short list[LCAP];
     __shared__ unsigned ws[32];
@@ -235,7 +233,7 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P, PairSpec Sp) {
     const uint4 ctr = make_uint4((uint32_t)step, Sp.tag_pair, 0u, (uint32_t)(step >> 32));
     unsigned gt1 = 0;
 
-    if (blockIdx.x == 0) {
+    if (blk == 0) {
         unsigned pairs = 0;   // at most 2^32 ions in all
         for (int c = tid; c < Nc; c += PAIR_T) {
             const unsigned a = tot[c], b = tot[Nc + c];
@@ -245,7 +243,7 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P, PairSpec Sp) {
         if (tid == 0 && s) atomicAdd(Sp.tested, (unsigned long long)s);
     }
 
-    for (unsigned tile = blockIdx.x; tile < ntm; tile += gridDim.x) {
+    for (unsigned tile = blk; tile < ntm; tile += nblk) {
         const unsigned long long base = (unsigned long long)tile * TILE;
         if (tid == 0) nflag = 0u;
         __syncthreads();
@@ -307,22 +305,71 @@ __global__ void __launch_bounds__(PAIR_T) k_pair(Params P, PairSpec Sp) {
 
 // The removals of a pair process that runs before another (16 before 17):
 // mark both particles of every listed pair dead, count them, clear the list.
-__global__ void k_pair_apply(Params P, PairSpec Sp, unsigned long long* reacted) {
-    pdl_wait();
+__device__ __forceinline__ void pair_apply_body(const Params& P, const PairSpec& Sp) {
     DevCtrl* C = P.ctrl;
     const unsigned listed = *Sp.nremovals;
     const unsigned n = listed < Sp.max_removals ? listed : Sp.max_removals;
     const unsigned ca = C->cur[Sp.A], cb = C->cur[Sp.B];
-    for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    for (unsigned r = threadIdx.x; r < n; r += blockDim.x) {
         P.sp[Sp.A].x[ca][Sp.removal[2 * r]] = dead_marker();
         P.sp[Sp.B].x[cb][Sp.removal[2 * r + 1]] = dead_marker();
     }
     pdl_trigger();
-    if (blockIdx.x == 0 && threadIdx.x == 0 && n) {
+    if (threadIdx.x == 0 && n) {
         atomicAdd(&C->removed[Sp.A], (unsigned long long)n);
         atomicAdd(&C->removed[Sp.B], (unsigned long long)n);
-        atomicAdd(reacted, (unsigned long long)n);
+        atomicAdd(Sp.reacted, (unsigned long long)n);
     }
+}
+
+__global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P, PairSpec Sp) {
+    pdl_wait();
+    pair_hist_body(P, Sp, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(PAIR_T) k_pair(Params P, PairSpec Sp) {
+    pdl_wait();
+    pair_body(P, Sp, blockIdx.x, gridDim.x);
+}
+
+// one block: the lists are short
+__global__ void k_pair_apply(Params P, PairSpec Sp) {
+    pdl_wait();
+    pair_apply_body(P, Sp);
+}
+
+// batched: block b works for discharge map[b].x (block map[b].y of map[b].z)
+__global__ void __launch_bounds__(HIST_T) k_pair_hist_b(const Params* __restrict__ all,
+                                                         const PairSpec* __restrict__ specs,
+                                                         const uint4* __restrict__ map) {
+    __shared__ Params sP;
+    pdl_wait();
+    const uint4 m = map[blockIdx.x];
+    const PairSpec Sp = specs[m.x];
+    if (!Sp.active) return;   // block-uniform
+    load_params(sP, all + m.x);
+    pair_hist_body(sP, Sp, m.y, m.z);
+}
+
+__global__ void __launch_bounds__(PAIR_T) k_pair_b(const Params* __restrict__ all, const PairSpec* __restrict__ specs,
+                                                    const uint4* __restrict__ map) {
+    __shared__ Params sP;
+    pdl_wait();
+    const uint4 m = map[blockIdx.x];
+    const PairSpec Sp = specs[m.x];
+    if (!Sp.active) return;
+    load_params(sP, all + m.x);
+    pair_body(sP, Sp, m.y, m.z);
+}
+
+// batched: block d applies discharge d's list
+__global__ void k_pair_apply_b(const Params* __restrict__ all, const PairSpec* __restrict__ specs) {
+    __shared__ Params sP;
+    pdl_wait();
+    const PairSpec Sp = specs[blockIdx.x];
+    if (!Sp.active) return;
+    load_params(sP, all + blockIdx.x);
+    pair_apply_body(sP, Sp);
 }
 
 }  // namespace
@@ -330,8 +377,12 @@ __global__ void k_pair_apply(Params P, PairSpec Sp, unsigned long long* reacted)
 size_t pair_hist_smem_bytes(int Nc) { return 3 * sizeof(unsigned) * (size_t)Nc; }
 
 cudaError_t configure_pair_hist_smem(int Nc) {
-    return cudaFuncSetAttribute(k_pair_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pair_hist_smem_bytes(Nc));
+    cudaError_t e = cudaFuncSetAttribute(k_pair_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pair_hist_smem_bytes(Nc));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pair_hist_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pair_hist_smem_bytes(Nc));
+    return e;
 }
 
 void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t s) {
@@ -344,7 +395,20 @@ void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s) {
 
 // the list counter is cleared by the end-of-step kernel
 void launch_pair_apply(const Params& P, const PairSpec& S, cudaStream_t s) {
-    launch_pdl(k_pair_apply, 8, 256, 0, s, P, S, &P.ctrl->cnt.recombined);
+    launch_pdl(k_pair_apply, 1, 256, 0, s, P, S);
+}
+
+void launch_pair_hist_batched(const Params* all, const PairSpec* specs, const uint4* map, int nblocks, size_t smem,
+                              cudaStream_t s) {
+    launch_pdl(k_pair_hist_b, nblocks, HIST_T, smem, s, all, specs, map);
+}
+
+void launch_pair_batched(const Params* all, const PairSpec* specs, const uint4* map, int nblocks, cudaStream_t s) {
+    launch_pdl(k_pair_b, nblocks, PAIR_T, 0, s, all, specs, map);
+}
+
+void launch_pair_apply_batched(const Params* all, const PairSpec* specs, int n, cudaStream_t s) {
+    launch_pdl(k_pair_apply_b, n, 256, 0, s, all, specs);
 }
 
 }  // namespace o2

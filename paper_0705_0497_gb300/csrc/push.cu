@@ -221,10 +221,11 @@ __device__ __forceinline__ bool electron_is_real(const Params& P, const float* _
     return (u1 * P.numax[SP_E]) < grid_interp(cum, np, np - 1, i, w);
 }
 
+// Body of the particle kernel for block blk of nblk blocks (the launch's own
+// block, or a block a batched launch maps to this discharge).
 template <int S>
-__global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P) {
+__device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigned nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
-    pdl_wait();
     const int np = P.nproc[S];
     PushShared& sh = *reinterpret_cast<PushShared*>(smem);
     float* Es = reinterpret_cast<float*>(smem + align16(sizeof(PushShared)));
@@ -251,8 +252,8 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
     __syncthreads();
 
     // this warp's contiguous slot range
-    const unsigned W = gridDim.x * WARPS;
-    const unsigned gw = blockIdx.x * WARPS + warp;
+    const unsigned W = nblk * WARPS;
+    const unsigned gw = blk * WARPS + warp;
     const unsigned R = warp_range_len(nslots, W);
     const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
     const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
@@ -349,8 +350,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P)
 // kinematics 32 at a time.  Births are ranked with ballots and staged at the
 // particle warp's slot range with their count.
 template <int S>
-__global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand(Params P) {
-    pdl_wait();
+__device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigned nblk) {
     __shared__ unsigned events[MAXPROC];
     __shared__ unsigned sh_removed, sh_wtries, sh_wemax;
     __shared__ uint4 q2w_all[WARPS][Q2];
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand(Params P)
     const unsigned R = warp_range_len(nslots, W);
     unsigned wtries = 0, wemax = 0, nremoved = 0;
 
-    for (unsigned gw = blockIdx.x * WARPS + warp; gw < W; gw += gridDim.x * WARPS) {
+    for (unsigned gw = blk * WARPS + warp; gw < W; gw += nblk * WARPS) {
         const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
         const unsigned n = P.ccount[S][gw];
         unsigned q2n = 0, nb1 = 0, nb2 = 0;   // warp-uniform
@@ -507,6 +507,42 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand(Params P)
     }
 }
 
+template <int S>
+__global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P) {
+    pdl_wait();
+    push_body<S>(P, blockIdx.x, gridDim.x);
+}
+
+template <int S>
+__global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand(Params P) {
+    pdl_wait();
+    cand_body<S>(P, blockIdx.x, gridDim.x);
+}
+
+// Batched launches: block b works for discharge map[b].x as its block
+// map[b].y of map[b].z, with that discharge's parameters copied to shared
+// memory (load_params).
+template <int S>
+__global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push_b(const Params* __restrict__ all,
+                                                                        const uint4* __restrict__ map) {
+    __shared__ Params sP;
+    pdl_wait();
+    const uint4 m = map[blockIdx.x];
+    load_params(sP, all + m.x);
+    push_body<S>(sP, m.y, m.z);
+}
+
+template <int S>
+__global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand_b(const Params* __restrict__ all,
+                                                                        const uint4* __restrict__ map) {
+    __shared__ Params sP;
+    pdl_wait();
+    const uint4 m = map[blockIdx.x];
+    load_params(sP, all + m.x);
+    if (sP.nproc[S] == 0) return;   // block-uniform
+    cand_body<S>(sP, m.y, m.z);
+}
+
 // Deposit of all live particles of one species into Qf (used after a load).
 template <int S>
 __global__ void __launch_bounds__(BLOCK) k_deposit(Params P) {
@@ -554,6 +590,18 @@ void launch_push(int species, const Params& P, int grid, cudaStream_t s) {
     else launch_pdl(k_push<SP_OP>, grid, BLOCK, sm, s, P);
 }
 
+void launch_push_batched(int species, const Params* all, const uint4* map, int nblocks, size_t smem, cudaStream_t s) {
+    if (species == SP_E) launch_pdl(k_push_b<SP_E>, nblocks, BLOCK, smem, s, all, map);
+    else if (species == SP_OM) launch_pdl(k_push_b<SP_OM>, nblocks, BLOCK, smem, s, all, map);
+    else launch_pdl(k_push_b<SP_OP>, nblocks, BLOCK, smem, s, all, map);
+}
+
+void launch_cand_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s) {
+    if (species == SP_E) launch_pdl(k_cand_b<SP_E>, nblocks, BLOCK, 0, s, all, map);
+    else if (species == SP_OM) launch_pdl(k_cand_b<SP_OM>, nblocks, BLOCK, 0, s, all, map);
+    else launch_pdl(k_cand_b<SP_OP>, nblocks, BLOCK, 0, s, all, map);
+}
+
 void launch_cand(int species, const Params& P, int grid, cudaStream_t s) {
     if (species == SP_E) launch_pdl(k_cand<SP_E>, grid, BLOCK, 0, s, P);
     else if (species == SP_OM) launch_pdl(k_cand<SP_OM>, grid, BLOCK, 0, s, P);
@@ -573,6 +621,9 @@ cudaError_t configure_push_smem(size_t max_bytes) {
     if ((e = cudaFuncSetAttribute(k_push<SP_E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_push<SP_OM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_push<SP_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_push_b<SP_E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_push_b<SP_OM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_push_b<SP_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_deposit<SP_E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_deposit<SP_OM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes))) return e;
     return cudaFuncSetAttribute(k_deposit<SP_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes);

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -19,6 +20,7 @@
 #include "internal.h"
 
 namespace o2 {
+thread_local bool pdl_enabled = true;
 }
 
 // particle kernels run at most this many blocks per SM (bounds the per-warp
@@ -287,7 +289,7 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
             if (P.have_recomb) {
                 const PairSpec R{SP_E, SP_OP, P.rhist[0], P.rhist[1], P.rtot, P.Ktab_r, P.Kmax_r_hi, P.kappa_r,
                                  TAG_REC, TAG_SHIFT_REC, P.rremoval, &c->d_ctrl->rremovals, P.max_rremovals,
-                                 &c->d_ctrl->cnt.rec_candidates};
+                                 &c->d_ctrl->cnt.rec_candidates, &c->d_ctrl->cnt.recombined, 1};
                 launch(c, KK_REC, s, [&] { launch_pair_hist(P, R, c->grid_compact, s); });
                 launch(c, KK_REC, s, [&] { launch_pair(P, R, c->grid_pair_e, s); });
                 launch(c, KK_REC, s, [&] { launch_pair_apply(P, R, s); });
@@ -295,7 +297,7 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
             if (P.have_neutral) {
                 const PairSpec N{SP_OM, SP_OP, P.hist[0], P.hist[1], P.ptot, P.Ktab, P.Kmax_hi, P.kappa_n,
                                  TAG_PAIR, TAG_SHIFT, P.removal, &c->d_ctrl->removals, P.max_removals,
-                                 &c->d_ctrl->cnt.pair_candidates};
+                                 &c->d_ctrl->cnt.pair_candidates, &c->d_ctrl->cnt.neutralized, 1};
                 launch(c, KK_PAIR_HIST, s, [&] { launch_pair_hist(P, N, c->grid_compact, s); });
                 launch(c, KK_PAIR, s, [&] { launch_pair(P, N, c->grid_pair, s); });
             }
@@ -923,6 +925,16 @@ struct o2pic_batch {
     std::vector<unsigned long long> launches_per_replay;
     std::vector<unsigned long long> phase_step;   // host_step of each context at capture
     std::vector<unsigned long long> gen;          // generation of each context at capture
+    // fused mode: one batched launch per kernel and step for all contexts
+    bool fused = false;
+    Params* dP = nullptr;                 // [n] parameters of each context
+    PairSpec* dR = nullptr;               // [n] (16) of each context
+    PairSpec* dN = nullptr;               // [n] (17)
+    uint4* dmap = nullptr;                // block maps, concatenated
+    size_t map_push[NSP] = {0, 0, 0}, map_comp[NSP] = {0, 0, 0}, map_rh = 0, map_rp = 0, map_nh = 0, map_np = 0;
+    int nb_push[NSP] = {0, 0, 0}, nb_comp[NSP] = {0, 0, 0}, nb_rh = 0, nb_rp = 0, nb_nh = 0, nb_np = 0;
+    bool any_recomb = false, any_neutral = false;
+    size_t smem_push = 0, smem_field = 0, smem_hist = 0;
 };
 
 namespace {
@@ -934,10 +946,121 @@ void batch_release_graph(o2pic_batch* b) {
     b->graph = nullptr;
 }
 
-// Records K steps of every context into a graph, one branch per context.
-// Nothing runs; the contexts' host counters are restored afterwards.
+// Device tables of the fused mode: each context's Params and PairSpecs, and
+// the block maps (discharge, block, blocks) of every batched launch.
+int fused_tables(o2pic_batch* b) {
+    const size_t n = b->ctx.size();
+    std::vector<Params> hp(n);
+    std::vector<PairSpec> hr(n), hn(n);
+    std::vector<uint4> map;
+    auto add_map = [&](size_t& off, int& nb, auto blocks_of) {
+        off = map.size();
+        for (size_t i = 0; i < n; ++i) {
+            const unsigned k = (unsigned)blocks_of(b->ctx[i]);
+            for (unsigned j = 0; j < k; ++j) map.push_back(make_uint4((unsigned)i, j, k, 0u));
+        }
+        nb = (int)(map.size() - off);
+    };
+    auto tiles = [](unsigned long long cap) { return std::max<unsigned long long>(1, ceil_div(cap, TILE)); };
+    b->any_recomb = b->any_neutral = false;
+    b->smem_push = b->smem_field = b->smem_hist = 0;
+    for (size_t i = 0; i < n; ++i) {
+        o2pic_ctx* c = b->ctx[i];
+        const Params& P = c->P;
+        hp[i] = P;
+        hr[i] = PairSpec{SP_E, SP_OP, P.rhist[0], P.rhist[1], P.rtot, P.Ktab_r, P.Kmax_r_hi, P.kappa_r, TAG_REC,
+                         TAG_SHIFT_REC, P.rremoval, &c->d_ctrl->rremovals, P.max_rremovals,
+                         &c->d_ctrl->cnt.rec_candidates, &c->d_ctrl->cnt.recombined, P.have_recomb};
+        hn[i] = PairSpec{SP_OM, SP_OP, P.hist[0], P.hist[1], P.ptot, P.Ktab, P.Kmax_hi, P.kappa_n, TAG_PAIR,
+                         TAG_SHIFT, P.removal, &c->d_ctrl->removals, P.max_removals,
+                         &c->d_ctrl->cnt.pair_candidates, &c->d_ctrl->cnt.neutralized, P.have_neutral};
+        b->any_recomb |= P.have_recomb != 0;
+        b->any_neutral |= P.have_neutral != 0;
+        for (int sp = 0; sp < NSP; ++sp) b->smem_push = std::max(b->smem_push, push_smem_bytes(sp, P));
+        b->smem_field = std::max(b->smem_field, field_smem_bytes(P));
+        b->smem_hist = std::max(b->smem_hist, 3 * sizeof(unsigned) * (size_t)P.Nc);
+    }
+    for (int sp = 0; sp < NSP; ++sp) {
+        add_map(b->map_push[sp], b->nb_push[sp], [&](o2pic_ctx* c) { return c->grid_push[sp]; });
+        add_map(b->map_comp[sp], b->nb_comp[sp],
+                [&](o2pic_ctx* c) { return std::min<unsigned long long>(tiles(c->P.sp[sp].cap), 16); });
+    }
+    add_map(b->map_rh, b->nb_rh, [&](o2pic_ctx* c) {
+        return std::min<unsigned long long>(tiles(c->P.sp[SP_E].cap) + tiles(c->P.sp[SP_OP].cap), 32); });
+    add_map(b->map_rp, b->nb_rp, [&](o2pic_ctx* c) { return std::min<unsigned long long>(tiles(c->P.sp[SP_E].cap), 64); });
+    add_map(b->map_nh, b->nb_nh, [&](o2pic_ctx* c) {
+        return std::min<unsigned long long>(tiles(c->P.sp[SP_OM].cap) + tiles(c->P.sp[SP_OP].cap), 32); });
+    add_map(b->map_np, b->nb_np, [&](o2pic_ctx* c) { return std::min<unsigned long long>(tiles(c->P.sp[SP_OM].cap), 64); });
+    if (b->dP) cudaFree(b->dP);
+    if (b->dR) cudaFree(b->dR);
+    if (b->dN) cudaFree(b->dN);
+    if (b->dmap) cudaFree(b->dmap);
+    b->dP = nullptr; b->dR = b->dN = nullptr; b->dmap = nullptr;
+    if (cudaMalloc((void**)&b->dP, sizeof(Params) * n) != cudaSuccess ||
+        cudaMalloc((void**)&b->dR, sizeof(PairSpec) * n) != cudaSuccess ||
+        cudaMalloc((void**)&b->dN, sizeof(PairSpec) * n) != cudaSuccess ||
+        cudaMalloc((void**)&b->dmap, sizeof(uint4) * std::max<size_t>(map.size(), 1)) != cudaSuccess)
+        return O2PIC_E_CUDA;
+    if (cudaMemcpy(b->dP, hp.data(), sizeof(Params) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dR, hr.data(), sizeof(PairSpec) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dN, hn.data(), sizeof(PairSpec) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dmap, map.data(), sizeof(uint4) * map.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return O2PIC_E_CUDA;
+    return O2PIC_OK;
+}
+
+// The fused kernel sequence of K steps on stream s (contexts share the
+// schedule: ion subcycle, compaction period and their phases).
+void enqueue_fused(o2pic_batch* b, cudaStream_t s) {
+    o2pic_ctx* c0 = b->ctx[0];
+    const unsigned S = (unsigned)c0->cfg.ion_subcycle;
+    const int n = (int)b->ctx.size();
+    unsigned long long step = c0->host_step;
+    unsigned since = c0->since_check;
+    unsigned long long launches = 0;
+    for (uint64_t k = 0; k < b->K; ++k) {
+        const bool ion = (step % S) == 0;
+        launch_push_batched(SP_E, b->dP, b->dmap + b->map_push[SP_E], b->nb_push[SP_E], b->smem_push, s);
+        launch_cand_batched(SP_E, b->dP, b->dmap + b->map_push[SP_E], b->nb_push[SP_E], s);
+        launches += 2;
+        if (ion) {
+            for (int sp = SP_OM; sp <= SP_OP; ++sp) {
+                launch_push_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], b->smem_push, s);
+                launch_cand_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
+                launches += 2;
+            }
+            if (b->any_recomb) {
+                launch_pair_hist_batched(b->dP, b->dR, b->dmap + b->map_rh, b->nb_rh, b->smem_hist, s);
+                launch_pair_batched(b->dP, b->dR, b->dmap + b->map_rp, b->nb_rp, s);
+                launch_pair_apply_batched(b->dP, b->dR, n, s);
+                launches += 3;
+            }
+            if (b->any_neutral) {
+                launch_pair_hist_batched(b->dP, b->dN, b->dmap + b->map_nh, b->nb_nh, b->smem_hist, s);
+                launch_pair_batched(b->dP, b->dN, b->dmap + b->map_np, b->nb_np, s);
+                launches += 2;
+            }
+        }
+        launch_field_batched(b->dP, n, b->smem_field, 0, ion ? 7 : 1, s);
+        launches += 1;
+        step += 1;
+        if (++since >= c0->cfg.compact_check) {
+            for (int sp = 0; sp < NSP; ++sp)
+                launch_compact_batched(sp, b->dP, b->dmap + b->map_comp[sp], b->nb_comp[sp], s);
+            launches += 3;
+            since = 0;
+        }
+    }
+    for (o2pic_ctx* c : b->ctx) { c->host_step = step; c->since_check = since; c->launches += launches; }
+}
+
+// Records K steps of every context into a graph: in fused mode one batched
+// launch per kernel and step, else one branch per context.  Nothing runs;
+// the contexts' host counters are restored afterwards.
 int batch_capture(o2pic_batch* b) {
     batch_release_graph(b);
+    if (b->fused)
+        if (int rc = fused_tables(b)) return rc;
     const size_t n = b->ctx.size();
     std::vector<unsigned long long> hs(n), launches(n), nl(n * NKK);
     std::vector<unsigned> sc(n);
@@ -948,12 +1071,18 @@ int batch_capture(o2pic_batch* b) {
     }
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return O2PIC_E_CUDA;
-    cudaEventRecord(b->fork, b->stream);
-    for (size_t i = 0; i < n; ++i) {
-        cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-        enqueue_steps(b->ctx[i], b->K, b->branch[i]);
-        cudaEventRecord(b->join[i], b->branch[i]);
-        cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    if (b->fused) {
+        enqueue_fused(b, b->stream);
+    } else {
+        pdl_enabled = false;
+        cudaEventRecord(b->fork, b->stream);
+        for (size_t i = 0; i < n; ++i) {
+            cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+            enqueue_steps(b->ctx[i], b->K, b->branch[i]);
+            cudaEventRecord(b->join[i], b->branch[i]);
+            cudaStreamWaitEvent(b->stream, b->join[i], 0);
+        }
+        pdl_enabled = true;
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
@@ -1054,6 +1183,17 @@ int o2pic_batch_create(o2pic_ctx* const* ctxs, int32_t n, uint64_t K, o2pic_batc
             if (rc) { o2pic_batch_destroy(b); return rc; }
         }
     }
+    // fused when the contexts share the step schedule and its phase
+    b->fused = true;
+    for (o2pic_ctx* c : b->ctx) {
+        const o2pic_ctx* c0 = b->ctx[0];
+        if (c->cfg.ion_subcycle != c0->cfg.ion_subcycle || c->cfg.compact_check != c0->cfg.compact_check ||
+            c->host_step % (unsigned long long)c->cfg.ion_subcycle !=
+                c0->host_step % (unsigned long long)c0->cfg.ion_subcycle ||
+            c->since_check != c0->since_check)
+            b->fused = false;
+    }
+    if (const char* env = std::getenv("O2PIC_BATCH_BRANCHES")) if (env[0] == '1') b->fused = false;
     int rc = batch_capture(b);
     if (rc) { o2pic_batch_destroy(b); return rc; }
     *out = b;
@@ -1167,6 +1307,7 @@ void o2pic_batch_destroy(o2pic_batch* b) {
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
     if (b->stream) cudaStreamDestroy(b->stream);
+    for (void* p : {(void*)b->dP, (void*)b->dR, (void*)b->dN, (void*)b->dmap}) if (p) cudaFree(p);
     delete b;
 }
 

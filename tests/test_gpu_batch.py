@@ -41,9 +41,14 @@ def _same(a, b):
     assert np.array_equal(a.currents(n - k, k), b.currents(n - k, k))
 
 
-def test_batch_equals_single_runs(torch_cuda):
+@pytest.mark.parametrize("branches", [False, True])
+def test_batch_equals_single_runs(torch_cuda, monkeypatch, branches):
+    """Fused batched launches (the default for a shared schedule) and one
+    graph branch per discharge both give the single runs bit for bit."""
     from paper_0705_0497_gb300 import api
-    procs = xsec.oxygen_set()
+    if branches:
+        monkeypatch.setenv("O2PIC_BATCH_BRANCHES", "1")
+    procs = xsec.oxygen_set(include_rec=True)
     sweep = _sweep(4)
     batched = [_discharge(c, n, T, procs) for c, n, T in sweep]
     alone = [_discharge(c, n, T, procs) for c, n, T in sweep]
@@ -119,4 +124,23 @@ def test_batch_refuses_stale_graph(torch_cuda):
     assert e.value.code == -7
     with pytest.raises(api.O2picError):
         api.Batch(gs, steps_per_launch=15)   # not a multiple of S = 10
+    b.close()
+
+
+def test_batch_of_different_schedules(torch_cuda):
+    """Discharges with different ion subcycles cannot share batched launches:
+    the batch falls back to one branch each and still matches single runs."""
+    from paper_0705_0497_gb300 import api
+    procs = xsec.oxygen_set()
+    (c0, n0, T0), (c1, n1, T1) = _sweep(2, seed=13)
+    c1 = dict(c1, ion_subcycle=5)
+    gs = [_discharge(c0, n0, T0, procs), _discharge(c1, n1, T1, procs)]
+    alone = [_discharge(c0, n0, T0, procs), _discharge(c1, n1, T1, procs)]
+    b = api.Batch(gs, steps_per_launch=20)
+    b.step(2)
+    b.synchronize()
+    for g in alone:
+        g.step(40)
+    for x, y in zip(gs, alone):
+        _same(x, y)
     b.close()
