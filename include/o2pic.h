@@ -293,15 +293,19 @@ int o2pic_batch_synchronize(o2pic_batch* b);
 /* Autotuner: tries launch-shape policies (particle-kernel blocks from a
  * target number of particles per warp, and the default full-GPU shape),
  * times one graph replay of each on the real batch (these replays are real
- * steps of the discharges: 7 policies x steps_per_launch steps), keeps the
- * fastest and re-captures the graph.  The shapes stay set on the contexts,
- * so a batch created afterwards with another steps_per_launch uses them. */
+ * steps of the discharges: 7 policies x steps_per_launch steps, plus one
+ * replay of the other launch mode when the contexts share their schedule),
+ * keeps the fastest shape and mode and re-captures the graph.  The shapes
+ * stay set on the contexts, so a batch created afterwards with another
+ * steps_per_launch uses them. */
 #define O2PIC_TUNE_MAX 8
 typedef struct {
     int32_t n;                                   /* policies tried */
     int32_t particles_per_warp[O2PIC_TUNE_MAX];  /* 0 = default full-GPU shape */
     double ms[O2PIC_TUNE_MAX];                   /* one replay, CUDA events */
     int32_t chosen;                              /* index of the policy kept */
+    int32_t fused;                               /* 1: batched launches kept, 0: one branch per context */
+    double other_mode_ms;                        /* the other mode at the chosen shape (0: not tried) */
 } o2pic_tune_report;
 int o2pic_batch_autotune(o2pic_batch* b, o2pic_tune_report* report);
 

@@ -49,7 +49,8 @@ TUNE_MAX = 8
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("particles_per_warp", ctypes.c_int32 * TUNE_MAX),
-                ("ms", ctypes.c_double * TUNE_MAX), ("chosen", ctypes.c_int32)]
+                ("ms", ctypes.c_double * TUNE_MAX), ("chosen", ctypes.c_int32), ("fused", ctypes.c_int32),
+                ("other_mode_ms", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -413,7 +414,8 @@ class Batch:
         r = TuneReport()
         _check(lib().o2pic_batch_autotune(self.h, ctypes.byref(r)), "o2pic_batch_autotune")
         return {"particles_per_warp": [int(r.particles_per_warp[i]) for i in range(r.n)],
-                "ms": [float(r.ms[i]) for i in range(r.n)], "chosen": int(r.chosen)}
+                "ms": [float(r.ms[i]) for i in range(r.n)], "chosen": int(r.chosen),
+                "fused": bool(r.fused), "other_mode_ms": float(r.other_mode_ms)}
 
     def close(self):
         if getattr(self, "h", None):

@@ -926,7 +926,7 @@ struct o2pic_batch {
     std::vector<unsigned long long> phase_step;   // host_step of each context at capture
     std::vector<unsigned long long> gen;          // generation of each context at capture
     // fused mode: one batched launch per kernel and step for all contexts
-    bool fused = false;
+    bool fused = false, fusable = false;
     Params* dP = nullptr;                 // [n] parameters of each context
     PairSpec* dR = nullptr;               // [n] (16) of each context
     PairSpec* dN = nullptr;               // [n] (17)
@@ -1183,8 +1183,9 @@ int o2pic_batch_create(o2pic_ctx* const* ctxs, int32_t n, uint64_t K, o2pic_batc
             if (rc) { o2pic_batch_destroy(b); return rc; }
         }
     }
-    // fused when the contexts share the step schedule and its phase
-    b->fused = true;
+    // fused when several contexts share the step schedule and its phase (one
+    // context runs its own kernels directly)
+    b->fused = n > 1;
     for (o2pic_ctx* c : b->ctx) {
         const o2pic_ctx* c0 = b->ctx[0];
         if (c->cfg.ion_subcycle != c0->cfg.ion_subcycle || c->cfg.compact_check != c0->cfg.compact_check ||
@@ -1194,6 +1195,7 @@ int o2pic_batch_create(o2pic_ctx* const* ctxs, int32_t n, uint64_t K, o2pic_batc
             b->fused = false;
     }
     if (const char* env = std::getenv("O2PIC_BATCH_BRANCHES")) if (env[0] == '1') b->fused = false;
+    b->fusable = b->fused;
     int rc = batch_capture(b);
     if (rc) { o2pic_batch_destroy(b); return rc; }
     *out = b;
@@ -1290,8 +1292,29 @@ int o2pic_batch_autotune(o2pic_batch* b, o2pic_tune_report* report) {
     }
     for (size_t i = 0; i < n; ++i)
         if (int rc = o2pic_set_launch_shape(b->ctx[i], &shapes[best][3 * i])) return rc;
+    // with a shared schedule, also the other launch mode at the best shape
+    if (b->fusable) {
+        b->fused = !b->fused;
+        if (int rc = batch_capture(b)) return rc;
+        if (cudaGraphUpload(b->exec, b->stream) != cudaSuccess) return O2PIC_E_CUDA;
+        for (o2pic_ctx* c : b->ctx)
+            if (int rc = fill_vring(c, c->host_step + 1, c->host_step + b->K, b->stream)) return rc;
+        cudaEventRecord(b->t0, b->stream);
+        if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return O2PIC_E_CUDA;
+        cudaEventRecord(b->t1, b->stream);
+        for (size_t i = 0; i < n; ++i) {
+            b->ctx[i]->host_step += b->K;
+            b->ctx[i]->launches += b->launches_per_replay[i];
+        }
+        if (int rc = o2pic_batch_synchronize(b)) return rc;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, b->t0, b->t1);
+        rep.other_mode_ms = ms;
+        if (!(ms < best_ms)) b->fused = !b->fused;   // keep the faster mode
+    }
     if (int rc = batch_capture(b)) return rc;
     rep.chosen = best;
+    rep.fused = b->fused ? 1 : 0;
     if (report) *report = rep;
     return O2PIC_OK;
 }
