@@ -150,6 +150,12 @@ int o2pic_load_particles(o2pic_ctx* ctx, int species, const float* x, const floa
                          const float* vy, const float* vz, const uint32_t* id, uint64_t n,
                          int mem_kind, void* stream);
 
+/* Sets the id the next particle born in `species` gets (it must exceed every
+ * id of that species): with o2pic_set_step and the particles of a saved state
+ * (o2pic_read_particles, o2pic_get_stats().next_id and .step) a run resumes
+ * bit for bit.  Errors: INVALID_ARG, CUDA. */
+int o2pic_set_next_id(o2pic_ctx* ctx, int species, uint32_t next_id);
+
 /* Enqueues nsteps time steps (Sec. 2 loop; see the file header) on `stream`.
  * Asynchronous; errors of the enqueued work appear at the next sync. */
 int o2pic_step(o2pic_ctx* ctx, uint64_t nsteps, void* stream);

@@ -91,6 +91,7 @@ SIGNATURES = [
     ("o2pic_create", _i32, [_P(Config), _P(_vp)]),
     ("o2pic_set_processes", _i32, [_vp, _P(Process), _i32]),
     ("o2pic_load_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _i32, _vp]),
+    ("o2pic_set_next_id", _i32, [_vp, _i32, _u32]),
     ("o2pic_step", _i32, [_vp, _u64, _vp]),
     ("o2pic_synchronize", _i32, [_vp]),
     ("o2pic_read_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _P(_u64), _i32]),
@@ -311,6 +312,9 @@ class Discharge:
 
     def set_step(self, n):
         _check(lib().o2pic_set_step(self.h, int(n)), "o2pic_set_step")
+
+    def set_next_id(self, species, next_id):
+        _check(lib().o2pic_set_next_id(self.h, int(species), int(next_id)), "o2pic_set_next_id")
 
     def set_timing(self, on):
         _check(lib().o2pic_set_timing(self.h, int(bool(on))), "o2pic_set_timing")

@@ -694,6 +694,16 @@ int o2pic_step(o2pic_ctx* c, uint64_t nsteps, void* stream) {
     return cuda_fail(c, cudaGetLastError());
 }
 
+int o2pic_set_next_id(o2pic_ctx* c, int species, uint32_t next_id) {
+    if (!c || species < 0 || species >= NSP) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    cudaError_t e = cudaMemcpy(&c->d_ctrl->next_id[species], &next_id, sizeof(next_id), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->gen += 1;
+    return O2PIC_OK;
+}
+
 int o2pic_synchronize(o2pic_ctx* c) {
     if (!c) return O2PIC_E_INVALID_ARG;
     return sync_all(c);

@@ -52,23 +52,28 @@ def _check_species(o, g_before, g_after, s, step, E, rng):
     return same, gone
 
 
-def test_scale_512_sampled_particles_charge_and_field(torch_cuda):
+@pytest.mark.parametrize("name", ["scale_512", "stress_2048"])
+def test_full_size_sampled_particles_charge_and_field(torch_cuda, name):
+    """scale_512 (the benchmark: 512 cells, 1.6e7 particles, ions every 10th
+    step) and stress_2048 (2048 cells, 1.2e8 particles, ions every step)."""
     import oracle
     from paper_0705_0497_gb300 import api, inputs, xsec
-    cfg, counts, T, _ = inputs.workload("scale_512")
+    cfg, counts, T, _ = inputs.workload(name)
     procs = xsec.oxygen_set()
     g = api.Discharge(cfg, tuple(int(n * 1.5) + (1 << 20) for n in counts), compact_check=20)
     g.set_processes(procs)
     g.load_state(inputs.initial_state(cfg, counts, T))
     b = api.Batch([g], steps_per_launch=20)
-    b.step(2)                       # steps 0..39 through the step graph
+    b.step(2 if name == "scale_512" else 1)   # through the step graph
     b.synchronize()
     b.close()
     o = oracle.Oracle(cfg, 32)
     o.set_processes(procs)
     rng = np.random.default_rng(12)
-    g.step(1)                       # ion step 40
-    for step, species in ((41, (0,)), (50, (0, 1, 2))):
+    S = cfg["ion_subcycle"]
+    first = g.stats()["step"] + 1
+    checks = ((first, (0,) if first % S else (0, 1, 2)), ((first // S + 1) * S, (0, 1, 2)))
+    for step, species in checks:
         while g.stats()["step"] < step:
             g.step(1)
         before = [g.particles(s) for s in range(3)]

@@ -327,3 +327,33 @@ def test_oxygen_set_with_recombination_100_steps(torch_cuda):
     compare_particles(g, o)
     compare_counters(g.stats(), o.counters(), nproc_of(procs))
     assert o.counters()["rec_candidates"] > 0
+
+
+def test_checkpoint_and_resume_bit_for_bit(torch_cuda):
+    """Saving the particles, step and next ids after 40 steps and resuming
+    them in a new context gives, 40 steps later, exactly the uninterrupted
+    run (the random streams are keyed by id and step only)."""
+    from paper_0705_0497_gb300 import api
+    cfg, counts, T, _ = inputs.workload("parity_128", ion_subcycle=2)
+    procs = xsec.oxygen_set(include_rec=True)
+    st = inputs.initial_state(cfg, counts, T)
+    cap = capacity_for(counts)
+    a = api.Discharge(cfg, cap)
+    a.set_processes(procs)
+    a.load_state(st)
+    a.step(40)
+    saved = [a.particles(s) for s in range(3)]
+    s40 = a.stats()
+    a.step(40)
+    b = api.Discharge(cfg, cap)
+    b.set_processes(procs)
+    b.load_state(saved)
+    b.set_step(s40["step"])
+    for s in range(3):
+        b.set_next_id(s, s40[f"next_id_{s}"])
+    b.step(40)
+    for s in range(3):
+        pa, pb = a.particles(s), b.particles(s)
+        for k in ("x", "vx", "vy", "vz", "id"):
+            assert np.array_equal(pa[k], pb[k]), (s, k)
+    assert np.array_equal(a.field()[1], b.field()[1])
