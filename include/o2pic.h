@@ -145,7 +145,9 @@ int o2pic_set_processes(o2pic_ctx* ctx, const o2pic_process* procs, int nproc);
  * uint32 ids, unique within the species); velocities are taken as
  * v^{n-1/2}.  mem_kind = O2PIC_HOST or O2PIC_DEVICE.  The next step starts
  * with a fresh deposit and field solve.  New ids continue at max(id) + 1.
- * Errors: INVALID_ARG (n > capacity, x outside [0, L), non-finite), CUDA. */
+ * The particles are checked on the device after the copy; on INVALID_ARG
+ * (x outside [0, L) or a non-finite velocity) the species is left empty.
+ * Errors: INVALID_ARG (also n > capacity, no copy made), CUDA. */
 int o2pic_load_particles(o2pic_ctx* ctx, int species, const float* x, const float* vx,
                          const float* vy, const float* vz, const uint32_t* id, uint64_t n,
                          int mem_kind, void* stream);

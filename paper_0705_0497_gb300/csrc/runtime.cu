@@ -604,15 +604,7 @@ int o2pic_load_particles(o2pic_ctx* c, int species, const float* x, const float*
     if (n > c->P.sp[species].cap) return O2PIC_E_INVALID_ARG;
     if (n > 0 && (!x || !vx || !vy || !vz || !id)) return O2PIC_E_INVALID_ARG;
     if (mem_kind != O2PIC_HOST && mem_kind != O2PIC_DEVICE) return O2PIC_E_INVALID_ARG;
-    unsigned next = 0;
-    if (mem_kind == O2PIC_HOST) {
-        const float Lf = c->P.Lf;
-        for (uint64_t i = 0; i < n; ++i) {
-            if (!(x[i] >= 0.0f && x[i] < Lf) || !std::isfinite(vx[i]) || !std::isfinite(vy[i]) || !std::isfinite(vz[i]))
-                return O2PIC_E_INVALID_ARG;
-            next = std::max(next, id[i] + 1u);
-        }
-    }
+    const unsigned next = 0;   // the check kernel raises it to max(id) + 1
     int rc = sync_all(c);
     if (rc == O2PIC_E_CUDA) return rc;
     c->latched = 0;
@@ -638,7 +630,9 @@ int o2pic_load_particles(o2pic_ctx* c, int species, const float* x, const float*
     h.error_flags = 0;
     e = cudaMemcpyAsync(c->d_ctrl, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e);
-    if (mem_kind == O2PIC_DEVICE && n > 0) {
+    if (n > 0) {
+        // both memory kinds: the particles are checked (and max(id) found) on
+        // the device once they are there
         launch_load_check(species, c->P, n, s);
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(c, e);

@@ -187,6 +187,17 @@ def test_invalid_load_rejected(torch_cuda):
         g.load(0, torch.from_numpy(x).cuda(), *(torch.from_numpy(z).cuda() for _ in range(3)),
                torch.arange(10, dtype=torch.int32).cuda())
     assert ei.value.code == -1
+    # a non-finite velocity from host memory; the species stays empty and a
+    # valid load afterwards is accepted
+    xs = np.full(10, cfg["L"] * 0.5, np.float32)
+    vbad = z.copy()
+    vbad[7] = np.inf
+    with pytest.raises(api.O2picError) as ei:
+        g.load(0, xs, z, vbad, z, np.arange(10))
+    assert ei.value.code == -1
+    assert g.count(0) == 0
+    g.load(0, xs, z, z, z, np.arange(10))
+    assert g.count(0) == 10
 
 
 def test_long_run_profiles(torch_cuda):
