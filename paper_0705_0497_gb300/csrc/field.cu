@@ -26,18 +26,32 @@ namespace o2 {
 namespace {
 
 constexpr int FT = 1024;                          // threads of the field block
+// The block works as two groups that meet only for U sin(2 pi f t):
+// warps 0-15 commit the charge and solve the field, warps 16-31 place the
+// births and commit the step.  Each group synchronizes on its own named
+// barrier (0 is __syncthreads).
+constexpr int GA = 512;                           // charge commit and field solve
+constexpr int GB = FT - GA;                       // births and the step commit
+constexpr int BAR_A = 1, BAR_B = 2, BAR_V0 = 3;
+
+template <int BAR, int NT>
+__device__ __forceinline__ void group_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+template <int BAR, int NT>
+__device__ __forceinline__ void group_arrive() {
+    asm volatile("bar.arrive %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
 
 // Births of one step, placed in the order the method defines (source species
 // e then O-, parent order, e before O2+ for an ionization): each warp of a
 // particle kernel staged the births of its slot range [u R, ...) with their
-// count.  The counts are scanned into per-warp offsets in shared memory, and
-// every thread then places single births (found by a binary search over the
-// offsets), so the work spreads over the block however the births cluster.
-// A birth's CIC charge goes to the shared-memory accumulator bq[species][node]
-// (32-bit: at most 65535 births per species and step, checked by the caller),
-// or, above that, straight to the global Qb.
+// count (their charge already went to Qb there).  The counts are scanned into
+// per-warp offsets in shared memory, and every thread of the births group
+// then places single births (found by a binary search over the offsets), so
+// the work spreads over the group however the births cluster.
 __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP], int d, unsigned long long slot,
-                            unsigned long long id64, float4 b, unsigned* bq) {
+                            unsigned long long id64, float4 b) {
     const SpeciesBuf& B = P.sp[d];
     if (slot >= B.cap) { atomicOr(&C->error_flags, ERR_CAPACITY); return; }
     if (id64 > 0xFFFFFFFFull) atomicOr(&C->error_flags, ERR_ID);
@@ -47,22 +61,12 @@ __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP]
     B.vy[cb][slot] = b.z;
     B.vz[cb][slot] = b.w;
     B.id[cb][slot] = (uint32_t)id64;
-    int j; float frac;
-    cell_of(b.x, P.inv_dx, P.Nc, j, frac);
-    const uint32_t r = cic_r(frac);
-    if (bq) {
-        atomicAdd(&bq[d * P.Ng + j], 65536u - r);
-        atomicAdd(&bq[d * P.Ng + j + 1], r);
-    } else {
-        atomicAdd(&P.Qb[d][j], (unsigned long long)(65536u - r));
-        atomicAdd(&P.Qb[d][j + 1], (unsigned long long)r);
-    }
 }
 
-// Exclusive block scan of two 32-bit counts packed in 64 bits (FT threads).
-__device__ __forceinline__ unsigned long long block_excl_scan2(unsigned long long v, unsigned long long* ws,
-                                                              unsigned long long* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Exclusive scan over the births group of two 32-bit counts packed in 64 bits.
+__device__ __forceinline__ unsigned long long groupB_excl_scan2(unsigned long long v, unsigned long long* ws,
+                                                               unsigned long long* total) {
+    const int tB = threadIdx.x - GA, lane = tB & 31, warp = tB >> 5;
     unsigned long long x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -70,28 +74,29 @@ __device__ __forceinline__ unsigned long long block_excl_scan2(unsigned long lon
         if (lane >= o) x += y;
     }
     if (lane == 31) ws[warp] = x;
-    __syncthreads();
+    group_sync<BAR_B, GB>();
     if (warp == 0) {
-        unsigned long long t = ws[lane];
+        unsigned long long s = (lane < GB / 32) ? ws[lane] : 0ull;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
         }
-        ws[lane] = t;
+        if (lane < GB / 32) ws[lane] = s;
     }
-    __syncthreads();
+    group_sync<BAR_B, GB>();
     const unsigned long long excl = (warp == 0 ? 0ull : ws[warp - 1]) + x - v;
-    *total = ws[31];
-    __syncthreads();
+    *total = ws[GB / 32 - 1];
+    group_sync<BAR_B, GB>();
     return excl;
 }
 
-// Offsets of the per-warp counts c1 (and c2) of nu warps into p1[0..nu] (p2).
+// Offsets of the per-warp counts c1 (and c2) of nu warps into p1[0..nu] (p2),
+// over the births group.
 __device__ unsigned long long unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu, unsigned* p1,
                                            unsigned* p2, unsigned long long* ws) {
-    const int t = threadIdx.x;
-    const unsigned per = (nu + FT - 1) / FT, u0 = t * per, u1 = (u0 + per < nu) ? u0 + per : nu;
+    const int tB = threadIdx.x - GA;
+    const unsigned per = (nu + GB - 1) / GB, u0 = tB * per, u1 = (u0 + per < nu) ? u0 + per : nu;
     unsigned long long mine = 0;
     for (unsigned u = u0; u < u1; ++u) {
         const unsigned a = c1[u], b = c2 ? c2[u] : 0u;
@@ -99,15 +104,15 @@ __device__ unsigned long long unit_offsets(const unsigned* c1, const unsigned* c
         mine += (unsigned long long)a | ((unsigned long long)b << 32);
     }
     unsigned long long all;
-    const unsigned long long ex = block_excl_scan2(mine, ws, &all);
+    const unsigned long long ex = groupB_excl_scan2(mine, ws, &all);
     unsigned r1 = (unsigned)ex, r2 = (unsigned)(ex >> 32);
     for (unsigned u = u0; u < u1; ++u) {
         const unsigned a = p1[u], b = p2[u];
         p1[u] = r1; p2[u] = r2;
         r1 += a; r2 += b;
     }
-    if (t == 0) { p1[nu] = (unsigned)all; p2[nu] = (unsigned)(all >> 32); }
-    __syncthreads();
+    if (tB == 0) { p1[nu] = (unsigned)all; p2[nu] = (unsigned)(all >> 32); }
+    group_sync<BAR_B, GB>();
     return all;
 }
 
@@ -116,9 +121,9 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// Prefetch a thread's share of the per-warp counts of unit_offsets.
+// Prefetch a births-group thread's share of the per-warp counts.
 __device__ __forceinline__ void prefetch_units(const unsigned* c1, const unsigned* c2, unsigned nu) {
-    const unsigned per = (nu + FT - 1) / FT, u0 = threadIdx.x * per, u1 = (u0 + per < nu) ? u0 + per : nu;
+    const unsigned per = (nu + GB - 1) / GB, u0 = (threadIdx.x - GA) * per, u1 = (u0 + per < nu) ? u0 + per : nu;
     for (unsigned u = u0; u < u1; u += 32) {   // 32 counts per 128-byte line
         prefetch_l1(c1 + u);
         if (c2) prefetch_l1(c2 + u);
@@ -140,11 +145,11 @@ struct CtrlSnap {
     unsigned next_id[NSP], cur[NSP], removals;
 };
 
-// Block-wide inclusive scans of two int64 arrays a, b [0..n) in shared memory
-// at once (blocked: thread t owns [t*per, (t+1)*per)).
-__device__ __forceinline__ void block_scan_smem_pair(long long* a, long long* b, int n, long long* ws) {
+// Inclusive scans over the charge group of two int64 arrays a, b [0..n) in
+// shared memory at once (blocked: thread t owns [t*per, (t+1)*per)).
+__device__ __forceinline__ void groupA_scan_pair(long long* a, long long* b, int n, long long* ws) {
     const int t = threadIdx.x;
-    const int per = (n + FT - 1) / FT;
+    const int per = (n + GA - 1) / GA;
     const int j0 = t * per;
     long long ra = 0, rb = 0;
     for (int i = 0; i < per; ++i) {
@@ -160,141 +165,193 @@ __device__ __forceinline__ void block_scan_smem_pair(long long* a, long long* b,
         if (lane >= o) { xa += ya; xb += yb; }
     }
     if (lane == 31) { ws[warp] = xa; ws[32 + warp] = xb; }
-    __syncthreads();
+    group_sync<BAR_A, GA>();
     if (warp == 0) {
-        long long va = ws[lane], vb = ws[32 + lane];
+        long long va = (lane < GA / 32) ? ws[lane] : 0, vb = (lane < GA / 32) ? ws[32 + lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const long long ya = __shfl_up_sync(0xffffffffu, va, o);
             const long long yb = __shfl_up_sync(0xffffffffu, vb, o);
             if (lane >= o) { va += ya; vb += yb; }
         }
-        ws[lane] = va; ws[32 + lane] = vb;
+        if (lane < GA / 32) { ws[lane] = va; ws[32 + lane] = vb; }
     }
-    __syncthreads();
+    group_sync<BAR_A, GA>();
     const long long offa = (warp == 0 ? 0 : ws[warp - 1]) + (xa - ra);
     const long long offb = (warp == 0 ? 0 : ws[32 + warp - 1]) + (xb - rb);
     for (int i = 0; i < per; ++i) {
         const int j = j0 + i;
         if (j < n) { a[j] += offa; b[j] += offb; }
     }
-    __syncthreads();
+    group_sync<BAR_A, GA>();
 }
 
 // mode 0: end of a step (pushed_mask = species pushed this step);
 // mode 1: after a load (all species freshly deposited into Qf).
-// Dynamic shared memory: S, U as int64 [Ng] (before the charge commit the
-// same bytes hold the births' 32-bit charge bq[3][Ng]), then two u32
-// [max warps + 1].  Every load that does not depend on another is issued at
-// the start: the step state, the charges of the thread's nodes, the per-warp
-// birth counts and U sin(2 pi f t).
+// Dynamic shared memory: S, U as int64 [Ng] (charge group), then two u32
+// [max warps + 1] (births group).
 __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed_mask) {
     extern __shared__ long long fsm[];
-    __shared__ long long ws[64];
-    __shared__ unsigned long long ws2[32];
+    __shared__ long long wsA[64];
+    __shared__ unsigned long long wsB[GB / 32];
     __shared__ CtrlSnap cs;
     __shared__ long long sh_R0, sh_RN;
     __shared__ double sh_V0, sh_D0;
     DevCtrl* C = P.ctrl;
     const int N = P.Nc, Ng = P.Ng;
     const int t = threadIdx.x;
-    long long* Ss = fsm;          // S_j = sum_{k=1..j} R_k
-    long long* Us = fsm + Ng;     // U_j = sum_{k=1..j} k R_k   (T_j = j S_{j-1} - U_{j-1})
-    unsigned* bq = reinterpret_cast<unsigned*>(fsm);
+
+    if (t < GA) {
+        // ================= charge commit, cycle moments, field solve
+        long long* Ss = fsm;          // S_j = sum_{k=1..j} R_k
+        long long* Us = fsm + Ng;     // U_j = sum_{k=1..j} k R_k   (T_j = j S_{j-1} - U_{j-1})
+        // Q = (this step's deposit Qf, or the kept Q of a species not pushed)
+        // + the births' deposit Qb; two nodes per thread with all their
+        // loads issued before any store
+        for (int j0 = t; j0 < Ng; j0 += 2 * GA) {
+            unsigned long long q[2][NSP], qa[2][NSP];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + h * GA;
+#pragma unroll
+                for (int s = 0; s < NSP; ++s) {
+                    q[h][s] = 0ull; qa[h][s] = 0ull;
+                    if (j < Ng) {
+                        const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
+                        q[h][s] = (fresh ? P.Qf[s][j] : P.Q[s][j]) + P.Qb[s][j];
+                        if (mode == 0) qa[h][s] = P.Qacc[s][j];
+                    }
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + h * GA;
+                if (j >= Ng) continue;
+                long long net = 0;
+#pragma unroll
+                for (int s = 0; s < NSP; ++s) {
+                    P.Q[s][j] = q[h][s];
+                    P.Qf[s][j] = 0ull;
+                    P.Qb[s][j] = 0ull;
+                    if (mode == 0) P.Qacc[s][j] = qa[h][s] + q[h][s];
+                    net += (s == SP_OP) ? (long long)q[h][s] : -(long long)q[h][s];
+                }
+                Ss[j] = (j >= 1) ? net : 0;                    // scanned below
+                Us[j] = (j >= 1) ? (long long)j * net : 0;
+                if (j == 0) sh_R0 = net;
+                if (j == N) sh_RN = net;
+            }
+        }
+        group_sync<BAR_A, GA>();
+        groupA_scan_pair(Ss, Us, Ng, wsA);
+        const double c = P.c_field;
+        // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load),
+        // evaluated on the host in FP64, staged in a ring indexed by the step
+        // and read by the births group (the owner of the step state).  D0 once
+        // per block: FP64 throughput on this GPU is low.
+        if (t < 32) {
+            group_sync<BAR_V0, 64>();
+            if (t == 0) {
+                const long long TN = (long long)N * Ss[N - 1] - Us[N - 1];
+                const double D0 = (c * (double)TN - sh_V0) / (double)N;
+                sh_D0 = D0;
+                P.fVD[0] = sh_V0;
+                P.fVD[1] = D0;
+            }
+        }
+        group_sync<BAR_A, GA>();
+        // E on the nodes (what the next push gathers).  The potential needs as
+        // much FP64 work again and only diagnostics read it: S, U, V0 and D0
+        // are kept so that k_phi evaluates it with the same expressions.
+        const double D0 = sh_D0, D2 = 2.0 * sh_D0;   // 2 D0 is exact
+        const long long R0 = sh_R0, RN = sh_RN;
+        for (int j = t; j < Ng; j += GA) {
+            double E;
+            if (j == 0) E = (-D0 - c * (double)R0) * P.inv_dx64;
+            else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)RN) * P.inv_dx64;
+            else E = (c * (double)(Ss[j] + Ss[j - 1]) - D2) * P.inv_2dx64;
+            P.Ef[j] = (float)E;
+            P.fS[j] = Ss[j];
+            P.fU[j] = Us[j];
+        }
+        return;
+    }
+
+    // ===================== births, (17) removals and the commit of the step
+    const int tB = t - GA;
     unsigned* p1 = reinterpret_cast<unsigned*>(fsm + 2 * Ng);
     unsigned* p2 = p1 + (P.max_push_warps + 1);
     const bool births_e = mode == 0 && P.births_possible[SP_E];
     const bool births_om = mode == 0 && ((pushed_mask >> SP_OM) & 1) && P.births_possible[SP_OM];
-
-    // ---- loads: the step state and U sin(2 pi f t) now; the charges and the
-    // birth counts into L1, read where they are used
-    if (t < NSP) {
-        cs.slots[t] = C->slots[t]; cs.live[t] = C->live[t]; cs.removed[t] = C->removed[t];
-        cs.next_id[t] = C->next_id[t]; cs.cur[t] = C->cur[t];
-    } else if (t == 32) {
-        const unsigned long long step = C->step;
-        cs.step = step;
-        cs.epoch = C->epoch;
-        cs.acc_steps = C->acc_steps;
-        cs.removals = C->removals;
-        sh_V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
-    }
-    for (int j = t * 16; j < Ng; j += FT * 16) {   // 16 u64 per 128-byte line
-#pragma unroll
-        for (int s = 0; s < NSP; ++s) {
-            prefetch_l1(&P.Qf[s][j]);
-            prefetch_l1(&P.Q[s][j]);
-            if (mode == 0) prefetch_l1(&P.Qacc[s][j]);
+    if (tB < NSP) {
+        cs.slots[tB] = C->slots[tB]; cs.live[tB] = C->live[tB]; cs.removed[tB] = C->removed[tB];
+        cs.next_id[tB] = C->next_id[tB]; cs.cur[tB] = C->cur[tB];
+    } else if (tB >= 32 && tB < 64) {
+        if (tB == 32) {
+            const unsigned long long step = C->step;
+            cs.step = step;
+            cs.epoch = C->epoch;
+            cs.acc_steps = C->acc_steps;
+            cs.removals = C->removals;
+            sh_V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
         }
+        __syncwarp();
+        group_arrive<BAR_V0, 64>();   // sh_V0 for the charge group's D0
     }
     if (births_e) prefetch_units(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], P.push_warps[SP_E]);
     if (births_om) prefetch_units(P.wcount[B_E_FROM_OM], nullptr, P.push_warps[SP_OM]);
-    for (int i = t; i < NSP * Ng; i += FT) bq[i] = 0u;
-    __syncthreads();
+    group_sync<BAR_B, GB>();
 
-    // ---- births
     unsigned long long btot[NB];
     for (int k = 0; k < NB; ++k) btot[k] = 0;
-    bool bq_used = true;
     if (births_e) {
         const unsigned ns = (unsigned)(cs.slots[SP_E] < P.sp[SP_E].cap ? cs.slots[SP_E] : P.sp[SP_E].cap);
         const unsigned nu = P.push_warps[SP_E], R = warp_range_len(ns, nu);
-        const unsigned long long all = unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu, p1, p2, ws2);
+        const unsigned long long all = unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu, p1, p2, wsB);
         const unsigned n1 = (unsigned)all, n2 = (unsigned)(all >> 32);
-        unsigned* acc = (n1 < 65536u && n2 < 65536u) ? bq : nullptr;
-        bq_used = acc != nullptr;
-        for (unsigned b = t; b < n1; b += FT) {
+        for (unsigned b = tB; b < n1; b += GB) {
             const unsigned u = find_unit(p1, nu, b);
             const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
             const float4 be = P.stage[B_E_FROM_E][sb], bo = P.stage[B_OP_FROM_E][sb];
-            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + b, (unsigned long long)cs.next_id[SP_E] + b, be, acc);
-            place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + b, (unsigned long long)cs.next_id[SP_OP] + b, bo, acc);
+            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + b, (unsigned long long)cs.next_id[SP_E] + b, be);
+            place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + b, (unsigned long long)cs.next_id[SP_OP] + b, bo);
         }
-        for (unsigned b = t; b < n2; b += FT) {
+        for (unsigned b = tB; b < n2; b += GB) {
             const unsigned u = find_unit(p2, nu, b);
             const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p2[u]);
             place_birth(P, C, cs.cur, SP_OM, cs.slots[SP_OM] + b, (unsigned long long)cs.next_id[SP_OM] + b,
-                        P.stage[B_OM_FROM_E][sb], acc);
+                        P.stage[B_OM_FROM_E][sb]);
         }
         btot[B_E_FROM_E] = n1;
         btot[B_OP_FROM_E] = n1;
         btot[B_OM_FROM_E] = n2;
-        __syncthreads();
+        group_sync<BAR_B, GB>();   // p1, p2 are reused below
     }
     // O- kernel (ion steps): detachment electrons, after the electron kernel's
     if (births_om) {
         const unsigned ns = (unsigned)(cs.slots[SP_OM] < P.sp[SP_OM].cap ? cs.slots[SP_OM] : P.sp[SP_OM].cap);
         const unsigned nu = P.push_warps[SP_OM], R = warp_range_len(ns, nu);
-        const unsigned n = (unsigned)unit_offsets(P.wcount[B_E_FROM_OM], nullptr, nu, p1, p2, ws2);
+        const unsigned n = (unsigned)unit_offsets(P.wcount[B_E_FROM_OM], nullptr, nu, p1, p2, wsB);
         const unsigned long long base = btot[B_E_FROM_E];
-        unsigned* acc = (bq_used && base + n < 65536u) ? bq : nullptr;
-        for (unsigned b = t; b < n; b += FT) {
+        for (unsigned b = tB; b < n; b += GB) {
             const unsigned u = find_unit(p1, nu, b);
             const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
             place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + base + b, (unsigned long long)cs.next_id[SP_E] + base + b,
-                        P.stage[B_E_FROM_OM][sb], acc);
+                        P.stage[B_E_FROM_OM][sb]);
         }
         btot[B_E_FROM_OM] = n;
-        if (!acc) bq_used = false;
-        __syncthreads();
     }
-    // births that went to the global accumulator (a step with > 65535 births)
-    const bool qb_global = __syncthreads_or(!bq_used);
-    if (qb_global) __threadfence();
-    __syncthreads();
 
-    // ---- commit of the step (early: its stores overlap the field solve,
-    // which reads only the snapshot).  Removals of (17) first.
     if (mode == 0) {
         // (17) removals: mark both ions of every reacted pair dead
         const unsigned nrem = (cs.removals < P.max_removals) ? cs.removals : P.max_removals;
-        for (unsigned r = t; r < nrem; r += FT) {
+        for (unsigned r = tB; r < nrem; r += GB) {
             P.sp[SP_OM].x[cs.cur[SP_OM]][P.removal[2 * r]] = dead_marker();
             P.sp[SP_OP].x[cs.cur[SP_OP]][P.removal[2 * r + 1]] = dead_marker();
         }
         // commit of the step: one thread per species, then the step counters
-        if (t < NSP) {
-            const int s = t;
+        if (tB < NSP) {
+            const int s = tB;
             const unsigned long long bs = (s == SP_E) ? btot[B_E_FROM_E] + btot[B_E_FROM_OM]
                                                       : (s == SP_OP ? btot[B_OP_FROM_E] : btot[B_OM_FROM_E]);
             const unsigned long long rem = cs.removed[s] + ((s != SP_E) ? (unsigned long long)nrem : 0ull);
@@ -312,97 +369,33 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
             C->next_id[s] = (unsigned)nid;
             C->removed[s] = 0ull;
             if (bs) atomicAdd(&C->cnt.born[s], bs);
-        } else if (t == 32) {
+        } else if (tB == 32) {
             if (nrem) atomicAdd(&C->cnt.neutralized, (unsigned long long)nrem);
-            // this block is the only writer of the step state: plain stores
+            // this group is the only writer of the step state: plain stores
             C->removals = 0u;
             C->rremovals = 0u;
             C->acc_steps = cs.acc_steps + 1;
             C->step = cs.step + 1;
             C->epoch = cs.epoch + 1;
-        } else if (t >= 64 && t < 64 + NKK + NSP) {
-            C->ticket[t - 64] = 0u;
+        } else if (tB >= 64 && tB < 64 + NKK + NSP) {
+            C->ticket[tB - 64] = 0u;
         }
-    }
-
-    // ---- charge commit, moments, net charge.  bq shares its bytes with S and
-    // U: every bq value is read (and net kept in registers) before S, U are
-    // written.
-    constexpr int JK = (MAX_NODES + FT - 1) / FT;
-    long long netr[JK];
-#pragma unroll
-    for (int k = 0; k < JK; ++k) {
-        const int j = t + k * FT;
-        netr[k] = 0;
-        if (j < Ng) {
-            long long net = 0;
-#pragma unroll
-            for (int s = 0; s < NSP; ++s) {
-                const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
-                unsigned long long q = (fresh ? P.Qf[s][j] : P.Q[s][j]) + bq[s * Ng + j];
-                if (qb_global) { q += __ldcg(&P.Qb[s][j]); P.Qb[s][j] = 0ull; }
-                P.Q[s][j] = q;
-                P.Qf[s][j] = 0ull;
-                if (mode == 0) P.Qacc[s][j] += q;
-                net += (s == SP_OP) ? (long long)q : -(long long)q;
-            }
-            netr[k] = net;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < JK; ++k) {
-        const int j = t + k * FT;
-        if (j < Ng) {
-            Ss[j] = (j >= 1) ? netr[k] : 0;                    // scanned below
-            Us[j] = (j >= 1) ? (long long)j * netr[k] : 0;
-            if (j == 0) sh_R0 = netr[k];
-            if (j == N) sh_RN = netr[k];
-        }
-    }
-    __syncthreads();
-    block_scan_smem_pair(Ss, Us, Ng, ws);
-    const double c = P.c_field;
-    // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load), evaluated
-    // on the host in FP64 and staged in a ring indexed by the step.  D0 once
-    // per block: FP64 throughput on this GPU is low.
-    if (t == 0) {
-        const long long TN = (long long)N * Ss[N - 1] - Us[N - 1];
-        const double D0 = (c * (double)TN - sh_V0) / (double)N;
-        sh_D0 = D0;
-        P.fVD[0] = sh_V0;
-        P.fVD[1] = D0;
-    }
-    __syncthreads();
-    // E on the nodes (what the next push gathers).  The potential needs as
-    // much FP64 work again and only diagnostics read it: S, U, V0 and D0 are
-    // kept so that k_phi evaluates it with the same expressions on request.
-    const double D0 = sh_D0, D2 = 2.0 * sh_D0;   // 2 D0 is exact
-    const long long R0 = sh_R0, RN = sh_RN;
-    for (int j = t; j < Ng; j += FT) {
-        double E;
-        if (j == 0) E = (-D0 - c * (double)R0) * P.inv_dx64;
-        else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)RN) * P.inv_dx64;
-        else E = (c * (double)(Ss[j] + Ss[j - 1]) - D2) * P.inv_2dx64;
-        P.Ef[j] = (float)E;
-        P.fS[j] = Ss[j];
-        P.fU[j] = Us[j];
     }
     // per-cell ion totals of (17): zero for the next ion step
-    for (int k = t; k < 2 * N; k += FT) { P.ptot[k] = 0u; P.rtot[k] = 0u; }
+    for (int k = tB; k < 2 * N; k += GB) { P.ptot[k] = 0u; P.rtot[k] = 0u; }
     // conduction-current sums: after a load the ring restarts; at the end of
     // step n the ions' entries of a step without an ion push repeat those of
     // step n-1, and the slot of step n+1 is cleared for its pushes
     if (mode != 0) {
-        for (int k = t; k < JRING * NSP; k += FT) P.jring[k] = 0ull;
-    } else if (t >= 96 && t < 96 + NSP) {
-        const int sp = t - 96;
+        for (int k = tB; k < JRING * NSP; k += GB) P.jring[k] = 0ull;
+        if (tB < NKK + NSP) C->ticket[tB] = 0u;
+    } else if (tB >= 96 && tB < 96 + NSP) {
+        const int sp = tB - 96;
         const unsigned long long n = cs.step;
         if (sp != SP_E && !((pushed_mask >> sp) & 1))
             P.jring[(n & (JRING - 1)) * NSP + sp] = P.jring[((n - 1) & (JRING - 1)) * NSP + sp];
         P.jring[((n + 1) & (JRING - 1)) * NSP + sp] = 0ull;
     }
-    if (mode != 0 && t < NKK + NSP) C->ticket[t] = 0u;
 }
 
 // Stable compaction of the live slots of one species into the other buffer
@@ -511,8 +504,6 @@ __device__ __forceinline__ void compact_body(const Params& P, int mode, unsigned
     }
 }
 
-// Validation of freshly loaded particles (x in [0, L), finite velocities)
-// and the largest id (+1) for the species' next id.
 __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
     pdl_wait();
     pdl_trigger();   // one block on one SM: the next step's push may take the others
@@ -547,6 +538,8 @@ __global__ void __launch_bounds__(BLOCK) k_compact_b(const Params* __restrict__ 
     compact_body<S>(sP, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
 }
 
+// Validation of freshly loaded particles (x in [0, L), finite velocities)
+// and the largest id (+1) for the species' next id.
 template <int S>
 __global__ void k_load_check(Params P, unsigned long long n) {
     DevCtrl* C = P.ctrl;

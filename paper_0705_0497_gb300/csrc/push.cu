@@ -199,6 +199,15 @@ __device__ __forceinline__ void deposit_sub_global(unsigned long long* Q, float 
     atomicAdd(&Q[j + 1], 0ull - (unsigned long long)r);
 }
 
+// A birth's CIC charge, into the births' accumulator Qb of its species.
+__device__ __forceinline__ void deposit_add_global(unsigned long long* Q, float x, float inv_dx, int Nc) {
+    int j; float frac;
+    cell_of(x, inv_dx, Nc, j, frac);
+    const uint32_t r = cic_r(frac);
+    atomicAdd(&Q[j], (unsigned long long)(65536u - r));
+    if (r) atomicAdd(&Q[j + 1], (unsigned long long)r);
+}
+
 __device__ __forceinline__ void flush_hist(unsigned* hist, unsigned long long* Q, int Ng) {
     for (int j = threadIdx.x; j < Ng; j += BLOCK) {
         const unsigned v = hist[j];
@@ -413,16 +422,24 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
             if (births) {
                 const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1);
                 const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2);
+                // staged for the end-of-step kernel, which places them; their
+                // charge goes to Qb now
                 if (S == SP_E) {
                     if (bkind == 1) {
                         const unsigned r = nb1 + __popc(m1 & lt_mask);
                         P.stage[B_E_FROM_E][r0 + r] = b1;
                         P.stage[B_OP_FROM_E][r0 + r] = b2;
+                        deposit_add_global(P.Qb[SP_E], b1.x, inv_dx, Nc);
+                        deposit_add_global(P.Qb[SP_OP], b2.x, inv_dx, Nc);
                     } else if (bkind == 2) {
                         P.stage[B_OM_FROM_E][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
+                        deposit_add_global(P.Qb[SP_OM], b1.x, inv_dx, Nc);
                     }
                 } else if (S == SP_OM) {
-                    if (bkind == 2) P.stage[B_E_FROM_OM][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
+                    if (bkind == 2) {
+                        P.stage[B_E_FROM_OM][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
+                        deposit_add_global(P.Qb[SP_E], b1.x, inv_dx, Nc);
+                    }
                 }
                 nb1 += __popc(m1);
                 nb2 += __popc(m2);
