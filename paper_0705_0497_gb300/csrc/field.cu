@@ -63,57 +63,103 @@ __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP]
     B.id[cb][slot] = (uint32_t)id64;
 }
 
-// Exclusive scan over the births group of two 32-bit counts packed in 64 bits.
-__device__ __forceinline__ unsigned long long groupB_excl_scan2(unsigned long long v, unsigned long long* ws,
-                                                               unsigned long long* total) {
+// Exclusive scan over the births group of two 64-bit values per thread, with
+// the totals.
+__device__ __forceinline__ void groupB_excl_scan_pair(unsigned long long v, unsigned long long w,
+                                                      unsigned long long* ws, unsigned long long& ev,
+                                                      unsigned long long& ew, unsigned long long& tv,
+                                                      unsigned long long& tw) {
     const int tB = threadIdx.x - GA, lane = tB & 31, warp = tB >> 5;
-    unsigned long long x = v;
+    constexpr int NW = GB / 32;
+    unsigned long long x = v, y = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        const unsigned long long xo = __shfl_up_sync(0xffffffffu, x, o);
+        const unsigned long long yo = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) { x += xo; y += yo; }
     }
-    if (lane == 31) ws[warp] = x;
+    if (lane == 31) { ws[warp] = x; ws[NW + warp] = y; }
     group_sync<BAR_B, GB>();
     if (warp == 0) {
-        unsigned long long s = (lane < GB / 32) ? ws[lane] : 0ull;
+        unsigned long long a = (lane < NW) ? ws[lane] : 0ull, b = (lane < NW) ? ws[NW + lane] : 0ull;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+            const unsigned long long ao = __shfl_up_sync(0xffffffffu, a, o);
+            const unsigned long long bo = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { a += ao; b += bo; }
         }
-        if (lane < GB / 32) ws[lane] = s;
+        if (lane < NW) { ws[lane] = a; ws[NW + lane] = b; }
     }
     group_sync<BAR_B, GB>();
-    const unsigned long long excl = (warp == 0 ? 0ull : ws[warp - 1]) + x - v;
-    *total = ws[GB / 32 - 1];
+    ev = (warp == 0 ? 0ull : ws[warp - 1]) + x - v;
+    ew = (warp == 0 ? 0ull : ws[NW + warp - 1]) + y - w;
+    tv = ws[NW - 1];
+    tw = ws[2 * NW - 1];
     group_sync<BAR_B, GB>();
-    return excl;
 }
 
-// Offsets of the per-warp counts c1 (and c2) of nu warps into p1[0..nu] (p2),
-// over the births group.
-__device__ unsigned long long unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu, unsigned* p1,
-                                           unsigned* p2, unsigned long long* ws) {
+// Offsets of the per-warp birth counts: c1, c2 of the electron kernel's nu1
+// warps into p1, p2 [0..nu1], c3 of the O- kernel's nu3 warps into p3
+// [0..nu3] (nu1 or nu3 may be 0), by one scan over the births group; returns
+// the totals (c1 | c2 << 32 and c3).  A thread owns a range of a multiple of 4
+// units, read as 16-byte vectors (the count arrays are 256-byte aligned).
+__device__ __forceinline__ void unit_range(unsigned nu, unsigned& u0, unsigned& u1) {
+    const unsigned tB = threadIdx.x - GA;
+    const unsigned per = (((nu + GB - 1) / GB) + 3u) & ~3u;
+    u0 = tB * per < nu ? tB * per : nu;
+    u1 = (u0 + per < nu) ? u0 + per : nu;
+}
+
+__device__ __forceinline__ uint4 count4(const unsigned* c, unsigned u, unsigned nu) {
+    if (u + 4 <= nu) return *reinterpret_cast<const uint4*>(c + u);
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (u < nu) r.x = c[u];
+    if (u + 1 < nu) r.y = c[u + 1];
+    if (u + 2 < nu) r.z = c[u + 2];
+    return r;
+}
+
+__device__ void unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu1, const unsigned* c3, unsigned nu3,
+                             unsigned* p1, unsigned* p2, unsigned* p3, unsigned long long* ws,
+                             unsigned long long& tot12, unsigned long long& tot3) {
     const int tB = threadIdx.x - GA;
-    const unsigned per = (nu + GB - 1) / GB, u0 = tB * per, u1 = (u0 + per < nu) ? u0 + per : nu;
-    unsigned long long mine = 0;
-    for (unsigned u = u0; u < u1; ++u) {
-        const unsigned a = c1[u], b = c2 ? c2[u] : 0u;
-        p1[u] = a; p2[u] = b;
-        mine += (unsigned long long)a | ((unsigned long long)b << 32);
+    unsigned u0, u1;
+    unit_range(nu1 > nu3 ? nu1 : nu3, u0, u1);
+    unsigned long long m12 = 0, m3 = 0;
+    for (unsigned ub = u0; ub < u1; ub += 8) {
+        uint4 a[2], b[2], d[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {       // all loads first
+            const unsigned u = ub + 4u * k;
+            const bool in = u < u1;
+            a[k] = in ? count4(c1, u, nu1) : make_uint4(0u, 0u, 0u, 0u);
+            b[k] = in ? count4(c2, u, nu1) : make_uint4(0u, 0u, 0u, 0u);
+            d[k] = in ? count4(c3, u, nu3) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const unsigned u = ub + 4u * k;
+            const unsigned av[4] = {a[k].x, a[k].y, a[k].z, a[k].w}, bv[4] = {b[k].x, b[k].y, b[k].z, b[k].w},
+                           dv[4] = {d[k].x, d[k].y, d[k].z, d[k].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool mine = u + e < u1;   // the next thread's units are its own
+                if (mine && u + e < nu1) { p1[u + e] = av[e]; p2[u + e] = bv[e]; }
+                if (mine && u + e < nu3) p3[u + e] = dv[e];
+                m12 += (unsigned long long)av[e] | ((unsigned long long)bv[e] << 32);
+                m3 += dv[e];
+            }
+        }
     }
-    unsigned long long all;
-    const unsigned long long ex = groupB_excl_scan2(mine, ws, &all);
-    unsigned r1 = (unsigned)ex, r2 = (unsigned)(ex >> 32);
+    unsigned long long e12, e3;
+    groupB_excl_scan_pair(m12, m3, ws, e12, e3, tot12, tot3);
+    unsigned r1 = (unsigned)e12, r2 = (unsigned)(e12 >> 32), r3 = (unsigned)e3;
     for (unsigned u = u0; u < u1; ++u) {
-        const unsigned a = p1[u], b = p2[u];
-        p1[u] = r1; p2[u] = r2;
-        r1 += a; r2 += b;
+        if (u < nu1) { const unsigned x = p1[u], y = p2[u]; p1[u] = r1; p2[u] = r2; r1 += x; r2 += y; }
+        if (u < nu3) { const unsigned z = p3[u]; p3[u] = r3; r3 += z; }
     }
-    if (tB == 0) { p1[nu] = (unsigned)all; p2[nu] = (unsigned)(all >> 32); }
+    if (tB == 0) { p1[nu1] = (unsigned)tot12; p2[nu1] = (unsigned)(tot12 >> 32); p3[nu3] = (unsigned)tot3; }
     group_sync<BAR_B, GB>();
-    return all;
 }
 
 // Start moving a line into this SM's L1 (the loads that follow hit it).
@@ -121,12 +167,20 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// Prefetch a births-group thread's share of the per-warp counts.
-__device__ __forceinline__ void prefetch_units(const unsigned* c1, const unsigned* c2, unsigned nu) {
-    const unsigned per = (nu + GB - 1) / GB, u0 = (threadIdx.x - GA) * per, u1 = (u0 + per < nu) ? u0 + per : nu;
-    for (unsigned u = u0; u < u1; u += 32) {   // 32 counts per 128-byte line
-        prefetch_l1(c1 + u);
-        if (c2) prefetch_l1(c2 + u);
+// Prefetch a births-group thread's share [u0, u1) of the per-warp counts
+// (the lines of its first and last unit: a share spans at most two lines
+// while it holds at most 32 units).
+__device__ __forceinline__ void prefetch_units(const unsigned* c1, const unsigned* c2, unsigned nu1, const unsigned* c3,
+                                               unsigned nu3) {
+    unsigned u0, u1;
+    unit_range(nu1 > nu3 ? nu1 : nu3, u0, u1);
+    if (u0 >= u1) return;
+    const unsigned ends[2] = {u0, u1 - 1};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const unsigned u = ends[k];
+        if (u < nu1) { prefetch_l1(c1 + u); prefetch_l1(c2 + u); }
+        if (u < nu3) prefetch_l1(c3 + u);
     }
 }
 
@@ -145,16 +199,19 @@ struct CtrlSnap {
     unsigned next_id[NSP], cur[NSP], removals;
 };
 
-// Inclusive scans over the charge group of two int64 arrays a, b [0..n) in
-// shared memory at once (blocked: thread t owns [t*per, (t+1)*per)).
-__device__ __forceinline__ void groupA_scan_pair(long long* a, long long* b, int n, long long* ws) {
+// Over the charge group: the inclusive scan S_j of R_j held in a[0..n)
+// (a[0] = 0; in place), and U_j = sum_{k<=j} k R_k straight to global U[j]
+// (its only readers are the potential and D0, which gets U_{n-2} in *u_last).
+// Blocked: thread t owns [t*per, (t+1)*per); the two scans share their
+// warp shuffles and barriers.
+__device__ __forceinline__ void groupA_scan_SU(long long* a, int n, long long* ws, long long* U, long long* u_last) {
     const int t = threadIdx.x;
     const int per = (n + GA - 1) / GA;
     const int j0 = t * per;
     long long ra = 0, rb = 0;
     for (int i = 0; i < per; ++i) {
         const int j = j0 + i;
-        if (j < n) { ra += a[j]; a[j] = ra; rb += b[j]; b[j] = rb; }
+        if (j < n) { const long long r = a[j]; ra += r; a[j] = ra; rb += (long long)j * r; }
     }
     const int lane = t & 31, warp = t >> 5;
     long long xa = ra, xb = rb;
@@ -179,23 +236,31 @@ __device__ __forceinline__ void groupA_scan_pair(long long* a, long long* b, int
     group_sync<BAR_A, GA>();
     const long long offa = (warp == 0 ? 0 : ws[warp - 1]) + (xa - ra);
     const long long offb = (warp == 0 ? 0 : ws[32 + warp - 1]) + (xb - rb);
+    long long prev = 0, ub = 0;
     for (int i = 0; i < per; ++i) {
         const int j = j0 + i;
-        if (j < n) { a[j] += offa; b[j] += offb; }
+        if (j < n) {
+            const long long sl = a[j];          // thread-local inclusive S
+            ub += (long long)j * (sl - prev);
+            prev = sl;
+            a[j] = sl + offa;
+            U[j] = ub + offb;
+            if (j == n - 2) *u_last = ub + offb;
+        }
     }
     group_sync<BAR_A, GA>();
 }
 
 // mode 0: end of a step (pushed_mask = species pushed this step);
 // mode 1: after a load (all species freshly deposited into Qf).
-// Dynamic shared memory: S, U as int64 [Ng] (charge group), then two u32
+// Dynamic shared memory: S as int64 [Ng] (charge group), then three u32
 // [max warps + 1] (births group).
 __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed_mask) {
     extern __shared__ long long fsm[];
     __shared__ long long wsA[64];
-    __shared__ unsigned long long wsB[GB / 32];
+    __shared__ unsigned long long wsB[2 * (GB / 32)];
     __shared__ CtrlSnap cs;
-    __shared__ long long sh_R0, sh_RN;
+    __shared__ long long sh_R0, sh_RN, sh_UN1;
     __shared__ double sh_V0, sh_D0;
     DevCtrl* C = P.ctrl;
     const int N = P.Nc, Ng = P.Ng;
@@ -203,23 +268,21 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
 
     if (t < GA) {
         // ================= charge commit, cycle moments, field solve
-        long long* Ss = fsm;          // S_j = sum_{k=1..j} R_k
-        long long* Us = fsm + Ng;     // U_j = sum_{k=1..j} k R_k   (T_j = j S_{j-1} - U_{j-1})
+        long long* Ss = fsm;          // S_j = sum_{k=1..j} R_k   (T_j = j S_{j-1} - U_{j-1})
         // Q = (this step's deposit Qf, or the kept Q of a species not pushed)
         // + the births' deposit Qb; two nodes per thread with all their
         // loads issued before any store
         for (int j0 = t; j0 < Ng; j0 += 2 * GA) {
-            unsigned long long q[2][NSP], qa[2][NSP];
+            unsigned long long q[2][NSP];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = j0 + h * GA;
 #pragma unroll
                 for (int s = 0; s < NSP; ++s) {
-                    q[h][s] = 0ull; qa[h][s] = 0ull;
+                    q[h][s] = 0ull;
                     if (j < Ng) {
                         const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
                         q[h][s] = (fresh ? P.Qf[s][j] : P.Q[s][j]) + P.Qb[s][j];
-                        if (mode == 0) qa[h][s] = P.Qacc[s][j];
                     }
                 }
             }
@@ -233,17 +296,15 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
                     P.Q[s][j] = q[h][s];
                     P.Qf[s][j] = 0ull;
                     P.Qb[s][j] = 0ull;
-                    if (mode == 0) P.Qacc[s][j] = qa[h][s] + q[h][s];
                     net += (s == SP_OP) ? (long long)q[h][s] : -(long long)q[h][s];
                 }
                 Ss[j] = (j >= 1) ? net : 0;                    // scanned below
-                Us[j] = (j >= 1) ? (long long)j * net : 0;
                 if (j == 0) sh_R0 = net;
                 if (j == N) sh_RN = net;
             }
         }
         group_sync<BAR_A, GA>();
-        groupA_scan_pair(Ss, Us, Ng, wsA);
+        groupA_scan_SU(Ss, Ng, wsA, P.fU, &sh_UN1);
         const double c = P.c_field;
         // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load),
         // evaluated on the host in FP64, staged in a ring indexed by the step
@@ -252,8 +313,11 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         if (t < 32) {
             group_sync<BAR_V0, 64>();
             if (t == 0) {
-                const long long TN = (long long)N * Ss[N - 1] - Us[N - 1];
-                const double D0 = (c * (double)TN - sh_V0) / (double)N;
+                const long long TN = (long long)N * Ss[N - 1] - sh_UN1;
+                // a power-of-two N divides exactly by its reciprocal (same
+                // IEEE result as the division, which is slow in FP64 here)
+                const double num = c * (double)TN - sh_V0;
+                const double D0 = (P.inv_Nc64 != 0.0) ? num * P.inv_Nc64 : num / (double)N;
                 sh_D0 = D0;
                 P.fVD[0] = sh_V0;
                 P.fVD[1] = D0;
@@ -265,22 +329,33 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         // are kept so that k_phi evaluates it with the same expressions.
         const double D0 = sh_D0, D2 = 2.0 * sh_D0;   // 2 D0 is exact
         const long long R0 = sh_R0, RN = sh_RN;
+        // Cycle moments (Qacc += Q) ride along: their loads are in flight
+        // during the FP64 work.
         for (int j = t; j < Ng; j += GA) {
+            unsigned long long qa[NSP], qn[NSP];
+            if (mode == 0) {
+#pragma unroll
+                for (int s = 0; s < NSP; ++s) { qa[s] = P.Qacc[s][j]; qn[s] = P.Q[s][j]; }
+            }
             double E;
             if (j == 0) E = (-D0 - c * (double)R0) * P.inv_dx64;
             else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)RN) * P.inv_dx64;
             else E = (c * (double)(Ss[j] + Ss[j - 1]) - D2) * P.inv_2dx64;
             P.Ef[j] = (float)E;
             P.fS[j] = Ss[j];
-            P.fU[j] = Us[j];
+            if (mode == 0) {
+#pragma unroll
+                for (int s = 0; s < NSP; ++s) P.Qacc[s][j] = qa[s] + qn[s];
+            }
         }
         return;
     }
 
     // ===================== births, (17) removals and the commit of the step
     const int tB = t - GA;
-    unsigned* p1 = reinterpret_cast<unsigned*>(fsm + 2 * Ng);
+    unsigned* p1 = reinterpret_cast<unsigned*>(fsm + Ng);
     unsigned* p2 = p1 + (P.max_push_warps + 1);
+    unsigned* p3 = p2 + (P.max_push_warps + 1);
     const bool births_e = mode == 0 && P.births_possible[SP_E];
     const bool births_om = mode == 0 && ((pushed_mask >> SP_OM) & 1) && P.births_possible[SP_OM];
     if (tB < NSP) {
@@ -298,48 +373,51 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         __syncwarp();
         group_arrive<BAR_V0, 64>();   // sh_V0 for the charge group's D0
     }
-    if (births_e) prefetch_units(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], P.push_warps[SP_E]);
-    if (births_om) prefetch_units(P.wcount[B_E_FROM_OM], nullptr, P.push_warps[SP_OM]);
+    prefetch_units(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], births_e ? P.push_warps[SP_E] : 0u,
+                   P.wcount[B_E_FROM_OM], births_om ? P.push_warps[SP_OM] : 0u);
     group_sync<BAR_B, GB>();
 
+    // births of the step: n1 ionizations (e + O2+) and n2 attachments (O-)
+    // staged by the electron kernel, n3 detachment electrons staged by the O-
+    // kernel (ion steps), placed after the electrons' own
     unsigned long long btot[NB];
     for (int k = 0; k < NB; ++k) btot[k] = 0;
-    if (births_e) {
-        const unsigned ns = (unsigned)(cs.slots[SP_E] < P.sp[SP_E].cap ? cs.slots[SP_E] : P.sp[SP_E].cap);
-        const unsigned nu = P.push_warps[SP_E], R = warp_range_len(ns, nu);
-        const unsigned long long all = unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu, p1, p2, wsB);
-        const unsigned n1 = (unsigned)all, n2 = (unsigned)(all >> 32);
-        for (unsigned b = tB; b < n1; b += GB) {
-            const unsigned u = find_unit(p1, nu, b);
-            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
-            const float4 be = P.stage[B_E_FROM_E][sb], bo = P.stage[B_OP_FROM_E][sb];
-            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + b, (unsigned long long)cs.next_id[SP_E] + b, be);
-            place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + b, (unsigned long long)cs.next_id[SP_OP] + b, bo);
-        }
-        for (unsigned b = tB; b < n2; b += GB) {
-            const unsigned u = find_unit(p2, nu, b);
-            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p2[u]);
-            place_birth(P, C, cs.cur, SP_OM, cs.slots[SP_OM] + b, (unsigned long long)cs.next_id[SP_OM] + b,
-                        P.stage[B_OM_FROM_E][sb]);
+    if (births_e || births_om) {
+        const unsigned ns1 = (unsigned)(cs.slots[SP_E] < P.sp[SP_E].cap ? cs.slots[SP_E] : P.sp[SP_E].cap);
+        const unsigned ns3 = (unsigned)(cs.slots[SP_OM] < P.sp[SP_OM].cap ? cs.slots[SP_OM] : P.sp[SP_OM].cap);
+        const unsigned nu1 = births_e ? P.push_warps[SP_E] : 0u, nu3 = births_om ? P.push_warps[SP_OM] : 0u;
+        const unsigned R1 = warp_range_len(ns1, nu1 ? nu1 : 1u), R3 = warp_range_len(ns3, nu3 ? nu3 : 1u);
+        unsigned long long t12, t3;
+        unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu1, P.wcount[B_E_FROM_OM], nu3, p1, p2, p3, wsB,
+                     t12, t3);
+        const unsigned n1 = (unsigned)t12, n2 = (unsigned)(t12 >> 32), n3 = (unsigned)t3;
+        const unsigned ntot = n1 + n2 + n3;
+        // one birth per thread and pass: which list, its rank there, the warp
+        // that staged it (binary search over that list's offsets) and its
+        // staging slot; all loads of the birth before its stores
+        for (unsigned b = tB; b < ntot; b += GB) {
+            const int kind = b < n1 ? 0 : (b < n1 + n2 ? 1 : 2);
+            const unsigned r = kind == 0 ? b : (kind == 1 ? b - n1 : b - n1 - n2);
+            const unsigned* p = kind == 0 ? p1 : (kind == 1 ? p2 : p3);
+            const unsigned nu = kind == 2 ? nu3 : nu1, R = kind == 2 ? R3 : R1, ns = kind == 2 ? ns3 : ns1;
+            const unsigned u = find_unit(p, nu, r);
+            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (r - p[u]);
+            if (kind == 0) {
+                const float4 be = P.stage[B_E_FROM_E][sb], bo = P.stage[B_OP_FROM_E][sb];
+                place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + r, (unsigned long long)cs.next_id[SP_E] + r, be);
+                place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + r, (unsigned long long)cs.next_id[SP_OP] + r, bo);
+            } else if (kind == 1) {
+                place_birth(P, C, cs.cur, SP_OM, cs.slots[SP_OM] + r, (unsigned long long)cs.next_id[SP_OM] + r,
+                            P.stage[B_OM_FROM_E][sb]);
+            } else {
+                place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + n1 + r, (unsigned long long)cs.next_id[SP_E] + n1 + r,
+                            P.stage[B_E_FROM_OM][sb]);
+            }
         }
         btot[B_E_FROM_E] = n1;
         btot[B_OP_FROM_E] = n1;
         btot[B_OM_FROM_E] = n2;
-        group_sync<BAR_B, GB>();   // p1, p2 are reused below
-    }
-    // O- kernel (ion steps): detachment electrons, after the electron kernel's
-    if (births_om) {
-        const unsigned ns = (unsigned)(cs.slots[SP_OM] < P.sp[SP_OM].cap ? cs.slots[SP_OM] : P.sp[SP_OM].cap);
-        const unsigned nu = P.push_warps[SP_OM], R = warp_range_len(ns, nu);
-        const unsigned n = (unsigned)unit_offsets(P.wcount[B_E_FROM_OM], nullptr, nu, p1, p2, wsB);
-        const unsigned long long base = btot[B_E_FROM_E];
-        for (unsigned b = tB; b < n; b += GB) {
-            const unsigned u = find_unit(p1, nu, b);
-            const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (b - p1[u]);
-            place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + base + b, (unsigned long long)cs.next_id[SP_E] + base + b,
-                        P.stage[B_E_FROM_OM][sb]);
-        }
-        btot[B_E_FROM_OM] = n;
+        btot[B_E_FROM_OM] = n3;
     }
 
     if (mode == 0) {
@@ -580,7 +658,7 @@ __global__ void k_ln(const float* x, float* out, unsigned long long n) {
 }  // namespace
 
 size_t field_smem_bytes(const Params& P) {
-    return 2 * sizeof(long long) * (size_t)P.Ng + 2 * sizeof(unsigned) * ((size_t)P.max_push_warps + 1);
+    return sizeof(long long) * (size_t)P.Ng + 3 * sizeof(unsigned) * ((size_t)P.max_push_warps + 1);
 }
 
 // The potential of the last field solve: phi_0 = V0, phi_N = 0,

@@ -132,6 +132,7 @@ struct Params {
     float inv_dx, Lf;
     double dx, c_field, U, two_pi_f, dt;   // c_field = e w dx / (A eps0 2^16)
     double inv_dx64, inv_2dx64;            // 1/dx and 1/(2 dx)
+    double inv_Nc64;                       // 1/Nc when Nc is a power of two (exact), else 0
     const double* vring;         // electrode voltage U sin(2 pi f t_k) at t_k = k dt, slot k & vring_mask
     unsigned int vring_mask;
     float* Ef;                   // [Ng] gather field (FP32)

@@ -228,6 +228,8 @@ void set_constants(o2pic_ctx* c) {
     P.c_field = QE * g.weight * dx / (g.area * EPS0 * 65536.0);
     P.inv_dx64 = 1.0 / dx;
     P.inv_2dx64 = 1.0 / (2.0 * dx);
+    // x / Nc and x * (1 / Nc) are the same IEEE result when 1 / Nc is exact
+    P.inv_Nc64 = (g.n_cells & (g.n_cells - 1)) == 0 ? 1.0 / (double)g.n_cells : 0.0;
     P.U = g.U;
     P.two_pi_f = TWO_PI * g.f;
     P.dt = g.dt;
