@@ -25,31 +25,22 @@ namespace o2 {
 
 namespace {
 
-constexpr int FT = 1024;                          // threads of the field block
-// The block works as two groups that meet only for U sin(2 pi f t):
-// warps 0-15 commit the charge and solve the field, warps 16-31 place the
-// births and commit the step.  Each group synchronizes on its own named
-// barrier (0 is __syncthreads).
-constexpr int GA = 512;                           // charge commit and field solve
-constexpr int GB = FT - GA;                       // births and the step commit
-constexpr int BAR_A = 1, BAR_B = 2, BAR_V0 = 3;
-
-template <int BAR, int NT>
-__device__ __forceinline__ void group_sync() {
-    asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
-}
-template <int BAR, int NT>
-__device__ __forceinline__ void group_arrive() {
-    asm volatile("bar.arrive %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
-}
+// The end-of-step kernel is two independent blocks of FT threads, each on its
+// own SM (twice the memory-level parallelism of one): block 0 commits the
+// charge and solves the field, block 1 places the births and commits the step.
+// They share nothing; block 0 keeps its own copy of the step counter
+// (field_step) for U sin(2 pi f t).
+constexpr int FT = 512;
+constexpr int GA = FT;                            // threads of the charge block
+constexpr int GB = FT;                            // threads of the births block
 
 // Births of one step, placed in the order the method defines (source species
 // e then O-, parent order, e before O2+ for an ionization): each warp of a
 // particle kernel staged the births of its slot range [u R, ...) with their
 // count (their charge already went to Qb there).  The counts are scanned into
-// per-warp offsets in shared memory, and every thread of the births group
+// per-warp offsets in shared memory, and every thread of the births block
 // then places single births (found by a binary search over the offsets), so
-// the work spreads over the group however the births cluster.
+// the work spreads over the block however the births cluster.
 __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP], int d, unsigned long long slot,
                             unsigned long long id64, float4 b) {
     const SpeciesBuf& B = P.sp[d];
@@ -63,13 +54,13 @@ __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP]
     B.id[cb][slot] = (uint32_t)id64;
 }
 
-// Exclusive scan over the births group of two 64-bit values per thread, with
+// Exclusive scan over the births block of two 64-bit values per thread, with
 // the totals.
 __device__ __forceinline__ void groupB_excl_scan_pair(unsigned long long v, unsigned long long w,
                                                       unsigned long long* ws, unsigned long long& ev,
                                                       unsigned long long& ew, unsigned long long& tv,
                                                       unsigned long long& tw) {
-    const int tB = threadIdx.x - GA, lane = tB & 31, warp = tB >> 5;
+    const int tB = threadIdx.x, lane = tB & 31, warp = tB >> 5;
     constexpr int NW = GB / 32;
     unsigned long long x = v, y = w;
 #pragma unroll
@@ -79,7 +70,7 @@ __device__ __forceinline__ void groupB_excl_scan_pair(unsigned long long v, unsi
         if (lane >= o) { x += xo; y += yo; }
     }
     if (lane == 31) { ws[warp] = x; ws[NW + warp] = y; }
-    group_sync<BAR_B, GB>();
+    __syncthreads();
     if (warp == 0) {
         unsigned long long a = (lane < NW) ? ws[lane] : 0ull, b = (lane < NW) ? ws[NW + lane] : 0ull;
 #pragma unroll
@@ -90,21 +81,21 @@ __device__ __forceinline__ void groupB_excl_scan_pair(unsigned long long v, unsi
         }
         if (lane < NW) { ws[lane] = a; ws[NW + lane] = b; }
     }
-    group_sync<BAR_B, GB>();
+    __syncthreads();
     ev = (warp == 0 ? 0ull : ws[warp - 1]) + x - v;
     ew = (warp == 0 ? 0ull : ws[NW + warp - 1]) + y - w;
     tv = ws[NW - 1];
     tw = ws[2 * NW - 1];
-    group_sync<BAR_B, GB>();
+    __syncthreads();
 }
 
 // Offsets of the per-warp birth counts: c1, c2 of the electron kernel's nu1
 // warps into p1, p2 [0..nu1], c3 of the O- kernel's nu3 warps into p3
-// [0..nu3] (nu1 or nu3 may be 0), by one scan over the births group; returns
+// [0..nu3] (nu1 or nu3 may be 0), by one scan over the births block; returns
 // the totals (c1 | c2 << 32 and c3).  A thread owns a range of a multiple of 4
 // units, read as 16-byte vectors (the count arrays are 256-byte aligned).
 __device__ __forceinline__ void unit_range(unsigned nu, unsigned& u0, unsigned& u1) {
-    const unsigned tB = threadIdx.x - GA;
+    const unsigned tB = threadIdx.x;
     const unsigned per = (((nu + GB - 1) / GB) + 3u) & ~3u;
     u0 = tB * per < nu ? tB * per : nu;
     u1 = (u0 + per < nu) ? u0 + per : nu;
@@ -122,7 +113,7 @@ __device__ __forceinline__ uint4 count4(const unsigned* c, unsigned u, unsigned 
 __device__ void unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu1, const unsigned* c3, unsigned nu3,
                              unsigned* p1, unsigned* p2, unsigned* p3, unsigned long long* ws,
                              unsigned long long& tot12, unsigned long long& tot3) {
-    const int tB = threadIdx.x - GA;
+    const int tB = threadIdx.x;
     unsigned u0, u1;
     unit_range(nu1 > nu3 ? nu1 : nu3, u0, u1);
     unsigned long long m12 = 0, m3 = 0;
@@ -159,7 +150,7 @@ __device__ void unit_offsets(const unsigned* c1, const unsigned* c2, unsigned nu
         if (u < nu3) { const unsigned z = p3[u]; p3[u] = r3; r3 += z; }
     }
     if (tB == 0) { p1[nu1] = (unsigned)tot12; p2[nu1] = (unsigned)(tot12 >> 32); p3[nu3] = (unsigned)tot3; }
-    group_sync<BAR_B, GB>();
+    __syncthreads();
 }
 
 // Start moving a line into this SM's L1 (the loads that follow hit it).
@@ -167,7 +158,7 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// Prefetch a births-group thread's share [u0, u1) of the per-warp counts
+// Prefetch a births-block thread's share [u0, u1) of the per-warp counts
 // (the lines of its first and last unit: a share spans at most two lines
 // while it holds at most 32 units).
 __device__ __forceinline__ void prefetch_units(const unsigned* c1, const unsigned* c2, unsigned nu1, const unsigned* c3,
@@ -199,7 +190,7 @@ struct CtrlSnap {
     unsigned next_id[NSP], cur[NSP], removals;
 };
 
-// Over the charge group: the inclusive scan S_j of R_j held in a[0..n)
+// Over the charge block: the inclusive scan S_j of R_j held in a[0..n)
 // (a[0] = 0; in place), and U_j = sum_{k<=j} k R_k straight to global U[j]
 // (its only readers are the potential and D0, which gets U_{n-2} in *u_last).
 // Blocked: thread t owns [t*per, (t+1)*per); the two scans share their
@@ -222,7 +213,7 @@ __device__ __forceinline__ void groupA_scan_SU(long long* a, int n, long long* w
         if (lane >= o) { xa += ya; xb += yb; }
     }
     if (lane == 31) { ws[warp] = xa; ws[32 + warp] = xb; }
-    group_sync<BAR_A, GA>();
+    __syncthreads();
     if (warp == 0) {
         long long va = (lane < GA / 32) ? ws[lane] : 0, vb = (lane < GA / 32) ? ws[32 + lane] : 0;
 #pragma unroll
@@ -233,7 +224,7 @@ __device__ __forceinline__ void groupA_scan_SU(long long* a, int n, long long* w
         }
         if (lane < GA / 32) { ws[lane] = va; ws[32 + lane] = vb; }
     }
-    group_sync<BAR_A, GA>();
+    __syncthreads();
     const long long offa = (warp == 0 ? 0 : ws[warp - 1]) + (xa - ra);
     const long long offb = (warp == 0 ? 0 : ws[32 + warp - 1]) + (xb - rb);
     long long prev = 0, ub = 0;
@@ -248,27 +239,36 @@ __device__ __forceinline__ void groupA_scan_SU(long long* a, int n, long long* w
             if (j == n - 2) *u_last = ub + offb;
         }
     }
-    group_sync<BAR_A, GA>();
+    __syncthreads();
 }
 
 // mode 0: end of a step (pushed_mask = species pushed this step);
 // mode 1: after a load (all species freshly deposited into Qf).
 // Dynamic shared memory: S as int64 [Ng] (charge group), then three u32
 // [max warps + 1] (births group).
-__device__ __forceinline__ void field_body(const Params& P, int mode, int pushed_mask) {
+__device__ __forceinline__ void field_body(const Params& P, int mode, int pushed_mask, int role) {
     extern __shared__ long long fsm[];
     __shared__ long long wsA[64];
     __shared__ unsigned long long wsB[2 * (GB / 32)];
     __shared__ CtrlSnap cs;
     __shared__ long long sh_R0, sh_RN, sh_UN1;
     __shared__ double sh_V0, sh_D0;
+    __shared__ unsigned long long sh_fstep;
     DevCtrl* C = P.ctrl;
     const int N = P.Nc, Ng = P.Ng;
     const int t = threadIdx.x;
 
-    if (t < GA) {
+    if (role == 0) {
         // ================= charge commit, cycle moments, field solve
         long long* Ss = fsm;          // S_j = sum_{k=1..j} R_k   (T_j = j S_{j-1} - U_{j-1})
+        if (t == 0) {
+            // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load),
+            // evaluated on the host in FP64 and staged in a ring indexed by
+            // the step
+            const unsigned long long fstep = C->field_step;
+            sh_fstep = fstep;
+            sh_V0 = P.vring[(mode == 0 ? fstep + 1 : fstep) & P.vring_mask];
+        }
         // Q = (this step's deposit Qf, or the kept Q of a species not pushed)
         // + the births' deposit Qb; two nodes per thread with all their
         // loads issued before any store
@@ -303,27 +303,22 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
                 if (j == N) sh_RN = net;
             }
         }
-        group_sync<BAR_A, GA>();
+        __syncthreads();
         groupA_scan_SU(Ss, Ng, wsA, P.fU, &sh_UN1);
         const double c = P.c_field;
-        // U sin(2 pi f t) at t^{n+1} (end of step) or t^n (after a load),
-        // evaluated on the host in FP64, staged in a ring indexed by the step
-        // and read by the births group (the owner of the step state).  D0 once
-        // per block: FP64 throughput on this GPU is low.
-        if (t < 32) {
-            group_sync<BAR_V0, 64>();
-            if (t == 0) {
-                const long long TN = (long long)N * Ss[N - 1] - sh_UN1;
-                // a power-of-two N divides exactly by its reciprocal (same
-                // IEEE result as the division, which is slow in FP64 here)
-                const double num = c * (double)TN - sh_V0;
-                const double D0 = (P.inv_Nc64 != 0.0) ? num * P.inv_Nc64 : num / (double)N;
-                sh_D0 = D0;
-                P.fVD[0] = sh_V0;
-                P.fVD[1] = D0;
-            }
+        // D0 once per block: FP64 throughput on this GPU is low
+        if (t == 0) {
+            const long long TN = (long long)N * Ss[N - 1] - sh_UN1;
+            // a power-of-two N divides exactly by its reciprocal (same IEEE
+            // result as the division, which is slow in FP64 here)
+            const double num = c * (double)TN - sh_V0;
+            const double D0 = (P.inv_Nc64 != 0.0) ? num * P.inv_Nc64 : num / (double)N;
+            sh_D0 = D0;
+            P.fVD[0] = sh_V0;
+            P.fVD[1] = D0;
+            if (mode == 0) C->field_step = sh_fstep + 1;   // only this block reads it
         }
-        group_sync<BAR_A, GA>();
+        __syncthreads();
         // E on the nodes (what the next push gathers).  The potential needs as
         // much FP64 work again and only diagnostics read it: S, U, V0 and D0
         // are kept so that k_phi evaluates it with the same expressions.
@@ -352,7 +347,7 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
     }
 
     // ===================== births, (17) removals and the commit of the step
-    const int tB = t - GA;
+    const int tB = t;
     unsigned* p1 = reinterpret_cast<unsigned*>(fsm + Ng);
     unsigned* p2 = p1 + (P.max_push_warps + 1);
     unsigned* p3 = p2 + (P.max_push_warps + 1);
@@ -361,21 +356,15 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
     if (tB < NSP) {
         cs.slots[tB] = C->slots[tB]; cs.live[tB] = C->live[tB]; cs.removed[tB] = C->removed[tB];
         cs.next_id[tB] = C->next_id[tB]; cs.cur[tB] = C->cur[tB];
-    } else if (tB >= 32 && tB < 64) {
-        if (tB == 32) {
-            const unsigned long long step = C->step;
-            cs.step = step;
-            cs.epoch = C->epoch;
-            cs.acc_steps = C->acc_steps;
-            cs.removals = C->removals;
-            sh_V0 = P.vring[(mode == 0 ? step + 1 : step) & P.vring_mask];
-        }
-        __syncwarp();
-        group_arrive<BAR_V0, 64>();   // sh_V0 for the charge group's D0
+    } else if (tB == 32) {
+        cs.step = C->step;
+        cs.epoch = C->epoch;
+        cs.acc_steps = C->acc_steps;
+        cs.removals = C->removals;
     }
     prefetch_units(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], births_e ? P.push_warps[SP_E] : 0u,
                    P.wcount[B_E_FROM_OM], births_om ? P.push_warps[SP_OM] : 0u);
-    group_sync<BAR_B, GB>();
+    __syncthreads();
 
     // births of the step: n1 ionizations (e + O2+) and n2 attachments (O-)
     // staged by the electron kernel, n3 detachment electrons staged by the O-
@@ -449,7 +438,7 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
             if (bs) atomicAdd(&C->cnt.born[s], bs);
         } else if (tB == 32) {
             if (nrem) atomicAdd(&C->cnt.neutralized, (unsigned long long)nrem);
-            // this group is the only writer of the step state: plain stores
+            // this block is the only writer of the step state: plain stores
             C->removals = 0u;
             C->rremovals = 0u;
             C->acc_steps = cs.acc_steps + 1;
@@ -584,17 +573,17 @@ __device__ __forceinline__ void compact_body(const Params& P, int mode, unsigned
 
 __global__ void __launch_bounds__(FT) k_field(Params P, int mode, int pushed_mask) {
     pdl_wait();
-    pdl_trigger();   // one block on one SM: the next step's push may take the others
-    field_body(P, mode, pushed_mask);
+    pdl_trigger();   // two blocks on two SMs: the next step's push may take the others
+    field_body(P, mode, pushed_mask, (int)blockIdx.x);
 }
 
-// batched: block d is the end-of-step kernel of discharge d
+// batched: blocks 2d and 2d + 1 are the end-of-step kernel of discharge d
 __global__ void __launch_bounds__(FT) k_field_b(const Params* __restrict__ all, int mode, int pushed_mask) {
     __shared__ Params sP;
     pdl_wait();
     pdl_trigger();
-    load_params(sP, all + blockIdx.x);
-    field_body(sP, mode, pushed_mask);
+    load_params(sP, all + (blockIdx.x >> 1));
+    field_body(sP, mode, pushed_mask, (int)(blockIdx.x & 1u));
 }
 
 template <int S>
@@ -678,7 +667,7 @@ void launch_phi(const Params& P, cudaStream_t s) {
 }
 
 void launch_field_batched(const Params* all, int n, size_t smem, int mode, int pushed_mask, cudaStream_t s) {
-    launch_pdl(k_field_b, n, FT, smem, s, all, mode, pushed_mask);
+    launch_pdl(k_field_b, 2 * n, FT, smem, s, all, mode, pushed_mask);
 }
 
 void launch_compact_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s) {
@@ -687,7 +676,7 @@ void launch_compact_batched(int species, const Params* all, const uint4* map, in
 }
 
 void launch_field(const Params& P, int mode, int pushed_mask, cudaStream_t s) {
-    launch_pdl(k_field, 1, FT, field_smem_bytes(P), s, P, mode, pushed_mask);
+    launch_pdl(k_field, 2, FT, field_smem_bytes(P), s, P, mode, pushed_mask);
 }
 
 cudaError_t configure_field_smem(size_t bytes) {

@@ -88,6 +88,7 @@ enum BirthSlot { B_E_FROM_E = 0, B_OP_FROM_E = 1, B_OM_FROM_E = 2, B_E_FROM_OM =
 // Device-resident step state; read by every kernel, committed by the field kernel.
 struct DevCtrl {
     unsigned long long step;               // current step n
+    unsigned long long field_step;         // the same, kept by the field-solve block
     unsigned long long epoch;              // distinct per step, never reused (look-back flags)
     unsigned long long slots[NSP];         // array slots in use (live + dead) before this step's births
     unsigned long long live[NSP];

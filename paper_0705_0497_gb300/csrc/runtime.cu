@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -659,11 +660,15 @@ int o2pic_load_particles(o2pic_ctx* c, int species, const float* x, const float*
     return O2PIC_OK;
 }
 
+static_assert(offsetof(DevCtrl, field_step) == offsetof(DevCtrl, step) + sizeof(unsigned long long),
+              "o2pic_set_step writes step and field_step together");
+
 int o2pic_set_step(o2pic_ctx* c, uint64_t step) {
     if (!c) return O2PIC_E_INVALID_ARG;
     int rc = sync_all(c);
     if (rc == O2PIC_E_CUDA) return rc;
-    cudaError_t e = cudaMemcpy(&c->d_ctrl->step, &step, sizeof(step), cudaMemcpyHostToDevice);
+    const unsigned long long both[2] = {step, step};   // step and field_step (adjacent)
+    cudaError_t e = cudaMemcpy(&c->d_ctrl->step, both, sizeof(both), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->host_step = step;
     c->dirty = true;
