@@ -446,6 +446,22 @@ def bench_batch(args, world, rank, local):
     return 0
 
 
+def profile_steps(n):
+    """The workload stepped n single steps through the public API, nothing
+    timed: a short, fixed launch sequence for ncu captures (with ion
+    subcycling 10, the electron push of step 6 is launch 8 of k_push)."""
+    from paper_0705_0497_gb300 import api, inputs, xsec
+    cfg, counts, T, _ = inputs.workload(WORKLOAD)
+    g = api.Discharge(cfg, tuple(int(c * 1.5) + 65536 for c in counts))
+    g.set_processes(xsec.oxygen_set())
+    g.load_state(inputs.initial_state(cfg, counts, T))
+    g.step(n)
+    g.synchronize()
+    print(json.dumps({"profile_steps": n, "step": g.stats()["step"], "live": [g.count(s) for s in range(3)]}))
+    g.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,7 +470,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_sweep_64"])
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only step the workload this many single steps (a fixed launch sequence for ncu) and exit")
     args = ap.parse_args()
+    if args.profile_steps > 0:
+        return profile_steps(args.profile_steps)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

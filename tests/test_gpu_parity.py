@@ -97,6 +97,34 @@ def test_parity_ragged_sizes(torch_cuda, n):
     compare_counters(g.stats(), o.counters(), nproc_of(procs))
 
 
+@pytest.mark.parametrize("Nc", [97, 8192])
+def test_parity_grid_sizes(torch_cuda, Nc):
+    """A cell count that is not a power of two (the solve divides by N, where
+    a power of two multiplies by the exact 1/N) and the largest grid (8192
+    cells, 8193 nodes): 30 coupled steps with ion subcycling; particles,
+    counters and charge against the oracle, then the field against the
+    oracle's closed-form solve of the GPU's charge, bit for bit."""
+    import oracle
+    cfg, _, T, _ = inputs.workload("parity_128", n_cells=Nc, ion_subcycle=3)
+    counts = (6000, 1500, 7500)
+    procs = xsec.oxygen_set()
+    g, o, _ = make_pair(cfg, counts, T, procs)
+    for chunk in (1, 29):
+        g.step(chunk)
+        o.step(chunk)
+        compare_particles(g, o)
+        compare_counters(g.stats(), o.counters(), nproc_of(procs))
+        Qg, _, _ = g.charge()
+        Qo, _, _ = o.charge()
+        assert np.array_equal(Qg, Qo)
+    Rnet = Qg[2].astype(np.int64) - Qg[0].astype(np.int64) - Qg[1].astype(np.int64)
+    V0 = cfg["U"] * math.sin(2.0 * math.pi * cfg["f"] * g.stats()["step"] * cfg["dt"])
+    phi64, E64 = oracle.solve_field(Nc, cfg["L"] / Nc, cfg["weight"], cfg["area"], V0, Rnet)
+    phi, E = g.field()
+    assert np.array_equal(E, E64.astype(np.float32))
+    assert np.array_equal(phi, phi64)
+
+
 def test_parity_walls_and_edges(torch_cuda):
     """Particles exactly at x = 0, just below L and at cell boundaries."""
     cfg, counts, T, _ = inputs.workload("parity_128")
