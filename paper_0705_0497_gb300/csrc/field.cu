@@ -1,13 +1,14 @@
-// End-of-step kernel (one block): charge commit, cycle moments, Poisson solve
-// and E on the nodes, removals of (17), and the commit of the step's births;
-// plus the stable compaction of dead slots and small utility kernels.
+// End-of-step kernel (two blocks): charge commit, cycle moments, Poisson solve
+// and E on the nodes; placement of the step's births, removals of (17) and the
+// commit of the step; plus the stable compaction of dead slots and small
+// utility kernels.
 //
 // Poisson (Sec. 2): interior nodes satisfy
 //     -phi_{j-1} + 2 phi_j - phi_{j+1} = rho_j dx^2 / eps0,
 // phi_0 = U sin(2 pi f t) (driven electrode at x = 0), phi_N = 0 (grounded).
 // With the net fixed-point charge R_j (2^16 per macro-particle, exact int64)
 // and c = e w dx / (A eps0 2^16), the system is solved in closed form by
-// exact integer prefix sums (one block scan of the pair S, U):
+// exact integer prefix sums (one block-wide scan of the pair S, U):
 //     S_m = sum_{k=1..m} R_k,  U_m = sum_{k=1..m} k R_k,
 //     T_j = sum_{m<j} S_m = j S_{j-1} - U_{j-1},
 //     D_0 = phi_1 - phi_0 = (c T_N - V0) / N,  phi_j = V0 + j D_0 - c T_j,
