@@ -283,7 +283,14 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
                     q[h][s] = 0ull;
                     if (j < Ng) {
                         const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
-                        q[h][s] = (fresh ? P.Qf[s][j] : P.Q[s][j]) + P.Qb[s][j];
+                        unsigned long long v = P.Qb[s][j];
+                        if (fresh) {
+#pragma unroll
+                            for (int k = 0; k < QCOPIES; ++k) v += P.Qf[s][(size_t)k * Ng + j];
+                        } else {
+                            v += P.Q[s][j];
+                        }
+                        q[h][s] = v;
                     }
                 }
             }
@@ -296,6 +303,10 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
                 for (int s = 0; s < NSP; ++s) {
                     P.Q[s][j] = q[h][s];
                     P.Qf[s][j] = 0ull;
+                    if ((mode == 1) || ((pushed_mask >> s) & 1)) {   // only pushes fill copies 1..
+#pragma unroll
+                        for (int k = 1; k < QCOPIES; ++k) P.Qf[s][(size_t)k * Ng + j] = 0ull;
+                    }
                     P.Qb[s][j] = 0ull;
                     net += (s == SP_OP) ? (long long)q[h][s] : -(long long)q[h][s];
                 }

@@ -56,6 +56,12 @@ constexpr uint32_t FIX_ONE = 65536u;    // CIC fixed point per particle
 constexpr int QCAP = BLOCK - 1 + CHUNK; // candidate queue capacity
 constexpr int MAX_NODES = 8193;         // grid limit (smem field and histograms)
 constexpr int JRING = 8192;             // steps of conduction-current sums kept on the device
+// Copies of a species' fresh deposit Qf (Ng each): the particle kernel's
+// blocks flush their cell histograms into copy (block mod QCOPIES), so the
+// 64-bit reductions of one step spread over QCOPIES times more L2 lines; the
+// end-of-step kernel sums the copies (integers: the sum is exact).  Other
+// deposits into Qf use copy 0.
+constexpr int QCOPIES = 4;
 
 enum Kind { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6 };
 enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6 };
@@ -143,7 +149,7 @@ struct Params {
     double* fVD;                 // [2] V0, D0 of the last field solve
     unsigned long long* jring;   // [JRING][NSP] conduction-current sums (int64 mod 2^64), slot = step % JRING
     unsigned long long* Q[NSP];  // committed node charge
-    unsigned long long* Qf[NSP]; // fresh deposit of the species pushed this step
+    unsigned long long* Qf[NSP]; // fresh deposit of the species pushed this step, QCOPIES x Ng
     unsigned long long* Qb[NSP]; // deposit of this step's births
     unsigned long long* Qacc[NSP];
     // per-species constants (FP32, computed once on the host)

@@ -331,12 +331,13 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     if (nabs0 + nabs1 + nnf) atomicAdd(&sh.removed, nabs0 + nabs1 + nnf);
     if (nnf) atomicAdd(&sh.nonfinite, nnf);
     __syncthreads();
+    unsigned long long* __restrict__ Qcopy = P.Qf[S] + (size_t)(blk & (QCOPIES - 1)) * Ng;
     for (int c = tid; c < Nc; c += BLOCK) {
         const unsigned long long v = hist[c];
         if (v) {
             const unsigned long long count = v >> 40, rsum = v & ((1ull << 40) - 1);
-            atomicAdd(&P.Qf[S][c], (count << 16) - rsum);
-            if (rsum) atomicAdd(&P.Qf[S][c + 1], rsum);
+            atomicAdd(&Qcopy[c], (count << 16) - rsum);
+            if (rsum) atomicAdd(&Qcopy[c + 1], rsum);
         }
     }
     if (tid == 0) {

@@ -262,7 +262,7 @@ int prepare(o2pic_ctx* c, cudaStream_t s) {
     if (int rc = fill_vring(c, c->host_step, c->host_step, s)) return rc;
     Params& P = c->P;
     for (int sp = 0; sp < NSP; ++sp) {
-        cudaMemsetAsync(P.Qf[sp], 0, sizeof(unsigned long long) * P.Ng, s);
+        cudaMemsetAsync(P.Qf[sp], 0, sizeof(unsigned long long) * QCOPIES * P.Ng, s);
         cudaMemsetAsync(P.Qb[sp], 0, sizeof(unsigned long long) * P.Ng, s);
     }
     for (int sp = 0; sp < NSP; ++sp)
@@ -387,7 +387,7 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
         TRY(ctx_alloc(c, &cum, (size_t)NGRID * MAXPROC));
         P.cum[s] = cum;
         TRY(ctx_alloc(c, &P.Q[s], Ng));
-        TRY(ctx_alloc(c, &P.Qf[s], Ng));
+        TRY(ctx_alloc(c, &P.Qf[s], (size_t)QCOPIES * Ng));
         TRY(ctx_alloc(c, &P.Qb[s], Ng));
         TRY(ctx_alloc(c, &P.Qacc[s], Ng));
     }
