@@ -643,10 +643,10 @@ int o2pic_load_particles(o2pic_ctx* c, int species, const float* x, const float*
         e = cudaMemcpy(&flags, &c->d_ctrl->error_flags, sizeof(flags), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(c, e);
         if (flags & ERR_NONFINITE) {
-            const unsigned long long zero = 0;
-            cudaMemcpy(&c->d_ctrl->error_flags, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+            // leave the species empty (h.error_flags is 0)
             h.slots[species] = 0; h.live[species] = 0;
-            cudaMemcpy(c->d_ctrl, &h, sizeof(h), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(c->d_ctrl, &h, sizeof(h), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(c, e);
             return O2PIC_E_INVALID_ARG;
         }
     } else {
