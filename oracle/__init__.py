@@ -78,6 +78,8 @@ def lib():
         L.oracle_solve_field.argtypes = [i32, dbl, dbl, dbl, dbl, vp, vp, vp]
         L.oracle_solve_field_thomas.argtypes = [i32, dbl, dbl, dbl, dbl, vp, vp, vp]
         L.oracle_deposit.argtypes = [i32, dbl, vp, u64, vp]
+        L.oracle_lookup.restype = dbl
+        L.oracle_lookup.argtypes = [vp, i32, i32, dbl]
         L.oracle_grid_energy.restype = dbl
         L.oracle_grid_energy.argtypes = [i32]
         L.oracle_ngrid.restype = i32
@@ -202,6 +204,11 @@ class Oracle:
         pmax = ctypes.c_double()
         np_ = lib().oracle_table(self.h, species, _ptr(cum), _ptr(nu), ctypes.byref(numax), ctypes.byref(pmax))
         return (cum[:G * np_].reshape(G, np_), nu[:G * np_].reshape(G, np_), numax.value, pmax.value)
+
+    def lookup(self, which, k, E):
+        """The tabulated rate at energy E as the collision step reads it:
+        which = species (cumulative column k), 3 = (17) table, 4 = (16)."""
+        return lib().oracle_lookup(self.h, which, k, float(E))
 
     def neutral_table(self):
         K = np.zeros(ngrid())

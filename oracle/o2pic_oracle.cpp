@@ -42,6 +42,7 @@
 #include <vector>
 #include <algorithm>
 #include <limits>
+#include <type_traits>
 
 namespace {
 
@@ -1031,6 +1032,28 @@ void oracle_deposit(int n_cells, double L, const float* x, uint64_t n, uint64_t*
     std::vector<uint64_t> q(n_cells + 1, 0);
     for (uint64_t i = 0; i < n; ++i) O.deposit_one(q, x[i]);
     for (int j = 0; j <= n_cells; ++j) Q[j] = q[j];
+}
+
+// The tabulated rate at an arbitrary energy E [eV], exactly as the collision
+// step looks it up (grid_locate + grid_interp in precision R): which = 0..2
+// -> cumulative rate column k of species `which`; 3 -> the (17) table sigma_n g;
+// 4 -> the (16) table sigma_r g.  Test use (pins the lookup off the grid).
+double oracle_lookup(void* p, int which, int k, double E) {
+    Handle* h = (Handle*)p; double v = 0.0;
+    DISPATCH(h, {
+        using RR = typename std::remove_reference<decltype(O.Eg[0])>::type;
+        int i; RR w; bool above;
+        grid_locate<RR>((RR)E, i, w, above);
+        if (which >= 0 && which < NSP) {
+            const int np = (int)O.procs[which].size();
+            if (k >= 0 && k < np) v = (double)O.cum_at(which, k, i, w);
+        } else if (which == 3) {
+            v = (double)grid_interp<RR>(O.Ktab, 1, 0, i, w);
+        } else if (which == 4) {
+            v = (double)grid_interp<RR>(O.Ktab_r, 1, 0, i, w);
+        }
+    });
+    return v;
 }
 
 double oracle_grid_energy(int i) { return grid_energy(i); }

@@ -768,3 +768,127 @@ def test_recombination_expected_count_and_order(oracle_mod):
     c = o.counters()
     assert c["recombined"] == int(npl.sum()) and c["neutralized"] == 0
     assert o.count(2) == 0 and o.count(1) == int(nm.sum()) and o.count(0) == int((ne - npl).sum())
+
+
+# ------------------------------------------- table lookup and process choice
+def _lookup_energies(thresholds, seed=11):
+    """Off-grid energies for the lookup pin: log-uniform draws over the whole
+    grid, the octave edges and their neighbours, the grid ends, just below
+    2^12 eV, and the thresholds with their neighbours."""
+    rng = np.random.default_rng(seed)
+    e = list(np.exp(rng.uniform(math.log(2.0 ** -10), math.log(2.0 ** 12), 1500)))
+    for k in range(-10, 13):
+        x = 2.0 ** k
+        e += [x, np.nextafter(x, 0.0), np.nextafter(x, np.inf), x * (1 + 1.0 / 64)]
+    e += [2.0 ** -11, 0.5 * 2.0 ** -10, np.nextafter(4096.0, 0.0), 4096.0 * (1 - 2 ** -20), 5000.0]
+    for t in thresholds:
+        if t > 0:
+            e += [t, np.nextafter(t, 0.0), np.nextafter(t, np.inf)]
+    # midpoints of grid intervals and points just off the grid points
+    G = xsec.GRID
+    e += list(0.5 * (G[:-1] + G[1:])[::7]) + list((G * (1 + 1e-9))[::11])
+    return np.array(e, dtype=np.float64)
+
+
+def test_rate_lookup_off_grid_is_linear_interpolation(oracle_mod):
+    """At any energy the collision step reads a rate that is the linear
+    interpolation between the two bracketing table points (numpy.interp on
+    the 32-per-octave grid), the first point below the grid and the last
+    point above it: FP64 oracle to 1e-12, FP32 oracle to float rounding.
+    An off-by-one grid index or a wrong interpolation weight moves the value
+    by the rate's change over one grid interval (percents), far outside."""
+    cfg = _cfg(p=20.0, C_meta=0.05)
+    procs = xsec.oxygen_set(include_rec=True)
+    thr = sorted({p["threshold_eV"] for p in procs})
+    for precision, rtol in ((64, 1e-12), (32, 4e-7)):
+        o = oracle_mod.Oracle(cfg, precision)
+        o.set_processes(procs)
+        E = _lookup_energies(thr)
+        if precision == 32:
+            E = E.astype(np.float32).astype(np.float64)
+        G = xsec.GRID
+        cols = []
+        for s in range(3):
+            cum, _, _, _ = o.table(s)
+            cols += [(s, k, cum[:, k]) for k in range(cum.shape[1])]
+        cols += [(3, 0, o.neutral_table())]
+        n_checked = 0
+        for which, k, col in cols:
+            ref = np.interp(E, G, col)
+            got = np.array([o.lookup(which, k, e) for e in E])
+            scale = np.abs(col).max()
+            err = np.abs(got - ref)
+            bad = err > rtol * np.abs(ref) + 1e-14 * scale
+            assert not bad.any(), (precision, which, k, E[bad][:5], got[bad][:5], ref[bad][:5])
+            n_checked += len(E)
+        assert n_checked > 1000 * len(cols) // 2
+
+
+def _beam_processes():
+    """Four energy-dependent electron processes with different shapes and
+    thresholds plus one (ionization) above every beam but one; sigma falls
+    off at high energy so that nu_max lies near the beam energies."""
+    Ea = np.geomspace(1e-3, 4096.0, 300)
+
+    def shaped(thr, amp, peak):
+        E = np.geomspace(thr, 4096.0, 300) if thr > 0 else Ea
+        y = np.clip(E - thr, 0.0, None) / peak
+        return E, amp * y / (1.0 + y * y) if thr > 0 else amp / (1.0 + (E / peak) ** 2)
+
+    out = []
+    E, s = shaped(0.0, 6e-20, 8.0)
+    out.append(dict(species=0, kind=xsec.ELASTIC, target=xsec.T_O2, threshold_eV=0.0, E=E, sigma=s))
+    E, s = shaped(1.1, 3e-20, 3.0)
+    out.append(dict(species=0, kind=xsec.EXCITE, target=xsec.T_O2, threshold_eV=1.1, E=E, sigma=s))
+    E, s = shaped(5.3, 5e-20, 6.0)
+    out.append(dict(species=0, kind=xsec.EXCITE, target=xsec.T_O2, threshold_eV=5.3, E=E, sigma=s))
+    E = np.geomspace(3.0, 4096.0, 300)
+    out.append(dict(species=0, kind=xsec.ATTACH, target=xsec.T_O2, threshold_eV=3.0, E=E,
+                    sigma=2e-20 * np.exp(-((E - 6.0) / 2.5) ** 2)))
+    E, s = shaped(12.06, 4e-20, 30.0)
+    out.append(dict(species=0, kind=xsec.IONIZE, target=xsec.T_O2, threshold_eV=12.06, E=E, sigma=s))
+    return out
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_process_choice_mono_energetic_beams(oracle_mod, precision):
+    """Null-collision process choice: N electrons of one (off-grid) energy E0
+    in zero field, one step.  Each process k must fire
+    Binomial(N, P_max nu_k(E0) / nu_max) times, nu_k = n sigma_k(E0) g(E0)
+    computed here from the given sigma tables (numpy.interp, zero below the
+    threshold); processes above E0 never fire.  A shifted cumulative column
+    or a wrong choice rule moves events between processes whose rates differ
+    by far more than the 5 sigma bounds."""
+    procs = _beam_processes()
+    probe = oracle_mod.Oracle(_cfg(p=20.0), 64)
+    probe.set_processes(procs)
+    numax = probe.table(0)[2]
+    cfg = _cfg(p=20.0, dt=0.7 / numax)
+    nO2 = cfg["p"] / (KB * cfg["T_gas"])
+    kap = 0.5 * ME / QE
+    N = 200_000
+    for E0 in (2.0, 6.3, 7.999, 13.37, 16.0):
+        o = oracle_mod.Oracle(cfg, precision)
+        o.set_processes(procs)
+        cum, nu, numax, pmax = o.table(0)
+        v = np.float32(math.sqrt(E0 / kap))
+        p = dict(x=np.full(N, 0.5 * cfg["L"], np.float32), vx=np.zeros(N, np.float32),
+                 vy=np.full(N, v, np.float32), vz=np.zeros(N, np.float32), id=np.arange(N, dtype=np.uint32))
+        _empty(o)
+        _load(o, 0, p)
+        o.step(1)
+        c = o.counters()
+        g = math.sqrt(2 * QE * E0 / ME)
+        for k, pr in enumerate(procs):
+            sig = float(np.interp(E0, pr["E"], pr["sigma"])) if E0 >= pr["threshold_eV"] else 0.0
+            q = pmax * nO2 * sig * g / numax
+            got = c[f"events_0_{k}"]
+            if q == 0.0:
+                assert got == 0, (E0, k, got)
+                continue
+            mean = N * q
+            assert abs(got - mean) < 5 * math.sqrt(mean * (1 - q)) + 1, (E0, k, got, mean)
+        # the candidates that are not real collisions are null collisions
+        tot = sum(c[f"events_0_{k}"] for k in range(len(procs)))
+        q_tot = pmax * float(np.interp(E0, xsec.GRID, cum[:, -1])) / numax
+        assert abs(tot - N * q_tot) < 5 * math.sqrt(N * q_tot) + 1
