@@ -155,7 +155,11 @@ int o2pic_load_particles(o2pic_ctx* ctx, int species, const float* x, const floa
 /* Sets the id the next particle born in `species` gets (it must exceed every
  * id of that species): with o2pic_set_step and the particles of a saved state
  * (o2pic_read_particles, o2pic_get_stats().next_id and .step) a run resumes
- * bit for bit.  Errors: INVALID_ARG, CUDA. */
+ * bit for bit.  Ids are 32-bit: a birth whose id would reach 2^32 sets
+ * O2PIC_E_ID_OVERFLOW (counted per birth in o2pic_stats.id_overflow; the
+ * particle keeps the low 32 bits of its id).
+ * Errors: INVALID_ARG (also next_id below the current next id, e.g. below
+ * the largest loaded id + 1), CUDA. */
 int o2pic_set_next_id(o2pic_ctx* ctx, int species, uint32_t next_id);
 
 /* Enqueues nsteps time steps (Sec. 2 loop; see the file header) on `stream`.
@@ -239,6 +243,16 @@ int o2pic_compact_particles(const float* x, const float* vx, const float* vy, co
                             const uint32_t* id, uint64_t n, float* ox, float* ovx, float* ovy, float* ovz,
                             uint32_t* oid, uint64_t* n_out, void* stream);
 
+/* Failure detection of the bounded device waits: runs the decoupled
+ * look-back wait that the compaction kernels use (one thread waiting, as tile
+ * 1, for a tile 0 whose flag nothing ever sets) on `stream`.  The wait must
+ * give up after its spin limit, record the timeout and return, so that the
+ * context stays usable; *seconds (may be NULL) gets the kernel's duration.
+ * Returns O2PIC_E_TIMEOUT when the wait gave up as designed, O2PIC_OK if it
+ * did not (never expected), CUDA on a CUDA error.  No counterpart in the
+ * paper: this is a property of the library. */
+int o2pic_check_bounded_wait(double* seconds, void* stream);
+
 /* The same compaction for callers that cannot allocate device memory when
  * they need it: a framework whose caching allocator already holds the free
  * memory of the device, or a pipeline that cannot accept the synchronization
@@ -247,9 +261,10 @@ int o2pic_compact_particles(const float* x, const float* vx, const float* vy, co
  * o2pic_compact_particles, except that it calls no allocator: its scratch is
  * a static device array sized for at most O2PIC_NOALLOC_MAX_PARTICLES
  * particles (about 96 KB, held on every GPU that loads the library until the
- * process exits); n beyond that returns INVALID_ARG.  The first call on a
- * device looks up the array's device address (the current device must be
- * that device); make that first call before any stream capture.  All calls
+ * process exits); n beyond that returns INVALID_ARG.  Every call looks up the
+ * array's device address on the current device (which must be the device of
+ * the pointers).  The call copies its error word back and synchronizes
+ * `stream`, so it cannot be made while `stream` is being captured.  All calls
  * on a device share the array, so calls whose GPU work overlaps (e.g. on two
  * streams at once) race: serialize them.  The call resets what must start at
  * zero itself and returns once the work on `stream` is done. */
@@ -273,8 +288,9 @@ int o2pic_compact_particles_noalloc(const float* x, const float* vx, const float
  * o2pic_step, whatever the batch, the mode and the launch shape. */
 
 /* Blocks of the particle kernels (push and collisions) per species, in
- * [1, 8 * SMs]; results do not depend on them.  Defaults (set by
- * o2pic_set_processes): as many as fit the GPU at once. */
+ * [max(1, capacity / 2^23), 8 * SMs] (a block's shared-memory deposit counts
+ * fewer than 2^24 particles per cell); results do not depend on them.
+ * Defaults (set by o2pic_set_processes): as many as fit the GPU at once. */
 int o2pic_set_launch_shape(o2pic_ctx* ctx, const int32_t push_blocks[3]);
 int o2pic_get_launch_shape(o2pic_ctx* ctx, int32_t push_blocks[3]);
 

@@ -60,7 +60,7 @@ def lib():
         L.oracle_count.restype = u64
         L.oracle_count.argtypes = [vp, i32]
         L.oracle_read.argtypes = [vp, i32, vp, vp, vp, vp, vp]
-        L.oracle_next_id.restype = u32
+        L.oracle_next_id.restype = u64
         L.oracle_next_id.argtypes = [vp, i32]
         L.oracle_read_field.argtypes = [vp, vp, vp, vp]
         L.oracle_read_charge.restype = u64

@@ -320,7 +320,7 @@ template <class R> struct Oracle {
     R kappa_r;
     // state
     Particles<R> sp[NSP];
-    uint32_t next_id[NSP];
+    uint64_t next_id[NSP];           // id of the next birth (64-bit: ids past 2^32 - 1 are detected)
     uint64_t step;
     std::vector<uint64_t> Q[NSP];
     std::vector<double> phi, Efield;
@@ -733,11 +733,15 @@ template <class R> struct Oracle {
         P = out;
     }
 
+    // Births take ids next_id, next_id + 1, ... in canonical order.  Ids are
+    // 32-bit: a birth whose id would be 2^32 or more is an id overflow (counted
+    // per birth; the particle keeps the low 32 bits of its id).
     void append_births(std::vector<Birth4>* births) {
         for (int s = 0; s < NSP; ++s) {
             for (const Birth4& b : births[s]) {
-                if (next_id[s] == 0xFFFFFFFFu) cnt.id_overflow += 1;
-                sp[s].push((R)b.x, (R)b.vx, (R)b.vy, (R)b.vz, next_id[s]++);
+                const uint64_t id64 = next_id[s]++;
+                if (id64 > 0xFFFFFFFFull) cnt.id_overflow += 1;
+                sp[s].push((R)b.x, (R)b.vx, (R)b.vy, (R)b.vz, (uint32_t)id64);
                 cnt.born[s] += 1;
             }
         }
@@ -839,10 +843,10 @@ int oracle_load(void* p, int s, const float* x, const float* vx, const float* vy
     if (s < 0 || s >= NSP) return -1;
     DISPATCH(h, {
         O.sp[s].clear();
-        uint32_t mx = 0;
+        uint64_t mx = 0;
         for (uint64_t i = 0; i < n; ++i) {
             O.sp[s].push(x[i], vx[i], vy[i], vz[i], id[i]);
-            mx = std::max(mx, id[i] + 1u);
+            mx = std::max<uint64_t>(mx, (uint64_t)id[i] + 1u);
         }
         O.next_id[s] = mx;
         O.field_valid = false;
@@ -907,8 +911,8 @@ int oracle_read(void* p, int s, double* x, double* vx, double* vy, double* vz, u
     return 0;
 }
 
-uint32_t oracle_next_id(void* p, int s) {
-    Handle* h = (Handle*)p; uint32_t v = 0;
+uint64_t oracle_next_id(void* p, int s) {
+    Handle* h = (Handle*)p; uint64_t v = 0;
     DISPATCH(h, v = O.next_id[s]);
     return v;
 }

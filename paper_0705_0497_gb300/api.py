@@ -108,6 +108,7 @@ SIGNATURES = [
     ("o2pic_ln_f32", _i32, [_vp, _vp, _u64, _vp]),
     ("o2pic_compact_particles", _i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("o2pic_compact_particles_noalloc", _i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("o2pic_check_bounded_wait", _i32, [_P(ctypes.c_double), _vp]),
     ("o2pic_set_launch_shape", _i32, [_vp, _P(ctypes.c_int32)]),
     ("o2pic_get_launch_shape", _i32, [_vp, _P(ctypes.c_int32)]),
     ("o2pic_batch_create", _i32, [_P(_vp), ctypes.c_int32, _u64, _P(_vp)]),

@@ -78,6 +78,15 @@ __global__ void __launch_bounds__(BLOCK) k_compact_arrays(const float* __restric
     }
 }
 
+// One thread waits, as tile 1 of a look-back, for tile 0, whose flag nothing
+// ever sets (epoch 1 against the zeroed flag): the bounded wait must give up,
+// set the timeout bit and return.  words = [err, flag[2], val[4]].
+__global__ void k_lookback_probe(unsigned long long* words) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    bool ok;
+    (void)lookback(words + 1, words + 3, 1u, pack2(1u, 0u), 1ull, words, &ok);
+}
+
 }  // namespace
 
 size_t compact_scratch_words(unsigned long long n) {
@@ -97,6 +106,33 @@ void launch_compact_arrays(const float* x, const float* vx, const float* vy, con
 }  // namespace o2
 
 using namespace o2;
+
+extern "C" int o2pic_check_bounded_wait(double* seconds, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* w = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc((void**)&w, 7 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, 7 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) {
+        k_lookback_probe<<<1, 32, 0, s>>>(w);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    unsigned long long err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, w, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (seconds) *seconds = 1e-3 * ms;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (w) cudaFree(w);
+    if (e != cudaSuccess) return O2PIC_E_CUDA;
+    return (err & ERR_TIMEOUT) ? O2PIC_E_TIMEOUT : O2PIC_OK;
+}
 
 extern "C" int o2pic_compact_particles(const float* x, const float* vx, const float* vy, const float* vz,
                                        const uint32_t* id, uint64_t n, float* ox, float* ovx, float* ovy, float* ovz,

@@ -46,7 +46,12 @@ __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP]
                             unsigned long long id64, float4 b) {
     const SpeciesBuf& B = P.sp[d];
     if (slot >= B.cap) { atomicOr(&C->error_flags, ERR_CAPACITY); return; }
-    if (id64 > 0xFFFFFFFFull) atomicOr(&C->error_flags, ERR_ID);
+    // ids are 32-bit: a birth whose id would be 2^32 or more overflows
+    // (counted per birth; the particle keeps the low 32 bits)
+    if (id64 > 0xFFFFFFFFull) {
+        atomicOr(&C->error_flags, ERR_ID);
+        atomicAdd(&C->cnt.id_overflow, 1ull);
+    }
     const unsigned cb = cur[d];
     B.x[cb][slot] = b.x;
     B.vx[cb][slot] = b.y;
@@ -188,7 +193,8 @@ __device__ __forceinline__ unsigned find_unit(const unsigned* p, unsigned nu, un
 
 struct CtrlSnap {
     unsigned long long step, epoch, acc_steps, slots[NSP], live[NSP], removed[NSP];
-    unsigned next_id[NSP], cur[NSP], removals;
+    unsigned long long next_id[NSP];
+    unsigned cur[NSP], removals;
 };
 
 // Over the charge block: the inclusive scan S_j of R_j held in a[0..n)
@@ -441,11 +447,9 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
                 nl -= (ns - P.sp[s].cap) < nl ? (ns - P.sp[s].cap) : nl;
                 ns = P.sp[s].cap;
             }
-            const unsigned long long nid = (unsigned long long)cs.next_id[s] + bs;
-            if (nid > 0xFFFFFFFFull) { atomicOr(&C->error_flags, ERR_ID); atomicAdd(&C->cnt.id_overflow, 1ull); }
             C->slots[s] = ns;
             C->live[s] = nl;
-            C->next_id[s] = (unsigned)nid;
+            C->next_id[s] = cs.next_id[s] + bs;
             C->removed[s] = 0ull;
             if (bs) atomicAdd(&C->cnt.born[s], bs);
         } else if (tB == 32) {
@@ -628,13 +632,13 @@ __global__ void k_load_check(Params P, unsigned long long n) {
     const float* VY = P.sp[S].vy[cb];
     const float* VZ = P.sp[S].vz[cb];
     const uint32_t* ID = P.sp[S].id[cb];
-    unsigned mx = 0;
+    unsigned long long mx = 0;
     bool bad = false;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const float x = X[i];
         if (!(x >= 0.0f && x < P.Lf) || !isfinite(VX[i]) || !isfinite(VY[i]) || !isfinite(VZ[i])) bad = true;
-        const unsigned v = ID[i] + 1u;
+        const unsigned long long v = (unsigned long long)ID[i] + 1ull;
         mx = v > mx ? v : mx;
     }
     if (bad) atomicOr(&C->error_flags, ERR_NONFINITE);

@@ -102,7 +102,7 @@ struct DevCtrl {
     unsigned long long births[NB];         // this step's births per BirthSlot
     unsigned long long acc_steps;          // steps summed into Qacc
     unsigned long long error_flags;
-    unsigned int next_id[NSP];
+    unsigned long long next_id[NSP];       // id of the next birth (ids above 2^32 - 1 overflow)
     unsigned int cur[NSP];                 // current buffer (ping-pong) per species
     unsigned int ticket[NKK + NSP];        // tile tickets per kernel kind, + compaction per species
     unsigned int removals;                 // (17) pairs to remove

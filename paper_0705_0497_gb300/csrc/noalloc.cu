@@ -36,7 +36,6 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_WO
 constexpr int MAX_DEVICES = 64;
 
 struct DeviceSlot {
-    unsigned long long* ptr = nullptr;   // device address of g_noalloc_scratch on this device
     unsigned long long epoch = 0;        // last look-back epoch used on this device
     int sms = 0;
 };
@@ -54,24 +53,22 @@ extern "C" int o2pic_compact_particles_noalloc(const float* x, const float* vx, 
     if (n > NOALLOC_MAX_N) return O2PIC_E_INVALID_ARG;   // beyond the static scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return O2PIC_E_CUDA;
-    unsigned long long* scratch;
+    // The host-side name of the array is only a stand-in: its device address
+    // on the current device is looked up on every call (cheap), so it stays
+    // right even after cudaDeviceReset has reloaded the module.
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return O2PIC_E_CUDA;
+    unsigned long long* scratch = (unsigned long long*)p;
     unsigned long long epoch;
     int sms;
     {
         std::lock_guard<std::mutex> lock(g_mutex);
         DeviceSlot& d = g_slots[dev];
-        if (!d.ptr) {
-            // first call on this device (the device is current): the host-side
-            // name of the array is only a stand-in, so fetch its device address
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return O2PIC_E_CUDA;
-            if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-                return O2PIC_E_CUDA;
-            d.ptr = (unsigned long long*)p;
-        }
+        if (d.sms == 0 && cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return O2PIC_E_CUDA;
         // a fresh epoch per call: flags left by earlier calls never match it
+        // (after a reset the array is zero again, which no epoch >= 1 matches)
         epoch = ++d.epoch;
-        scratch = d.ptr;
         sms = d.sms;
     }
     cudaStream_t s = (cudaStream_t)stream;

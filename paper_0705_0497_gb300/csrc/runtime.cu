@@ -28,6 +28,14 @@ thread_local bool pdl_enabled = true;
 // birth counts the field kernel scans in shared memory)
 constexpr int MAX_PUSH_BLOCKS_PER_SM = 8;
 
+// The particle kernel keeps its shared-memory deposit as (count << 40) + sum
+// of CIC weights per cell, so one block may deposit fewer than 2^24 particles
+// into one cell.  A block handles at most slots / blocks + 8 * 128 slots, so
+// at least capacity / 2^23 blocks per species keep it below 2^24 with margin.
+int min_push_blocks(unsigned long long cap) {
+    return (int)std::max<unsigned long long>(1, o2::ceil_div(cap, 1ull << 23));
+}
+
 using namespace o2;
 
 namespace {
@@ -593,7 +601,7 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
         int bps = 0;
         if (push_occupancy(s, P, &bps) || bps < 1) bps = 1;
         if (bps > MAX_PUSH_BLOCKS_PER_SM) bps = MAX_PUSH_BLOCKS_PER_SM;
-        c->grid_push[s] = bps * c->num_sms;
+        c->grid_push[s] = std::max(bps * c->num_sms, min_push_blocks(P.sp[s].cap));
         P.push_warps[s] = (unsigned)c->grid_push[s] * (BLOCK / 32);
     }
     c->have_tables = true;
@@ -699,7 +707,15 @@ int o2pic_set_next_id(o2pic_ctx* c, int species, uint32_t next_id) {
     if (!c || species < 0 || species >= NSP) return O2PIC_E_INVALID_ARG;
     int rc = sync_all(c);
     if (rc == O2PIC_E_CUDA) return rc;
-    cudaError_t e = cudaMemcpy(&c->d_ctrl->next_id[species], &next_id, sizeof(next_id), cudaMemcpyHostToDevice);
+    // the next id must not fall below the current one (after a load: the
+    // largest loaded id + 1), or newborns would repeat live ids and share
+    // their random streams
+    unsigned long long cur = 0;
+    cudaError_t e = cudaMemcpy(&cur, &c->d_ctrl->next_id[species], sizeof(cur), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if ((unsigned long long)next_id < cur) return O2PIC_E_INVALID_ARG;
+    const unsigned long long v = next_id;
+    e = cudaMemcpy(&c->d_ctrl->next_id[species], &v, sizeof(v), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->gen += 1;
     return O2PIC_OK;
@@ -1123,7 +1139,7 @@ int default_push_blocks(o2pic_ctx* c, int s) {
     int bps = 0;
     if (push_occupancy(s, c->P, &bps) || bps < 1) bps = 1;
     if (bps > MAX_PUSH_BLOCKS_PER_SM) bps = MAX_PUSH_BLOCKS_PER_SM;
-    return bps * c->num_sms;
+    return std::max(bps * c->num_sms, min_push_blocks(c->P.sp[s].cap));
 }
 
 }  // namespace
@@ -1134,7 +1150,8 @@ int o2pic_set_launch_shape(o2pic_ctx* c, const int32_t push_blocks[3]) {
     if (!c || !push_blocks) return O2PIC_E_INVALID_ARG;
     if (!c->have_tables) return O2PIC_E_STATE;
     for (int s = 0; s < NSP; ++s)
-        if (push_blocks[s] < 1 || push_blocks[s] > MAX_PUSH_BLOCKS_PER_SM * c->num_sms) return O2PIC_E_INVALID_ARG;
+        if (push_blocks[s] < min_push_blocks(c->P.sp[s].cap) || push_blocks[s] > MAX_PUSH_BLOCKS_PER_SM * c->num_sms)
+            return O2PIC_E_INVALID_ARG;
     int rc = sync_all(c);
     if (rc == O2PIC_E_CUDA) return rc;
     for (int s = 0; s < NSP; ++s) {
@@ -1271,7 +1288,8 @@ int o2pic_batch_autotune(o2pic_batch* b, o2pic_tune_report* report) {
                 if (policies[p] == 0) g = default_push_blocks(c, s);
                 else g = (long long)((slots[s] + (unsigned long long)policies[p] * (BLOCK / 32) - 1) /
                                      ((unsigned long long)policies[p] * (BLOCK / 32)));
-                g = std::max<long long>(1, std::min<long long>(g, (long long)MAX_PUSH_BLOCKS_PER_SM * c->num_sms));
+                g = std::max<long long>(min_push_blocks(c->P.sp[s].cap),
+                                        std::min<long long>(g, (long long)MAX_PUSH_BLOCKS_PER_SM * c->num_sms));
                 shapes[p][3 * i + s] = (int32_t)g;
             }
     }

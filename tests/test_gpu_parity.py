@@ -368,23 +368,27 @@ def test_oxygen_set_with_recombination_100_steps(torch_cuda):
     assert o.counters()["rec_candidates"] > 0
 
 
-def test_checkpoint_and_resume_bit_for_bit(torch_cuda):
-    """Saving the particles, step and next ids after 40 steps and resuming
-    them in a new context gives, 40 steps later, exactly the uninterrupted
-    run (the random streams are keyed by id and step only)."""
+@pytest.mark.parametrize("save_at,S,check", [(40, 2, 16), (41, 10, 16), (43, 10, 7)])
+def test_checkpoint_and_resume_bit_for_bit(torch_cuda, save_at, S, check):
+    """Saving the particles, step and next ids after `save_at` steps and
+    resuming them in a new context gives, 40 steps later, exactly the
+    uninterrupted run (the random streams are keyed by id and step only):
+    also when the save falls between two ion steps (the resumed context
+    re-deposits the ions' charge, which must equal the charge the
+    uninterrupted run kept) and between two compaction checks."""
     from paper_0705_0497_gb300 import api
-    cfg, counts, T, _ = inputs.workload("parity_128", ion_subcycle=2)
+    cfg, counts, T, _ = inputs.workload("parity_128", ion_subcycle=S)
     procs = xsec.oxygen_set(include_rec=True)
     st = inputs.initial_state(cfg, counts, T)
     cap = capacity_for(counts)
-    a = api.Discharge(cfg, cap)
+    a = api.Discharge(cfg, cap, compact_check=check)
     a.set_processes(procs)
     a.load_state(st)
-    a.step(40)
+    a.step(save_at)
     saved = [a.particles(s) for s in range(3)]
     s40 = a.stats()
     a.step(40)
-    b = api.Discharge(cfg, cap)
+    b = api.Discharge(cfg, cap, compact_check=check)
     b.set_processes(procs)
     b.load_state(saved)
     b.set_step(s40["step"])
