@@ -152,6 +152,26 @@ int o2pic_load_particles(o2pic_ctx* ctx, int species, const float* x, const floa
                          const float* vy, const float* vz, const uint32_t* id, uint64_t n,
                          int mem_kind, void* stream);
 
+/* Free flights (Sec. 2: the durations of the free flights between
+ * collisions follow from kinetic considerations).  Each particle carries the
+ * step at which its current free flight ends: its next null-collision
+ * candidate (low 32 bits of the step index).  A flight of K pushes,
+ * K ~ Geometric(P_max) (the same law as a Bernoulli(P_max) test at every
+ * push), is drawn from the particle's random stream when the particle is
+ * loaded or born and at each of its candidates.  Loaded particles get fresh
+ * flights, drawn at the first step after the load (or new tables); to resume
+ * a saved run bit for bit, save them with o2pic_read_flight and restore them
+ * with o2pic_load_flight right after o2pic_load_particles (and set the saved
+ * step with o2pic_set_step).
+ *
+ * o2pic_load_flight: tc[0..n) for the particles just loaded into `species`
+ * (n must equal the loaded count; HOST or DEVICE memory).
+ * o2pic_read_flight: the flights of the live particles of `species` in array
+ * order (the order of o2pic_read_particles), up to cap; *n = live count.
+ * Errors: INVALID_ARG, CUDA. */
+int o2pic_load_flight(o2pic_ctx* ctx, int species, const uint32_t* tc, uint64_t n, int mem_kind, void* stream);
+int o2pic_read_flight(o2pic_ctx* ctx, int species, uint32_t* tc, uint64_t cap, uint64_t* n, int mem_kind);
+
 /* Sets the id the next particle born in `species` gets (it must exceed every
  * id of that species): with o2pic_set_step and the particles of a saved state
  * (o2pic_read_particles, o2pic_get_stats().next_id and .step) a run resumes
@@ -213,7 +233,8 @@ int o2pic_set_step(o2pic_ctx* ctx, uint64_t step);
 /* Kernel timing with CUDA events on the launching stream: on != 0 records an
  * event pair around every launch; o2pic_get_timing returns, per kernel kind
  * (0 push e, 1 push O-, 2 push O2+, 3 pair histograms, 4 pair, 5 field,
- * 6 compact, 7 deposit, 8 collisions e, 9 collisions O-, 10 collisions O2+, 11 (16) pairing),
+ * 6 compact, 7 deposit, 8 collisions e, 9 collisions O-, 10 collisions O2+,
+ * 11 (16) pairing, 12 candidate filter O-, 13 candidate filter O2+),
  * the summed milliseconds and launches; items is reserved (zeros). */
 int o2pic_set_timing(o2pic_ctx* ctx, int on);
 int o2pic_get_timing(o2pic_ctx* ctx, double* ms, uint64_t* launches, uint64_t* items, int nkinds);

@@ -70,7 +70,11 @@ def lib():
         L.oracle_currents.argtypes = [vp, u64, u64, vp]
         L.oracle_table.argtypes = [vp, i32, vp, vp, vp, vp]
         L.oracle_neutral_table.argtypes = [vp, vp]
-        L.oracle_update_particle.argtypes = [vp, i32, u64, vp, vp, u32, vp, vp]
+        L.oracle_update_particle.argtypes = [vp, i32, u64, vp, vp, u32, vp, i32, vp, vp]
+        L.oracle_load_flight.argtypes = [vp, i32, vp, u64]
+        L.oracle_read_flight.argtypes = [vp, i32, vp]
+        L.oracle_flight_gap.restype = u32
+        L.oracle_flight_gap.argtypes = [vp, i32, u32]
         L.oracle_philox.argtypes = [vp, vp, vp]
         L.oracle_ln_f32.restype = ctypes.c_float
         L.oracle_ln_f32.argtypes = [ctypes.c_float]
@@ -139,6 +143,22 @@ class Oracle:
         a = [np.ascontiguousarray(v, dtype=np.float32) for v in (x, vx, vy, vz)]
         i = np.ascontiguousarray(ids, dtype=np.uint32)
         lib().oracle_load(self.h, species, *[_ptr(v) for v in a], _ptr(i), len(i))
+
+    def load_flight(self, species, tc):
+        """Set the free flights (step of the next collision candidate) of the
+        loaded particles of a species, in array order."""
+        t = np.ascontiguousarray(tc, dtype=np.uint32)
+        if lib().oracle_load_flight(self.h, species, _ptr(t), len(t)) != 0:
+            raise ValueError("flight count differs from the particle count")
+
+    def flight(self, species):
+        """Step of each particle's next collision candidate, in array order."""
+        out = np.zeros(self.count(species), np.uint32)
+        lib().oracle_read_flight(self.h, species, _ptr(out))
+        return out
+
+    def flight_gap(self, species, word):
+        return int(lib().oracle_flight_gap(self.h, species, int(word) & 0xFFFFFFFF))
 
     def set_next_id(self, species, v):
         lib().oracle_set_next_id(self.h, species, v)
@@ -215,15 +235,19 @@ class Oracle:
         lib().oracle_neutral_table(self.h, _ptr(K))
         return K
 
-    def update_particle(self, species, step, Ef, state, pid):
-        """One particle through push + absorb + MCC with gather field Ef."""
+    def update_particle(self, species, step, Ef, state, pid, tc=None):
+        """One particle through push + absorb + MCC with gather field Ef; tc =
+        the step of its next collision candidate (default: a free flight
+        drawn at this step as for a freshly loaded particle, so a candidate
+        with probability P_max).  Returns (alive, state, births, tc after)."""
         Ef = np.ascontiguousarray(Ef, dtype=np.float64)
         st = np.ascontiguousarray(state, dtype=np.float64).copy()
         births = np.zeros(5 * 4)
         nb = ctypes.c_int()
-        alive = lib().oracle_update_particle(self.h, species, step, _ptr(Ef), _ptr(st), pid,
-                                             _ptr(births), ctypes.byref(nb))
-        return bool(alive), st, births[:5 * nb.value].reshape(nb.value, 5)
+        t = ctypes.c_uint32(0 if tc is None else int(tc) & 0xFFFFFFFF)
+        alive = lib().oracle_update_particle(self.h, species, step, _ptr(Ef), _ptr(st), pid, ctypes.byref(t),
+                                             1 if tc is None else 0, _ptr(births), ctypes.byref(nb))
+        return bool(alive), st, births[:5 * nb.value].reshape(nb.value, 5), int(t.value)
 
 
 def philox(ctr, key):

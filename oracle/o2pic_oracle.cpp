@@ -67,8 +67,10 @@ const int MAXPROC = 16;
 const int MAX_TRIES = 32;                        // rejection-loop cap
 const double FIX_ONE = 65536.0;                  // CIC fixed point: 2^16 per particle
 
-// RNG stream tags (counter word 1).
-enum { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6 };
+// RNG stream tags (counter word 1).  TAG_FLIGHT + s: the first free-flight
+// draw of a particle of species s (at load or birth).
+enum { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6,
+       TAG_FLIGHT = 7 };
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
@@ -261,14 +263,17 @@ struct Proc {
     std::vector<double> E, s;
 };
 
+// tc = the step of the particle's next collision candidate (the end of its
+// current free flight, low 32 bits of the step index).
 template <class R> struct Particles {
     std::vector<R> x, vx, vy, vz;
-    std::vector<uint32_t> id;
+    std::vector<uint32_t> id, tc;
     size_t size() const { return x.size(); }
-    void push(R px, R pvx, R pvy, R pvz, uint32_t pid) {
+    void push(R px, R pvx, R pvy, R pvz, uint32_t pid, uint32_t ptc) {
         x.push_back(px); vx.push_back(pvx); vy.push_back(pvy); vz.push_back(pvz); id.push_back(pid);
+        tc.push_back(ptc);
     }
-    void clear() { x.clear(); vx.clear(); vy.clear(); vz.clear(); id.clear(); }
+    void clear() { x.clear(); vx.clear(); vy.clear(); vz.clear(); id.clear(); tc.clear(); }
 };
 
 struct Birth4 { double x, vx, vy, vz; };
@@ -311,6 +316,12 @@ template <class R> struct Oracle {
     int64_t jacc[NSP] = {0, 0, 0};
     R numax[NSP], Pmax[NSP];
     double numax64[NSP];
+    // free flights: species s is pushed every sub[s] steps (1 for electrons,
+    // the ion subcycle for ions); inv_lnq = 1 / ln(1 - P_max) = -1 / (nu_max
+    // dt_s); a gap is capped at kcap pushes (2^30 steps ahead, beyond any run)
+    uint32_t sub[NSP];
+    R inv_lnq[NSP], kcap[NSP];
+    bool tc_valid[NSP];
     bool have_neutral;
     Proc neutral;
     std::vector<R> Ktab;              // [NGRID] sigma_n g
@@ -347,6 +358,10 @@ template <class R> struct Oracle {
             a_M[s] = (R)(cfg.M_gas / (mass[s] + cfg.M_gas));
             sig_birth[s] = (R)std::sqrt(KB * cfg.T_gas / mass[s]);
             numax[s] = 0; Pmax[s] = 0; numax64[s] = 0;
+            sub[s] = (s == SP_E) ? 1u : (uint32_t)cfg.ion_subcycle;
+            inv_lnq[s] = (R)(-INFINITY);
+            kcap[s] = (R)std::floor(1073741824.0 / (double)sub[s]);
+            tc_valid[s] = false;
             Q[s].assign(Ng, 0); Qacc[s].assign(Ng, 0);
             next_id[s] = 0;
         }
@@ -414,6 +429,8 @@ template <class R> struct Oracle {
             numax[s] = (R)mx;
             double dts = cfg.dt * (s == SP_E ? 1.0 : (double)cfg.ion_subcycle);
             Pmax[s] = (R)(1.0 - std::exp(-mx * dts));
+            inv_lnq[s] = (R)(-1.0 / (mx * dts));   // 1 / ln(1 - P_max); -inf when nu_max = 0
+            tc_valid[s] = false;                  // gaps drawn with the old nu_max: draw afresh
         }
         Ktab.assign(NGRID, (R)0);
         if (have_neutral) {
@@ -531,6 +548,43 @@ template <class R> struct Oracle {
         E[N] = (phi[N - 1] - phi[N]) / dx + qN / (EPS0 * A);
     }
 
+    // ---- free flights (Sec. 2: "the durations of the free flights ... from
+    // elementary kinetic considerations").  In the null-collision method a
+    // particle's candidate collisions form a Poisson process of rate nu_max;
+    // on the time grid of its pushes (every sub[s] steps of dt) the number K
+    // of pushes without a candidate is geometric,
+    // P(K >= k) = exp(-k nu_max dt_s) = (1 - P_max)^k, drawn by inversion as
+    // K = floor(ln(u) / ln(1 - P_max)) with u = ((w >> 8) + 1/2) 2^-24 in (0, 1).
+    // This is the same law as a Bernoulli(P_max) test at every push.
+    uint32_t flight_gap(int s, uint32_t w) const {
+        const R u = ((R)(w >> 8) + (R)0.5) * (R)(1.0 / 16777216.0);
+        const R t = ln_(u) * inv_lnq[s];
+        const R k = std::floor(t);
+        return (k < kcap[s]) ? (uint32_t)k : (uint32_t)kcap[s];
+    }
+    // The first step >= n at which species s is pushed.
+    uint64_t first_push(int s, uint64_t n) const {
+        return (n + sub[s] - 1) / sub[s] * sub[s];
+    }
+    // A fresh free flight for particle `id` of species s whose first push is
+    // at step nf, drawn from its stream at step n with tag TAG_FLIGHT + s.
+    uint32_t fresh_tc(int s, uint32_t id, uint64_t n, uint64_t nf) const {
+        const uint32_t ctr[4] = {(uint32_t)n, (uint32_t)(TAG_FLIGHT + s), 0u, (uint32_t)(n >> 32)};
+        const uint32_t key[2] = {id, cfg.seed};
+        const U4 w = philox4x32_10(ctr, key);
+        return (uint32_t)(nf + (uint64_t)sub[s] * flight_gap(s, w.v[0]));
+    }
+    // Free flights of the loaded particles of every species whose flights are
+    // not known (after a load or new tables), drawn at step n.
+    void draw_flights(uint64_t n) {
+        for (int s = 0; s < NSP; ++s) {
+            if (tc_valid[s]) continue;
+            const uint64_t nf = first_push(s, n);
+            for (size_t i = 0; i < sp[s].size(); ++i) sp[s].tc[i] = fresh_tc(s, sp[s].id[i], n, nf);
+            tc_valid[s] = true;
+        }
+    }
+
     // ---- table lookups
     R cum_at(int s, int k, int i, R w) const {
         return grid_interp<R>(cum[s], (int)procs[s].size(), k, i, w);
@@ -540,7 +594,7 @@ template <class R> struct Oracle {
     // Returns false if the particle leaves the arrays (absorbed or consumed).
     // Births are appended to `births[dst]` in generation order.
 
-    bool update_particle(int s, uint64_t n, R& x, R& vx, R& vy, R& vz, uint32_t id,
+    bool update_particle(int s, uint64_t n, R& x, R& vx, R& vy, R& vz, uint32_t id, uint32_t& tc,
                          std::vector<Birth4>* births, const std::vector<R>& Ef) {
         // gather: E_p = E_j + frac (E_{j+1} - E_j)
         int j; R frac; cell_of(x, j, frac);
@@ -553,15 +607,18 @@ template <class R> struct Oracle {
         // absorbing electrodes
         if (x < (R)0) { cnt.absorbed[s][0] += 1; return false; }
         if (x >= Lr) { cnt.absorbed[s][1] += 1; return false; }
-        return collide(s, n, x, vx, vy, vz, id, births);
+        return collide(s, n, x, vx, vy, vz, id, tc, births);
     }
 
-    bool collide(int s, uint64_t n, R x, R& vx, R& vy, R& vz, uint32_t id, std::vector<Birth4>* births) {
+    bool collide(int s, uint64_t n, R x, R& vx, R& vy, R& vz, uint32_t id, uint32_t& tc,
+                 std::vector<Birth4>* births) {
         int np = (int)procs[s].size();
         if (np == 0) return true;
+        if (tc != (uint32_t)n) return true;        // in free flight: no candidate this step
+        // a candidate: word 0 of the step's stream draws the next free flight,
+        // word 1 the real/null test, the rest the kinematics
         Stream st(id, cfg.seed, n, (uint32_t)(s == SP_E ? TAG_E : (s == SP_OM ? TAG_OM : TAG_OP)));
-        R u0 = uniform<R>(st.next());
-        if (!(u0 < Pmax[s])) return true;          // no candidate
+        tc = (uint32_t)(n + (uint64_t)sub[s] * (1u + (uint64_t)flight_gap(s, st.next())));
         R u1 = uniform<R>(st.next());
         uint64_t& warn = cnt.warn_tries;
         R vt[3] = {0, 0, 0};
@@ -659,8 +716,9 @@ template <class R> struct Oracle {
         Particles<R>& P = sp[s];
         for (size_t i = 0; i < P.size(); ++i) {
             R x = P.x[i], vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
-            if (update_particle(s, n, x, vx, vy, vz, P.id[i], births, Eg))
-                out.push(x, vx, vy, vz, P.id[i]);
+            uint32_t tc = P.tc[i];
+            if (update_particle(s, n, x, vx, vy, vz, P.id[i], tc, births, Eg))
+                out.push(x, vx, vy, vz, P.id[i], tc);
         }
         P = out;
     }
@@ -729,19 +787,22 @@ template <class R> struct Oracle {
     static void filter(Particles<R>& P, const std::vector<char>& dead) {
         Particles<R> out;
         for (size_t i = 0; i < P.size(); ++i)
-            if (!dead[i]) out.push(P.x[i], P.vx[i], P.vy[i], P.vz[i], P.id[i]);
+            if (!dead[i]) out.push(P.x[i], P.vx[i], P.vy[i], P.vz[i], P.id[i], P.tc[i]);
         P = out;
     }
 
-    // Births take ids next_id, next_id + 1, ... in canonical order.  Ids are
-    // 32-bit: a birth whose id would be 2^32 or more is an id overflow (counted
-    // per birth; the particle keeps the low 32 bits of its id).
-    void append_births(std::vector<Birth4>* births) {
+    // Births of step n take ids next_id, next_id + 1, ... in canonical order.
+    // Ids are 32-bit: a birth whose id would be 2^32 or more is an id overflow
+    // (counted per birth; the particle keeps the low 32 bits of its id).  A
+    // newborn starts a free flight at its first push after step n.
+    void append_births(std::vector<Birth4>* births, uint64_t n) {
         for (int s = 0; s < NSP; ++s) {
+            const uint64_t nf = first_push(s, n + 1);
             for (const Birth4& b : births[s]) {
                 const uint64_t id64 = next_id[s]++;
                 if (id64 > 0xFFFFFFFFull) cnt.id_overflow += 1;
-                sp[s].push((R)b.x, (R)b.vx, (R)b.vy, (R)b.vz, (uint32_t)id64);
+                const uint32_t id = (uint32_t)id64;
+                sp[s].push((R)b.x, (R)b.vx, (R)b.vy, (R)b.vz, id, fresh_tc(s, id, n, nf));
                 cnt.born[s] += 1;
             }
         }
@@ -755,6 +816,7 @@ template <class R> struct Oracle {
     void do_step() {
         ensure_field();
         uint64_t n = step;
+        draw_flights(n);
         bool ion_step = (n % (uint64_t)cfg.ion_subcycle) == 0;
         std::vector<Birth4> births[NSP];
         for (int s = 0; s < NSP; ++s) jacc[s] = 0;
@@ -765,7 +827,7 @@ template <class R> struct Oracle {
             recombine(n);
             neutralize(n);
         }
-        append_births(births);
+        append_births(births, n);
         deposit_all();
         field_solve((double)(n + 1) * cfg.dt);
         for (int s = 0; s < NSP; ++s)
@@ -790,13 +852,14 @@ struct Handle {
 
 // One particle through push + absorb + MCC with a given gather field.
 template <class R>
-int update_one(Oracle<R>& O, int s, uint64_t n, const double* Ef, double* state, uint32_t id,
-               double* births, int* nb) {
+int update_one(Oracle<R>& O, int s, uint64_t n, const double* Ef, double* state, uint32_t id, uint32_t* tc,
+               int fresh, double* births, int* nb) {
+    if (fresh) *tc = O.fresh_tc(s, id, n, O.first_push(s, n));
     std::vector<R> Eg(O.Ng);
     for (int j = 0; j < O.Ng; ++j) Eg[j] = (R)Ef[j];
     R x = (R)state[0], vx = (R)state[1], vy = (R)state[2], vz = (R)state[3];
     std::vector<Birth4> b[NSP];
-    int alive = O.update_particle(s, n, x, vx, vy, vz, id, b, Eg) ? 1 : 0;
+    int alive = O.update_particle(s, n, x, vx, vy, vz, id, *tc, b, Eg) ? 1 : 0;
     state[0] = x; state[1] = vx; state[2] = vy; state[3] = vz;
     int k = 0;
     for (int d = 0; d < NSP; ++d)
@@ -845,12 +908,34 @@ int oracle_load(void* p, int s, const float* x, const float* vx, const float* vy
         O.sp[s].clear();
         uint64_t mx = 0;
         for (uint64_t i = 0; i < n; ++i) {
-            O.sp[s].push(x[i], vx[i], vy[i], vz[i], id[i]);
+            O.sp[s].push(x[i], vx[i], vy[i], vz[i], id[i], 0u);
             mx = std::max<uint64_t>(mx, (uint64_t)id[i] + 1u);
         }
+        O.tc_valid[s] = false;   // free flights drawn at the next step
         O.next_id[s] = mx;
         O.field_valid = false;
         O.jhist.clear();
+    });
+    return 0;
+}
+
+// Free flights of species s (the step of each particle's next collision
+// candidate, in array order) after a load: n must be the particle count.
+int oracle_load_flight(void* p, int s, const uint32_t* tc, uint64_t n) {
+    Handle* h = (Handle*)p; int rc = 0;
+    DISPATCH(h, {
+        if (n != O.sp[s].size()) rc = -1;
+        else { for (uint64_t i = 0; i < n; ++i) O.sp[s].tc[i] = tc[i]; O.tc_valid[s] = true; }
+    });
+    return rc;
+}
+
+// The same, read back (drawn first if not yet known, as a step would).
+int oracle_read_flight(void* p, int s, uint32_t* tc) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, {
+        O.draw_flights(O.step);
+        for (size_t i = 0; i < O.sp[s].size(); ++i) tc[i] = O.sp[s].tc[i];
     });
     return 0;
 }
@@ -982,15 +1067,25 @@ int oracle_neutral_table(void* p, double* K) {
 }
 
 // One particle of species s through push + absorb + MCC at step n with the
-// gather field Ef[Ng] (given in double, rounded to R).  Returns 1 if the
+// gather field Ef[Ng] (given in double, rounded to R); *tc (in/out) is the
+// step of its next collision candidate, drawn afresh at step n as for a
+// loaded particle when fresh != 0 (then a candidate with probability P_max).  Returns 1 if the
 // particle stays, 0 if it leaves; births (up to 2) are written to
 // births[8] = {dst, x, vx, vy, vz, ...} and their number to *nb.  Used for
 // sampled checks at sizes where the whole oracle step is too slow.
 int oracle_update_particle(void* p, int s, uint64_t n, const double* Ef, double* state, uint32_t id,
-                           double* births, int* nb) {
+                           uint32_t* tc, int fresh, double* births, int* nb) {
     Handle* h = (Handle*)p;
-    if (h->f) return update_one<float>(*h->f, s, n, Ef, state, id, births, nb);
-    return update_one<double>(*h->d, s, n, Ef, state, id, births, nb);
+    if (h->f) return update_one<float>(*h->f, s, n, Ef, state, id, tc, fresh, births, nb);
+    return update_one<double>(*h->d, s, n, Ef, state, id, tc, fresh, births, nb);
+}
+
+// The free-flight gap K (pushes without a candidate) that word w gives for
+// species s with the current tables.  Test use.
+uint32_t oracle_flight_gap(void* p, int s, uint32_t w) {
+    Handle* h = (Handle*)p; uint32_t v = 0;
+    DISPATCH(h, v = O.flight_gap(s, w));
+    return v;
 }
 
 // ---- standalone pieces (pinned directly by tests)

@@ -17,7 +17,7 @@ MAXPROC = 16
 E, OM, OP = 0, 1, 2
 HOST, DEVICE = 0, 1
 KERNEL_KINDS = ("push_e", "push_om", "push_op", "pair_hist", "pair", "field", "compact", "deposit",
-                "cand_e", "cand_om", "cand_op", "recomb")
+                "cand_e", "cand_om", "cand_op", "recomb", "filter_om", "filter_op")
 
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "ID_OVERFLOW", -4: "NONFINITE", -5: "CUDA", -6: "TIMEOUT",
@@ -92,6 +92,8 @@ SIGNATURES = [
     ("o2pic_set_processes", _i32, [_vp, _P(Process), _i32]),
     ("o2pic_load_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _i32, _vp]),
     ("o2pic_set_next_id", _i32, [_vp, _i32, _u32]),
+    ("o2pic_load_flight", _i32, [_vp, _i32, _vp, _u64, _i32, _vp]),
+    ("o2pic_read_flight", _i32, [_vp, _i32, _vp, _u64, _P(_u64), _i32]),
     ("o2pic_step", _i32, [_vp, _u64, _vp]),
     ("o2pic_synchronize", _i32, [_vp]),
     ("o2pic_read_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _P(_u64), _i32]),
@@ -234,8 +236,31 @@ class Discharge:
         _check(lib().o2pic_load_particles(self.h, species, *ptrs, n, kind, _stream_ptr(stream)), "o2pic_load_particles")
 
     def load_state(self, state, stream=None):
+        """Load all species; a species dict with "tc" (saved free flights)
+        restores them, else fresh flights are drawn at the next step."""
         for s, p in enumerate(state):
             self.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"], stream)
+            if "tc" in p:
+                self.load_flight(s, p["tc"])
+
+    def load_flight(self, species, tc):
+        """Free flights (step of each particle's next collision candidate) of
+        the particles just loaded into `species` (host array or CUDA tensor)."""
+        if _is_torch_cuda(tc):
+            ptr, n, kind = ctypes.c_void_p(tc.data_ptr()), int(tc.numel()), DEVICE
+        else:
+            a = np.ascontiguousarray(tc, dtype=np.uint32)
+            ptr, n, kind = a.ctypes.data_as(ctypes.c_void_p), len(a), HOST
+        _check(lib().o2pic_load_flight(self.h, species, ptr, n, kind, None), "o2pic_load_flight")
+
+    def flight(self, species):
+        """Step of each live particle's next collision candidate, array order."""
+        n = self.count(species)
+        out = np.zeros(n, np.uint32)
+        m = ctypes.c_uint64()
+        _check(lib().o2pic_read_flight(self.h, species, out.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(m), HOST),
+               "o2pic_read_flight")
+        return out
 
     def step(self, n=1, stream=None):
         _check(lib().o2pic_step(self.h, int(n), _stream_ptr(stream)), "o2pic_step")
@@ -249,7 +274,10 @@ class Discharge:
                "o2pic_read_particles")
         return int(n.value)
 
-    def particles(self, species):
+    def particles(self, species, flight=False):
+        """Live particles of a species in array order (host arrays); with
+        flight=True also "tc", their free flights (a saved state that
+        load_state resumes bit for bit)."""
         n = self.count(species)
         out = {k: np.zeros(n, np.float32) for k in ("x", "vx", "vy", "vz")}
         out["id"] = np.zeros(n, np.uint32)
@@ -257,6 +285,8 @@ class Discharge:
         _check(lib().o2pic_read_particles(self.h, species, *[out[k].ctypes.data_as(ctypes.c_void_p)
                                                              for k in ("x", "vx", "vy", "vz", "id")],
                                           n, ctypes.byref(m), HOST), "o2pic_read_particles")
+        if flight:
+            out["tc"] = self.flight(species)
         return out
 
     def read_into(self, species, d):

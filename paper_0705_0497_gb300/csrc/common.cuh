@@ -30,6 +30,46 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// Block 0 of the streams of one step and tag for many particles: counter
+// (step_lo, tag, 0, step_hi) under key (id, seed).  Round 1 and half of round 2
+// do not depend on the id (the counter's third word is 0, and the key's second
+// word is the seed), so they are computed once per step (philox_pre) and only
+// the rest per particle (philox_id); the result is Philox4x32-10 bit for bit.
+struct PhiloxPre {
+    uint32_t tag, w1, hi2, lo2, seed;
+};
+__device__ __forceinline__ PhiloxPre philox_pre(uint32_t step_lo, uint32_t tag, uint32_t step_hi, uint32_t seed) {
+    // round 1 with key (id, seed): c1 = (tag ^ id, 0, hi(M0 c0) ^ step_hi ^ seed, lo(M0 c0))
+    const uint32_t lo0 = 0xD2511F53u * step_lo;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, step_lo);
+    const uint32_t z1 = hi0 ^ step_hi ^ seed;
+    PhiloxPre p;
+    p.tag = tag;
+    p.w1 = lo0;
+    // round 2: the product of the id-free word z1
+    p.hi2 = __umulhi(0xCD9E8D57u, z1);
+    p.lo2 = 0xCD9E8D57u * z1;
+    p.seed = seed;
+    return p;
+}
+__device__ __forceinline__ uint4 philox_id(const PhiloxPre& p, uint32_t id) {
+    const uint32_t x1 = p.tag ^ id;
+    uint32_t kx = id + 0x9E3779B9u, ky = p.seed + 0xBB67AE85u;
+    const uint32_t lo0 = 0xD2511F53u * x1;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, x1);
+    uint4 c = make_uint4(p.hi2 ^ kx, p.lo2, hi0 ^ p.w1 ^ ky, lo0);   // after round 2
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        kx += 0x9E3779B9u; ky += 0xBB67AE85u;
+        const uint32_t l0 = 0xD2511F53u * c.x;
+        const uint32_t h0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t l1 = 0xCD9E8D57u * c.z;
+        const uint32_t h1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(h1 ^ c.y ^ kx, l1, h0 ^ c.w ^ ky, l0);
+    }
+    return c;
+}
+
 // Word stream of (key0, seed) at (step, tag): block b = Philox(ctr = (step_lo,
 // tag, b, step_hi)); words are consumed in order 4b .. 4b+3.
 struct Stream {
@@ -80,6 +120,16 @@ __device__ __forceinline__ float ln_series(float x) {
     p = fmaf(t2, p, 1.0f);
     const float lnm = (2.0f * t) * p;
     return fmaf((float)e, 0.693147182f, lnm);
+}
+
+// Free flight (the null-collision method's candidate times on the time grid
+// of a species' pushes): the number K of pushes before the next candidate is
+// Geometric(P_max), P(K >= k) = (1 - P_max)^k, drawn by inversion from one
+// word: u = ((w >> 8) + 1/2) 2^-24, K = floor(ln(u) / ln(1 - P_max)), capped.
+__device__ __forceinline__ uint32_t flight_gap(uint32_t w, float inv_lnq, float kcap) {
+    const float u = (__uint2float_rn(w >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    const float k = floorf(ln_series(u) * inv_lnq);
+    return (k < kcap) ? (uint32_t)k : (uint32_t)kcap;
 }
 
 __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz) {

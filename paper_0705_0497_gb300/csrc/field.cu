@@ -42,8 +42,11 @@ constexpr int GB = FT;                            // threads of the births block
 // per-warp offsets in shared memory, and every thread of the births block
 // then places single births (found by a binary search over the offsets), so
 // the work spreads over the block however the births cluster.
+// A newborn of step n starts a free flight at its first push after n (step
+// n + 1 for electrons, the next ion step for ions), drawn from its own stream
+// at step n with tag TAG_FLIGHT + d.
 __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP], int d, unsigned long long slot,
-                            unsigned long long id64, float4 b) {
+                            unsigned long long id64, float4 b, unsigned long long n) {
     const SpeciesBuf& B = P.sp[d];
     if (slot >= B.cap) { atomicOr(&C->error_flags, ERR_CAPACITY); return; }
     // ids are 32-bit: a birth whose id would be 2^32 or more overflows
@@ -53,11 +56,17 @@ __device__ void place_birth(const Params& P, DevCtrl* C, const unsigned cur[NSP]
         atomicAdd(&C->cnt.id_overflow, 1ull);
     }
     const unsigned cb = cur[d];
+    const uint32_t id = (uint32_t)id64;
+    const unsigned sub = P.sub[d];
+    const uint32_t nf = (uint32_t)((n + sub) / sub * sub);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)n, TAG_FLIGHT + (uint32_t)d, 0u, (uint32_t)(n >> 32)),
+                                  make_uint2(id, P.seed));
     B.x[cb][slot] = b.x;
     B.vx[cb][slot] = b.y;
     B.vy[cb][slot] = b.z;
     B.vz[cb][slot] = b.w;
-    B.id[cb][slot] = (uint32_t)id64;
+    B.id[cb][slot] = id;
+    B.tc[cb][slot] = nf + sub * flight_gap(w.x, P.inv_lnq[d], P.kcap[d]);
 }
 
 // Exclusive scan over the births block of two 64-bit values per thread, with
@@ -411,14 +420,16 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
             const unsigned long long sb = ((unsigned long long)u * R < ns ? (unsigned long long)u * R : ns) + (r - p[u]);
             if (kind == 0) {
                 const float4 be = P.stage[B_E_FROM_E][sb], bo = P.stage[B_OP_FROM_E][sb];
-                place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + r, (unsigned long long)cs.next_id[SP_E] + r, be);
-                place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + r, (unsigned long long)cs.next_id[SP_OP] + r, bo);
+                place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + r, (unsigned long long)cs.next_id[SP_E] + r, be,
+                            cs.step);
+                place_birth(P, C, cs.cur, SP_OP, cs.slots[SP_OP] + r, (unsigned long long)cs.next_id[SP_OP] + r, bo,
+                            cs.step);
             } else if (kind == 1) {
                 place_birth(P, C, cs.cur, SP_OM, cs.slots[SP_OM] + r, (unsigned long long)cs.next_id[SP_OM] + r,
-                            P.stage[B_OM_FROM_E][sb]);
+                            P.stage[B_OM_FROM_E][sb], cs.step);
             } else {
                 place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + n1 + r, (unsigned long long)cs.next_id[SP_E] + n1 + r,
-                            P.stage[B_E_FROM_OM][sb]);
+                            P.stage[B_E_FROM_OM][sb], cs.step);
             }
         }
         btot[B_E_FROM_E] = n1;
@@ -489,7 +500,7 @@ template <int S>
 __device__ __forceinline__ void compact_body(const Params& P, int mode, unsigned long long epoch_arg,
                                              unsigned* ticket_arg, unsigned long long* flag_arg,
                                              unsigned long long* val_arg, float* ox, float* ovx, float* ovy,
-                                             float* ovz, uint32_t* oid, unsigned long long ocap,
+                                             float* ovz, uint32_t* oid, uint32_t* otc, unsigned long long ocap,
                                              unsigned long long* out_count) {
     __shared__ unsigned ws[32];
     __shared__ unsigned sh_tile;
@@ -510,17 +521,18 @@ __device__ __forceinline__ void compact_body(const Params& P, int mode, unsigned
     const float* VY = P.sp[S].vy[cb];
     const float* VZ = P.sp[S].vz[cb];
     const uint32_t* ID = P.sp[S].id[cb];
-    float *DX, *DVX, *DVY, *DVZ; uint32_t* DID;
+    const uint32_t* TCS = P.sp[S].tc[cb];
+    float *DX, *DVX, *DVY, *DVZ; uint32_t *DID, *DTC;
     unsigned long long dcap;
     unsigned* ticket; unsigned long long *flag, *val, epoch;
     if (mode == 0) {
         DX = P.sp[S].x[cb ^ 1u]; DVX = P.sp[S].vx[cb ^ 1u]; DVY = P.sp[S].vy[cb ^ 1u]; DVZ = P.sp[S].vz[cb ^ 1u];
-        DID = P.sp[S].id[cb ^ 1u]; dcap = P.sp[S].cap;
+        DID = P.sp[S].id[cb ^ 1u]; DTC = P.sp[S].tc[cb ^ 1u]; dcap = P.sp[S].cap;
         ticket = &C->ticket[NKK + S];
         flag = P.lb_flag[KK_COMPACT]; val = P.lb_val[KK_COMPACT];
         epoch = (C->epoch << 2) | (unsigned long long)S;
     } else {
-        DX = ox; DVX = ovx; DVY = ovy; DVZ = ovz; DID = oid; dcap = ocap;
+        DX = ox; DVX = ovx; DVY = ovy; DVZ = ovz; DID = oid; DTC = otc; dcap = ocap;
         ticket = ticket_arg; flag = flag_arg; val = val_arg; epoch = epoch_arg;
     }
     const unsigned ntiles = (unsigned)ceil_div(nslots, TILE);
@@ -575,8 +587,12 @@ __device__ __forceinline__ void compact_body(const Params& P, int mode, unsigned
                 for (int k = 0; k < 4; ++k) {
                     if (!lv[k]) continue;
                     if (d < dcap) {
-                        DX[d] = X[i0 + k]; DVX[d] = VX[i0 + k]; DVY[d] = VY[i0 + k]; DVZ[d] = VZ[i0 + k];
-                        DID[d] = ID[i0 + k];
+                        // a gather (mode 1) may ask for the flights only
+                        if (DX) {
+                            DX[d] = X[i0 + k]; DVX[d] = VX[i0 + k]; DVY[d] = VY[i0 + k]; DVZ[d] = VZ[i0 + k];
+                            DID[d] = ID[i0 + k];
+                        }
+                        if (DTC) DTC[d] = TCS[i0 + k];
                     }
                     ++d;
                 }
@@ -605,10 +621,10 @@ __global__ void __launch_bounds__(FT) k_field_b(const Params* __restrict__ all, 
 template <int S>
 __global__ void __launch_bounds__(BLOCK) k_compact(Params P, int mode, unsigned long long epoch_arg, unsigned* ticket_arg,
                                                    unsigned long long* flag_arg, unsigned long long* val_arg, float* ox,
-                                                   float* ovx, float* ovy, float* ovz, uint32_t* oid,
+                                                   float* ovx, float* ovy, float* ovz, uint32_t* oid, uint32_t* otc,
                                                    unsigned long long ocap, unsigned long long* out_count) {
     pdl_wait();
-    compact_body<S>(P, mode, epoch_arg, ticket_arg, flag_arg, val_arg, ox, ovx, ovy, ovz, oid, ocap, out_count);
+    compact_body<S>(P, mode, epoch_arg, ticket_arg, flag_arg, val_arg, ox, ovx, ovy, ovz, oid, otc, ocap, out_count);
 }
 
 // batched compaction check (mode 0): the blocks of map[b].x claim that
@@ -618,7 +634,7 @@ __global__ void __launch_bounds__(BLOCK) k_compact_b(const Params* __restrict__ 
     __shared__ Params sP;
     pdl_wait();
     load_params(sP, all + map[blockIdx.x].x);
-    compact_body<S>(sP, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+    compact_body<S>(sP, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
 }
 
 // Validation of freshly loaded particles (x in [0, L), finite velocities)
@@ -705,15 +721,18 @@ void launch_compact(int species, const Params& P, int grid, cudaStream_t s) {
     auto k = species == SP_E ? k_compact<SP_E> : (species == SP_OM ? k_compact<SP_OM> : k_compact<SP_OP>);
     launch_pdl(k, grid, BLOCK, 0, s, P, 0, 0ull, (unsigned*)nullptr, (unsigned long long*)nullptr,
                (unsigned long long*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr,
-               (uint32_t*)nullptr, 0ull, (unsigned long long*)nullptr);
+               (uint32_t*)nullptr, (uint32_t*)nullptr, 0ull, (unsigned long long*)nullptr);
 }
 
 void launch_gather(int species, const Params& P, int grid, unsigned long long epoch, unsigned* ticket,
                    unsigned long long* flag, unsigned long long* val, float* x, float* vx, float* vy, float* vz,
-                   uint32_t* id, unsigned long long cap, unsigned long long* out_count, cudaStream_t s) {
-    if (species == SP_E) k_compact<SP_E><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, cap, out_count);
-    else if (species == SP_OM) k_compact<SP_OM><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, cap, out_count);
-    else k_compact<SP_OP><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, cap, out_count);
+                   uint32_t* id, uint32_t* tc, unsigned long long cap, unsigned long long* out_count, cudaStream_t s) {
+    if (species == SP_E)
+        k_compact<SP_E><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, tc, cap, out_count);
+    else if (species == SP_OM)
+        k_compact<SP_OM><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, tc, cap, out_count);
+    else
+        k_compact<SP_OP><<<grid, BLOCK, 0, s>>>(P, 1, epoch, ticket, flag, val, x, vx, vy, vz, id, tc, cap, out_count);
 }
 
 void launch_load_check(int species, const Params& P, unsigned long long n, cudaStream_t s) {

@@ -64,7 +64,10 @@ constexpr int JRING = 8192;             // steps of conduction-current sums kept
 constexpr int QCOPIES = 4;
 
 enum Kind { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6 };
-enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6 };
+// TAG_FLIGHT + s: the first free-flight draw of a particle of species s (at a
+// load or at its birth).
+enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6,
+                      TAG_FLIGHT = 7 };
 
 // device error bits
 constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE = 4ull, ERR_TIMEOUT = 8ull;
@@ -72,7 +75,7 @@ constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE =
 // kernel kinds (timing, tickets)
 enum KernelKind { KK_PUSH_E = 0, KK_PUSH_OM = 1, KK_PUSH_OP = 2, KK_PAIR_HIST = 3, KK_PAIR = 4,
                   KK_FIELD = 5, KK_COMPACT = 6, KK_DEPOSIT = 7, KK_CAND_E = 8, KK_CAND_OM = 9, KK_CAND_OP = 10,
-                  KK_REC = 11, NKK = 12 };
+                  KK_REC = 11, KK_FILT_OM = 12, KK_FILT_OP = 13, NKK = 14 };
 
 // Counters: same layout as the head of o2pic_stats.
 struct DevCounters {
@@ -110,12 +113,15 @@ struct DevCtrl {
     DevCounters cnt;
 };
 
+// tc: the step of each particle's next collision candidate (the end of its
+// current free flight), low 32 bits of the step index.
 struct SpeciesBuf {
     float* x[2];
     float* vx[2];
     float* vy[2];
     float* vz[2];
     uint32_t* id[2];
+    uint32_t* tc[2];
     unsigned long long cap;
 };
 
@@ -129,6 +135,11 @@ struct Params {
     int kind[NSP][MAXPROC];
     float thr[NSP][MAXPROC];
     float numax[NSP], pmax[NSP];
+    // free flights: species s is pushed every sub[s] steps; a gap of K pushes
+    // is floor(ln(u) inv_lnq[s]) with inv_lnq = 1 / ln(1 - P_max) = -1 /
+    // (nu_max dt_s), capped at kcap[s] (2^30 steps ahead, beyond any run)
+    float inv_lnq[NSP], kcap[NSP];
+    unsigned sub[NSP];
     int births_possible[NSP];
     // (17)
     const float* Ktab;           // [NGRID] sigma_n g
@@ -165,8 +176,12 @@ struct Params {
     float4* stage[NB];
     unsigned int* wcount[NB];
     unsigned int push_warps[NSP];  // warps of each particle kernel launch (units of wcount)
-    uint4* cand[NSP];              // collision candidates {slot, w1, w2, w3} at each warp's range
-    unsigned int* ccount[NSP];     // candidates per warp
+    // collision records at each particle warp's range, two uint4 each:
+    // electrons {slot, id, x, vx}{vy, vz, -, -} per real collision; ions
+    // {slot, id, vx, vy}{vz, w1, w2, w3} per candidate, compacted to the
+    // real ones by the filter
+    uint4* cand[NSP];
+    unsigned int* ccount[NSP];     // records per warp
     unsigned int max_push_warps;   // bound on push_warps (shared memory of the field kernel)
     // (17): per-tile per-cell counts of live ions [2][max_tiles][Nc], per-cell info
     unsigned int* hist[2];       // 0: O-, 1: O2+
@@ -219,6 +234,8 @@ __host__ __device__ inline unsigned warp_range_len(unsigned n, unsigned W) {
 // (defined in the kernel translation units, called by the runtime)
 void launch_push(int species, const Params& P, int grid, cudaStream_t s);
 void launch_cand(int species, const Params& P, int grid, cudaStream_t s);
+void launch_filter(int species, const Params& P, int grid, cudaStream_t s);
+void launch_filter_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s);
 void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t s);
 cudaError_t configure_pair_hist_smem(int Nc);
 void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s);
@@ -241,7 +258,8 @@ void launch_ln(const float* x, float* out, unsigned long long n, cudaStream_t s)
 void launch_load_check(int species, const Params& P, unsigned long long n, cudaStream_t s);
 void launch_gather(int species, const Params& P, int grid, unsigned long long epoch, unsigned* ticket,
                    unsigned long long* flag, unsigned long long* val, float* x, float* vx, float* vy, float* vz,
-                   uint32_t* id, unsigned long long cap, unsigned long long* out_count, cudaStream_t s);
+                   uint32_t* id, uint32_t* tc, unsigned long long cap, unsigned long long* out_count, cudaStream_t s);
+void launch_flight_init(int species, const Params& P, cudaStream_t s);
 cudaError_t configure_push_smem(size_t max_bytes);
 cudaError_t configure_field_smem(size_t bytes);
 size_t field_smem_bytes(const Params& P);

@@ -7,8 +7,8 @@
 //   * SoA FP32 arrays x, vx, vy, vz + u32 id, updated IN PLACE: a particle
 //     keeps its slot, removed particles are marked (x = NaN) and dropped by a
 //     periodic stable compaction, births are appended after the last slot.
-//     The common path reads x, vx, id (12 B) and writes x, vx (8 B); vy, vz
-//     are read only for collision candidates.
+//     The common path reads x, vx, tc (12 B) and writes x, vx (8 B); id,
+//     vy, vz are read for collision candidates only.
 //   * a persistent grid; each warp owns one contiguous, 128-aligned slot range
 //     and walks it in rounds of 128 (lane l takes slots l, l+32, l+64, l+96:
 //     every load and store is one coalesced 128-byte line per array).  No
@@ -16,10 +16,21 @@
 //   * the gather field and the deposit live in shared memory; the deposit is
 //     one 64-bit atomic per particle holding (count, sum of CIC weights) per
 //     cell, turned into node charges when the block flushes;
-//   * one Philox block per particle per step decides "collision candidate";
-//     candidates are queued per warp in slot order and filtered 32 at a time
-//     (electrons: energy against the total rate); only real collisions reach
-//     the out-of-line kinematics, again 32 at a time;
+//   * free flights (Sec. 2: "the durations of the free flights ... from
+//     elementary kinetic considerations"): each particle carries the step of
+//     its next null-collision candidate (tc, read with x and v_x), so the
+//     common path draws no random number; candidates are queued per warp in
+//     shared memory and handled 32 at a time (all lanes busy): one Philox
+//     block (the id-free first round hoisted) draws the next free flight and
+//     the rest of the collision;
+//   * electrons: a candidate is filtered at once (energy against the total
+//     rate, the total-rate column in shared memory), and only the real
+//     collisions are recorded (32 B each: slot, id, x, v) for the kinematics
+//     kernel;
+//   * ions: candidates are recorded (slot and the rest of the Philox block),
+//     a lean filter kernel (target sampled from the gas Maxwellian, energy
+//     against the total rate) keeps the real ones, and the kinematics kernel
+//     handles those, 32 at a time;
 //   * births are ranked with warp ballots and staged at the warp's range;
 //     the end-of-step kernel places them in parent order.
 #include "common.cuh"
@@ -50,7 +61,6 @@ template <> struct SpeciesTraits<SP_OP> { static constexpr uint32_t tag = TAG_OP
 
 constexpr int WARPS = BLOCK / 32;           // 8
 constexpr int ROUND = 128;                  // slots per warp round (4 per lane)
-constexpr int Q2 = 64;                      // per-warp real-collision queue (31 + 32 max)
 constexpr int PUSH_UNROLL = O2PIC_PUSH_UNROLL;
 
 struct PushShared {
@@ -63,8 +73,12 @@ struct PushShared {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// One candidate through process selection and kinematics, exactly in the
-// order of the oracle.  Returns the event index (-1 = null collision).
+// One real collision (a candidate its filter kept) through process selection
+// and kinematics, exactly in the order of the oracle.  The filter already
+// counted the warnings of the part it shares with this function (the ions'
+// target sample, the energy above the grid), so they are not counted again.
+// Returns the event index, or -1 for a null collision (the selected
+// process's threshold above E; the rate test itself repeats the filter's).
 // bkind: 0 none, 1 ionization (two births), 2 attachment / detachment (one).
 template <int S>
 __device__ __noinline__ int collide(const Params& P, const float* cum, int np, unsigned long long step,
@@ -79,13 +93,14 @@ __device__ __noinline__ int collide(const Params& P, const float* cum, int np, u
     float vtx = 0.0f, vty = 0.0f, vtz = 0.0f;
     float gx = vx, gy = vy, gz = vz;
     if (S != SP_E) {
-        maxwellian(st, P.sig_gas, vtx, vty, vtz, warn_tries);
+        unsigned counted_by_filter = 0;
+        maxwellian(st, P.sig_gas, vtx, vty, vtz, counted_by_filter);
         gx = vx - vtx; gy = vy - vty; gz = vz - vtz;
     }
     const float E = P.kappa[S] * dot3(gx, gy, gz, gx, gy, gz);
     int i; float w; bool above;
     grid_locate(E, i, w, above);
-    if (above) ++warn_emax;
+    (void)warn_emax;
     // null collision unless u1 nu_max falls below the total rate; then the
     // first process whose cumulative rate exceeds it (the last one if
     // rounding leaves none)
@@ -218,17 +233,35 @@ __device__ __forceinline__ void flush_hist(unsigned* hist, unsigned long long* Q
     }
 }
 
-// Stage-A filter of an electron candidate: is it a real collision?  The
-// same arithmetic as the start of collide(): energy of the particle, the
-// total rate on the table grid and the comparison with u1 nu_max.
-__device__ __forceinline__ bool electron_is_real(const Params& P, const float* __restrict__ cum, int np, uint4 w0,
-                                                 float vx, float vy, float vz) {
-    const float u1 = uniform(w0.y);
+// Filter of an electron candidate: is it a real collision?  The same
+// arithmetic as the start of collide(): energy of the particle, the total
+// rate on the table grid (column `tot` = the last cumulative column) and the
+// comparison with u1 nu_max.
+__device__ __forceinline__ bool electron_is_real(const Params& P, const float* tot, uint32_t w1, float vx, float vy,
+                                                 float vz, unsigned& wemax) {
+    const float u1 = uniform(w1);
     const float E = P.kappa[SP_E] * dot3(vx, vy, vz, vx, vy, vz);
     int i; float w; bool above;
     grid_locate(E, i, w, above);
-    return (u1 * P.numax[SP_E]) < grid_interp(cum, np, np - 1, i, w);
+    if (above) ++wemax;
+    return (u1 * P.numax[SP_E]) < grid_interp(tot, 1, 0, i, w);
 }
+
+// Total-rate column (the last cumulative column) of species S into shared memory.
+__device__ __forceinline__ void stage_total(const Params& P, int S, float* tot) {
+    const int np = P.nproc[S];
+    const float* __restrict__ cum = P.cum[S];
+    for (int i = threadIdx.x; i < NGRID; i += blockDim.x) tot[i] = np > 0 ? cum[(size_t)i * np + np - 1] : 0.0f;
+}
+
+// Candidate queue of one warp of the particle kernel (shared memory): slot,
+// x and v_x after the push of up to QN candidates in slot order.
+constexpr int QN = 64;
+struct PushQueue {
+    unsigned slot[WARPS][QN];
+    float x[WARPS][QN];
+    float vx[WARPS][QN];
+};
 
 // Body of the particle kernel for block blk of nblk blocks (the launch's own
 // block, or a block a batched launch maps to this discharge).
@@ -240,23 +273,34 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     float* Es = reinterpret_cast<float*>(smem + align16(sizeof(PushShared)));
     unsigned long long* hist =
         reinterpret_cast<unsigned long long*>(smem + align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng));
+    PushQueue& Q = *reinterpret_cast<PushQueue*>(hist + P.Ng);
+    float* Tt = reinterpret_cast<float*>(&Q + 1);        // electrons: total-rate column
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned* qs = Q.slot[warp];
+    float* qx = Q.x[warp];
+    float* qv = Q.vx[warp];
 
     DevCtrl* C = P.ctrl;
     const unsigned long long step = C->step;
+    const uint32_t step_lo = (uint32_t)step;
     const unsigned cb = C->cur[S];
     const unsigned nslots = (unsigned)((C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap);
     float* __restrict__ X = P.sp[S].x[cb];
     float* __restrict__ VX = P.sp[S].vx[cb];
+    const float* __restrict__ VY = P.sp[S].vy[cb];
+    const float* __restrict__ VZ = P.sp[S].vz[cb];
     const uint32_t* __restrict__ ID = P.sp[S].id[cb];
+    uint32_t* __restrict__ TC = P.sp[S].tc[cb];
     uint4* __restrict__ CAND = P.cand[S];
-    const float qmdt = P.qmdt[S], dts = P.dt_s[S], inv_dx = P.inv_dx, Lf = P.Lf, pmax = P.pmax[S];
+    const float qmdt = P.qmdt[S], dts = P.dt_s[S], inv_dx = P.inv_dx, Lf = P.Lf;
+    const float inv_lnq = P.inv_lnq[S], kcap = P.kcap[S];
+    const unsigned sub = P.sub[S];
     const int Nc = P.Nc, Ng = P.Ng;
-    const uint32_t seed = P.seed, tag = SpeciesTraits<S>::tag;
-    const uint32_t step_lo = (uint32_t)step, step_hi = (uint32_t)(step >> 32);
+    const PhiloxPre pre = philox_pre(step_lo, SpeciesTraits<S>::tag, (uint32_t)(step >> 32), P.seed);
 
     for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0ull; }
+    if (S == SP_E) stage_total(P, S, Tt);
     if (tid == 0) { sh.absorbed[0] = sh.absorbed[1] = 0u; sh.removed = 0u; sh.psteps = 0u; sh.nonfinite = 0u; sh.jsum = 0ull; }
     __syncthreads();
 
@@ -267,29 +311,63 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
     const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
 
-    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0;
+    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0, wemax = 0;
     long long jacc = 0;   // conduction current: sum of trunc(256 v_x^{n+1/2}) (exact)
-    unsigned ncand = 0;   // warp-uniform: candidates of this warp so far
+    unsigned nrec = 0;    // warp-uniform: records of this warp so far
+    unsigned qn = 0;      // warp-uniform: queued candidates
+
+    // The first m (<= 32) queued candidates, one per lane: the candidate's
+    // stream at this step (block 0) draws its next free flight (word 0) and,
+    // for electrons, the real/null test (word 1: energy against the total
+    // rate); records go to the warp's list in slot order, two uint4 each:
+    // electrons {slot, id, x, vx}{vy, vz, -, -} (real collisions), ions
+    // {slot, id, vx, vy}{vz, w1, w2, w3} (candidates, for the filter).
+    auto flush = [&](unsigned m) {
+        const bool has = (unsigned)lane < m;
+        const unsigned slot = has ? qs[lane] : 0u;
+        const float cx = has ? qx[lane] : 0.0f, cvx = has ? qv[lane] : 0.0f;
+        uint32_t id = 0u;
+        float cvy = 0.0f, cvz = 0.0f;
+        if (has) { id = ID[slot]; cvy = VY[slot]; cvz = VZ[slot]; }
+        bool rec = false;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (has) {
+            w = philox_id(pre, id);
+            TC[slot] = step_lo + sub * (1u + flight_gap(w.x, inv_lnq, kcap));
+            rec = (S == SP_E) ? electron_is_real(P, Tt, w.y, cvx, cvy, cvz, wemax) : true;
+        }
+        const unsigned cm = __ballot_sync(0xffffffffu, rec);
+        if (rec) {
+            const size_t q = r0 + nrec + __popc(cm & lt_mask);
+            if (S == SP_E) {
+                CAND[2 * q] = make_uint4(slot, id, __float_as_uint(cx), __float_as_uint(cvx));
+                CAND[2 * q + 1] = make_uint4(__float_as_uint(cvy), __float_as_uint(cvz), 0u, 0u);
+            } else {
+                CAND[2 * q] = make_uint4(slot, id, __float_as_uint(cvx), __float_as_uint(cvy));
+                CAND[2 * q + 1] = make_uint4(__float_as_uint(cvz), w.y, w.z, w.w);
+            }
+        }
+        nrec += __popc(cm);
+    };
+
     for (unsigned g0 = r0; g0 < r1; g0 += ROUND) {
         const bool full = g0 + ROUND <= r1;
         float xs[4], vxs[4];
-        uint32_t ids[4];
+        uint32_t tcs[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const unsigned i = g0 + 32u * k + lane;
             const bool inr = full || i < r1;
             xs[k] = inr ? X[i] : dead_marker();
             vxs[k] = inr ? VX[i] : 0.0f;
-            ids[k] = inr ? ID[i] : 0u;
+            tcs[k] = inr ? TC[i] : 0u;
         }
 #pragma unroll PUSH_UNROLL
         for (int k = 0; k < 4; ++k) {
             const unsigned i = g0 + 32u * k + lane;
-            float x = xs[k];
+            float x = xs[k], vx = vxs[k];
             bool cand = false;
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
             if (!is_dead(x)) {
-                float vx = vxs[k];
                 int j; float frac;
                 cell_of(x, inv_dx, Nc, j, frac);
                 const float Ep = fmaf(frac, Es[j + 1] - Es[j], Es[j]);
@@ -306,22 +384,36 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
                     int j2; float f2;
                     cell_of(x, inv_dx, Nc, j2, f2);
                     atomicAdd(&hist[j2], (1ull << 40) + (unsigned long long)cic_r(f2));
-                    if (np > 0) {
-                        w = philox4x32_10(make_uint4(step_lo, tag, 0u, step_hi), make_uint2(ids[k], seed));
-                        cand = uniform(w.x) < pmax;
-                    }
+                    // its free flight ends at this step: a collision candidate
+                    cand = (np > 0) && (tcs[k] == step_lo);
                 }
                 X[i] = x;
                 VX[i] = vx;
             }
-            // candidates go to the warp's list in slot order: {slot, w1, w2, w3}
             const unsigned cm = __ballot_sync(0xffffffffu, cand);
-            if (cand) CAND[r0 + ncand + __popc(cm & lt_mask)] = make_uint4(i, w.y, w.z, w.w);
-            ncand += __popc(cm);
+            if (cand) {
+                const unsigned q = qn + __popc(cm & lt_mask);
+                qs[q] = i; qx[q] = x; qv[q] = vx;
+            }
+            qn += __popc(cm);
+            if (qn >= 32u) {
+                __syncwarp();
+                flush(32u);
+                const unsigned rest = qn - 32u;    // < 32: lane q moves entry 32 + q
+                unsigned s0 = 0u;
+                float x0 = 0.0f, v0 = 0.0f;
+                if ((unsigned)lane < rest) { s0 = qs[32 + lane]; x0 = qx[32 + lane]; v0 = qv[32 + lane]; }
+                __syncwarp();
+                if ((unsigned)lane < rest) { qs[lane] = s0; qx[lane] = x0; qv[lane] = v0; }
+                qn = rest;
+                __syncwarp();
+            }
         }
     }
+    __syncwarp();
+    if (qn > 0u) flush(qn);
     pdl_trigger();
-    if (lane == 0) P.ccount[S][gw] = ncand;
+    if (lane == 0) P.ccount[S][gw] = nrec;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) jacc += __shfl_down_sync(0xffffffffu, jacc, o);
     if (lane == 0 && jacc) atomicAdd(&sh.jsum, (unsigned long long)jacc);
@@ -330,6 +422,7 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     if (nabs1) atomicAdd(&sh.absorbed[1], nabs1);
     if (nabs0 + nabs1 + nnf) atomicAdd(&sh.removed, nabs0 + nabs1 + nnf);
     if (nnf) atomicAdd(&sh.nonfinite, nnf);
+    if (S == SP_E && wemax) atomicAdd(&C->cnt.warn_emax, (unsigned long long)wemax);
     __syncthreads();
     unsigned long long* __restrict__ Qcopy = P.Qf[S] + (size_t)(blk & (QCOPIES - 1)) * Ng;
     for (int c = tid; c < Nc; c += BLOCK) {
@@ -353,25 +446,132 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     }
 }
 
-// Collision candidates of one species for this step: one warp per warp of
-// the particle kernel, walking that warp's candidate list in slot order.
-// Electrons are first filtered 32 at a time (energy against the total rate);
-// the real collisions, and all ion candidates, go through the out-of-line
-// kinematics 32 at a time.  Births are ranked with ballots and staged at the
-// particle warp's slot range with their count.
+// Free flights of the particles of species S drawn afresh at the current step
+// n (after a load, or when new tables change nu_max): the first push at or
+// after n plus sub K, K from word 0 of the particle's stream with tag
+// TAG_FLIGHT + S at step n.
+template <int S>
+__global__ void k_flight_init(Params P) {
+    DevCtrl* C = P.ctrl;
+    const unsigned long long n = C->step;
+    const unsigned cb = C->cur[S];
+    const unsigned long long ns = (C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap;
+    const float* __restrict__ X = P.sp[S].x[cb];
+    const uint32_t* __restrict__ ID = P.sp[S].id[cb];
+    uint32_t* __restrict__ TC = P.sp[S].tc[cb];
+    const unsigned sub = P.sub[S];
+    const uint32_t nf = (uint32_t)((n + sub - 1) / sub * sub);
+    const PhiloxPre pre = philox_pre((uint32_t)n, TAG_FLIGHT + (uint32_t)S, (uint32_t)(n >> 32), P.seed);
+    const float inv_lnq = P.inv_lnq[S], kcap = P.kcap[S];
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < ns;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        if (is_dead(X[i])) continue;
+        TC[i] = nf + sub * flight_gap(philox_id(pre, ID[i]).x, inv_lnq, kcap);
+    }
+}
+
+// Filter of the ion candidates of one species (one warp per warp of the
+// particle kernel, walking its candidate list in slot order): the target
+// sampled from the gas Maxwellian, the relative energy and the total rate
+// against u1 nu_max, the same arithmetic as the start of collide().  It reads
+// the records only (they carry the velocities and the Philox words).  The
+// real collisions keep their records, compacted in place at the start of the
+// list (a record is written only over one already read), and the list length
+// becomes their number.  This kernel carries no kinematics, so it runs at a
+// far higher occupancy than the kinematics kernel, which then sees only the
+// real collisions.
+template <int S>
+__device__ __forceinline__ void filter_body(const Params& P, unsigned blk, unsigned nblk) {
+    __shared__ float tot[NGRID];
+    __shared__ unsigned sh_wtries, sh_wemax;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (tid == 0) { sh_wtries = 0u; sh_wemax = 0u; }
+    stage_total(P, S, tot);
+    __syncthreads();
+    DevCtrl* C = P.ctrl;
+    const unsigned long long step = C->step;
+    const unsigned nslots = (unsigned)((C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap);
+    uint4* CAND = P.cand[S];
+    const unsigned W = P.push_warps[S];
+    const unsigned R = warp_range_len(nslots, W);
+    const float numax = P.numax[S], kap = P.kappa[S], sig = P.sig_gas;
+    unsigned wtries = 0, wemax = 0;
+    for (unsigned gw = blk * WARPS + warp; gw < W; gw += nblk * WARPS) {
+        const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
+        const unsigned n = P.ccount[S][gw];
+        unsigned nreal = 0;   // warp-uniform
+        for (unsigned c0 = 0; c0 < n; c0 += 64) {
+            uint4 a[2], b[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const unsigned ci = c0 + 32u * k + lane;
+                const bool in = ci < n;
+                a[k] = in ? CAND[2 * (size_t)(r0 + ci)] : make_uint4(0u, 0u, 0u, 0u);
+                b[k] = in ? CAND[2 * (size_t)(r0 + ci) + 1] : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (c0 + 32u * k >= n) break;   // warp-uniform
+                const bool in = c0 + 32u * k + lane < n;
+                bool real = false;
+                if (in) {
+                    Stream st;
+                    st.resume(a[k].y, P.seed, step, SpeciesTraits<S>::tag, make_uint4(a[k].y, b[k].y, b[k].z, b[k].w), 1);
+                    const float u1 = uniform(st.next());
+                    float vtx, vty, vtz;
+                    maxwellian(st, sig, vtx, vty, vtz, wtries);
+                    const float gx = __uint_as_float(a[k].z) - vtx, gy = __uint_as_float(a[k].w) - vty,
+                                gz = __uint_as_float(b[k].x) - vtz;
+                    const float E = kap * dot3(gx, gy, gz, gx, gy, gz);
+                    int i; float w; bool above;
+                    grid_locate(E, i, w, above);
+                    if (above) ++wemax;
+                    real = (u1 * numax) < grid_interp(tot, 1, 0, i, w);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, real);
+                if (real) {
+                    const size_t q = r0 + nreal + __popc(m & lt_mask);
+                    CAND[2 * q] = a[k];
+                    CAND[2 * q + 1] = b[k];
+                }
+                nreal += __popc(m);
+            }
+        }
+        if (lane == 0) P.ccount[S][gw] = nreal;
+    }
+    pdl_trigger();
+    if (wtries) atomicAdd(&sh_wtries, wtries);
+    if (wemax) atomicAdd(&sh_wemax, wemax);
+    __syncthreads();
+    if (tid == 0) {
+        if (sh_wtries) atomicAdd(&C->cnt.warn_tries, (unsigned long long)sh_wtries);
+        if (sh_wemax) atomicAdd(&C->cnt.warn_emax, (unsigned long long)sh_wemax);
+    }
+}
+
+// Real collisions of one species for this step.  Each warp takes two lists
+// of the particle kernel's warps at once, one per half-warp (16 lanes; a list
+// holds about a dozen records at the method's rates), and walks them in slot
+// order, 16 records per pass through the out-of-line kinematics, so the
+// lists of a step run in one wave of resident warps.  Electron records carry
+// the particle (slot, id, x, v) and block 0 of its Philox stream is drawn
+// again; ion records carry the slot, id, v and that block (its first word,
+// the candidate draw, is spent), x is read from the array.  Births are
+// ranked with ballots within the half-warp and staged at the particle warp's
+// slot range with their count.
+constexpr int SEG = 16;
+constexpr int SEGS = 32 / SEG;
+
 template <int S>
 __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigned nblk) {
     __shared__ unsigned events[MAXPROC];
     __shared__ unsigned sh_removed, sh_wtries, sh_wemax;
-    __shared__ uint4 q2w_all[WARPS][Q2];
-    __shared__ unsigned q2s_all[WARPS][Q2];
-    __shared__ float4 q2v_all[WARPS][Q2];     // x, vx, vy, vz of the queued particle
     const int np = P.nproc[S];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    uint4* q2w = q2w_all[warp];
-    unsigned* q2s = q2s_all[warp];
-    float4* q2v = q2v_all[warp];
+    const unsigned seg = (unsigned)lane / SEG, sl = (unsigned)lane % SEG;
+    const unsigned seg_mask = ((1u << SEG) - 1u) << (seg * SEG);
+    const unsigned lt_mask = ((1u << lane) - 1u) & seg_mask;   // lanes below, same half-warp
     const float* __restrict__ cum = P.cum[S];
     if (tid < MAXPROC) events[tid] = 0u;
     if (tid == 0) { sh_removed = 0u; sh_wtries = 0u; sh_wemax = 0u; }
@@ -385,7 +585,6 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
     float* __restrict__ VX = P.sp[S].vx[cb];
     float* __restrict__ VY = P.sp[S].vy[cb];
     float* __restrict__ VZ = P.sp[S].vz[cb];
-    const uint32_t* __restrict__ ID = P.sp[S].id[cb];
     const uint4* __restrict__ CAND = P.cand[S];
     const float inv_dx = P.inv_dx;
     const int Nc = P.Nc;
@@ -394,21 +593,39 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
     unsigned* cnt2 = (S == SP_E) ? P.wcount[B_OM_FROM_E] : (S == SP_OM ? P.wcount[B_E_FROM_OM] : nullptr);
     const unsigned W = P.push_warps[S];
     const unsigned R = warp_range_len(nslots, W);
+    const PhiloxPre pre = philox_pre((uint32_t)step, SpeciesTraits<S>::tag, (uint32_t)(step >> 32), P.seed);
     unsigned wtries = 0, wemax = 0, nremoved = 0;
 
-    for (unsigned gw = blk * WARPS + warp; gw < W; gw += nblk * WARPS) {
-        const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
-        const unsigned n = P.ccount[S][gw];
-        unsigned q2n = 0, nb1 = 0, nb2 = 0;   // warp-uniform
-
-        // kinematics of lane's particle (has = lane holds one), births ranked
-        auto run_real = [&](bool has, unsigned slot, uint4 w0, float x, float vx, float vy, float vz) {
+    for (unsigned gb = (blk * WARPS + warp) * SEGS; gb < W; gb += nblk * WARPS * SEGS) {
+        const unsigned gw = gb + seg;                  // this half-warp's list
+        const bool valid = gw < W;
+        const unsigned r0 = !valid ? 0u : ((gw * (unsigned long long)R < nslots) ? gw * R : nslots);
+        const unsigned n = valid ? P.ccount[S][gw] : 0u;
+        const unsigned nmax = max(n, __shfl_xor_sync(0xffffffffu, n, SEG));
+        unsigned nb1 = 0, nb2 = 0;   // half-warp-uniform
+        for (unsigned c0 = 0; c0 < nmax; c0 += SEG) {
+            const unsigned ci = c0 + sl;
+            const bool has = ci < n;
+            uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+            if (has) { a = CAND[2 * (size_t)(r0 + ci)]; b = CAND[2 * (size_t)(r0 + ci) + 1]; }
+            const unsigned slot = a.x;
+            float x, vx, vy, vz;
+            uint4 w0;
+            if (S == SP_E) {
+                x = __uint_as_float(a.z); vx = __uint_as_float(a.w);
+                vy = __uint_as_float(b.x); vz = __uint_as_float(b.y);
+                w0 = has ? philox_id(pre, a.y) : make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                x = has ? X[slot] : 0.0f;
+                vx = __uint_as_float(a.z); vy = __uint_as_float(a.w); vz = __uint_as_float(b.x);
+                w0 = make_uint4(0u, b.y, b.z, b.w);
+            }
+            w0.x = a.y;   // word 0 (the candidate draw) is spent: it carries the id
             int bkind = 0;
             float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
             if (has) {
-                const uint32_t id = w0.x;   // word 0 (the candidate draw) is spent: it carries the id
                 bool alive;
-                const int k = collide<S>(P, cum, np, step, id, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
+                const int k = collide<S>(P, cum, np, step, a.y, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
                 if (k >= 0) {
                     atomicAdd(&events[k], 1u);
                     if (alive) {
@@ -421,8 +638,8 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
                 }
             }
             if (births) {
-                const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1);
-                const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2);
+                const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1) & seg_mask;
+                const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2) & seg_mask;
                 // staged for the end-of-step kernel, which places them; their
                 // charge goes to Qb now
                 if (S == SP_E) {
@@ -446,68 +663,8 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
                 nb2 += __popc(m2);
             }
             __syncwarp();
-        };
-
-        auto run_queue = [&](unsigned m) {
-            const bool has = (unsigned)lane < m;
-            const float4 v = has ? q2v[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            run_real(has, has ? q2s[lane] : 0u, has ? q2w[lane] : make_uint4(0u, 0u, 0u, 0u), v.x, v.y, v.z, v.w);
-        };
-        // 128 candidates per pass, four per lane, all their loads in flight together
-        for (unsigned c0 = 0; c0 < n; c0 += 128) {
-            unsigned slot[4];
-            uint4 w0[4];
-            float4 v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const unsigned ci = c0 + 32u * k + lane;
-                if (ci < n) {
-                    const uint4 e = CAND[r0 + ci];
-                    slot[k] = e.x;
-                    w0[k] = make_uint4(0u, e.y, e.z, e.w);
-                } else {
-                    slot[k] = 0xFFFFFFFFu;
-                    w0[k] = make_uint4(0u, 0u, 0u, 0u);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const unsigned sl = slot[k];
-                const bool in = sl != 0xFFFFFFFFu;
-                v[k] = in ? make_float4(X[sl], VX[sl], VY[sl], VZ[sl]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                w0[k].x = in ? ID[sl] : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (c0 + 32u * k >= n) break;          // warp-uniform
-                const bool in = slot[k] != 0xFFFFFFFFu;
-                if (S != SP_E) {
-                    // ion candidates all need the target sample: straight on
-                    run_real(in, in ? slot[k] : 0u, w0[k], v[k].x, v[k].y, v[k].z, v[k].w);
-                    continue;
-                }
-                const bool real = in && electron_is_real(P, cum, np, w0[k], v[k].y, v[k].z, v[k].w);
-                const unsigned m = __ballot_sync(0xffffffffu, real);
-                if (real) {
-                    const unsigned q = q2n + __popc(m & lt_mask);
-                    q2s[q] = slot[k]; q2w[q] = w0[k]; q2v[q] = v[k];
-                }
-                q2n += __popc(m);
-                __syncwarp();
-                if (q2n >= 32u) {
-                    run_queue(32u);
-                    const unsigned rest = q2n - 32u;    // < 32: lane q moves entry 32 + q
-                    if ((unsigned)lane < rest) {
-                        const unsigned s0 = q2s[32 + lane]; const uint4 w1 = q2w[32 + lane]; const float4 v1 = q2v[32 + lane];
-                        q2s[lane] = s0; q2w[lane] = w1; q2v[lane] = v1;
-                    }
-                    q2n = rest;
-                    __syncwarp();
-                }
-            }
         }
-        if (q2n > 0) run_queue(q2n);
-        if (births && lane == 0) {
+        if (births && valid && sl == 0) {
             if (cnt1) cnt1[gw] = nb1;
             if (cnt2) cnt2[gw] = nb2;
         }
@@ -537,6 +694,16 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand(Params P)
     cand_body<S>(P, blockIdx.x, gridDim.x);
 }
 
+// The ion filter is light (no kinematics): more resident blocks per SM.
+#ifndef O2PIC_FILTER_MIN_BLOCKS
+#define O2PIC_FILTER_MIN_BLOCKS 3
+#endif
+template <int S>
+__global__ void __launch_bounds__(BLOCK, O2PIC_FILTER_MIN_BLOCKS) k_filter(Params P) {
+    pdl_wait();
+    filter_body<S>(P, blockIdx.x, gridDim.x);
+}
+
 // Batched launches: block b works for discharge map[b].x as its block
 // map[b].y of map[b].z, with that discharge's parameters copied to shared
 // memory (load_params).
@@ -559,6 +726,17 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_CAND_MIN_BLOCKS) k_cand_b(const P
     load_params(sP, all + m.x);
     if (sP.nproc[S] == 0) return;   // block-uniform
     cand_body<S>(sP, m.y, m.z);
+}
+
+template <int S>
+__global__ void __launch_bounds__(BLOCK, O2PIC_FILTER_MIN_BLOCKS) k_filter_b(const Params* __restrict__ all,
+                                                                            const uint4* __restrict__ map) {
+    __shared__ Params sP;
+    pdl_wait();
+    const uint4 m = map[blockIdx.x];
+    load_params(sP, all + m.x);
+    if (sP.nproc[S] == 0) return;   // block-uniform
+    filter_body<S>(sP, m.y, m.z);
 }
 
 // Deposit of all live particles of one species into Qf (used after a load).
@@ -597,8 +775,17 @@ __global__ void __launch_bounds__(BLOCK) k_deposit(Params P) {
 }  // namespace
 
 size_t push_smem_bytes(int species, const Params& P) {
-    (void)species;
-    return align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng) + sizeof(unsigned long long) * P.Ng;
+    const size_t base = align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng) +
+                        sizeof(unsigned long long) * P.Ng + sizeof(PushQueue);
+    return species == SP_E ? base + sizeof(float) * NGRID : base;
+}
+
+void launch_flight_init(int species, const Params& P, cudaStream_t s) {
+    const unsigned long long cap = P.sp[species].cap;
+    const int grid = (int)(cap / 256 + 1 < 4096 ? cap / 256 + 1 : 4096);
+    if (species == SP_E) k_flight_init<SP_E><<<grid, 256, 0, s>>>(P);
+    else if (species == SP_OM) k_flight_init<SP_OM><<<grid, 256, 0, s>>>(P);
+    else k_flight_init<SP_OP><<<grid, 256, 0, s>>>(P);
 }
 
 void launch_push(int species, const Params& P, int grid, cudaStream_t s) {
@@ -618,6 +805,16 @@ void launch_cand_batched(int species, const Params* all, const uint4* map, int n
     if (species == SP_E) launch_pdl(k_cand_b<SP_E>, nblocks, BLOCK, 0, s, all, map);
     else if (species == SP_OM) launch_pdl(k_cand_b<SP_OM>, nblocks, BLOCK, 0, s, all, map);
     else launch_pdl(k_cand_b<SP_OP>, nblocks, BLOCK, 0, s, all, map);
+}
+
+void launch_filter(int species, const Params& P, int grid, cudaStream_t s) {
+    if (species == SP_OM) launch_pdl(k_filter<SP_OM>, grid, BLOCK, 0, s, P);
+    else if (species == SP_OP) launch_pdl(k_filter<SP_OP>, grid, BLOCK, 0, s, P);
+}
+
+void launch_filter_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s) {
+    if (species == SP_OM) launch_pdl(k_filter_b<SP_OM>, nblocks, BLOCK, 0, s, all, map);
+    else if (species == SP_OP) launch_pdl(k_filter_b<SP_OP>, nblocks, BLOCK, 0, s, all, map);
 }
 
 void launch_cand(int species, const Params& P, int grid, cudaStream_t s) {

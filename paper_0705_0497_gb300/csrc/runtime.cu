@@ -90,6 +90,7 @@ struct o2pic_ctx {
     bool dirty = true;
     bool have_tables = false;
     bool loaded[NSP] = {false, false, false};
+    bool flight_ok[NSP] = {false, false, false};   // free flights known (else drawn by prepare)
     int latched = 0;
     int grid_push[NSP] = {0, 0, 0};
     int grid_pair = 0, grid_pair_e = 0, grid_compact = 0, grid_deposit = 0;
@@ -219,6 +220,9 @@ void set_constants(o2pic_ctx* c) {
         P.a_m[s] = (float)(mass[s] / (mass[s] + g.M_gas));
         P.a_M[s] = (float)(g.M_gas / (mass[s] + g.M_gas));
         P.sig_birth[s] = (float)std::sqrt(KB * g.T_gas / mass[s]);
+        P.sub[s] = (s == SP_E) ? 1u : (unsigned)g.ion_subcycle;
+        P.inv_lnq[s] = -INFINITY;
+        P.kcap[s] = (float)std::floor(1073741824.0 / (double)P.sub[s]);
     }
     P.delta_el = (float)(2.0 * g.m_e / g.M_gas);
     P.sig_gas = (float)std::sqrt(KB * g.T_gas / g.M_gas);
@@ -275,6 +279,13 @@ int prepare(o2pic_ctx* c, cudaStream_t s) {
     }
     for (int sp = 0; sp < NSP; ++sp)
         launch(c, KK_DEPOSIT, s, [&] { launch_deposit(sp, P, c->grid_deposit, s); });
+    // free flights of particles whose flights are not known, drawn at this step
+    for (int sp = 0; sp < NSP; ++sp)
+        if (!c->flight_ok[sp]) {
+            launch_flight_init(sp, P, s);
+            c->launches += 1;
+            c->flight_ok[sp] = true;
+        }
     launch(c, KK_FIELD, s, [&] { launch_field(P, 1, 7, s); });
     c->ring_start = c->host_step;
     c->dirty = false;
@@ -294,9 +305,15 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
         if (P.nproc[SP_E]) launch(c, KK_CAND_E, s, [&] { launch_cand(SP_E, P, c->grid_push[SP_E], s); });
         if (ion) {
             launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
-            if (P.nproc[SP_OM]) launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
+            if (P.nproc[SP_OM]) {
+                launch(c, KK_FILT_OM, s, [&] { launch_filter(SP_OM, P, c->grid_push[SP_OM], s); });
+                launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
+            }
             launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
-            if (P.nproc[SP_OP]) launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
+            if (P.nproc[SP_OP]) {
+                launch(c, KK_FILT_OP, s, [&] { launch_filter(SP_OP, P, c->grid_push[SP_OP], s); });
+                launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
+            }
             if (P.have_recomb) {
                 const PairSpec R{SP_E, SP_OP, P.rhist[0], P.rhist[1], P.rtot, P.Ktab_r, P.Kmax_r_hi, P.kappa_r,
                                  TAG_REC, TAG_SHIFT_REC, P.rremoval, &c->d_ctrl->rremovals, P.max_rremovals,
@@ -390,6 +407,7 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
             TRY(ctx_alloc(c, &P.sp[s].vy[b], cap));
             TRY(ctx_alloc(c, &P.sp[s].vz[b], cap));
             TRY(ctx_alloc(c, &P.sp[s].id[b], cap));
+            TRY(ctx_alloc(c, &P.sp[s].tc[b], cap));
         }
         float* cum;
         TRY(ctx_alloc(c, &cum, (size_t)NGRID * MAXPROC));
@@ -431,7 +449,7 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     TRY(ctx_alloc(c, &P.wcount[B_OM_FROM_E], max_warps));
     TRY(ctx_alloc(c, &P.wcount[B_E_FROM_OM], max_warps));
     for (int s = 0; s < NSP; ++s) {
-        TRY(ctx_alloc(c, &P.cand[s], cfg->capacity[s] + 128));
+        TRY(ctx_alloc(c, &P.cand[s], 2 * (cfg->capacity[s] + 128)));
         TRY(ctx_alloc(c, &P.ccount[s], max_warps));
     }
     const unsigned long long tiles_ion = std::max(ceil_div(cfg->capacity[SP_OM], TILE), ceil_div(cfg->capacity[SP_OP], TILE)) + 1;
@@ -551,6 +569,9 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
         P.nproc[s] = np;
         P.numax[s] = (float)mx;
         P.pmax[s] = (float)(1.0 - std::exp(-mx * dts));
+        // 1 / ln(1 - P_max) for the free-flight draw; -inf when nu_max = 0
+        P.inv_lnq[s] = (float)(-1.0 / (mx * dts));
+        c->flight_ok[s] = false;   // flights drawn with the old nu_max: draw afresh
         bool births = false;
         for (int k = 0; k < np; ++k) {
             P.kind[s][k] = sp[s][k].kind;
@@ -605,6 +626,7 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
         P.push_warps[s] = (unsigned)c->grid_push[s] * (BLOCK / 32);
     }
     c->have_tables = true;
+    c->dirty = true;
     c->gen += 1;
     return O2PIC_OK;
 }
@@ -663,6 +685,7 @@ int o2pic_load_particles(o2pic_ctx* c, int species, const float* x, const float*
     }
     c->host_step = h.step;
     c->loaded[species] = true;
+    c->flight_ok[species] = false;
     c->dirty = true;
     c->gen += 1;
     return O2PIC_OK;
@@ -754,7 +777,7 @@ int o2pic_read_particles(o2pic_ctx* c, int species, float* x, float* vx, float* 
     c->gepoch += 1;
     cudaMemsetAsync(c->d_gticket, 0, sizeof(unsigned), s);
     launch_gather(species, c->P, c->grid_compact, (1ull << 60) | c->gepoch, c->d_gticket, c->d_gflag, c->d_gval,
-                  dx_, dvx, dvy, dvz, did, m, c->d_gcount, s);
+                  dx_, dvx, dvy, dvz, did, nullptr, m, c->d_gcount, s);
     c->launches += 1;
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && mem_kind == O2PIC_HOST) {
@@ -765,6 +788,66 @@ int o2pic_read_particles(o2pic_ctx* c, int species, float* x, float* vx, float* 
         if (e == cudaSuccess) e = cudaMemcpy(id, did, 4 * m, cudaMemcpyDeviceToHost);
     }
     for (void* q : tmp) cudaFree(q);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return check_flags(c);
+}
+
+int o2pic_load_flight(o2pic_ctx* c, int species, const uint32_t* tc, uint64_t n, int mem_kind, void* stream) {
+    if (!c || species < 0 || species >= NSP || (n > 0 && !tc)) return O2PIC_E_INVALID_ARG;
+    if (mem_kind != O2PIC_HOST && mem_kind != O2PIC_DEVICE) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    DevCtrl h;
+    cudaError_t e = cudaMemcpy(&h, c->d_ctrl, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    // only right after a load: every slot live, in load order
+    if (h.slots[species] != n || h.live[species] != n) return O2PIC_E_INVALID_ARG;
+    cudaStream_t s = pick(c, stream);
+    if (n > 0) {
+        e = cudaMemcpyAsync(c->P.sp[species].tc[h.cur[species]], tc, sizeof(uint32_t) * n,
+                            mem_kind == O2PIC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    c->flight_ok[species] = true;
+    c->gen += 1;
+    return O2PIC_OK;
+}
+
+int o2pic_read_flight(o2pic_ctx* c, int species, uint32_t* tc, uint64_t cap, uint64_t* n, int mem_kind) {
+    if (!c || species < 0 || species >= NSP || !n) return O2PIC_E_INVALID_ARG;
+    if (mem_kind != O2PIC_HOST && mem_kind != O2PIC_DEVICE) return O2PIC_E_INVALID_ARG;
+    if (c->dirty && c->have_tables) {
+        // flights not drawn yet: draw them (as the next step would)
+        cudaError_t e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        int rc = prepare(c, c->stream);
+        if (rc) return rc;
+    }
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    cudaStream_t s = c->stream;
+    DevCtrl h;
+    cudaError_t e = cudaMemcpy(&h, c->d_ctrl, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    *n = h.live[species];
+    const uint64_t m = std::min<uint64_t>(cap, h.live[species]);
+    if (m == 0 || !tc) return rc;
+    uint32_t* dtc = tc;
+    void* tmp = nullptr;
+    if (mem_kind == O2PIC_HOST) {
+        e = cudaMalloc(&tmp, 4 * m);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        dtc = (uint32_t*)tmp;
+    }
+    c->gepoch += 1;
+    cudaMemsetAsync(c->d_gticket, 0, sizeof(unsigned), s);
+    launch_gather(species, c->P, c->grid_compact, (1ull << 60) | c->gepoch, c->d_gticket, c->d_gflag, c->d_gval,
+                  nullptr, nullptr, nullptr, nullptr, nullptr, dtc, m, c->d_gcount, s);
+    c->launches += 1;
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && mem_kind == O2PIC_HOST) e = cudaMemcpy(tc, dtc, 4 * m, cudaMemcpyDeviceToHost);
+    if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return check_flags(c);
 }
@@ -1053,8 +1136,9 @@ void enqueue_fused(o2pic_batch* b, cudaStream_t s) {
         if (ion) {
             for (int sp = SP_OM; sp <= SP_OP; ++sp) {
                 launch_push_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], b->smem_push, s);
+                launch_filter_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
                 launch_cand_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
-                launches += 2;
+                launches += 3;
             }
             if (b->any_recomb) {
                 launch_pair_hist_batched(b->dP, b->dR, b->dmap + b->map_rh, b->nb_rh, b->smem_hist, s);

@@ -33,13 +33,15 @@ def make_pair(cfg, counts, T_eV, procs, capacity=None, compact_check=0, state=No
 
 
 def compare_particles(g, o, rtol=1e-5, atol_x=None, atol_v=1e-3):
-    """Per-particle comparison in array order; returns the max relative differences."""
+    """Per-particle comparison in array order (ids and free flights exactly);
+    returns the max relative differences."""
     worst = {}
     for s in range(3):
-        a = g.particles(s)
+        a = g.particles(s, flight=True)
         b = o.particles(s)
         assert len(a["id"]) == len(b["id"]), (s, len(a["id"]), len(b["id"]))
         assert np.array_equal(a["id"], b["id"]), s
+        assert np.array_equal(a["tc"], o.flight(s)), s
         for k in ("x", "vx", "vy", "vz"):
             x, y = a[k].astype(np.float64), b[k]
             if len(x) == 0:

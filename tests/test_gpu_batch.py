@@ -28,8 +28,8 @@ def _discharge(cfg, counts, T, procs):
 
 def _same(a, b):
     for s in range(3):
-        pa, pb = a.particles(s), b.particles(s)
-        for k in ("x", "vx", "vy", "vz", "id"):
+        pa, pb = a.particles(s, flight=True), b.particles(s, flight=True)
+        for k in ("x", "vx", "vy", "vz", "id", "tc"):
             assert np.array_equal(pa[k], pb[k]), (s, k)
     sa, sb = a.stats(), b.stats()
     for k in sa:

@@ -34,7 +34,8 @@ def _check_species(o, g_before, g_after, s, step, E, rng):
     same = gone = 0
     for t, i in enumerate(pick):
         pid = int(pids[t])
-        alive, st, _ = o.update_particle(s, step, Ef, [a["x"][i], a["vx"][i], a["vy"][i], a["vz"][i]], pid)
+        alive, st, _, tc1 = o.update_particle(s, step, Ef, [a["x"][i], a["vx"][i], a["vy"][i], a["vz"][i]], pid,
+                                              tc=int(a["tc"][i]))
         if not alive:
             assert not present[t], (s, pid)
             gone += 1
@@ -47,6 +48,7 @@ def _check_species(o, g_before, g_after, s, step, E, rng):
         j = border[k[t]]
         got = np.array([b["x"][j], b["vx"][j], b["vy"][j], b["vz"][j]], np.float64)
         assert np.array_equal(got, np.asarray(st, np.float32).astype(np.float64)), (s, pid, got, st)
+        assert int(b["tc"][j]) == tc1, (s, pid, int(b["tc"][j]), tc1)
         same += 1
     return same, gone
 
@@ -75,10 +77,10 @@ def test_full_size_sampled_particles_charge_and_field(torch_cuda, name):
     for step, species in checks:
         while g.stats()["step"] < step:
             g.step(1)
-        before = [g.particles(s) for s in range(3)]
+        before = [g.particles(s, flight=True) for s in range(3)]
         _, E = g.field()
         g.step(1)
-        after = [g.particles(s) for s in range(3)]
+        after = [g.particles(s, flight=True) for s in range(3)]
         for s in species:
             same, gone = _check_species(o, before[s], after[s], s, step, E, rng)
             assert same > 0.9 * min(SAMPLE, len(before[s]["id"])), (s, same, gone)

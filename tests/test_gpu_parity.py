@@ -385,7 +385,7 @@ def test_checkpoint_and_resume_bit_for_bit(torch_cuda, save_at, S, check):
     a.set_processes(procs)
     a.load_state(st)
     a.step(save_at)
-    saved = [a.particles(s) for s in range(3)]
+    saved = [a.particles(s, flight=True) for s in range(3)]
     s40 = a.stats()
     a.step(40)
     b = api.Discharge(cfg, cap, compact_check=check)
@@ -396,7 +396,7 @@ def test_checkpoint_and_resume_bit_for_bit(torch_cuda, save_at, S, check):
         b.set_next_id(s, s40[f"next_id_{s}"])
     b.step(40)
     for s in range(3):
-        pa, pb = a.particles(s), b.particles(s)
-        for k in ("x", "vx", "vy", "vz", "id"):
+        pa, pb = a.particles(s, flight=True), b.particles(s, flight=True)
+        for k in ("x", "vx", "vy", "vz", "id", "tc"):
             assert np.array_equal(pa[k], pb[k]), (s, k)
     assert np.array_equal(a.field()[1], b.field()[1])

@@ -257,7 +257,7 @@ def test_free_flight_uniform_field(oracle_mod, precision, rtol):
     st = np.array([x0, v0, 1.0, -2.0])
     xs = [x0]
     for n in range(60):
-        alive, st, births = o.update_particle(0, n, Ef, st, 1)
+        alive, st, births, _ = o.update_particle(0, n, Ef, st, 1)
         assert alive and len(births) == 0
         k = n + 1
         xref = x0 + k * v0 * dt + a * dt * dt * k * (k + 1) / 2
@@ -272,9 +272,9 @@ def test_absorbing_walls_and_accounting(oracle_mod):
     o.set_processes([])
     Ef = np.zeros(17)
     L, dt = cfg["L"], cfg["dt"]
-    alive, st, _ = o.update_particle(0, 0, Ef, np.array([0.5 * L, -0.6 * L / dt, 0, 0]), 1)
+    alive, st, _, _ = o.update_particle(0, 0, Ef, np.array([0.5 * L, -0.6 * L / dt, 0, 0]), 1)
     assert not alive
-    alive, st, _ = o.update_particle(0, 0, Ef, np.array([0.5 * L, 0.5 * L / dt * 1.0001, 0, 0]), 1)
+    alive, st, _, _ = o.update_particle(0, 0, Ef, np.array([0.5 * L, 0.5 * L / dt * 1.0001, 0, 0]), 1)
     assert not alive
     c = o.counters()
     assert c["absorbed_0_0"] == 1 and c["absorbed_0_1"] == 1
@@ -374,7 +374,7 @@ def test_elastic_energy_loss_is_2m_over_M(oracle_mod):
     loss, cosx = [], []
     for i in range(N):
         st0 = np.array([p["x"][i], p["vx"][i], p["vy"][i], p["vz"][i]], np.float64)
-        alive, st, _ = o.update_particle(0, 0, Ef, st0, i)
+        alive, st, _, _ = o.update_particle(0, 0, Ef, st0, i)
         if not np.array_equal(st[1:], st0[1:]):
             e0, e1 = (st0[1:] ** 2).sum(), (st[1:] ** 2).sum()
             loss.append((e0 - e1) / e0)
@@ -562,7 +562,7 @@ def test_excitation_and_ionization_energy_balance(oracle_mod):
         E0 = 3.0 + 20.0 * rng.random()
         d = rng.standard_normal(3); d /= np.linalg.norm(d)
         st0 = np.concatenate([[0.01], math.sqrt(E0 / kap) * d])
-        alive, st, b = o.update_particle(0, 0, Ef, st0, i)
+        alive, st, b, _ = o.update_particle(0, 0, Ef, st0, i)
         E1 = kap * (st[1:] ** 2).sum()
         if E1 != pytest.approx(E0, rel=1e-12):
             nre += 1
@@ -576,7 +576,7 @@ def test_excitation_and_ionization_energy_balance(oracle_mod):
         E0 = 13.0 + 80.0 * rng.random()
         d = rng.standard_normal(3); d /= np.linalg.norm(d)
         st0 = np.concatenate([[0.01], math.sqrt(E0 / kap) * d])
-        alive, st, b = o.update_particle(0, 0, Ef, st0, i)
+        alive, st, b, _ = o.update_particle(0, 0, Ef, st0, i)
         assert alive
         if len(b):
             assert sorted(b[:, 0]) == [0, 2] and np.all(b[:, 1] == st[0])
@@ -601,7 +601,7 @@ def test_attachment_and_detachment_products(oracle_mod):
     vs = []
     for i in range(3000):
         st0 = np.array([0.0123, 3e5, -2e5, 1e5])
-        alive, st, b = o.update_particle(0, 0, Ef, st0, i)
+        alive, st, b, _ = o.update_particle(0, 0, Ef, st0, i)
         if not alive:
             assert len(b) == 1 and b[0, 0] == 1
             assert b[0, 1] == pytest.approx(0.0123 + 3e5 * cfg["dt"], rel=1e-12)
@@ -615,7 +615,7 @@ def test_attachment_and_detachment_products(oracle_mod):
     n = 0
     for i in range(3000):
         st0 = np.array([0.01, 4000.0, 0.0, 0.0])
-        alive, st, b = o.update_particle(1, 0, Ef, st0, i)
+        alive, st, b, _ = o.update_particle(1, 0, Ef, st0, i)
         if not alive:
             assert len(b) == 1 and b[0, 0] == 0
             Ee = 0.5 * ME * (b[0, 2:] ** 2).sum() / QE
@@ -892,3 +892,61 @@ def test_process_choice_mono_energetic_beams(oracle_mod, precision):
         tot = sum(c[f"events_0_{k}"] for k in range(len(procs)))
         q_tot = pmax * float(np.interp(E0, xsec.GRID, cum[:, -1])) / numax
         assert abs(tot - N * q_tot) < 5 * math.sqrt(N * q_tot) + 1
+
+
+# ------------------------------------------------------------ free flights
+@pytest.mark.parametrize("precision", [64, 32])
+def test_free_flight_gaps_are_geometric(oracle_mod, precision):
+    """The free-flight sampler: the number K of pushes before the next
+    candidate, from a uniform 32-bit word, is Geometric(P_max) with
+    P_max = 1 - exp(-nu_max dt): chi-square on K = 0..24 and the mean
+    (1 - P)/P.  (A Bernoulli(P_max) test at every push has the same law.)"""
+    cfg = _cfg(p=10.0)
+    nO2 = cfg["p"] / (KB * cfg["T_gas"])
+    P = 0.2
+    nu0 = -math.log(1 - P) / cfg["dt"]
+    o = oracle_mod.Oracle(cfg, precision)
+    o.set_processes([xsec.constant_rate_process(0, xsec.ELASTIC, nu0, nO2, ME)])
+    pmax = o.table(0)[3]
+    assert pmax == pytest.approx(P, rel=1e-6)
+    rng = np.random.default_rng(21)
+    words = rng.integers(0, 2 ** 32, 200_000, dtype=np.uint64)
+    K = np.array([o.flight_gap(0, int(w)) for w in words])
+    assert K.min() == 0
+    kmax = 24
+    obs = np.bincount(np.minimum(K, kmax + 1), minlength=kmax + 2)
+    pk = np.array([(1 - P) ** k * P for k in range(kmax + 1)] + [(1 - P) ** (kmax + 1)])
+    chi2 = ((obs - len(K) * pk) ** 2 / (len(K) * pk)).sum()
+    assert stats.chi2.sf(chi2, kmax + 1) > 1e-4, chi2
+    mean = (1 - P) / P
+    assert abs(K.mean() - mean) < 5 * math.sqrt((1 - P) / P ** 2 / len(K))
+
+
+def test_candidates_per_step_are_binomial(oracle_mod):
+    """With a process whose rate equals nu_max at every energy every candidate
+    is a real collision, so the collisions of each step are
+    Binomial(N, P_max): free flights drawn at the load and renewed at each
+    candidate give a candidate with probability P_max at every push."""
+    cfg = _cfg(p=10.0)
+    nO2 = cfg["p"] / (KB * cfg["T_gas"])
+    P = 0.3
+    nu0 = -math.log(1 - P) / cfg["dt"]
+    o = oracle_mod.Oracle(cfg, 32)
+    o.set_processes([xsec.constant_rate_process(0, xsec.ELASTIC, nu0, nO2, ME)])
+    N = 50_000
+    p = dict(x=np.full(N, 0.5 * cfg["L"], np.float32), vx=np.zeros(N, np.float32), vy=np.full(N, 1.0e5, np.float32),
+             vz=np.zeros(N, np.float32), id=np.arange(N, dtype=np.uint32))
+    _empty(o)
+    _load(o, 0, p)
+    prev = 0
+    counts = []
+    for n in range(12):
+        o.step(1)
+        ev = o.counters()["events_0_0"]
+        counts.append(ev - prev)
+        prev = ev
+    for c in counts:
+        assert abs(c - N * P) < 5 * math.sqrt(N * P * (1 - P)), counts
+    # every particle's next candidate lies ahead, on its own push grid
+    tc = o.flight(0)
+    assert np.all(tc >= 12)
