@@ -286,17 +286,19 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
             sh_V0 = P.vring[(mode == 0 ? fstep + 1 : fstep) & P.vring_mask];
         }
         // Q = (this step's deposit Qf, or the kept Q of a species not pushed)
-        // + the births' deposit Qb; two nodes per thread with all their
-        // loads issued before any store
+        // + the births' deposit Qb, and the cycle moments Qacc += Q; two
+        // nodes per thread with all their loads issued before any store
         for (int j0 = t; j0 < Ng; j0 += 2 * GA) {
-            unsigned long long q[2][NSP];
+            unsigned long long q[2][NSP], qa[2][NSP];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = j0 + h * GA;
 #pragma unroll
                 for (int s = 0; s < NSP; ++s) {
                     q[h][s] = 0ull;
+                    qa[h][s] = 0ull;
                     if (j < Ng) {
+                        if (mode == 0) qa[h][s] = P.Qacc[s][j];
                         const bool fresh = (mode == 1) || ((pushed_mask >> s) & 1);
                         unsigned long long v = P.Qb[s][j];
                         if (fresh) {
@@ -317,6 +319,7 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
 #pragma unroll
                 for (int s = 0; s < NSP; ++s) {
                     P.Q[s][j] = q[h][s];
+                    if (mode == 0) P.Qacc[s][j] = qa[h][s] + q[h][s];
                     P.Qf[s][j] = 0ull;
                     if ((mode == 1) || ((pushed_mask >> s) & 1)) {   // only pushes fill copies 1..
 #pragma unroll
@@ -351,24 +354,13 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         // are kept so that k_phi evaluates it with the same expressions.
         const double D0 = sh_D0, D2 = 2.0 * sh_D0;   // 2 D0 is exact
         const long long R0 = sh_R0, RN = sh_RN;
-        // Cycle moments (Qacc += Q) ride along: their loads are in flight
-        // during the FP64 work.
         for (int j = t; j < Ng; j += GA) {
-            unsigned long long qa[NSP], qn[NSP];
-            if (mode == 0) {
-#pragma unroll
-                for (int s = 0; s < NSP; ++s) { qa[s] = P.Qacc[s][j]; qn[s] = P.Q[s][j]; }
-            }
             double E;
             if (j == 0) E = (-D0 - c * (double)R0) * P.inv_dx64;
             else if (j == N) E = (c * (double)Ss[N - 1] - D0 + c * (double)RN) * P.inv_dx64;
             else E = (c * (double)(Ss[j] + Ss[j - 1]) - D2) * P.inv_2dx64;
             P.Ef[j] = (float)E;
             P.fS[j] = Ss[j];
-            if (mode == 0) {
-#pragma unroll
-                for (int s = 0; s < NSP; ++s) P.Qacc[s][j] = qa[s] + qn[s];
-            }
         }
         return;
     }

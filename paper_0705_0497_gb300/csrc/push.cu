@@ -44,10 +44,10 @@
 #ifndef O2PIC_PUSH_UNROLL
 #define O2PIC_PUSH_UNROLL 4
 #endif
-// Minimum resident blocks per SM of the collision kernel (caps its registers;
-// 2 timed fastest of 1-4 on the same workload).
+// Minimum resident blocks per SM of the kinematics kernel (caps its registers
+// at 85, no spills; 3 timed fastest of 2, 3, 4 on the same workload).
 #ifndef O2PIC_CAND_MIN_BLOCKS
-#define O2PIC_CAND_MIN_BLOCKS 2
+#define O2PIC_CAND_MIN_BLOCKS 3
 #endif
 
 namespace o2 {
@@ -81,7 +81,7 @@ __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t
 // process's threshold above E; the rate test itself repeats the filter's).
 // bkind: 0 none, 1 ionization (two births), 2 attachment / detachment (one).
 template <int S>
-__device__ __noinline__ int collide(const Params& P, const float* cum, int np, unsigned long long step,
+__device__ __forceinline__ int collide(const Params& P, const float* cum, int np, unsigned long long step,
                                        uint32_t id, uint4 w0, float x, float& vx, float& vy, float& vz,
                                        bool& alive, int& bkind, float4& b1, float4& b2,
                                        unsigned& warn_tries, unsigned& warn_emax) {
@@ -553,7 +553,7 @@ __device__ __forceinline__ void filter_body(const Params& P, unsigned blk, unsig
 // Real collisions of one species for this step.  Each warp takes two lists
 // of the particle kernel's warps at once, one per half-warp (16 lanes; a list
 // holds about a dozen records at the method's rates), and walks them in slot
-// order, 16 records per pass through the out-of-line kinematics, so the
+// order, 16 records per pass through the kinematics, so the
 // lists of a step run in one wave of resident warps.  Electron records carry
 // the particle (slot, id, x, v) and block 0 of its Philox stream is drawn
 // again; ion records carry the slot, id, v and that block (its first word,
