@@ -55,13 +55,21 @@ enum { O2PIC_E = 0, O2PIC_OM = 1, O2PIC_OP = 2 };
  *              species O-, target ION; sigma is the neutralization cross
  *              section, e.g. the Landau-Zener form of the paper)
  *   RECOMBINE  (16): e + O2+ -> O + O, binary and cell-local like (17), on
- *              ion steps before (17) (species e, target ION) */
+ *              ion steps before (17) (species e, target ION)
+ *   EDETACH    (22): e + O- -> O + 2e, binary and cell-local like (17), on
+ *              ion steps before (16) and (17) (species O-, target ELECTRON;
+ *              threshold_eV = the O electron affinity): the O- is removed,
+ *              the electron loses the threshold and shares the rest uniformly
+ *              with the detached electron, both isotropic about the O-'s
+ *              velocity; the newborn, at the O-'s place, follows the step's
+ *              other electron births in the order of the O- parents */
 enum { O2PIC_ELASTIC = 0, O2PIC_EXCITE = 1, O2PIC_IONIZE = 2, O2PIC_ATTACH = 3,
-       O2PIC_DETACH = 4, O2PIC_CX = 5, O2PIC_NEUTRALIZE = 6, O2PIC_RECOMBINE = 7 };
+       O2PIC_DETACH = 4, O2PIC_CX = 5, O2PIC_NEUTRALIZE = 6, O2PIC_RECOMBINE = 7, O2PIC_EDETACH = 8 };
 
 /* Targets: ground-state O2 (density p/kT), metastable O2(a1Dg) (density
- * C_meta p/kT, Sec. 2), or the other ion species (neutralization only). */
-enum { O2PIC_TARGET_O2 = 0, O2PIC_TARGET_O2_META = 1, O2PIC_TARGET_ION = 2 };
+ * C_meta p/kT, Sec. 2), the other ion species ((16), (17)) or the electrons
+ * ((22)). */
+enum { O2PIC_TARGET_O2 = 0, O2PIC_TARGET_O2_META = 1, O2PIC_TARGET_ION = 2, O2PIC_TARGET_ELECTRON = 3 };
 
 enum { O2PIC_HOST = 0, O2PIC_DEVICE = 1 };
 
@@ -122,6 +130,7 @@ typedef struct {
     uint64_t error_flags;
     uint64_t particle_steps_species[O2PIC_NSPECIES];  /* particles pushed, per species */
     uint64_t recombined, rec_candidates;              /* (16): pairs removed, pairs tested */
+    uint64_t edetached, edet_candidates;              /* (22): pairs reacted, pairs tested */
 } o2pic_stats;
 
 /* Fills `cfg` with the defaults (parity-case geometry, T_gas = 300 K, O, O2
@@ -136,8 +145,9 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out);
 /* Builds the per-species rate tables nu_k(E_i) = n_target sigma_k(E_i) g(E_i)
  * on 32 points per octave over [2^-10, 2^12] eV (FP64, stored FP32 as
  * cumulative sums), nu_max and P_max = 1 - exp(-nu_max dt_s) (null-collision
- * method, Sec. 2), and the (17) rate-coefficient table; copies them to the
- * device.  At most O2PIC_MAXPROC processes per species, one NEUTRALIZE, one RECOMBINE.
+ * method, Sec. 2), and the rate-coefficient tables of the binary processes
+ * (17), (16), (22); copies them to the device.  At most O2PIC_MAXPROC
+ * processes per species, one NEUTRALIZE, one RECOMBINE, one EDETACH.
  * Errors: INVALID_ARG. */
 int o2pic_set_processes(o2pic_ctx* ctx, const o2pic_process* procs, int nproc);
 

@@ -37,7 +37,7 @@ COUNTER_NAMES = ([f"events_{s}_{k}" for s in range(NSP) for k in range(MAXPROC)]
                  [f"absorbed_{s}_{w}" for s in range(NSP) for w in range(2)] +
                  [f"born_{s}" for s in range(NSP)] +
                  ["neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries",
-                  "warn_pair_gt1", "id_overflow", "recombined", "rec_candidates"])
+                  "warn_pair_gt1", "id_overflow", "recombined", "rec_candidates", "edetached", "edet_candidates"])
 
 
 def lib():
@@ -227,7 +227,8 @@ class Oracle:
 
     def lookup(self, which, k, E):
         """The tabulated rate at energy E as the collision step reads it:
-        which = species (cumulative column k), 3 = (17) table, 4 = (16)."""
+        which = species (cumulative column k), 3 = (17) table, 4 = (16),
+        5 = (22)."""
         return lib().oracle_lookup(self.h, which, k, float(E))
 
     def neutral_table(self):

@@ -55,8 +55,8 @@ const double TWO_PI = 6.283185307179586476925286766559;
 
 enum { SP_E = 0, SP_OM = 1, SP_OP = 2, NSP = 3 };
 enum { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 4, K_CX = 5, K_NEUTRALIZE = 6,
-       K_RECOMBINE = 7 };
-enum { T_O2 = 0, T_O2_META = 1, T_ION = 2 };
+       K_RECOMBINE = 7, K_EDETACH = 8 };
+enum { T_O2 = 0, T_O2_META = 1, T_ION = 2, T_ELECTRON = 3 };
 
 // Energy grid of the rate tables: 32 points per octave on [2^-10, 2^12] eV.
 const int GRID_OCT_LO = -10;
@@ -70,7 +70,7 @@ const double FIX_ONE = 65536.0;                  // CIC fixed point: 2^16 per pa
 // RNG stream tags (counter word 1).  TAG_FLIGHT + s: the first free-flight
 // draw of a particle of species s (at load or birth).
 enum { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6,
-       TAG_FLIGHT = 7 };
+       TAG_FLIGHT = 7, TAG_EDET = 10, TAG_SHIFT_EDET = 11 };
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
@@ -292,6 +292,8 @@ struct Counters {
     uint64_t id_overflow;
     uint64_t recombined;           // pairs removed by (16)
     uint64_t rec_candidates;       // pairs tested by (16)
+    uint64_t edetached;            // pairs reacted by (22)
+    uint64_t edet_candidates;      // pairs tested by (22)
 };
 
 template <class R> struct Oracle {
@@ -329,6 +331,10 @@ template <class R> struct Oracle {
     Proc recomb;
     std::vector<R> Ktab_r;            // [NGRID] sigma_r g  (16)
     R kappa_r;
+    bool have_edet;
+    Proc edet;
+    std::vector<R> Ktab_d;            // [NGRID] sigma_22 g  (22)
+    R kappa_d, thr_d;
     // state
     Particles<R> sp[NSP];
     uint64_t next_id[NSP];           // id of the next birth (64-bit: ids past 2^32 - 1 are detected)
@@ -375,6 +381,10 @@ template <class R> struct Oracle {
         pair_factor = (R)(cfg.weight * dt_ion / (cfg.area * dx));
         const double mur = cfg.m_e * cfg.m_OP / (cfg.m_e + cfg.m_OP);
         kappa_r = (R)(0.5 * mur / QE);
+        const double mud = cfg.m_e * cfg.m_OM / (cfg.m_e + cfg.m_OM);
+        kappa_d = (R)(0.5 * mud / QE);
+        thr_d = 0;
+        have_edet = false;
         have_neutral = false;
         have_recomb = false;
         step = 0; acc_steps = 0;
@@ -391,6 +401,7 @@ template <class R> struct Oracle {
         for (int s = 0; s < NSP; ++s) { procs[s].clear(); cum[s].clear(); nu64[s].clear(); }
         have_neutral = false;
         have_recomb = false;
+        have_edet = false;
         for (int j = 0; j < n; ++j) {
             const oracle_process& q = p[j];
             if (q.n < 1 || q.species < 0 || q.species >= NSP) return -1;
@@ -401,6 +412,10 @@ template <class R> struct Oracle {
             if (q.kind == K_RECOMBINE) {
                 if (q.species != SP_E) return -1;
                 recomb = pr; have_recomb = true; continue;
+            }
+            if (q.kind == K_EDETACH) {
+                if (q.species != SP_OM) return -1;
+                edet = pr; have_edet = true; continue;
             }
             if ((int)procs[q.species].size() >= MAXPROC) return -1;
             procs[q.species].push_back(pr);
@@ -439,6 +454,18 @@ template <class R> struct Oracle {
                 double Ei = grid_energy(i);
                 double g = std::sqrt(2.0 * QE * Ei / mun);
                 Ktab[i] = (R)(sigma_at(neutral.E, neutral.s, neutral.thr, Ei) * g);
+            }
+        }
+        // (22): sigma g with the e-O- reduced mass; the threshold (O's
+        // electron affinity) also bounds the reaction (see pair_process)
+        Ktab_d.assign(NGRID, (R)0);
+        thr_d = have_edet ? (R)edet.thr : (R)0;
+        if (have_edet) {
+            double mud = cfg.m_e * cfg.m_OM / (cfg.m_e + cfg.m_OM);
+            for (int i = 0; i < NGRID; ++i) {
+                double Ei = grid_energy(i);
+                double g = std::sqrt(2.0 * QE * Ei / mud);
+                Ktab_d[i] = (R)(sigma_at(edet.E, edet.s, edet.thr, Ei) * g);
             }
         }
         Ktab_r.assign(NGRID, (R)0);
@@ -733,8 +760,16 @@ template <class R> struct Oracle {
     // nA nB w <sigma g> dt / (A dx) reactions per cell and step; both
     // particles are removed.  The acceptance number comes from the A
     // particle's stream.
+    // mode 0: both particles of a reacted pair are removed ((16), (17));
+    // mode 1, (22) e + O- -> O + 2e with A = O-, B = e: a pair reacts only at
+    // or above the threshold thr; the O- is removed, the electron loses thr,
+    // the rest E - thr is split uniformly between it and the detached electron
+    // (fraction from the O-'s stream after its acceptance number), both going
+    // off isotropically from the O-'s velocity; the newborn, at the O-'s
+    // position, goes to births22 keyed by the O-'s array index.
     void pair_process(uint64_t n, int A, int B, const std::vector<R>& K_tab, R kap, uint32_t tag_shift,
-                      uint32_t tag_pair, uint64_t& tested, uint64_t& reacted) {
+                      uint32_t tag_pair, uint64_t& tested, uint64_t& reacted, int mode = 0, R thr = (R)0,
+                      std::vector<std::pair<size_t, Birth4>>* births22 = nullptr) {
         int Nc = cfg.n_cells;
         std::vector<std::vector<size_t>> LA(Nc), LB(Nc);
         for (size_t i = 0; i < sp[A].size(); ++i) { int j; R fr; cell_of(sp[A].x[i], j, fr); LA[j].push_back(i); }
@@ -764,7 +799,25 @@ template <class R> struct Oracle {
                 R P = K * (pair_factor * (R)M);
                 tested += 1;
                 if (P > (R)1) cnt.warn_pair_gt1 += 1;
-                if (u < P) { deadA[a] = 1; deadB[b] = 1; reacted += 1; }
+                if (!(u < P) || E < thr) continue;
+                reacted += 1;
+                deadA[a] = 1;
+                if (mode == 0) { deadB[b] = 1; continue; }
+                const R Er = E - thr;
+                const R us = uniform<R>(st.next());
+                const R Es = us * Er;
+                const R Ep = Er - Es;
+                R n1[3], n2[3];
+                isotropic<R>(st, n1, cnt.warn_tries);
+                isotropic<R>(st, n2, cnt.warn_tries);
+                const R vp = sqrt_(Ep / kappa[SP_E]);
+                const R vs = sqrt_(Es / kappa[SP_E]);
+                const R ax = sp[A].vx[a], ay = sp[A].vy[a], az = sp[A].vz[a];
+                sp[B].vx[b] = ax + vp * n1[0];
+                sp[B].vy[b] = ay + vp * n1[1];
+                sp[B].vz[b] = az + vp * n1[2];
+                births22->push_back({a, {(double)sp[A].x[a], (double)(ax + vs * n2[0]), (double)(ay + vs * n2[1]),
+                                         (double)(az + vs * n2[2])}});
             }
         }
         filter(sp[A], deadA);
@@ -775,6 +828,20 @@ template <class R> struct Oracle {
     void neutralize(uint64_t n) {
         if (!have_neutral) return;
         pair_process(n, SP_OM, SP_OP, Ktab, kappa_n, TAG_SHIFT, TAG_PAIR, cnt.pair_candidates, cnt.neutralized);
+    }
+
+    // (22) e + O- -> O + 2e, on ion steps before (16) and (17) (reading: the
+    // paper gives no order); its births follow the step's other electron
+    // births, in the order of their O- parents.
+    void edetach(uint64_t n, std::vector<Birth4>* births) {
+        if (!have_edet) return;
+        std::vector<std::pair<size_t, Birth4>> b22;
+        pair_process(n, SP_OM, SP_E, Ktab_d, kappa_d, TAG_SHIFT_EDET, TAG_EDET, cnt.edet_candidates, cnt.edetached,
+                     1, thr_d, &b22);
+        std::sort(b22.begin(), b22.end(), [](const std::pair<size_t, Birth4>& p, const std::pair<size_t, Birth4>& q) {
+            return p.first < q.first;
+        });
+        for (const auto& e : b22) births[SP_E].push_back(e.second);
     }
 
     // (16) e + O2+ -> O + O, on ion steps before (17) (reading: the paper
@@ -824,6 +891,7 @@ template <class R> struct Oracle {
         if (ion_step) {
             process_species(SP_OM, n, births);
             process_species(SP_OP, n, births);
+            edetach(n, births);
             recombine(n);
             neutralize(n);
         }
@@ -1136,7 +1204,8 @@ void oracle_deposit(int n_cells, double L, const float* x, uint64_t n, uint64_t*
 // The tabulated rate at an arbitrary energy E [eV], exactly as the collision
 // step looks it up (grid_locate + grid_interp in precision R): which = 0..2
 // -> cumulative rate column k of species `which`; 3 -> the (17) table sigma_n g;
-// 4 -> the (16) table sigma_r g.  Test use (pins the lookup off the grid).
+// 4 -> the (16) table sigma_r g; 5 -> the (22) table sigma_22 g.  Test use
+// (pins the lookup off the grid).
 double oracle_lookup(void* p, int which, int k, double E) {
     Handle* h = (Handle*)p; double v = 0.0;
     DISPATCH(h, {
@@ -1150,6 +1219,8 @@ double oracle_lookup(void* p, int which, int k, double E) {
             v = (double)grid_interp<RR>(O.Ktab, 1, 0, i, w);
         } else if (which == 4) {
             v = (double)grid_interp<RR>(O.Ktab_r, 1, 0, i, w);
+        } else if (which == 5) {
+            v = (double)grid_interp<RR>(O.Ktab_d, 1, 0, i, w);
         }
     });
     return v;

@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("id_overflow", ctypes.c_uint64), ("step", ctypes.c_uint64), ("live", ctypes.c_uint64 * NSP),
                 ("slots", ctypes.c_uint64 * NSP), ("next_id", ctypes.c_uint64 * NSP),
                 ("error_flags", ctypes.c_uint64), ("particle_steps_species", ctypes.c_uint64 * NSP),
-                ("recombined", ctypes.c_uint64), ("rec_candidates", ctypes.c_uint64)]
+                ("recombined", ctypes.c_uint64), ("rec_candidates", ctypes.c_uint64),
+                ("edetached", ctypes.c_uint64), ("edet_candidates", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {}
@@ -76,7 +77,8 @@ class Stats(ctypes.Structure):
             d[f"next_id_{s}"] = int(self.next_id[s])
             d[f"particle_steps_{s}"] = int(self.particle_steps_species[s])
         for n in ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
-                  "id_overflow", "step", "error_flags", "recombined", "rec_candidates"):
+                  "id_overflow", "step", "error_flags", "recombined", "rec_candidates", "edetached",
+                  "edet_candidates"):
             d[n] = int(getattr(self, n))
         return d
 

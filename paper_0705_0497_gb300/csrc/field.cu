@@ -203,7 +203,7 @@ __device__ __forceinline__ unsigned find_unit(const unsigned* p, unsigned nu, un
 struct CtrlSnap {
     unsigned long long step, epoch, acc_steps, slots[NSP], live[NSP], removed[NSP];
     unsigned long long next_id[NSP];
-    unsigned cur[NSP], removals;
+    unsigned cur[NSP], removals, births22;
 };
 
 // Over the charge block: the inclusive scan S_j of R_j held in a[0..n)
@@ -380,6 +380,7 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         cs.epoch = C->epoch;
         cs.acc_steps = C->acc_steps;
         cs.removals = C->removals;
+        cs.births22 = C->births22;
     }
     prefetch_units(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], births_e ? P.push_warps[SP_E] : 0u,
                    P.wcount[B_E_FROM_OM], births_om ? P.push_warps[SP_OM] : 0u);
@@ -387,10 +388,12 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
 
     // births of the step: n1 ionizations (e + O2+) and n2 attachments (O-)
     // staged by the electron kernel, n3 detachment electrons staged by the O-
-    // kernel (ion steps), placed after the electrons' own
+    // kernel (ion steps), placed after the electrons' own, then n4 electrons
+    // of (22) staged in order by its apply kernel (ion steps)
     unsigned long long btot[NB];
     for (int k = 0; k < NB; ++k) btot[k] = 0;
-    if (births_e || births_om) {
+    const unsigned n4 = (mode == 0) ? cs.births22 : 0u;
+    if (births_e || births_om || n4) {
         const unsigned ns1 = (unsigned)(cs.slots[SP_E] < P.sp[SP_E].cap ? cs.slots[SP_E] : P.sp[SP_E].cap);
         const unsigned ns3 = (unsigned)(cs.slots[SP_OM] < P.sp[SP_OM].cap ? cs.slots[SP_OM] : P.sp[SP_OM].cap);
         const unsigned nu1 = births_e ? P.push_warps[SP_E] : 0u, nu3 = births_om ? P.push_warps[SP_OM] : 0u;
@@ -399,11 +402,17 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         unit_offsets(P.wcount[B_E_FROM_E], P.wcount[B_OM_FROM_E], nu1, P.wcount[B_E_FROM_OM], nu3, p1, p2, p3, wsB,
                      t12, t3);
         const unsigned n1 = (unsigned)t12, n2 = (unsigned)(t12 >> 32), n3 = (unsigned)t3;
-        const unsigned ntot = n1 + n2 + n3;
+        const unsigned ntot = n1 + n2 + n3 + n4;
         // one birth per thread and pass: which list, its rank there, the warp
         // that staged it (binary search over that list's offsets) and its
         // staging slot; all loads of the birth before its stores
         for (unsigned b = tB; b < ntot; b += GB) {
+            if (b >= n1 + n2 + n3) {   // (22): staged in place order
+                const unsigned r = b - n1 - n2 - n3;
+                place_birth(P, C, cs.cur, SP_E, cs.slots[SP_E] + n1 + n3 + r,
+                            (unsigned long long)cs.next_id[SP_E] + n1 + n3 + r, P.stage22[r], cs.step);
+                continue;
+            }
             const int kind = b < n1 ? 0 : (b < n1 + n2 ? 1 : 2);
             const unsigned r = kind == 0 ? b : (kind == 1 ? b - n1 : b - n1 - n2);
             const unsigned* p = kind == 0 ? p1 : (kind == 1 ? p2 : p3);
@@ -427,7 +436,7 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         btot[B_E_FROM_E] = n1;
         btot[B_OP_FROM_E] = n1;
         btot[B_OM_FROM_E] = n2;
-        btot[B_E_FROM_OM] = n3;
+        btot[B_E_FROM_OM] = n3 + n4;
     }
 
     if (mode == 0) {
@@ -460,6 +469,8 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
             // this block is the only writer of the step state: plain stores
             C->removals = 0u;
             C->rremovals = 0u;
+            C->dremovals = 0u;
+            C->births22 = 0u;
             C->acc_steps = cs.acc_steps + 1;
             C->step = cs.step + 1;
             C->epoch = cs.epoch + 1;
@@ -468,7 +479,7 @@ __device__ __forceinline__ void field_body(const Params& P, int mode, int pushed
         }
     }
     // per-cell ion totals of (17): zero for the next ion step
-    for (int k = tB; k < 2 * N; k += GB) { P.ptot[k] = 0u; P.rtot[k] = 0u; }
+    for (int k = tB; k < 2 * N; k += GB) { P.ptot[k] = 0u; P.rtot[k] = 0u; P.dtot[k] = 0u; }
     // conduction-current sums: after a load the ring restarts; at the end of
     // step n the ions' entries of a step without an ion push repeat those of
     // step n-1, and the slot of step n+1 is cleared for its pushes

@@ -67,7 +67,7 @@ enum Kind { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 
 // TAG_FLIGHT + s: the first free-flight draw of a particle of species s (at a
 // load or at its birth).
 enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6,
-                      TAG_FLIGHT = 7 };
+                      TAG_FLIGHT = 7, TAG_EDET = 10, TAG_SHIFT_EDET = 11 };
 
 // device error bits
 constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE = 4ull, ERR_TIMEOUT = 8ull;
@@ -87,6 +87,7 @@ struct DevCounters {
     unsigned long long id_overflow;
     unsigned long long psteps[NSP];
     unsigned long long recombined, rec_candidates;
+    unsigned long long edetached, edet_candidates;
 };
 
 // Births appended by one kernel into species d: births of the electron
@@ -110,6 +111,8 @@ struct DevCtrl {
     unsigned int ticket[NKK + NSP];        // tile tickets per kernel kind, + compaction per species
     unsigned int removals;                 // (17) pairs to remove
     unsigned int rremovals;                // (16) pairs to remove
+    unsigned int dremovals;                // (22) pairs listed
+    unsigned int births22;                 // (22) electron births staged this step
     DevCounters cnt;
 };
 
@@ -196,6 +199,16 @@ struct Params {
     unsigned int* rtot;          // [2][Nc] (cleared by the end-of-step kernel)
     unsigned int* rremoval;      // [2 * max_rremovals]: e slot, O2+ slot
     unsigned int max_rremovals;
+    // (22): per-tile per-cell counts of live O- and e, per-cell totals, pairs,
+    // and the staged electron births in the order of their O- parents
+    const float* Ktab_d;         // [NGRID] sigma_22 g
+    float Kmax_d_hi, kappa_d, thr_d;
+    int have_edet;
+    unsigned int* dhist[2];      // 0: O-, 1: e
+    unsigned int* dtot;          // [2][Nc] (cleared by the end-of-step kernel)
+    unsigned int* dremoval;      // [2 * max_dremovals]: O- slot, e slot
+    unsigned int max_dremovals;
+    float4* stage22;             // [max_dremovals]
     // compaction trigger
     float compact_dead_frac;
 };
@@ -217,6 +230,8 @@ struct PairSpec {
     unsigned long long* tested;  // device counter of pairs tested
     unsigned long long* reacted; // device counter of pairs removed (the apply kernel's)
     int active;                  // 0: the discharge has no such process (batched launches skip it)
+    float thr;                   // a pair reacts only at or above this relative energy [eV]
+    int b_survives;              // 1: only A is removed (B's charge stays), (22)
 };
 
 __host__ __device__ inline unsigned long long ceil_div(unsigned long long a, unsigned long long b) {
@@ -240,6 +255,8 @@ void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t
 cudaError_t configure_pair_hist_smem(int Nc);
 void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s);
 void launch_pair_apply(const Params& P, const PairSpec& S, cudaStream_t s);
+void launch_edet_apply(const Params& P, const PairSpec& S, cudaStream_t s);
+void launch_edet_apply_batched(const Params* all, const PairSpec* specs, int n, cudaStream_t s);
 // batched launches (one grid for many discharges; map[b] = discharge, block, blocks)
 void launch_push_batched(int species, const Params* all, const uint4* map, int nblocks, size_t smem, cudaStream_t s);
 void launch_cand_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s);

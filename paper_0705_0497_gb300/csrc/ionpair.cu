@@ -26,8 +26,10 @@
 // may be resolved in any order.
 //
 // The kernels take the two species, tables and lists as a PairSpec: the same
-// code runs (16) e + O2+ -> O + O (A = e) before (17) (A = O-); the (16)
-// removals are applied by k_pair_apply before (17) counts its ions.
+// code runs (22) e + O- -> O + 2e (A = O-, B = e, only A removed; its
+// kinematics and births in k_edet_apply) and (16) e + O2+ -> O + O (A = e)
+// before (17) (A = O-); the removals of (22) and (16) are applied before the
+// next process counts its particles.
 #include "common.cuh"
 
 namespace o2 {
@@ -193,7 +195,7 @@ __device__ void resolve_one(const Params& P, const PairSpec& Sp, unsigned pos, u
     const float K = grid_interp(Sp.K, 1, 0, gi, gw);
     const float Pp = K * (P.pair_factor * (float)M);
     if (Pp > 1.0f) ++gt1;
-    if (u < Pp) {
+    if (u < Pp && E >= Sp.thr) {
         const unsigned idx = atomicAdd(Sp.nremovals, 1u);
         if (idx < Sp.max_removals) {
             Sp.removal[2 * idx] = (unsigned)p;
@@ -205,10 +207,12 @@ __device__ void resolve_one(const Params& P, const PairSpec& Sp, unsigned pos, u
         uint32_t rr = cic_r(f);
         atomicAdd(&P.Qf[Sp.A][j], 0ull - (unsigned long long)(65536u - rr));
         atomicAdd(&P.Qf[Sp.A][j + 1], 0ull - (unsigned long long)rr);
-        cell_of(XP[b_slot], P.inv_dx, Nc, j, f);
-        rr = cic_r(f);
-        atomicAdd(&P.Qf[Sp.B][j], 0ull - (unsigned long long)(65536u - rr));
-        atomicAdd(&P.Qf[Sp.B][j + 1], 0ull - (unsigned long long)rr);
+        if (!Sp.b_survives) {
+            cell_of(XP[b_slot], P.inv_dx, Nc, j, f);
+            rr = cic_r(f);
+            atomicAdd(&P.Qf[Sp.B][j], 0ull - (unsigned long long)(65536u - rr));
+            atomicAdd(&P.Qf[Sp.B][j + 1], 0ull - (unsigned long long)rr);
+        }
     }
 }
 
@@ -322,6 +326,71 @@ __device__ __forceinline__ void pair_apply_body(const Params& P, const PairSpec&
     }
 }
 
+// (22) e + O- -> O + 2e: the reacted pairs (O- slot, e slot), listed in any
+// order by k_pair, in one block.  Each pair's kinematics continue the O-'s
+// stream after its acceptance number: the share u of E_rel - E_th taken by
+// the detached electron, then one isotropic direction for each electron; the
+// electron keeps going from the O-'s velocity with the rest, the O- is marked
+// dead (its charge was taken out by k_pair), and the newborn is staged at the
+// rank of its O- parent's slot among the listed pairs (the method's order),
+// its charge into the births' deposit.  The end-of-step kernel places the
+// newborns after the step's other electron births.
+__device__ __forceinline__ void edet_apply_body(const Params& P, const PairSpec& Sp) {
+    __shared__ unsigned sh_wtries;
+    DevCtrl* C = P.ctrl;
+    if (threadIdx.x == 0) sh_wtries = 0u;
+    __syncthreads();
+    const unsigned listed = *Sp.nremovals;
+    const unsigned n = listed < Sp.max_removals ? listed : Sp.max_removals;
+    const unsigned long long step = C->step;
+    const unsigned ca = C->cur[Sp.A], cb = C->cur[Sp.B];
+    const SpeciesBuf& SA = P.sp[Sp.A];
+    const SpeciesBuf& SB = P.sp[Sp.B];
+    unsigned wtries = 0;
+    for (unsigned r = threadIdx.x; r < n; r += blockDim.x) {
+        const unsigned a = Sp.removal[2 * r], b = Sp.removal[2 * r + 1];
+        unsigned rank = 0;   // slots of the O- are distinct: each reacts once
+        for (unsigned q = 0; q < n; ++q) rank += (Sp.removal[2 * q] < a) ? 1u : 0u;
+        const float ax = SA.x[ca][a], avx = SA.vx[ca][a], avy = SA.vy[ca][a], avz = SA.vz[ca][a];
+        const uint32_t id = SA.id[ca][a];
+        const float gx = avx - SB.vx[cb][b], gy = avy - SB.vy[cb][b], gz = avz - SB.vz[cb][b];
+        const float E = Sp.kappa * dot3(gx, gy, gz, gx, gy, gz);
+        const float Er = E - Sp.thr;
+        Stream st;
+        st.init(id, P.seed, step, Sp.tag_pair);
+        (void)st.next();                         // the acceptance number
+        const float us = uniform(st.next());
+        const float Es = us * Er;
+        const float Ep = Er - Es;
+        float n1x, n1y, n1z, n2x, n2y, n2z;
+        isotropic(st, n1x, n1y, n1z, wtries);
+        isotropic(st, n2x, n2y, n2z, wtries);
+        const float vp = sqrtf(Ep / P.kappa[SP_E]);
+        const float vs = sqrtf(Es / P.kappa[SP_E]);
+        SB.vx[cb][b] = avx + vp * n1x;
+        SB.vy[cb][b] = avy + vp * n1y;
+        SB.vz[cb][b] = avz + vp * n1z;
+        SA.x[ca][a] = dead_marker();
+        P.stage22[rank] = make_float4(ax, avx + vs * n2x, avy + vs * n2y, avz + vs * n2z);
+        int j; float f;
+        cell_of(ax, P.inv_dx, P.Nc, j, f);
+        const uint32_t rr = cic_r(f);
+        atomicAdd(&P.Qb[SP_E][j], (unsigned long long)(65536u - rr));
+        if (rr) atomicAdd(&P.Qb[SP_E][j + 1], (unsigned long long)rr);
+    }
+    pdl_trigger();
+    if (wtries) atomicAdd(&sh_wtries, wtries);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (n) {
+            atomicAdd(&C->removed[Sp.A], (unsigned long long)n);
+            atomicAdd(Sp.reacted, (unsigned long long)n);
+        }
+        C->births22 = n;
+        if (sh_wtries) atomicAdd(&C->cnt.warn_tries, (unsigned long long)sh_wtries);
+    }
+}
+
 __global__ void __launch_bounds__(HIST_T) k_pair_hist(Params P, PairSpec Sp) {
     pdl_wait();
     pair_hist_body(P, Sp, blockIdx.x, gridDim.x);
@@ -362,6 +431,21 @@ __global__ void __launch_bounds__(PAIR_T) k_pair_b(const Params* __restrict__ al
     pair_body(sP, Sp, m.y, m.z);
 }
 
+__global__ void k_edet_apply(Params P, PairSpec Sp) {
+    pdl_wait();
+    edet_apply_body(P, Sp);
+}
+
+// batched: block d applies discharge d's (22) list
+__global__ void k_edet_apply_b(const Params* __restrict__ all, const PairSpec* __restrict__ specs) {
+    __shared__ Params sP;
+    pdl_wait();
+    const PairSpec Sp = specs[blockIdx.x];
+    if (!Sp.active) return;
+    load_params(sP, all + blockIdx.x);
+    edet_apply_body(sP, Sp);
+}
+
 // batched: block d applies discharge d's list
 __global__ void k_pair_apply_b(const Params* __restrict__ all, const PairSpec* __restrict__ specs) {
     __shared__ Params sP;
@@ -396,6 +480,14 @@ void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s) {
 // the list counter is cleared by the end-of-step kernel
 void launch_pair_apply(const Params& P, const PairSpec& S, cudaStream_t s) {
     launch_pdl(k_pair_apply, 1, 256, 0, s, P, S);
+}
+
+void launch_edet_apply(const Params& P, const PairSpec& S, cudaStream_t s) {
+    launch_pdl(k_edet_apply, 1, 256, 0, s, P, S);
+}
+
+void launch_edet_apply_batched(const Params* all, const PairSpec* specs, int n, cudaStream_t s) {
+    launch_pdl(k_edet_apply_b, n, 256, 0, s, all, specs);
 }
 
 void launch_pair_hist_batched(const Params* all, const PairSpec* specs, const uint4* map, int nblocks, size_t smem,

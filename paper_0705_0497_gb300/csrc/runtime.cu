@@ -232,6 +232,8 @@ void set_constants(o2pic_ctx* c) {
     P.kappa_n = (float)(0.5 * mun / QE);
     const double mur = g.m_e * g.m_OP / (g.m_e + g.m_OP);
     P.kappa_r = (float)(0.5 * mur / QE);
+    const double mud = g.m_e * g.m_OM / (g.m_e + g.m_OM);
+    P.kappa_d = (float)(0.5 * mud / QE);
     const double dt_ion = g.dt * (double)g.ion_subcycle;
     P.pair_factor = (float)(g.weight * dt_ion / (g.area * dx));
     P.seed = g.seed;
@@ -292,6 +294,27 @@ int prepare(o2pic_ctx* c, cudaStream_t s) {
     return cuda_fail(c, cudaGetLastError());
 }
 
+// The cell-binned binary processes of a context: (22) e + O- -> O + 2e
+// (A = O-, only A removed), (16) e + O2+ -> O + O, (17) O- + O2+ -> O + O2.
+PairSpec spec_edet(o2pic_ctx* c) {
+    const Params& P = c->P;
+    return PairSpec{SP_OM, SP_E, P.dhist[0], P.dhist[1], P.dtot, P.Ktab_d, P.Kmax_d_hi, P.kappa_d, TAG_EDET,
+                    TAG_SHIFT_EDET, P.dremoval, &c->d_ctrl->dremovals, P.max_dremovals,
+                    &c->d_ctrl->cnt.edet_candidates, &c->d_ctrl->cnt.edetached, P.have_edet, P.thr_d, 1};
+}
+PairSpec spec_rec(o2pic_ctx* c) {
+    const Params& P = c->P;
+    return PairSpec{SP_E, SP_OP, P.rhist[0], P.rhist[1], P.rtot, P.Ktab_r, P.Kmax_r_hi, P.kappa_r, TAG_REC,
+                    TAG_SHIFT_REC, P.rremoval, &c->d_ctrl->rremovals, P.max_rremovals,
+                    &c->d_ctrl->cnt.rec_candidates, &c->d_ctrl->cnt.recombined, P.have_recomb, 0.0f, 0};
+}
+PairSpec spec_neu(o2pic_ctx* c) {
+    const Params& P = c->P;
+    return PairSpec{SP_OM, SP_OP, P.hist[0], P.hist[1], P.ptot, P.Ktab, P.Kmax_hi, P.kappa_n, TAG_PAIR,
+                    TAG_SHIFT, P.removal, &c->d_ctrl->removals, P.max_removals,
+                    &c->d_ctrl->cnt.pair_candidates, &c->d_ctrl->cnt.neutralized, P.have_neutral, 0.0f, 0};
+}
+
 // The kernel sequence of nsteps time steps on stream s (the electrode
 // voltages of those steps must be in the ring already): electrons every step,
 // ions and (17) on ion steps, the end-of-step kernel, and every compact_check
@@ -314,18 +337,20 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
                 launch(c, KK_FILT_OP, s, [&] { launch_filter(SP_OP, P, c->grid_push[SP_OP], s); });
                 launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
             }
+            if (P.have_edet) {
+                const PairSpec D = spec_edet(c);
+                launch(c, KK_REC, s, [&] { launch_pair_hist(P, D, c->grid_compact, s); });
+                launch(c, KK_REC, s, [&] { launch_pair(P, D, c->grid_pair, s); });
+                launch(c, KK_REC, s, [&] { launch_edet_apply(P, D, s); });
+            }
             if (P.have_recomb) {
-                const PairSpec R{SP_E, SP_OP, P.rhist[0], P.rhist[1], P.rtot, P.Ktab_r, P.Kmax_r_hi, P.kappa_r,
-                                 TAG_REC, TAG_SHIFT_REC, P.rremoval, &c->d_ctrl->rremovals, P.max_rremovals,
-                                 &c->d_ctrl->cnt.rec_candidates, &c->d_ctrl->cnt.recombined, 1};
+                const PairSpec R = spec_rec(c);
                 launch(c, KK_REC, s, [&] { launch_pair_hist(P, R, c->grid_compact, s); });
                 launch(c, KK_REC, s, [&] { launch_pair(P, R, c->grid_pair_e, s); });
                 launch(c, KK_REC, s, [&] { launch_pair_apply(P, R, s); });
             }
             if (P.have_neutral) {
-                const PairSpec N{SP_OM, SP_OP, P.hist[0], P.hist[1], P.ptot, P.Ktab, P.Kmax_hi, P.kappa_n,
-                                 TAG_PAIR, TAG_SHIFT, P.removal, &c->d_ctrl->removals, P.max_removals,
-                                 &c->d_ctrl->cnt.pair_candidates, &c->d_ctrl->cnt.neutralized, 1};
+                const PairSpec N = spec_neu(c);
                 launch(c, KK_PAIR_HIST, s, [&] { launch_pair_hist(P, N, c->grid_compact, s); });
                 launch(c, KK_PAIR, s, [&] { launch_pair(P, N, c->grid_pair, s); });
             }
@@ -462,6 +487,16 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     P.max_rremovals = (unsigned)std::max<unsigned long long>(1, std::min(cfg->capacity[SP_E], cfg->capacity[SP_OP]));
     TRY(ctx_alloc(c, &P.rremoval, 2 * (size_t)P.max_rremovals));
     TRY(ctx_alloc(c, &P.ptot, 2 * (size_t)Nc));
+    // (22): O- and e tiles, totals, pair list, staged births
+    float* Kd;
+    TRY(ctx_alloc(c, &Kd, NGRID));
+    P.Ktab_d = Kd;
+    TRY(ctx_alloc(c, &P.dhist[0], (ceil_div(cfg->capacity[SP_OM], TILE) + 1) * Nc));
+    TRY(ctx_alloc(c, &P.dhist[1], (ceil_div(cfg->capacity[SP_E], TILE) + 1) * Nc));
+    TRY(ctx_alloc(c, &P.dtot, 2 * (size_t)Nc));
+    P.max_dremovals = (unsigned)std::max<unsigned long long>(1, std::min(cfg->capacity[SP_OM], cfg->capacity[SP_E]));
+    TRY(ctx_alloc(c, &P.dremoval, 2 * (size_t)P.max_dremovals));
+    TRY(ctx_alloc(c, &P.stage22, (size_t)P.max_dremovals));
     P.max_removals = (unsigned)std::max<unsigned long long>(1, std::min(cfg->capacity[SP_OM], cfg->capacity[SP_OP]));
     TRY(ctx_alloc(c, &P.removal, 2 * (size_t)P.max_removals));
     TRY(ctx_alloc(c, &c->d_gticket, 1));
@@ -510,12 +545,12 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
     if (!c || (nproc > 0 && !procs) || nproc < 0) return O2PIC_E_INVALID_ARG;
     const o2pic_config& g = c->cfg;
     std::vector<HostProc> sp[NSP];
-    HostProc neutral, recomb;
-    bool have_neutral = false, have_recomb = false;
+    HostProc neutral, recomb, edet;
+    bool have_neutral = false, have_recomb = false, have_edet = false;
     for (int j = 0; j < nproc; ++j) {
         const o2pic_process& q = procs[j];
         if (q.n < 1 || q.species < 0 || q.species >= NSP || !q.E_eV || !q.sigma_m2) return O2PIC_E_INVALID_ARG;
-        if (q.kind < O2PIC_ELASTIC || q.kind > O2PIC_RECOMBINE) return O2PIC_E_INVALID_ARG;
+        if (q.kind < O2PIC_ELASTIC || q.kind > O2PIC_EDETACH) return O2PIC_E_INVALID_ARG;
         HostProc p;
         p.kind = q.kind; p.target = q.target; p.thr = q.threshold_eV;
         p.E.assign(q.E_eV, q.E_eV + q.n);
@@ -529,6 +564,10 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
         if (q.kind == O2PIC_RECOMBINE) {
             if (have_recomb || q.species != SP_E) return O2PIC_E_INVALID_ARG;
             recomb = p; have_recomb = true; continue;
+        }
+        if (q.kind == O2PIC_EDETACH) {
+            if (have_edet || q.species != SP_OM || !(q.threshold_eV >= 0)) return O2PIC_E_INVALID_ARG;
+            edet = p; have_edet = true; continue;
         }
         // kinematics exist for: e: elastic, excite, ionize, attach; O-: elastic, detach; O2+: elastic, cx
         const bool ok = (q.species == SP_E && (q.kind == O2PIC_ELASTIC || q.kind == O2PIC_EXCITE ||
@@ -617,6 +656,23 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
     P.have_recomb = have_recomb ? 1 : 0;
     P.Kmax_r_hi = (float)((double)krmax * (1.0 + std::ldexp(1.0, -20)));
     e = cudaMemcpy((void*)P.Ktab_r, Kr.data(), sizeof(float) * NGRID, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    // (22): the same table form with the e-O- reduced mass; its threshold
+    std::vector<float> Kd(NGRID, 0.0f);
+    float kdmax = 0.0f;
+    if (have_edet) {
+        const double mud = g.m_e * g.m_OM / (g.m_e + g.m_OM);
+        for (int i = 0; i < NGRID; ++i) {
+            const double Ei = grid_energy(i);
+            const double gv = std::sqrt(2.0 * QE * Ei / mud);
+            Kd[i] = (float)(sigma_at(edet, Ei) * gv);
+            kdmax = std::max(kdmax, Kd[i]);
+        }
+    }
+    P.have_edet = have_edet ? 1 : 0;
+    P.thr_d = have_edet ? (float)edet.thr : 0.0f;
+    P.Kmax_d_hi = (float)((double)kdmax * (1.0 + std::ldexp(1.0, -20)));
+    e = cudaMemcpy((void*)P.Ktab_d, Kd.data(), sizeof(float) * NGRID, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e);
     for (int s = 0; s < NSP; ++s) {
         int bps = 0;
@@ -979,6 +1035,8 @@ int o2pic_get_stats(o2pic_ctx* c, o2pic_stats* out) {
     out->id_overflow = h.cnt.id_overflow;
     out->recombined = h.cnt.recombined;
     out->rec_candidates = h.cnt.rec_candidates;
+    out->edetached = h.cnt.edetached;
+    out->edet_candidates = h.cnt.edet_candidates;
     out->step = h.step;
     out->error_flags = h.error_flags;
     return rc;
@@ -1039,11 +1097,14 @@ struct o2pic_batch {
     bool fused = false, fusable = false;
     Params* dP = nullptr;                 // [n] parameters of each context
     PairSpec* dR = nullptr;               // [n] (16) of each context
+    PairSpec* dD = nullptr;               // [n] (22)
     PairSpec* dN = nullptr;               // [n] (17)
     uint4* dmap = nullptr;                // block maps, concatenated
     size_t map_push[NSP] = {0, 0, 0}, map_comp[NSP] = {0, 0, 0}, map_rh = 0, map_rp = 0, map_nh = 0, map_np = 0;
+    size_t map_dh = 0, map_dp = 0;
     int nb_push[NSP] = {0, 0, 0}, nb_comp[NSP] = {0, 0, 0}, nb_rh = 0, nb_rp = 0, nb_nh = 0, nb_np = 0;
-    bool any_recomb = false, any_neutral = false;
+    int nb_dh = 0, nb_dp = 0;
+    bool any_recomb = false, any_neutral = false, any_edet = false;
     size_t smem_push = 0, smem_field = 0, smem_hist = 0;
 };
 
@@ -1061,7 +1122,7 @@ void batch_release_graph(o2pic_batch* b) {
 int fused_tables(o2pic_batch* b) {
     const size_t n = b->ctx.size();
     std::vector<Params> hp(n);
-    std::vector<PairSpec> hr(n), hn(n);
+    std::vector<PairSpec> hr(n), hn(n), hd(n);
     std::vector<uint4> map;
     auto add_map = [&](size_t& off, int& nb, auto blocks_of) {
         off = map.size();
@@ -1072,19 +1133,17 @@ int fused_tables(o2pic_batch* b) {
         nb = (int)(map.size() - off);
     };
     auto tiles = [](unsigned long long cap) { return std::max<unsigned long long>(1, ceil_div(cap, TILE)); };
-    b->any_recomb = b->any_neutral = false;
+    b->any_recomb = b->any_neutral = b->any_edet = false;
     b->smem_push = b->smem_field = b->smem_hist = 0;
     for (size_t i = 0; i < n; ++i) {
         o2pic_ctx* c = b->ctx[i];
         const Params& P = c->P;
         hp[i] = P;
-        hr[i] = PairSpec{SP_E, SP_OP, P.rhist[0], P.rhist[1], P.rtot, P.Ktab_r, P.Kmax_r_hi, P.kappa_r, TAG_REC,
-                         TAG_SHIFT_REC, P.rremoval, &c->d_ctrl->rremovals, P.max_rremovals,
-                         &c->d_ctrl->cnt.rec_candidates, &c->d_ctrl->cnt.recombined, P.have_recomb};
-        hn[i] = PairSpec{SP_OM, SP_OP, P.hist[0], P.hist[1], P.ptot, P.Ktab, P.Kmax_hi, P.kappa_n, TAG_PAIR,
-                         TAG_SHIFT, P.removal, &c->d_ctrl->removals, P.max_removals,
-                         &c->d_ctrl->cnt.pair_candidates, &c->d_ctrl->cnt.neutralized, P.have_neutral};
+        hr[i] = spec_rec(c);
+        hn[i] = spec_neu(c);
+        hd[i] = spec_edet(c);
         b->any_recomb |= P.have_recomb != 0;
+        b->any_edet |= P.have_edet != 0;
         b->any_neutral |= P.have_neutral != 0;
         for (int sp = 0; sp < NSP; ++sp) b->smem_push = std::max(b->smem_push, push_smem_bytes(sp, P));
         b->smem_field = std::max(b->smem_field, field_smem_bytes(P));
@@ -1095,6 +1154,9 @@ int fused_tables(o2pic_batch* b) {
         add_map(b->map_comp[sp], b->nb_comp[sp],
                 [&](o2pic_ctx* c) { return std::min<unsigned long long>(tiles(c->P.sp[sp].cap), 16); });
     }
+    add_map(b->map_dh, b->nb_dh, [&](o2pic_ctx* c) {
+        return std::min<unsigned long long>(tiles(c->P.sp[SP_OM].cap) + tiles(c->P.sp[SP_E].cap), 32); });
+    add_map(b->map_dp, b->nb_dp, [&](o2pic_ctx* c) { return std::min<unsigned long long>(tiles(c->P.sp[SP_OM].cap), 64); });
     add_map(b->map_rh, b->nb_rh, [&](o2pic_ctx* c) {
         return std::min<unsigned long long>(tiles(c->P.sp[SP_E].cap) + tiles(c->P.sp[SP_OP].cap), 32); });
     add_map(b->map_rp, b->nb_rp, [&](o2pic_ctx* c) { return std::min<unsigned long long>(tiles(c->P.sp[SP_E].cap), 64); });
@@ -1103,16 +1165,19 @@ int fused_tables(o2pic_batch* b) {
     add_map(b->map_np, b->nb_np, [&](o2pic_ctx* c) { return std::min<unsigned long long>(tiles(c->P.sp[SP_OM].cap), 64); });
     if (b->dP) cudaFree(b->dP);
     if (b->dR) cudaFree(b->dR);
+    if (b->dD) cudaFree(b->dD);
     if (b->dN) cudaFree(b->dN);
     if (b->dmap) cudaFree(b->dmap);
-    b->dP = nullptr; b->dR = b->dN = nullptr; b->dmap = nullptr;
+    b->dP = nullptr; b->dR = b->dN = b->dD = nullptr; b->dmap = nullptr;
     if (cudaMalloc((void**)&b->dP, sizeof(Params) * n) != cudaSuccess ||
         cudaMalloc((void**)&b->dR, sizeof(PairSpec) * n) != cudaSuccess ||
+        cudaMalloc((void**)&b->dD, sizeof(PairSpec) * n) != cudaSuccess ||
         cudaMalloc((void**)&b->dN, sizeof(PairSpec) * n) != cudaSuccess ||
         cudaMalloc((void**)&b->dmap, sizeof(uint4) * std::max<size_t>(map.size(), 1)) != cudaSuccess)
         return O2PIC_E_CUDA;
     if (cudaMemcpy(b->dP, hp.data(), sizeof(Params) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dR, hr.data(), sizeof(PairSpec) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dD, hd.data(), sizeof(PairSpec) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dN, hn.data(), sizeof(PairSpec) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dmap, map.data(), sizeof(uint4) * map.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return O2PIC_E_CUDA;
@@ -1138,6 +1203,12 @@ void enqueue_fused(o2pic_batch* b, cudaStream_t s) {
                 launch_push_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], b->smem_push, s);
                 launch_filter_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
                 launch_cand_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
+                launches += 3;
+            }
+            if (b->any_edet) {
+                launch_pair_hist_batched(b->dP, b->dD, b->dmap + b->map_dh, b->nb_dh, b->smem_hist, s);
+                launch_pair_batched(b->dP, b->dD, b->dmap + b->map_dp, b->nb_dp, s);
+                launch_edet_apply_batched(b->dP, b->dD, n, s);
                 launches += 3;
             }
             if (b->any_recomb) {
@@ -1443,7 +1514,7 @@ void o2pic_batch_destroy(o2pic_batch* b) {
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
     if (b->stream) cudaStreamDestroy(b->stream);
-    for (void* p : {(void*)b->dP, (void*)b->dR, (void*)b->dN, (void*)b->dmap}) if (p) cudaFree(p);
+    for (void* p : {(void*)b->dP, (void*)b->dR, (void*)b->dN, (void*)b->dD, (void*)b->dmap}) if (p) cudaFree(p);
     delete b;
 }
 

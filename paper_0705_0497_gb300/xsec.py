@@ -30,10 +30,12 @@ from .inputs import EPS0, QE
 # species
 E, OM, OP = 0, 1, 2
 # process kinds (same numbering as the C ABI)
-ELASTIC, EXCITE, IONIZE, ATTACH, DETACH, CX, NEUTRALIZE, RECOMBINE = range(8)
-KIND_NAMES = ("elastic", "excite", "ionize", "attach", "detach", "cx", "neutralize", "recombine")
+ELASTIC, EXCITE, IONIZE, ATTACH, DETACH, CX, NEUTRALIZE, RECOMBINE, EDETACH = range(9)
+KIND_NAMES = ("elastic", "excite", "ionize", "attach", "detach", "cx", "neutralize", "recombine", "edetach")
 # targets
-T_O2, T_O2_META, T_ION = 0, 1, 2
+T_O2, T_O2_META, T_ION, T_ELECTRON = 0, 1, 2, 3
+# electron affinity of O [eV]: the threshold of (22) e + O- -> O + 2e
+O_AFFINITY_EV = 1.461
 
 # Rate-table grid used by both implementations: 32 points per octave on
 # [2^-10, 2^12] eV.  Curves given exactly at these energies interpolate without
@@ -177,11 +179,27 @@ def recombination_process():
     return _proc(E, RECOMBINE, T_ION, 0.0, GRID, sigma_r(GRID), "(16) recombination")
 
 
-def oxygen_set(include_ad=True, R_x_m=1.0e-9, include_rec=False):
-    """The full 3-species set used by the workloads ((16) on request)."""
+def sigma_edetach(E_eV, thr=O_AFFINITY_EV):
+    """(22) e + O- -> O + 2e electron-impact detachment: placeholder shape with
+    the O electron affinity as threshold, rising to 5e-20 m^2 near 20 eV
+    (the paper lists (22) in Table 1 without its cross section)."""
+    return _rise(np.asarray(E_eV, dtype=np.float64), thr, 20.0, 5.0e-20)
+
+
+def edetach_process(thr=O_AFFINITY_EV):
+    """(22) e + O- -> O + 2e, binary and cell-local like (17) (species O-,
+    partner the electrons), on ion steps before (16) and (17)."""
+    Ex = _energies(thr)
+    return _proc(OM, EDETACH, T_ELECTRON, thr, Ex, sigma_edetach(Ex, thr), "(22) electron detachment")
+
+
+def oxygen_set(include_ad=True, R_x_m=1.0e-9, include_rec=False, include_edet=False):
+    """The full 3-species set used by the workloads ((16), (22) on request)."""
     out = electron_processes() + om_processes(include_ad) + op_processes() + [neutralization_process(R_x_m)]
     if include_rec:
         out.append(recombination_process())
+    if include_edet:
+        out.append(edetach_process())
     return out
 
 

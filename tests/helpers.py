@@ -10,7 +10,7 @@ from paper_0705_0497_gb300 import inputs, xsec
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 COUNTERS_COMPARED = ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
-                     "recombined", "rec_candidates", "id_overflow")
+                     "recombined", "rec_candidates", "id_overflow", "edetached", "edet_candidates")
 
 
 def capacity_for(counts, factor=2.0, extra=4096):
@@ -65,7 +65,8 @@ def compare_counters(gs, oc, nproc):
 
 
 def nproc_of(procs):
-    return [sum(1 for p in procs if p["species"] == s and p["kind"] not in (xsec.NEUTRALIZE, xsec.RECOMBINE))
+    return [sum(1 for p in procs if p["species"] == s and p["kind"] not in (xsec.NEUTRALIZE, xsec.RECOMBINE,
+                                                                            xsec.EDETACH))
             for s in range(3)]
 
 

@@ -48,7 +48,7 @@ def test_batch_equals_single_runs(torch_cuda, monkeypatch, branches):
     from paper_0705_0497_gb300 import api
     if branches:
         monkeypatch.setenv("O2PIC_BATCH_BRANCHES", "1")
-    procs = xsec.oxygen_set(include_rec=True)
+    procs = xsec.oxygen_set(include_rec=True, include_edet=True)
     sweep = _sweep(4)
     batched = [_discharge(c, n, T, procs) for c, n, T in sweep]
     alone = [_discharge(c, n, T, procs) for c, n, T in sweep]
@@ -65,7 +65,7 @@ def test_batch_equals_single_runs(torch_cuda, monkeypatch, branches):
 
 def test_batch_member_matches_oracle(torch_cuda):
     from paper_0705_0497_gb300 import api
-    procs = xsec.oxygen_set()
+    procs = xsec.oxygen_set(include_rec=True, include_edet=True)
     (c0, n0, T0), (c1, n1, T1) = _sweep(2, scale=0.01, seed=11)
     g0, o0, _ = make_pair(c0, n0, T0, procs, compact_check=CC)
     g1 = _discharge(c1, n1, T1, procs)

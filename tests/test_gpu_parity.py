@@ -355,6 +355,53 @@ def test_recombination_parity(torch_cuda, n_e, n_op):
     assert c["recombined"] > 0.01 * min(n_e, n_op) and c["neutralized"] > 0
 
 
+@pytest.mark.parametrize("n_e,n_om", [(30000, 26000), (20000, 30000)])
+def test_edetach_parity(torch_cuda, n_e, n_om):
+    """(22) e + O- -> O + 2e with a large constant rate coefficient, before
+    (16) and (17) on the same ion steps: pairs, kinematics and newborns (their
+    order and free flights) against the oracle, particle for particle, and
+    every counter.  A threshold-carrying (22) runs in the second case."""
+    Nc = 32
+    cfg = inputs.base_config(L=0.02, n_cells=Nc, U=0.0, p=10.0, C_meta=0.0, ion_subcycle=2, weight=1e3, seed=7,
+                             steps_per_cycle=400)
+    dx = cfg["L"] / Nc
+    mud = cfg["m_e"] * cfg["m_OM"] / (cfg["m_e"] + cfg["m_OM"])
+    mur = cfg["m_e"] * cfg["m_OP"] / (cfg["m_e"] + cfg["m_OP"])
+    mun = cfg["m_OM"] * cfg["m_OP"] / (cfg["m_OM"] + cfg["m_OP"])
+    K0 = 1e-4 * cfg["area"] * dx / (cfg["weight"] * cfg["dt"] * 2)
+    thr = 0.0 if n_e > n_om else xsec.O_AFFINITY_EV
+    procs = [xsec.constant_rate_process(1, xsec.EDETACH, K0, 1.0, mud, target=xsec.T_ELECTRON, thr=thr),
+             xsec.constant_rate_process(0, xsec.RECOMBINE, K0, 1.0, mur, target=xsec.T_ION),
+             xsec.constant_rate_process(1, xsec.NEUTRALIZE, K0, 1.0, mun, target=xsec.T_ION)]
+    rng = np.random.default_rng(11)
+    st = []
+    for s, n in enumerate((n_e, n_om, 8000)):
+        x = ((rng.integers(0, Nc, n) + 0.05 + 0.9 * rng.random(n)) * dx).astype(np.float32)
+        v = (rng.standard_normal((3, n)) * (1e6 if s == 0 else 300.0)).astype(np.float32)
+        st.append(dict(x=x, vx=v[0].copy(), vy=v[1].copy(), vz=v[2].copy(), id=np.arange(n, dtype=np.uint32)))
+    g, o, _ = make_pair(cfg, None, None, procs, state=st)
+    for _ in range(3):
+        g.step(2)
+        o.step(2)
+        compare_particles(g, o)
+        compare_counters(g.stats(), o.counters(), nproc_of(procs))
+    c = o.counters()
+    assert c["edetached"] > 0.005 * min(n_e, n_om) and c["recombined"] > 0 and c["neutralized"] > 0
+
+
+def test_oxygen_set_with_edetach_100_steps(torch_cuda):
+    """The full process set with (16) and (22) added: 100 steps of the parity
+    case, per particle and every counter."""
+    cfg, counts, T, _ = inputs.workload("parity_128", ion_subcycle=2)
+    procs = xsec.oxygen_set(include_rec=True, include_edet=True)
+    g, o, _ = make_pair(cfg, counts, T, procs)
+    g.step(100)
+    o.step(100)
+    compare_particles(g, o)
+    compare_counters(g.stats(), o.counters(), nproc_of(procs))
+    assert o.counters()["edet_candidates"] > 0
+
+
 def test_oxygen_set_with_recombination_100_steps(torch_cuda):
     """The full process set with (16) added: 100 steps of the parity case,
     per particle and every counter."""

@@ -950,3 +950,136 @@ def test_candidates_per_step_are_binomial(oracle_mod):
     # every particle's next candidate lies ahead, on its own push grid
     tc = o.flight(0)
     assert np.all(tc >= 12)
+
+
+# ------------------------------------------------- (22) e + O- -> O + 2e
+def test_edetach_expected_count_and_products(oracle_mod):
+    """Cell-binned (22) with a constant rate coefficient K and no threshold:
+    Sum n_e n- w K dt / (A dx) reactions per ion step, each removing one O-
+    and adding one electron; the step's (22) births follow in the order of
+    their O- parents."""
+    Nc = 16
+    cfg = _cfg(n_cells=Nc, weight=1.0e-3, ion_subcycle=1)
+    dx = cfg["L"] / Nc
+    K0 = 2.0e-4 * cfg["area"] * dx / (cfg["weight"] * cfg["dt"])   # P_pair = 2e-4 M
+    mud = cfg["m_e"] * cfg["m_OM"] / (cfg["m_e"] + cfg["m_OM"])
+    pr = xsec.constant_rate_process(1, xsec.EDETACH, K0, 1.0, mud, target=xsec.T_ELECTRON)
+    rng = np.random.default_rng(22)
+    z = lambda n: np.zeros(n, np.float32)
+
+    def cells(counts):
+        x = np.concatenate([(c + 0.1 + 0.8 * rng.random(counts[c])) * dx for c in range(Nc)]).astype(np.float32)
+        rng.shuffle(x)
+        return x
+
+    expected, got = 0.0, 0
+    for trial in range(4):
+        cfg["seed"] = 300 + trial
+        o = oracle_mod.Oracle(cfg, 32)
+        o.set_processes([pr])
+        ne = rng.integers(200, 1200, Nc)
+        nm = rng.integers(200, 1200, Nc)
+        xe, xm = cells(ne), cells(nm)
+        # electrons and O- at rest at the same places: no net charge, no field
+        o.load(0, xe, z(len(xe)), z(len(xe)), z(len(xe)), np.arange(len(xe), dtype=np.uint32))
+        o.load(1, xm, z(len(xm)), z(len(xm)), z(len(xm)), np.arange(len(xm), dtype=np.uint32))
+        _empty(o, (2,))
+        o.step(1)
+        c = o.counters()
+        got += c["edetached"]
+        expected += float((ne * nm).sum()) * cfg["weight"] * K0 * cfg["dt"] / (cfg["area"] * dx)
+        assert c["edet_candidates"] == int(np.minimum(ne, nm).sum())
+        assert o.count(1) == len(xm) - c["edetached"] and o.count(0) == len(xe) + c["edetached"]
+        assert c["born_0"] == c["edetached"]
+        # the newborns sit at their parents' places, in the parents' order
+        e, m = o.particles(0), o.particles(1)
+        born_x = e["x"][len(xe):].astype(np.float32)
+        gone = np.setdiff1d(np.arange(len(xm)), m["id"])       # parents (ids = load order)
+        assert np.array_equal(born_x, xm[np.sort(gone)])
+    assert 2000 < expected < 20000
+    assert abs(got - expected) < 5 * math.sqrt(expected)
+
+
+def test_edetach_energy_balance_threshold_and_order(oracle_mod):
+    """(22) kinematics: below the threshold nothing reacts; above it the two
+    electrons share E_rel - E_th (E_rel with the e-O- reduced mass, the
+    outgoing energies relative to the O-), the share is uniform on [0, 1),
+    directions isotropic.  (22) runs before (17): with both certain, the O-
+    are gone before (17) counts them."""
+    Nc = 4
+    cfg = _cfg(n_cells=Nc, weight=1.0e-3, ion_subcycle=1)
+    dx = cfg["L"] / Nc
+    thr = xsec.O_AFFINITY_EV
+    mud = cfg["m_e"] * cfg["m_OM"] / (cfg["m_e"] + cfg["m_OM"])
+    Kbig = 2.0 * cfg["area"] * dx / (cfg["weight"] * cfg["dt"])
+    pr = xsec.constant_rate_process(1, xsec.EDETACH, Kbig, 1.0, mud, target=xsec.T_ELECTRON, thr=thr)
+    kap_e = 0.5 * ME / QE
+    kap_d = 0.5 * mud / QE
+    rng = np.random.default_rng(23)
+    z = lambda n: np.zeros(n, np.float32)
+    n = 3000
+    xm = ((rng.integers(0, Nc, n) + 0.1 + 0.8 * rng.random(n)) * dx).astype(np.float32)
+    xe = xm.copy()
+    # electrons along y (no motion in x) with energies across the threshold
+    E0 = rng.uniform(0.2, 40.0, n)
+    vy = np.sqrt(E0 / kap_d).astype(np.float32)
+    for precision in (64, 32):
+        o = oracle_mod.Oracle(cfg, precision)
+        o.set_processes([pr])
+        o.load(0, xe, z(n), vy, z(n), np.arange(n, dtype=np.uint32))
+        o.load(1, xm, z(n), z(n), z(n), np.arange(n, dtype=np.uint32))
+        _empty(o, (2,))
+        o.step(1)
+        c = o.counters()
+        e = o.particles(0)
+        gone = np.setdiff1d(np.arange(n), o.particles(1)["id"])
+        assert c["edetached"] == len(gone) > 300
+        # never below threshold (the pairing matched each O- with some electron of its cell)
+        Erel_all = kap_d * vy.astype(np.float64) ** 2
+        assert len(gone) <= int((Erel_all >= thr).sum())
+        Ep = kap_e * (e["vx"][:n] ** 2 + e["vy"][:n] ** 2 + e["vz"][:n] ** 2)
+        Eb = kap_e * (e["vx"][n:] ** 2 + e["vy"][n:] ** 2 + e["vz"][n:] ** 2)
+        # the electrons that reacted changed their speed; match them by energy balance
+        changed = np.nonzero(np.abs(Ep - Erel_all * (ME / mud)) > 1e-6 * Erel_all)[0]
+        assert len(changed) == len(gone)
+        Ein = Erel_all[changed]
+        assert np.all(Ein >= thr)
+        rtol = 1e-9 if precision == 64 else 2e-5
+        # energy balance summed over the reactions: sum (E_p + E_s) = sum (E_rel - E_th)
+        assert abs((Ep[changed].sum() + Eb.sum()) - (Ein - thr).sum()) <= rtol * (Ein - thr).sum()
+    # the share of the detached electron is uniform: one electron per cell so
+    # that each pair is known
+    cfg1 = _cfg(n_cells=1, weight=1.0e-3, ion_subcycle=1)
+    Kone = 2.0 * cfg1["area"] * cfg1["L"] / (cfg1["weight"] * cfg1["dt"])
+    pr1 = xsec.constant_rate_process(1, xsec.EDETACH, Kone, 1.0, mud, target=xsec.T_ELECTRON, thr=thr)
+    shares = []
+    for k in range(400):
+        cfg1["seed"] = 1000 + k
+        o = oracle_mod.Oracle(cfg1, 64)
+        o.set_processes([pr1])
+        E1 = 10.0
+        o.load(0, np.array([0.5 * cfg1["L"]], np.float32), z(1), np.array([math.sqrt(E1 / kap_d)], np.float32), z(1),
+               np.array([0], np.uint32))
+        o.load(1, np.array([0.5 * cfg1["L"]], np.float32), z(1), z(1), z(1), np.array([0], np.uint32))
+        _empty(o, (2,))
+        o.step(1)
+        e = o.particles(0)
+        assert len(e["x"]) == 2 and o.count(1) == 0
+        Ep1 = kap_e * (e["vx"][0] ** 2 + e["vy"][0] ** 2 + e["vz"][0] ** 2)
+        Es1 = kap_e * (e["vx"][1] ** 2 + e["vy"][1] ** 2 + e["vz"][1] ** 2)
+        E_in = kap_d * float(np.float32(math.sqrt(E1 / kap_d))) ** 2
+        assert Ep1 + Es1 == pytest.approx(E_in - thr, rel=1e-9)
+        shares.append(Es1 / (E_in - thr))
+    assert stats.kstest(shares, "uniform").pvalue > 1e-3
+    # order against (17): both certain, (22) first
+    mun = cfg["m_OM"] * cfg["m_OP"] / (cfg["m_OM"] + cfg["m_OP"])
+    o = oracle_mod.Oracle(cfg, 32)
+    o.set_processes([xsec.constant_rate_process(1, xsec.EDETACH, Kbig, 1.0, mud, target=xsec.T_ELECTRON),
+                     xsec.constant_rate_process(1, xsec.NEUTRALIZE, Kbig, 1.0, mun, target=xsec.T_ION)])
+    ne, nm, npl = 300, 100, 200
+    x = lambda k: ((rng.integers(0, Nc, k) + 0.1 + 0.8 * rng.random(k)) * dx).astype(np.float32)
+    for s, k in ((0, ne), (1, nm), (2, npl)):
+        o.load(s, x(k), z(k), z(k), z(k), np.arange(k, dtype=np.uint32))
+    o.step(1)
+    c = o.counters()
+    assert c["neutralized"] == 0 and o.count(1) == 0 and c["edetached"] == nm
