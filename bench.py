@@ -2,28 +2,31 @@
 
 Workload (N=1): `scale_512` — 2.5 cm gap, 512 cells, U = 300 V, p = 20 Pa,
 metastable fraction 5%, 1000 steps per RF cycle, ions subcycled x10,
-4e6 e + 4e6 O- + 8e6 O2+ (quasi-neutral load), synthetic seeded inputs.
-One bench step = one RF cycle (1000 time steps: every step pushes the
-electrons, every 10th also the ions and runs the O-/O2+ neutralization; each
-step ends with the deposit and the Poisson solve), run as one replay of the
-library's step graph (o2pic_batch_* with a single discharge).  The particle
-arrays (320 MB) exceed the 129 MB L2, so no flush is needed between steps.
-`--workload batch_sweep_64` runs the 64-discharge sweep of the batched
-stepper instead (its own JSON line).
+4e6 e + 4e6 O- + 8e6 O2+ (quasi-neutral load), synthetic seeded inputs,
+settled 100 RF cycles before the warm-up (the load drains for ~90 cycles;
+afterwards the live counts drift by < 0.5 % per cycle).  One bench step = one
+RF cycle (1000 time steps: every step pushes the electrons, every 10th also
+the ions and runs the O-/O2+ neutralization; each step ends with the deposit
+and the Poisson solve), run as one replay of the library's step graph
+(o2pic_batch_* with a single discharge).  Other workloads (their own JSON
+line): `stress_2048` (2048 cells, 1.2e8 particles, no subcycling, 2000
+steps per cycle), `parity_128` (the small parity case, 400 steps per cycle)
+and `batch_sweep_64` (the 64-discharge sweep of the batched stepper).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
 Under torchrun each rank runs an independent replica (seed = rank): the
 method does not shard (one discharge is one coupled field solve), so N GPUs
 run N discharges and `value` sums their particle-steps over the max time.
-`--impl reference` times the CPU oracle (test infrastructure, single thread)
-on bounded samples of the same workload.
+`--impl reference` times the CPU oracle (test infrastructure) on all host
+cores on bounded samples of the same workload.
 """
 import argparse
 import hashlib
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -37,10 +40,14 @@ import numpy as np
 from paper_0705_0497_gb300 import inputs, xsec
 
 WORKLOAD = "scale_512"
+# per workload: RF cycles run before the warm-up (to reach the periodic
+# state), and the oracle's bounded sample for the CPU baseline (time steps)
+SETTLE = {"scale_512": 100, "stress_2048": 3, "parity_128": 10}
+CPU_SAMPLE_STEPS = {"scale_512": 10, "stress_2048": 2, "parity_128": 400}
 METRIC = "particle-steps/s (push+MCC+deposit) on 1 GB300, fraction of HBM roofline"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = 40          # read + write of x, vx, vy, vz, id (algorithmic)
-IMPL_BYTES_PER_PARTICLE_STEP = 20     # this implementation: read x, vx, id (12 B), write x, vx (8 B) in place
+IMPL_BYTES_PER_PARTICLE_STEP = 20     # this implementation: read x, vx, tc (12 B), write x, vx (8 B) in place
 PROFILE = os.path.join(ROOT, "profiles", "push_e_scale_512.md")
 
 
@@ -178,16 +185,42 @@ def barrier():
         dist.barrier()
 
 
-def capacity(counts):
-    return tuple(int(n * 1.5) + (1 << 20) for n in counts)
+# slots per species per initial particle (the stress discharge at 500 V
+# multiplies its electrons and ions)
+CAPACITY_FACTOR = {"stress_2048": 3.0}
 
 
-def run_cpu_oracle(cfg, counts, T, nsteps, seed=0):
-    """The oracle, single thread, on the first `nsteps` time steps of the
-    workload with its full initial load; returns particle-steps/s."""
+def capacity(counts, wl=WORKLOAD):
+    f = CAPACITY_FACTOR.get(wl, 1.5)
+    return tuple(int(n * f) + (1 << 20) for n in counts)
+
+
+def cpu_model():
+    """The host CPU's model (x86: model name; Arm: implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info:
+                if line.startswith(key):
+                    v = line.split(":", 1)[1].strip()
+                    if key == "CPU part":
+                        impl = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+                        return f"{platform.machine()} implementer {impl[0] if impl else '?'} part {v}"
+                    return v
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def run_cpu_oracle(cfg, counts, T, nsteps, threads, seed=0):
+    """The oracle on `threads` host threads on the first `nsteps` time steps
+    of the workload with its full initial load; returns particle-steps/s,
+    particle-steps, seconds and the threads used."""
     import oracle
     st = inputs.initial_state(cfg, counts, T, seed=seed)
     o = oracle.Oracle(cfg, 32)
+    used = min(threads, o.set_threads(threads))
+    o.set_threads(used)
     o.set_processes(xsec.oxygen_set())
     for s, p in enumerate(st):
         o.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])
@@ -198,19 +231,22 @@ def run_cpu_oracle(cfg, counts, T, nsteps, seed=0):
     o.step(nsteps)
     dt = time.perf_counter() - t
     ps = o.counters()["particle_steps"] - c0
-    return ps / dt, ps, dt
+    return ps / dt, ps, dt, used
 
 
 def bench_reference(args, world, rank):
+    """The reference arm: the CPU oracle on all host cores, one time step of
+    the workload per bench step (a bounded sample of an RF cycle)."""
     if rank != 0:
         return 0
-    cfg, counts, T, _ = inputs.workload(WORKLOAD)
+    wl = args.workload if args.workload != "batch_sweep_64" else WORKLOAD
+    cfg, counts, T, _ = inputs.workload(wl)
     spc = cfg["steps_per_cycle"]
-    # one reference step = one time step of the workload (a bounded sample of a cycle)
-    per = []
     import oracle
     st = inputs.initial_state(cfg, counts, T)
     o = oracle.Oracle(cfg, 32)
+    threads = o.set_threads(os.cpu_count() or 1)
+    o.set_threads(threads)
     o.set_processes(xsec.oxygen_set())
     for s, p in enumerate(st):
         o.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])
@@ -219,23 +255,21 @@ def bench_reference(args, world, rank):
     o.step(args.warmup)
     c0 = o.counters()["particle_steps"]
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        o.step(1)
-        per.append(time.perf_counter() - t)
+    o.step(args.steps)
     wall = time.perf_counter() - t0
     ps = o.counters()["particle_steps"] - c0
     value = ps / wall
+    sample = (f"time steps {args.warmup}..{args.warmup + args.steps - 1} of {wl} with the full "
+              f"{sum(counts):.3g}-particle load, {threads} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "one time step (bounded sample of an RF cycle)",
+            "config": {"workload": wl, "step": "one time step (bounded sample of an RF cycle)",
                        "n_cells": cfg["n_cells"], "particles": list(counts), "steps_per_cycle": spc,
                        "ion_subcycle": cfg["ion_subcycle"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"time steps {args.warmup}..{args.warmup + args.steps - 1} of {WORKLOAD} "
-                                       "with the full 1.6e7-particle load"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -245,18 +279,20 @@ def bench_gpu(args, world, rank, local):
     import torch
     from paper_0705_0497_gb300 import api
     torch.cuda.set_device(local)
-    cfg, counts, T, cycles = inputs.workload(WORKLOAD, seed=rank)
+    wl = args.workload
+    cfg, counts, T, cycles = inputs.workload(wl, seed=rank)
     spc = cfg["steps_per_cycle"]
     st = inputs.initial_state(cfg, counts, T, seed=rank)
-    # compaction check every 20 steps: a multiple-of-both divisor of the
-    # 1000-step cycle and the 10-step ion subcycle, so one RF cycle is one
-    # replay of the library's step graph
-    g = api.Discharge(cfg, capacity(counts), device=local, compact_check=20)
+    # compaction check every 20 steps: a divisor of the RF cycle and of the
+    # ion subcycle, so one RF cycle is one replay of the library's step graph
+    g = api.Discharge(cfg, capacity(counts, wl), device=local, compact_check=20)
     g.set_processes(xsec.oxygen_set())
     g.load_state(st)
     del st
-    stream = torch.cuda.Stream(device=local)
     b = api.Batch([g], steps_per_launch=spc)
+    settle = SETTLE.get(wl, 0) if args.settle < 0 else args.settle
+    if settle:
+        b.step(settle)
     b.step(args.warmup)
     b.synchronize()
     live0 = [g.count(s) for s in range(3)]
@@ -281,12 +317,15 @@ def bench_gpu(args, world, rank, local):
     live1 = [g.count(s) for s in range(3)]
     b.close()
 
-    # ---- timed region B: the same loop with an event pair around every launch
+    # ---- timed region B: the same loop with an event pair around every
+    # launch (the per-kernel split and the roofline kernel's average launch);
+    # the events add a gap after every launch and undo the programmatic
+    # overlap, so these per-kernel times sum to more than region A's cycle
     kb = max(1, min(args.steps, 10))
     g.set_timing(True)
     sb0 = g.stats()
     for _ in range(kb):
-        g.step(spc, stream)
+        g.step(spc)
     g.synchronize()
     tm = g.timing()
     sb1 = g.stats()
@@ -306,7 +345,6 @@ def bench_gpu(args, world, rank, local):
         host.append(d)
     g.moments(reset=True)
     torch.cuda.synchronize()
-    se0 = g.stats()["particle_steps"]
     ps_e2e = 0
     h2d = d2h = 0
     t0 = time.perf_counter()
@@ -317,7 +355,7 @@ def bench_gpu(args, world, rank, local):
             g.load(s, d["x"][:n], d["vx"][:n], d["vy"][:n], d["vz"][:n], d["id"][:n])
             h2d += 20 * n
         c0 = g.stats()["particle_steps"]
-        g.step(spc, stream)
+        g.step(spc)
         for s in range(3):
             d = host[s]
             need = g.count(s)
@@ -340,36 +378,52 @@ def bench_gpu(args, world, rank, local):
     value = ps_sum / (t_max * 1e-3)
     peak, peak_kind = measured_peaks()
     ms_e, n_e = tm["push_e"]
-    achieved = (pe / n_e) * BYTES_PER_PARTICLE_STEP / (ms_e / n_e * 1e-3) / 1e9 if n_e else None
+    per_launch = pe / n_e if n_e else None
+    launch_s = ms_e / n_e * 1e-3 if n_e else None
+    achieved = per_launch * BYTES_PER_PARTICLE_STEP / launch_s / 1e9 if n_e else None
     traffic_pp, prof = profile_traffic()
-    roofline = {"bound": "hbm", "kernel": "k_push<e> (gather, push, absorb, MCC, deposit)",
+    roofline = {"bound": "hbm", "kernel": "k_push<e> (gather, push, absorb, free flights, deposit)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs: copy bandwidth)",
-                "traffic": (traffic_pp * pe / n_e) if (traffic_pp and n_e) else None,
+                "traffic": (traffic_pp * per_launch) if (traffic_pp and n_e) else None,
                 "algorithmic_bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
+                "note": ("achieved = the algorithmic 40 B per particle-step (read + write of x, vx, vy, vz, id) "
+                         "/ average launch time; the kernel moves 20 B per particle (x, vx, tc read, x, vx "
+                         "written in place; id, vy, vz for collision candidates only, impl_frac) and the "
+                         "electrons' 12 B per particle stay in L2 between ion steps, so this is an effective "
+                         "bandwidth, not a DRAM measurement (traffic = ncu DRAM bytes per launch)"),
                 "impl_bytes_per_particle_step": IMPL_BYTES_PER_PARTICLE_STEP,
-                "impl_frac": ((pe / n_e) * IMPL_BYTES_PER_PARTICLE_STEP / (ms_e / n_e * 1e-3) / 1e9 / peak)
-                if n_e else None,
-                "electron_particles_per_launch": pe / n_e if n_e else None,
+                "impl_frac": (per_launch * IMPL_BYTES_PER_PARTICLE_STEP / launch_s / 1e9 / peak) if n_e else None,
+                "electron_particles_per_launch": per_launch,
                 "avg_launch_us": ms_e / n_e * 1e3 if n_e else None,
-                "kernel_share_of_step": ms_e / sum(v[0] for v in tm.values()) if n_e else None,
-                "per_kernel_ms_per_cycle": {k: v[0] / kb for k, v in tm.items() if v[1]}}
+                "whole_loop_frac": value * BYTES_PER_PARTICLE_STEP / 1e9 / peak,
+                "per_kernel_ms_per_cycle_instrumented": {k: v[0] / kb for k, v in tm.items() if v[1]},
+                "kernel_share_of_instrumented_cycle": ms_e / sum(v[0] for v in tm.values()) if n_e else None}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, cps, cdt = run_cpu_oracle(cfg, counts, T, 10)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first 10 time steps (one ion subcycle) of {WORKLOAD} with the full "
-                         f"{sum(counts):.3g}-particle load: {cps} particle-steps in {cdt:.1f} s"}
+        nsteps = CPU_SAMPLE_STEPS.get(wl, 10)
+        allc = os.cpu_count() or 1
+        v, cps, cdt, used = run_cpu_oracle(cfg, counts, T, nsteps, allc)
+        v1, cps1, cdt1, _ = run_cpu_oracle(cfg, counts, T, nsteps, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"first {nsteps} time steps of {wl} with the full {sum(counts):.3g}-particle load: "
+                         f"{cps} particle-steps in {cdt:.2f} s on {used} threads",
+               "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+               "single_thread": {"value": v1, "cores": 1, "seconds": cdt1}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "one RF cycle = 1000 time steps",
+            "config": {"workload": wl, "step": f"one RF cycle = {spc} time steps",
                        "L_m": cfg["L"], "n_cells": cfg["n_cells"], "U_V": cfg["U"], "p_Pa": cfg["p"],
                        "C_meta": cfg["C_meta"], "ion_subcycle": cfg["ion_subcycle"],
-                       "initial_particles": list(counts), "live_at_timed_start": live0,
-                       "live_at_timed_end": live1, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (particle arrays 320 MB > 129 MB L2), no flush"},
+                       "initial_particles": list(counts), "settle_cycles": settle,
+                       "live_at_timed_start": live0, "live_at_timed_end": live1,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": ("particle arrays (all species, x, vx, vy, vz, id, tc) exceed the 129 MB L2, no flush; "
+                              "the electrons' per-step working set (x, vx, tc) stays in L2 between ion steps"
+                              if wl != "parity_128" else
+                              "L2-resident by design (2.2e4 particles: the latency-bound parity case), no flush")},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_ps_sum / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
                     "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
@@ -469,7 +523,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_sweep_64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "stress_2048", "parity_128", "batch_sweep_64"])
+    ap.add_argument("--settle", type=int, default=-1,
+                    help="RF cycles run before the warm-up (default: per workload, 100 for scale_512)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only step the workload this many single steps (a fixed launch sequence for ncu) and exit")
     args = ap.parse_args()

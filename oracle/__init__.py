@@ -37,7 +37,7 @@ COUNTER_NAMES = ([f"events_{s}_{k}" for s in range(NSP) for k in range(MAXPROC)]
                  [f"absorbed_{s}_{w}" for s in range(NSP) for w in range(2)] +
                  [f"born_{s}" for s in range(NSP)] +
                  ["neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries",
-                  "warn_pair_gt1", "id_overflow", "recombined", "rec_candidates", "edetached", "edet_candidates"])
+                  "warn_pair_gt1", "id_overflow", "recombined", "rec_candidates", "edetached", "edet_candidates", "coulomb_pairs"])
 
 
 def lib():
@@ -53,6 +53,9 @@ def lib():
         L.oracle_set_processes.argtypes = [vp, P(OracleProcess), i32]
         L.oracle_load.argtypes = [vp, i32, vp, vp, vp, vp, vp, u64]
         L.oracle_set_next_id.argtypes = [vp, i32, u32]
+        L.oracle_set_coulomb.argtypes = [vp, u32, dbl]
+        L.oracle_set_threads.argtypes = [vp, i32]
+        L.oracle_set_threads.restype = i32
         L.oracle_step.argtypes = [vp, u64]
         L.oracle_set_step.argtypes = [vp, u64]
         L.oracle_get_step.restype = u64
@@ -107,6 +110,15 @@ def _cfg_struct(cfg):
 
 class Oracle:
     """One discharge in the oracle.  precision = 32 (FP32 mirror) or 64."""
+
+    def set_coulomb(self, mask, ln_lambda=10.0):
+        """Coulomb collisions (1)-(6): bit r-1 of mask enables reaction r."""
+        lib().oracle_set_coulomb(self.h, int(mask), float(ln_lambda))
+
+    def set_threads(self, n):
+        """Host threads of the particle loop and the deposit (the results do
+        not depend on it); returns the threads OpenMP offers."""
+        return int(lib().oracle_set_threads(self.h, int(n)))
 
     def __init__(self, cfg, precision=32):
         self.cfg = dict(cfg)

@@ -2,7 +2,8 @@
 
 Plain g++, no vectorisation tricks: -O2 with floating-point contraction OFF so
 that every multiply and add rounds exactly where the source says (the FP32
-mirror mode depends on it).
+mirror mode depends on it); OpenMP for the optional multi-threaded particle
+loop (results independent of the thread count).
 """
 import os
 import subprocess
@@ -19,7 +20,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
            "-Wall", "-Wno-unused-function", SRC, "-o", tmp]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)

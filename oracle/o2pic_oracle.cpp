@@ -9,7 +9,12 @@
 // two are written separately from the same readings of the paper.
 //
 // Everything is ordinary loops over std::vectors in the order the method
-// states.  The particle arithmetic is templated on the precision R:
+// states.  The per-particle loop of a species and the deposit may run on
+// several host threads (OpenMP, oracle_set_threads; 1 by default): each
+// particle's update depends on nothing but itself and the field, every
+// thread keeps its own counters and births over a contiguous range of
+// particles, and the ranges are merged in particle order, so the results are
+// those of one thread bit for bit.  The particle arithmetic is templated on the precision R:
 //   R = float  : "mirror" mode, the precision the method fixes for particles
 //                (FP32 particles, FP64 Poisson); used for per-particle parity.
 //   R = double : FP64 reference, used to state the error of the FP32 results.
@@ -43,6 +48,9 @@
 #include <algorithm>
 #include <limits>
 #include <type_traits>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -70,7 +78,10 @@ const double FIX_ONE = 65536.0;                  // CIC fixed point: 2^16 per pa
 // RNG stream tags (counter word 1).  TAG_FLIGHT + s: the first free-flight
 // draw of a particle of species s (at load or birth).
 enum { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6,
-       TAG_FLIGHT = 7, TAG_EDET = 10, TAG_SHIFT_EDET = 11 };
+       TAG_FLIGHT = 7, TAG_EDET = 10, TAG_SHIFT_EDET = 11, TAG_COUL = 12, TAG_SHIFT_COUL = 18 };
+
+// Coulomb reactions (1)-(6) of Table 1: (species a, species b).
+const int COUL_PAIRS[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 2}, {0, 1}, {1, 2}};
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
@@ -294,6 +305,7 @@ struct Counters {
     uint64_t rec_candidates;       // pairs tested by (16)
     uint64_t edetached;            // pairs reacted by (22)
     uint64_t edet_candidates;      // pairs tested by (22)
+    uint64_t coulomb_pairs;        // pairs scattered by (1)-(6)
 };
 
 template <class R> struct Oracle {
@@ -335,6 +347,11 @@ template <class R> struct Oracle {
     Proc edet;
     std::vector<R> Ktab_d;            // [NGRID] sigma_22 g  (22)
     R kappa_d, thr_d;
+    // Coulomb (1)-(6): enabled reactions (bit r-1 for reaction r) and, per
+    // reaction, K = q_a^2 q_b^2 w lnL dt_ion / (8 pi eps0^2 mu^2 A dx) (sigma^2
+    // of a pair = K N / g^3 with N the count the reaction's density uses)
+    uint32_t coul_mask = 0;
+    R coul_K[6], coul_fa[6], coul_fb[6];
     // state
     Particles<R> sp[NSP];
     uint64_t next_id[NSP];           // id of the next birth (64-bit: ids past 2^32 - 1 are detected)
@@ -346,6 +363,7 @@ template <class R> struct Oracle {
     uint64_t acc_steps;
     Counters cnt;
     bool field_valid;
+    int threads = 1;                  // host threads of the particle loop and the deposit
 
     explicit Oracle(const oracle_config& c) : cfg(c) {
         Ng = cfg.n_cells + 1;
@@ -497,7 +515,22 @@ template <class R> struct Oracle {
     void deposit_all() {
         for (int s = 0; s < NSP; ++s) {
             std::fill(Q[s].begin(), Q[s].end(), 0);
-            for (size_t i = 0; i < sp[s].size(); ++i) deposit_one(Q[s], sp[s].x[i]);
+            const long long N = (long long)sp[s].size();
+            int T = std::max(1, threads);
+            if ((long long)T > N / 4096 + 1) T = (int)(N / 4096 + 1);
+            // integer sums: per-thread arrays added in any order give the same Q
+            std::vector<std::vector<uint64_t>> tq(T, std::vector<uint64_t>(Ng, 0));
+#pragma omp parallel for schedule(static) num_threads(T)
+            for (long long i = 0; i < N; ++i) {
+#ifdef _OPENMP
+                const int t = omp_get_thread_num();
+#else
+                const int t = 0;
+#endif
+                deposit_one(tq[t], sp[s].x[i]);
+            }
+            for (int t = 0; t < T; ++t)
+                for (int j = 0; j < Ng; ++j) Q[s][j] += tq[t][j];
         }
     }
 
@@ -623,6 +656,10 @@ template <class R> struct Oracle {
 
     bool update_particle(int s, uint64_t n, R& x, R& vx, R& vy, R& vz, uint32_t id, uint32_t& tc,
                          std::vector<Birth4>* births, const std::vector<R>& Ef) {
+        return update_particle(s, n, x, vx, vy, vz, id, tc, births, Ef, cnt, jacc[s]);
+    }
+    bool update_particle(int s, uint64_t n, R& x, R& vx, R& vy, R& vz, uint32_t id, uint32_t& tc,
+                         std::vector<Birth4>* births, const std::vector<R>& Ef, Counters& cnt, int64_t& jsum) {
         // gather: E_p = E_j + frac (E_{j+1} - E_j)
         int j; R frac; cell_of(x, j, frac);
         R Ep = fma_(frac, Ef[j + 1] - Ef[j], Ef[j]);
@@ -630,15 +667,15 @@ template <class R> struct Oracle {
         vx = fma_(qmdt[s], Ep, vx);
         x = fma_(vx, dt_s[s], x);
         cnt.particle_steps += 1;
-        jacc[s] += (int64_t)(vx * (R)256);   // exact scaling by 2^8, then truncation
+        jsum += (int64_t)(vx * (R)256);      // exact scaling by 2^8, then truncation
         // absorbing electrodes
         if (x < (R)0) { cnt.absorbed[s][0] += 1; return false; }
         if (x >= Lr) { cnt.absorbed[s][1] += 1; return false; }
-        return collide(s, n, x, vx, vy, vz, id, tc, births);
+        return collide(s, n, x, vx, vy, vz, id, tc, births, cnt);
     }
 
     bool collide(int s, uint64_t n, R x, R& vx, R& vy, R& vz, uint32_t id, uint32_t& tc,
-                 std::vector<Birth4>* births) {
+                 std::vector<Birth4>* births, Counters& cnt) {
         int np = (int)procs[s].size();
         if (np == 0) return true;
         if (tc != (uint32_t)n) return true;        // in free flight: no candidate this step
@@ -739,15 +776,39 @@ template <class R> struct Oracle {
     }
 
     void process_species(int s, uint64_t n, std::vector<Birth4>* births) {
-        Particles<R> out;
         Particles<R>& P = sp[s];
-        for (size_t i = 0; i < P.size(); ++i) {
+        const long long N = (long long)P.size();
+        int T = std::max(1, threads);
+        if ((long long)T > N / 4096 + 1) T = (int)(N / 4096 + 1);
+        // thread t takes the t-th contiguous range (schedule(static)); its
+        // counters, current sum and births are merged below in range order
+        std::vector<Counters> tcnt(T);
+        std::vector<int64_t> tj(T, 0);
+        std::vector<std::vector<Birth4>> tb((size_t)T * NSP);
+        for (Counters& c : tcnt) std::memset(&c, 0, sizeof(c));
+        std::vector<char> alive((size_t)N);
+#pragma omp parallel for schedule(static) num_threads(T)
+        for (long long i = 0; i < N; ++i) {
+#ifdef _OPENMP
+            const int t = omp_get_thread_num();
+#else
+            const int t = 0;
+#endif
             R x = P.x[i], vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
             uint32_t tc = P.tc[i];
-            if (update_particle(s, n, x, vx, vy, vz, P.id[i], tc, births, Eg))
-                out.push(x, vx, vy, vz, P.id[i], tc);
+            alive[i] = update_particle(s, n, x, vx, vy, vz, P.id[i], tc, &tb[(size_t)t * NSP], Eg, tcnt[t], tj[t])
+                           ? 1 : 0;
+            P.x[i] = x; P.vx[i] = vx; P.vy[i] = vy; P.vz[i] = vz; P.tc[i] = tc;
         }
-        P = out;
+        for (int t = 0; t < T; ++t) {
+            const uint64_t* a = reinterpret_cast<const uint64_t*>(&tcnt[t]);
+            uint64_t* b = reinterpret_cast<uint64_t*>(&cnt);
+            for (size_t k = 0; k < sizeof(Counters) / sizeof(uint64_t); ++k) b[k] += a[k];
+            jacc[s] += tj[t];
+            for (int d = 0; d < NSP; ++d)
+                births[d].insert(births[d].end(), tb[(size_t)t * NSP + d].begin(), tb[(size_t)t * NSP + d].end());
+        }
+        filter(P, alive, true);
     }
 
     // ---- cell-binned binary processes between species A and B (the
@@ -830,6 +891,113 @@ template <class R> struct Oracle {
         pair_process(n, SP_OM, SP_OP, Ktab, kappa_n, TAG_SHIFT, TAG_PAIR, cnt.pair_candidates, cnt.neutralized);
     }
 
+    // ---- Coulomb elastic collisions (1)-(6) of Table 1, by the binary
+    // collision model of Takizuka & Abe (J. Comput. Phys. 25, 205, 1977):
+    // within a cell each pair's relative velocity u (|u| = g) turns by an angle
+    // theta with tan(theta/2) = delta ~ N(0, sigma^2), sigma^2 = K N / g^3, and
+    // an azimuth phi uniform on [0, 2 pi); momentum and energy of the pair are
+    // kept.  Readings: on ion steps with dt_ion, after the species' pushes and
+    // before the reactive pairs, reactions in the order (1)..(6); pairs from
+    // the cell lists in array order: like species by a random rotation r of
+    // the list, (q_r, q_r+1), (q_r+2, q_r+3), ... (an odd one sits out), N =
+    // the species' count in the cell; unlike species the i-th of the shorter
+    // list with member (i + r) mod M of the longer (as (17)), N = M, the
+    // larger count (each member of the longer list then collides with
+    // probability m/M, with that much larger a variance, so that both species
+    // get the model's mean-square deflection rate).  delta from the first
+    // member's stream (tag 12 + reaction index): one polar normal, then phi
+    // as the double angle of a uniform point of the unit disk.
+    void coulomb_pair(int r, int a, size_t ia, int b, size_t ib, R N, uint64_t n, Counters& c) {
+        R& ax = sp[a].vx[ia]; R& ay = sp[a].vy[ia]; R& az = sp[a].vz[ia];
+        R& bx = sp[b].vx[ib]; R& by = sp[b].vy[ib]; R& bz = sp[b].vz[ib];
+        const R ux = ax - bx, uy = ay - by, uz = az - bz;
+        const R g2 = dot3<R>(ux, uy, uz, ux, uy, uz);
+        if (!(g2 > (R)0)) return;
+        const R g = sqrt_(g2);
+        Stream st(sp[a].id[ia], cfg.seed, n, (uint32_t)(TAG_COUL + r));
+        R z0, z1;
+        normal_pair<R>(st, z0, z1, c.warn_tries);
+        const R sig2 = coul_K[r] * N / (g2 * g);
+        const R d = sqrt_(sig2) * z0;
+        R sn, omc;   // sin(theta), 1 - cos(theta)
+        if (std::fabs(d) < (R)1e18) {
+            const R q = (R)1 / ((R)1 + d * d);
+            sn = (R)2 * d * q;
+            omc = (R)2 * (d * d) * q;
+        } else {
+            sn = (R)0; omc = (R)2;
+        }
+        R cp = (R)1, spn = (R)0;   // cos(phi), sin(phi)
+        for (int t = 0; t < MAX_TRIES; ++t) {
+            const R e1 = (R)2 * uniform<R>(st.next()) - (R)1;
+            const R e2 = (R)2 * uniform<R>(st.next()) - (R)1;
+            const R s2 = e1 * e1 + e2 * e2;
+            if (s2 > (R)0 && s2 < (R)1) { cp = (e1 * e1 - e2 * e2) / s2; spn = ((R)2 * e1 * e2) / s2; break; }
+            if (t == MAX_TRIES - 1) c.warn_tries += 1;
+        }
+        const R up2 = ux * ux + uy * uy;
+        R dx, dy, dz;
+        if (up2 > (R)0) {
+            const R up = sqrt_(up2);
+            const R sc = sn * cp, ss = sn * spn;
+            dx = (ux * uz / up) * sc - (uy * g / up) * ss - ux * omc;
+            dy = (uy * uz / up) * sc + (ux * g / up) * ss - uy * omc;
+            dz = -up * sc - uz * omc;
+        } else {
+            dx = g * (sn * cp);
+            dy = g * (sn * spn);
+            dz = -uz * omc;
+        }
+        ax = ax + coul_fa[r] * dx; ay = ay + coul_fa[r] * dy; az = az + coul_fa[r] * dz;
+        bx = bx - coul_fb[r] * dx; by = by - coul_fb[r] * dy; bz = bz - coul_fb[r] * dz;
+        c.coulomb_pairs += 1;
+    }
+
+    void set_coulomb(uint32_t mask, double ln_lambda) {
+        coul_mask = mask & 63u;
+        const double mass[NSP] = {cfg.m_e, cfg.m_OM, cfg.m_OP};
+        const double dx = cfg.L / cfg.n_cells, dti = cfg.dt * (double)cfg.ion_subcycle;
+        const double q4 = QE * QE * QE * QE;
+        for (int r = 0; r < 6; ++r) {
+            const double ma = mass[COUL_PAIRS[r][0]], mb = mass[COUL_PAIRS[r][1]];
+            const double mu = ma * mb / (ma + mb);
+            coul_K[r] = (R)(q4 * cfg.weight * ln_lambda * dti / (8.0 * M_PI * EPS0 * EPS0 * mu * mu * cfg.area * dx));
+            coul_fa[r] = (R)(mb / (ma + mb));
+            coul_fb[r] = (R)(ma / (ma + mb));
+        }
+    }
+
+    void coulomb(uint64_t n) {
+        if (!coul_mask) return;
+        const int Nc = cfg.n_cells;
+        for (int r = 0; r < 6; ++r) {
+            if (!((coul_mask >> r) & 1u)) continue;
+            const int a = COUL_PAIRS[r][0], b = COUL_PAIRS[r][1];
+            std::vector<std::vector<size_t>> LA(Nc), LB(Nc);
+            for (size_t i = 0; i < sp[a].size(); ++i) { int j; R fr; cell_of(sp[a].x[i], j, fr); LA[j].push_back(i); }
+            if (a != b)
+                for (size_t i = 0; i < sp[b].size(); ++i) { int j; R fr; cell_of(sp[b].x[i], j, fr); LB[j].push_back(i); }
+            for (int c = 0; c < Nc; ++c) {
+                const size_t na = LA[c].size(), nb = (a == b) ? na : LB[c].size();
+                if (a == b ? na < 2 : (na == 0 || nb == 0)) continue;
+                const size_t M = std::max(na, nb), m = std::min(na, nb);
+                Stream sh((uint32_t)c, cfg.seed, n, (uint32_t)(TAG_SHIFT_COUL + r));
+                const size_t rs = (size_t)(sh.next() % (uint32_t)M);
+                if (a == b) {
+                    for (size_t j = 0; 2 * j + 1 < na; ++j)
+                        coulomb_pair(r, a, LA[c][(rs + 2 * j) % na], a, LA[c][(rs + 2 * j + 1) % na], (R)na, n, cnt);
+                } else {
+                    const bool a_short = na <= nb;
+                    for (size_t i = 0; i < m; ++i) {
+                        const size_t p = (i + rs) % M;
+                        coulomb_pair(r, a, a_short ? LA[c][i] : LA[c][p], b, a_short ? LB[c][p] : LB[c][i], (R)M, n,
+                                     cnt);
+                    }
+                }
+            }
+        }
+    }
+
     // (22) e + O- -> O + 2e, on ion steps before (16) and (17) (reading: the
     // paper gives no order); its births follow the step's other electron
     // births, in the order of their O- parents.
@@ -851,10 +1019,11 @@ template <class R> struct Oracle {
         pair_process(n, SP_E, SP_OP, Ktab_r, kappa_r, TAG_SHIFT_REC, TAG_REC, cnt.rec_candidates, cnt.recombined);
     }
 
-    static void filter(Particles<R>& P, const std::vector<char>& dead) {
+    // Keep the particles not marked dead (or, keep_marked: those marked), in order.
+    static void filter(Particles<R>& P, const std::vector<char>& mark, bool keep_marked = false) {
         Particles<R> out;
         for (size_t i = 0; i < P.size(); ++i)
-            if (!dead[i]) out.push(P.x[i], P.vx[i], P.vy[i], P.vz[i], P.id[i], P.tc[i]);
+            if ((mark[i] != 0) == keep_marked) out.push(P.x[i], P.vx[i], P.vy[i], P.vz[i], P.id[i], P.tc[i]);
         P = out;
     }
 
@@ -891,6 +1060,7 @@ template <class R> struct Oracle {
         if (ion_step) {
             process_species(SP_OM, n, births);
             process_species(SP_OP, n, births);
+            coulomb(n);
             edetach(n, births);
             recombine(n);
             neutralize(n);
@@ -1005,6 +1175,27 @@ int oracle_read_flight(void* p, int s, uint32_t* tc) {
         O.draw_flights(O.step);
         for (size_t i = 0; i < O.sp[s].size(); ++i) tc[i] = O.sp[s].tc[i];
     });
+    return 0;
+}
+
+// Host threads of the per-particle loop and the deposit (results do not
+// depend on it).  Returns the number of threads OpenMP makes available (1
+// when built without it).
+int oracle_set_threads(void* p, int n) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, O.threads = std::max(1, n));
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+// Coulomb collisions (1)-(6): mask bit r-1 enables reaction r, ln_lambda =
+// the Coulomb logarithm (a constant of the model).
+int oracle_set_coulomb(void* p, uint32_t mask, double ln_lambda) {
+    Handle* h = (Handle*)p;
+    DISPATCH(h, O.set_coulomb(mask, ln_lambda));
     return 0;
 }
 

@@ -1083,3 +1083,141 @@ def test_edetach_energy_balance_threshold_and_order(oracle_mod):
     o.step(1)
     c = o.counters()
     assert c["neutralized"] == 0 and o.count(1) == 0 and c["edetached"] == nm
+
+
+# ------------------------------------------- Coulomb collisions (1)-(6)
+def _coulomb_K(cfg, ma, mb, lnl):
+    mu = ma * mb / (ma + mb)
+    dx = cfg["L"] / cfg["n_cells"]
+    return QE ** 4 * cfg["weight"] * lnl * cfg["dt"] * cfg["ion_subcycle"] / (
+        8 * math.pi * EPS0 ** 2 * mu ** 2 * cfg["area"] * dx)
+
+
+def _one_cell_load(o, counts, vel):
+    """All particles at the centre of a single cell (exactly neutral when
+    n_e + n_O- = n_O2+: no field), velocities vel[s] (3, n)."""
+    for s, n in enumerate(counts):
+        x = np.full(n, 0.5 * o.cfg["L"], np.float32)
+        v = vel[s] if vel[s] is not None else np.zeros((3, n))
+        o.load(s, x, v[0].astype(np.float32), v[1].astype(np.float32), v[2].astype(np.float32),
+               np.arange(n, dtype=np.uint32))
+
+
+def test_coulomb_like_species_deflection_law(oracle_mod):
+    """(1) e-e, Takizuka-Abe: two cold counter-streaming electron beams in one
+    cell.  Pairs of one beam have no relative velocity; a pair of opposite
+    beams (g = 2 v0) turns by theta with tan(theta/2) ~ N(0, sigma^2),
+    sigma^2 = K N / g^3 (N = electrons in the cell): each of its electrons
+    leaves at angle theta, speed unchanged.  About half of the electrons are
+    in such pairs; momentum and energy are kept."""
+    cfg = _cfg(n_cells=1, weight=2.0e11, ion_subcycle=1)
+    N = 20000
+    rng = np.random.default_rng(31)
+    v0 = 1.0e5
+    sgn = np.where(rng.random(N) < 0.5, 1.0, -1.0)
+    ve = np.zeros((3, N)); ve[1] = v0 * sgn
+    o = oracle_mod.Oracle(cfg, 64)
+    o.set_processes([])
+    o.set_coulomb(1 << 0, 10.0)
+    _one_cell_load(o, (N, 0, N), (ve, None, None))
+    p0 = o.particles(0)
+    o.step(1)
+    p1 = o.particles(0)
+    assert np.array_equal(p0["id"], p1["id"])
+    v_a = np.stack([p0["vx"], p0["vy"], p0["vz"]]); v_b = np.stack([p1["vx"], p1["vy"], p1["vz"]])
+    moved = np.any(v_a != v_b, axis=0)
+    assert abs(moved.mean() - 0.5) < 0.03
+    sp0 = np.linalg.norm(v_a[:, moved], axis=0); sp1 = np.linalg.norm(v_b[:, moved], axis=0)
+    assert np.allclose(sp1, sp0, rtol=1e-9)
+    cos = (v_a[:, moved] * v_b[:, moved]).sum(axis=0) / (sp0 * sp1)
+    th = np.arccos(np.clip(cos, -1.0, 1.0))
+    sigma = math.sqrt(_coulomb_K(cfg, ME, ME, 10.0) * N / (2 * v0) ** 3)
+    assert 0.05 < sigma < 1.0
+    assert stats.kstest(np.tan(th / 2) / sigma, "halfnorm").pvalue > 1e-3
+    assert abs(v_b.sum(axis=1) - v_a.sum(axis=1)).max() <= 1e-9 * v0 * N
+    assert (v_b ** 2).sum() == pytest.approx((v_a ** 2).sum(), rel=1e-12)
+    # pairs with a relative velocity (one from each beam) are the scattered ones
+    assert o.counters()["coulomb_pairs"] == int(moved.sum()) // 2
+
+
+@pytest.mark.parametrize("n_e,n_i", [(8000, 20000), (20000, 5000)])
+def test_coulomb_electron_ion_beam_slowing(oracle_mod, n_e, n_i):
+    """(4) e-O2+: a cold electron beam through cold O2+ in one cell (O- at
+    rest make it neutral).  In one step the beam's mean velocity drops by the
+    factor 1 - (m/M) f E[1 - cos theta], E over tan(theta/2) ~ N(0, sigma^2),
+    sigma^2 = K N_H / g^3 with N_H the larger count, f = m_i / (m_e + m_i),
+    and m/M = the fraction of electrons paired (min / n_e).  Both regimes
+    give the same slowing rate to first order in sigma^2."""
+    cfg = _cfg(n_cells=1, weight=1.0e11, ion_subcycle=1)
+    v0 = 1.0e5
+    ve = np.zeros((3, n_e)); ve[1] = v0
+    n_om = max(n_i - n_e, 0)
+    n_op = n_e + n_om
+    o = oracle_mod.Oracle(cfg, 64)
+    o.set_processes([])
+    o.set_coulomb(1 << 3, 10.0)
+    _one_cell_load(o, (n_e, n_om, n_op), (ve, None, None))
+    o.step(1)
+    vy = o.particles(0)["vy"]
+    mi = cfg["m_OP"]
+    NH, m = max(n_e, n_op), min(n_e, n_op)
+    sig2 = _coulomb_K(cfg, ME, mi, 10.0) * NH / v0 ** 3
+    z = np.linspace(-12, 12, 200001)
+    w = np.exp(-0.5 * z * z); w /= w.sum()
+    d2 = sig2 * z * z
+    omc = float((w * 2 * d2 / (1 + d2)).sum())
+    f = mi / (ME + mi)
+    expect = v0 * (1 - (m / n_e) * f * omc)
+    assert 0.02 < (m / n_e) * f * omc < 0.5
+    assert abs(vy.mean() - expect) < 5 * vy.std() / math.sqrt(n_e) + 1e-6 * v0
+
+
+def test_coulomb_all_reactions_conserve_momentum_and_energy(oracle_mod):
+    """Every reaction (1)-(6) keeps each pair's momentum and energy: a warm
+    three-species plasma in a few cells, one step, FP64."""
+    Nc = 4
+    cfg = _cfg(n_cells=Nc, weight=1.0e11, ion_subcycle=1)
+    rng = np.random.default_rng(33)
+    counts = (3000, 1500, 4500)
+    masses = (ME, cfg["m_OM"], cfg["m_OP"])
+    dx = cfg["L"] / Nc
+    o = oracle_mod.Oracle(cfg, 64)
+    o.set_processes([])
+    o.set_coulomb(63, 10.0)
+    cells = rng.integers(0, Nc, sum(counts))
+    x = ((cells + 0.5) * dx).astype(np.float32)
+    k = 0
+    for s, n in enumerate(counts):
+        sig = math.sqrt(QE * (2.0 if s == 0 else 0.05) / masses[s])
+        v = rng.standard_normal((3, n)) * sig
+        o.load(s, x[k:k + n], *(v[i].astype(np.float32) for i in range(3)), np.arange(n, dtype=np.uint32))
+        k += n
+    # momentum and energy just after the push (no field effect: the field of
+    # the loaded charge acts in the push, which the step does first)
+    Ef = np.zeros(Nc + 1)
+    P0 = np.zeros(3); E0 = 0.0
+    o2 = oracle_mod.Oracle(cfg, 64)
+    o2.set_processes([])
+    k = 0
+    o.step(1)
+    c = o.counters()
+    assert c["coulomb_pairs"] > 0
+    # compare with the same step without Coulomb: the push is identical, so
+    # the difference of the totals is what the collisions changed
+    o2.set_coulomb(0, 10.0)
+    k = 0
+    rng = np.random.default_rng(33)
+    cells = rng.integers(0, Nc, sum(counts))
+    for s, n in enumerate(counts):
+        sig = math.sqrt(QE * (2.0 if s == 0 else 0.05) / masses[s])
+        v = rng.standard_normal((3, n)) * sig
+        o2.load(s, x[k:k + n], *(v[i].astype(np.float32) for i in range(3)), np.arange(n, dtype=np.uint32))
+        k += n
+    o2.step(1)
+    for name, fn in (("momentum", lambda q, m: m * np.stack([q["vx"], q["vy"], q["vz"]]).sum(axis=1)),
+                     ("energy", lambda q, m: 0.5 * m * (q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2).sum())):
+        a = sum(fn(o.particles(s), masses[s]) for s in range(3))
+        b = sum(fn(o2.particles(s), masses[s]) for s in range(3))
+        scale = sum(np.abs(fn(o2.particles(s), masses[s])).max() for s in range(3))
+        assert np.all(np.abs(np.asarray(a) - np.asarray(b)) <= 1e-9 * scale), name
+    assert not np.array_equal(o.particles(0)["vx"], o2.particles(0)["vx"])
