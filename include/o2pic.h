@@ -131,6 +131,7 @@ typedef struct {
     uint64_t particle_steps_species[O2PIC_NSPECIES];  /* particles pushed, per species */
     uint64_t recombined, rec_candidates;              /* (16): pairs removed, pairs tested */
     uint64_t edetached, edet_candidates;              /* (22): pairs reacted, pairs tested */
+    uint64_t coulomb_pairs;                           /* (1)-(6): pairs scattered */
 } o2pic_stats;
 
 /* Fills `cfg` with the defaults (parity-case geometry, T_gas = 300 K, O, O2
@@ -150,6 +151,18 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out);
  * processes per species, one NEUTRALIZE, one RECOMBINE, one EDETACH.
  * Errors: INVALID_ARG. */
 int o2pic_set_processes(o2pic_ctx* ctx, const o2pic_process* procs, int nproc);
+
+/* Coulomb elastic collisions (1)-(6) of Table 1: e-e, O- - O-, O2+ - O2+,
+ * e - O2+, e - O-, O- - O2+; bit r-1 of `mask` enables reaction r (0 = off,
+ * the default).  Model: the binary collisions of Takizuka & Abe (J. Comput.
+ * Phys. 25, 205, 1977) with the Coulomb logarithm ln_lambda: on ion steps,
+ * with dt_ion, after the species' pushes and collisions and before the
+ * reactive pairs, within each cell each pair's relative velocity turns by
+ * theta, tan(theta/2) ~ N(0, sigma^2), sigma^2 = q_a^2 q_b^2 n lnL dt_ion /
+ * (8 pi eps0^2 mu^2 g^3) (n: the species' density for like pairs, the larger
+ * density for unlike pairs, paired min(n_a, n_b) times), azimuth uniform;
+ * each pair keeps its momentum and energy.  Errors: INVALID_ARG, CUDA. */
+int o2pic_set_coulomb(o2pic_ctx* ctx, uint32_t mask, double ln_lambda);
 
 /* Replaces species `species` by n particles (SoA float32 x, vx, vy, vz and
  * uint32 ids, unique within the species); velocities are taken as
@@ -244,7 +257,8 @@ int o2pic_set_step(o2pic_ctx* ctx, uint64_t step);
  * event pair around every launch; o2pic_get_timing returns, per kernel kind
  * (0 push e, 1 push O-, 2 push O2+, 3 pair histograms, 4 pair, 5 field,
  * 6 compact, 7 deposit, 8 collisions e, 9 collisions O-, 10 collisions O2+,
- * 11 (16) pairing, 12 candidate filter O-, 13 candidate filter O2+),
+ * 11 (16), (22) pairing, 12 candidate filter O-, 13 candidate filter O2+,
+ * 14 Coulomb collisions (cell sort and reactions)),
  * the summed milliseconds and launches; items is reserved (zeros). */
 int o2pic_set_timing(o2pic_ctx* ctx, int on);
 int o2pic_get_timing(o2pic_ctx* ctx, double* ms, uint64_t* launches, uint64_t* items, int nkinds);

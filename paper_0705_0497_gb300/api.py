@@ -17,7 +17,7 @@ MAXPROC = 16
 E, OM, OP = 0, 1, 2
 HOST, DEVICE = 0, 1
 KERNEL_KINDS = ("push_e", "push_om", "push_op", "pair_hist", "pair", "field", "compact", "deposit",
-                "cand_e", "cand_om", "cand_op", "recomb", "filter_om", "filter_op")
+                "cand_e", "cand_om", "cand_op", "recomb", "filter_om", "filter_op", "coulomb")
 
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "ID_OVERFLOW", -4: "NONFINITE", -5: "CUDA", -6: "TIMEOUT",
@@ -62,7 +62,8 @@ class Stats(ctypes.Structure):
                 ("slots", ctypes.c_uint64 * NSP), ("next_id", ctypes.c_uint64 * NSP),
                 ("error_flags", ctypes.c_uint64), ("particle_steps_species", ctypes.c_uint64 * NSP),
                 ("recombined", ctypes.c_uint64), ("rec_candidates", ctypes.c_uint64),
-                ("edetached", ctypes.c_uint64), ("edet_candidates", ctypes.c_uint64)]
+                ("edetached", ctypes.c_uint64), ("edet_candidates", ctypes.c_uint64),
+                ("coulomb_pairs", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {}
@@ -78,7 +79,7 @@ class Stats(ctypes.Structure):
             d[f"particle_steps_{s}"] = int(self.particle_steps_species[s])
         for n in ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
                   "id_overflow", "step", "error_flags", "recombined", "rec_candidates", "edetached",
-                  "edet_candidates"):
+                  "edet_candidates", "coulomb_pairs"):
             d[n] = int(getattr(self, n))
         return d
 
@@ -95,6 +96,7 @@ SIGNATURES = [
     ("o2pic_load_particles", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _u64, _i32, _vp]),
     ("o2pic_set_next_id", _i32, [_vp, _i32, _u32]),
     ("o2pic_load_flight", _i32, [_vp, _i32, _vp, _u64, _i32, _vp]),
+    ("o2pic_set_coulomb", _i32, [_vp, _u32, ctypes.c_double]),
     ("o2pic_read_flight", _i32, [_vp, _i32, _vp, _u64, _P(_u64), _i32]),
     ("o2pic_step", _i32, [_vp, _u64, _vp]),
     ("o2pic_synchronize", _i32, [_vp]),
@@ -342,6 +344,10 @@ class Discharge:
         st = Stats()
         _check(lib().o2pic_get_stats(self.h, ctypes.byref(st)), "o2pic_get_stats")
         return st.as_dict()
+
+    def set_coulomb(self, mask, ln_lambda=10.0):
+        """Coulomb collisions (1)-(6): bit r-1 of mask enables reaction r."""
+        _check(lib().o2pic_set_coulomb(self.h, int(mask), float(ln_lambda)), "o2pic_set_coulomb")
 
     def set_step(self, n):
         _check(lib().o2pic_set_step(self.h, int(n)), "o2pic_set_step")

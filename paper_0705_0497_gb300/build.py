@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libo2pic.so")
-SOURCES = ["push.cu", "ionpair.cu", "field.cu", "compact.cu", "noalloc.cu", "runtime.cu", "mlp.cu"]
+SOURCES = ["push.cu", "ionpair.cu", "field.cu", "compact.cu", "noalloc.cu", "runtime.cu", "mlp.cu", "coulomb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -67,7 +67,7 @@ enum Kind { K_ELASTIC = 0, K_EXCITE = 1, K_IONIZE = 2, K_ATTACH = 3, K_DETACH = 
 // TAG_FLIGHT + s: the first free-flight draw of a particle of species s (at a
 // load or at its birth).
 enum Tag : uint32_t { TAG_E = 0, TAG_OM = 1, TAG_OP = 2, TAG_PAIR = 3, TAG_SHIFT = 4, TAG_REC = 5, TAG_SHIFT_REC = 6,
-                      TAG_FLIGHT = 7, TAG_EDET = 10, TAG_SHIFT_EDET = 11 };
+                      TAG_FLIGHT = 7, TAG_EDET = 10, TAG_SHIFT_EDET = 11, TAG_COUL = 12, TAG_SHIFT_COUL = 18 };
 
 // device error bits
 constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE = 4ull, ERR_TIMEOUT = 8ull;
@@ -75,7 +75,7 @@ constexpr unsigned long long ERR_CAPACITY = 1ull, ERR_ID = 2ull, ERR_NONFINITE =
 // kernel kinds (timing, tickets)
 enum KernelKind { KK_PUSH_E = 0, KK_PUSH_OM = 1, KK_PUSH_OP = 2, KK_PAIR_HIST = 3, KK_PAIR = 4,
                   KK_FIELD = 5, KK_COMPACT = 6, KK_DEPOSIT = 7, KK_CAND_E = 8, KK_CAND_OM = 9, KK_CAND_OP = 10,
-                  KK_REC = 11, KK_FILT_OM = 12, KK_FILT_OP = 13, NKK = 14 };
+                  KK_REC = 11, KK_FILT_OM = 12, KK_FILT_OP = 13, KK_COUL = 14, NKK = 15 };
 
 // Counters: same layout as the head of o2pic_stats.
 struct DevCounters {
@@ -88,6 +88,7 @@ struct DevCounters {
     unsigned long long psteps[NSP];
     unsigned long long recombined, rec_candidates;
     unsigned long long edetached, edet_candidates;
+    unsigned long long coulomb_pairs;
 };
 
 // Births appended by one kernel into species d: births of the electron
@@ -209,6 +210,16 @@ struct Params {
     unsigned int* dremoval;      // [2 * max_dremovals]: O- slot, e slot
     unsigned int max_dremovals;
     float4* stage22;             // [max_dremovals]
+    // Coulomb (1)-(6): enabled reactions (bit r-1), per reaction the sigma^2
+    // factor K and the shares m_b/(m_a+m_b), m_a/(m_a+m_b) of the change of
+    // u; per species the cell sort of a Coulomb step: slots in cell order,
+    // per-tile cell offsets, cell totals and cell starts
+    unsigned int coul_mask;
+    float coul_K[6], coul_fa[6], coul_fb[6];
+    unsigned int* csort[NSP];
+    unsigned int* chist[NSP];
+    unsigned int* ctot[NSP];
+    unsigned int* cstart[NSP];
     // compaction trigger
     float compact_dead_frac;
 };
@@ -256,6 +267,8 @@ cudaError_t configure_pair_hist_smem(int Nc);
 void launch_pair(const Params& P, const PairSpec& S, int grid, cudaStream_t s);
 void launch_pair_apply(const Params& P, const PairSpec& S, cudaStream_t s);
 void launch_edet_apply(const Params& P, const PairSpec& S, cudaStream_t s);
+int launch_coulomb(const Params& P, unsigned mask, int grid, cudaStream_t s);
+cudaError_t configure_coulomb_smem(int Nc);
 void launch_edet_apply_batched(const Params* all, const PairSpec* specs, int n, cudaStream_t s);
 // batched launches (one grid for many discharges; map[b] = discharge, block, blocks)
 void launch_push_batched(int species, const Params* all, const uint4* map, int nblocks, size_t smem, cudaStream_t s);

@@ -91,6 +91,7 @@ struct o2pic_ctx {
     bool have_tables = false;
     bool loaded[NSP] = {false, false, false};
     bool flight_ok[NSP] = {false, false, false};   // free flights known (else drawn by prepare)
+    bool coul_alloc = false;                       // Coulomb cell-sort buffers allocated
     int latched = 0;
     int grid_push[NSP] = {0, 0, 0};
     int grid_pair = 0, grid_pair_e = 0, grid_compact = 0, grid_deposit = 0;
@@ -336,6 +337,11 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
             if (P.nproc[SP_OP]) {
                 launch(c, KK_FILT_OP, s, [&] { launch_filter(SP_OP, P, c->grid_push[SP_OP], s); });
                 launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
+            }
+            if (P.coul_mask) {
+                int k = 0;
+                launch(c, KK_COUL, s, [&] { k = launch_coulomb(P, P.coul_mask, c->grid_compact, s); });
+                c->launches += (unsigned long long)(k - 1);
             }
             if (P.have_edet) {
                 const PairSpec D = spec_edet(c);
@@ -848,6 +854,42 @@ int o2pic_read_particles(o2pic_ctx* c, int species, float* x, float* vx, float* 
     return check_flags(c);
 }
 
+int o2pic_set_coulomb(o2pic_ctx* c, uint32_t mask, double ln_lambda) {
+    if (!c || mask > 63u || !(ln_lambda > 0.0) || !std::isfinite(ln_lambda)) return O2PIC_E_INVALID_ARG;
+    int rc = sync_all(c);
+    if (rc == O2PIC_E_CUDA) return rc;
+    Params& P = c->P;
+    if (mask && !c->coul_alloc) {
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < NSP && e == cudaSuccess; ++s) {
+            const unsigned long long cap = P.sp[s].cap;
+            e = ctx_alloc(c, &P.csort[s], (size_t)cap);
+            if (e == cudaSuccess) e = ctx_alloc(c, &P.chist[s], (size_t)(ceil_div(cap, TILE) + 1) * P.Nc);
+            if (e == cudaSuccess) e = ctx_alloc(c, &P.ctot[s], (size_t)P.Nc);
+            if (e == cudaSuccess) e = ctx_alloc(c, &P.cstart[s], (size_t)P.Nc);
+        }
+        if (e == cudaSuccess) e = configure_coulomb_smem(P.Nc);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        c->coul_alloc = true;
+    }
+    const o2pic_config& g = c->cfg;
+    static const int pairs[6][2] = {{SP_E, SP_E}, {SP_OM, SP_OM}, {SP_OP, SP_OP}, {SP_E, SP_OP}, {SP_E, SP_OM},
+                                    {SP_OM, SP_OP}};
+    const double mass[NSP] = {g.m_e, g.m_OM, g.m_OP};
+    const double dx = g.L / g.n_cells, dti = g.dt * (double)g.ion_subcycle;
+    const double q4 = QE * QE * QE * QE;
+    for (int r = 0; r < 6; ++r) {
+        const double ma = mass[pairs[r][0]], mb = mass[pairs[r][1]];
+        const double mu = ma * mb / (ma + mb);
+        P.coul_K[r] = (float)(q4 * g.weight * ln_lambda * dti / (8.0 * M_PI * EPS0 * EPS0 * mu * mu * g.area * dx));
+        P.coul_fa[r] = (float)(mb / (ma + mb));
+        P.coul_fb[r] = (float)(ma / (ma + mb));
+    }
+    P.coul_mask = mask;
+    c->gen += 1;
+    return O2PIC_OK;
+}
+
 int o2pic_load_flight(o2pic_ctx* c, int species, const uint32_t* tc, uint64_t n, int mem_kind, void* stream) {
     if (!c || species < 0 || species >= NSP || (n > 0 && !tc)) return O2PIC_E_INVALID_ARG;
     if (mem_kind != O2PIC_HOST && mem_kind != O2PIC_DEVICE) return O2PIC_E_INVALID_ARG;
@@ -1037,6 +1079,7 @@ int o2pic_get_stats(o2pic_ctx* c, o2pic_stats* out) {
     out->rec_candidates = h.cnt.rec_candidates;
     out->edetached = h.cnt.edetached;
     out->edet_candidates = h.cnt.edet_candidates;
+    out->coulomb_pairs = h.cnt.coulomb_pairs;
     out->step = h.step;
     out->error_flags = h.error_flags;
     return rc;
@@ -1378,6 +1421,8 @@ int o2pic_batch_create(o2pic_ctx* const* ctxs, int32_t n, uint64_t K, o2pic_batc
             b->fused = false;
     }
     if (const char* env = std::getenv("O2PIC_BATCH_BRANCHES")) if (env[0] == '1') b->fused = false;
+    // the Coulomb collisions have no batched launches: their contexts get branches
+    for (o2pic_ctx* c : b->ctx) if (c->P.coul_mask) b->fused = false;
     b->fusable = b->fused;
     int rc = batch_capture(b);
     if (rc) { o2pic_batch_destroy(b); return rc; }

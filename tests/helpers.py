@@ -10,7 +10,8 @@ from paper_0705_0497_gb300 import inputs, xsec
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 COUNTERS_COMPARED = ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
-                     "recombined", "rec_candidates", "id_overflow", "edetached", "edet_candidates")
+                     "recombined", "rec_candidates", "id_overflow", "edetached", "edet_candidates",
+                     "coulomb_pairs")
 
 
 def capacity_for(counts, factor=2.0, extra=4096):
