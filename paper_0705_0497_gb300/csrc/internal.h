@@ -259,7 +259,10 @@ __host__ __device__ inline unsigned warp_range_len(unsigned n, unsigned W) {
 // ---------------------------------------------------------------- launchers
 // (defined in the kernel translation units, called by the runtime)
 void launch_push(int species, const Params& P, int grid, cudaStream_t s);
-void launch_cand(int species, const Params& P, int grid, cudaStream_t s);
+void launch_cand(int species, const Params& P, int grid, cudaStream_t s);   // ion species
+// true when the ion filter and kinematics run inside the ion particle kernels
+// (then the filter and kinematics kernels are not launched)
+bool ions_fused();
 void launch_filter(int species, const Params& P, int grid, cudaStream_t s);
 void launch_filter_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s);
 void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t s);

@@ -24,9 +24,10 @@
 //     block (the id-free first round hoisted) draws the next free flight and
 //     the rest of the collision;
 //   * electrons: a candidate is filtered at once (energy against the total
-//     rate, the total-rate column in shared memory), and only the real
-//     collisions are recorded (32 B each: slot, id, x, v) for the kinematics
-//     kernel;
+//     rate, the total-rate column in shared memory), only the real
+//     collisions are recorded (32 B each: slot, id, x, v), and the warp runs
+//     their kinematics itself once its range is pushed, while other warps
+//     are still pushing (no second kernel on electron steps);
 //   * ions: candidates are recorded (slot and the rest of the Philox block),
 //     a lean filter kernel (target sampled from the gas Maxwellian, energy
 //     against the total rate) keeps the real ones, and the kinematics kernel
@@ -40,6 +41,20 @@
 // workload) and unrolling of the four particles a lane handles per round.
 #ifndef O2PIC_PUSH_MIN_BLOCKS
 #define O2PIC_PUSH_MIN_BLOCKS 4
+#endif
+// The electron kernel also runs the kinematics of its real collisions.
+#ifndef O2PIC_PUSH_E_MIN_BLOCKS
+#define O2PIC_PUSH_E_MIN_BLOCKS 4
+#endif
+// Ion candidates filtered (gas target, energy against the total rate) and
+// their real collisions handled inside the particle kernel, as for the
+// electrons (1), or by the separate filter and kinematics kernels (0).  Both
+// give the same results; on the 512-cell, 1.6e7-particle discharge at its
+// periodic state the separate kernels were faster (48.4 against 49.1 ms per
+// RF cycle): the ion filter's Maxwellian target draws weigh on the particle
+// kernel's registers.
+#ifndef O2PIC_FUSE_IONS
+#define O2PIC_FUSE_IONS 0
 #endif
 #ifndef O2PIC_PUSH_UNROLL
 #define O2PIC_PUSH_UNROLL 4
@@ -69,6 +84,8 @@ struct PushShared {
     unsigned removed;
     unsigned psteps;
     unsigned nonfinite;
+    unsigned wtries;
+    unsigned events[MAXPROC];    // electrons: real collisions per process
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -247,11 +264,131 @@ __device__ __forceinline__ bool electron_is_real(const Params& P, const float* t
     return (u1 * P.numax[SP_E]) < grid_interp(tot, 1, 0, i, w);
 }
 
+// Filter of an ion candidate: the target sampled from the gas Maxwellian
+// (words 2, 3 of block 0 and the blocks after), the relative energy, and the
+// total rate on the table grid against u1 nu_max (word 1): the same
+// arithmetic as the start of collide().
+template <int S>
+__device__ __forceinline__ bool ion_is_real(const Params& P, const float* tot, unsigned long long step, uint32_t id,
+                                            uint4 w, float vx, float vy, float vz, unsigned& wtries,
+                                            unsigned& wemax) {
+    Stream st;
+    st.resume(id, P.seed, step, SpeciesTraits<S>::tag, w, 1);
+    const float u1 = uniform(st.next());
+    float vtx, vty, vtz;
+    maxwellian(st, P.sig_gas, vtx, vty, vtz, wtries);
+    const float gx = vx - vtx, gy = vy - vty, gz = vz - vtz;
+    const float E = P.kappa[S] * dot3(gx, gy, gz, gx, gy, gz);
+    int i; float wt; bool above;
+    grid_locate(E, i, wt, above);
+    if (above) ++wemax;
+    return (u1 * P.numax[S]) < grid_interp(tot, 1, 0, i, wt);
+}
+
 // Total-rate column (the last cumulative column) of species S into shared memory.
 __device__ __forceinline__ void stage_total(const Params& P, int S, float* tot) {
     const int np = P.nproc[S];
     const float* __restrict__ cum = P.cum[S];
     for (int i = threadIdx.x; i < NGRID; i += blockDim.x) tot[i] = np > 0 ? cum[(size_t)i * np + np - 1] : 0.0f;
+}
+
+// Real collisions of the list of one particle-kernel warp (records r0 ..
+// r0 + n - 1, in slot order), taken SEGW records per pass by the SEGW lanes
+// of one segment of the calling warp (seg_mask: its lanes; sl: this lane's
+// index in it; lt_mask: the segment's lanes below this one; nmax: the longest
+// list among the warp's segments, so that every lane makes the same passes).
+// Electron records carry the particle (slot, id, x, v) and block 0 of its
+// Philox stream is drawn again; ion records carry the slot, id, v and that
+// block (its first word, the candidate draw, is spent), x is read from the
+// array.  A removed particle's charge comes off the block's histogram when
+// `hist` is given (the particle kernel: the particle was deposited there),
+// else off the step's deposit in global memory.  Births are ranked with
+// ballots within the segment and staged at the particle warp's slot range;
+// nb1, nb2 count them.
+template <int S, int SEGW>
+__device__ __forceinline__ void collide_list(const Params& P, const PhiloxPre& pre, unsigned long long step,
+                                             unsigned r0, unsigned n, unsigned nmax, unsigned sl,
+                                             unsigned seg_mask, unsigned lt_mask, unsigned* events,
+                                             unsigned long long* hist, unsigned& nb1, unsigned& nb2,
+                                             unsigned& nremoved, unsigned& wtries, unsigned& wemax) {
+    const int np = P.nproc[S];
+    const float* __restrict__ cum = P.cum[S];
+    const unsigned cb = P.ctrl->cur[S];
+    float* __restrict__ X = P.sp[S].x[cb];
+    float* __restrict__ VX = P.sp[S].vx[cb];
+    float* __restrict__ VY = P.sp[S].vy[cb];
+    float* __restrict__ VZ = P.sp[S].vz[cb];
+    const uint4* __restrict__ CAND = P.cand[S];
+    const float inv_dx = P.inv_dx;
+    const int Nc = P.Nc;
+    const bool births = P.births_possible[S] != 0;
+    for (unsigned c0 = 0; c0 < nmax; c0 += SEGW) {
+        const unsigned ci = c0 + sl;
+        const bool has = ci < n;
+        uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+        if (has) { a = CAND[2 * (size_t)(r0 + ci)]; b = CAND[2 * (size_t)(r0 + ci) + 1]; }
+        const unsigned slot = a.x;
+        float x, vx, vy, vz;
+        uint4 w0;
+        if (S == SP_E) {
+            x = __uint_as_float(a.z); vx = __uint_as_float(a.w);
+            vy = __uint_as_float(b.x); vz = __uint_as_float(b.y);
+            w0 = has ? philox_id(pre, a.y) : make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            x = has ? X[slot] : 0.0f;
+            vx = __uint_as_float(a.z); vy = __uint_as_float(a.w); vz = __uint_as_float(b.x);
+            w0 = make_uint4(0u, b.y, b.z, b.w);
+        }
+        w0.x = a.y;   // word 0 (the candidate draw) is spent: it carries the id
+        int bkind = 0;
+        float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
+        if (has) {
+            bool alive;
+            const int k = collide<S>(P, cum, np, step, a.y, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
+            if (k >= 0) {
+                atomicAdd(&events[k], 1u);
+                if (alive) {
+                    VX[slot] = vx; VY[slot] = vy; VZ[slot] = vz;
+                } else {
+                    X[slot] = dead_marker();
+                    if (hist) {
+                        int j; float f;
+                        cell_of(x, inv_dx, Nc, j, f);
+                        atomicAdd(&hist[j], 0ull - ((1ull << 40) + (unsigned long long)cic_r(f)));
+                    } else {
+                        deposit_sub_global(P.Qf[S], x, inv_dx, Nc);
+                    }
+                    ++nremoved;
+                }
+            }
+        }
+        if (births) {
+            const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1) & seg_mask;
+            const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2) & seg_mask;
+            // staged for the end-of-step kernel, which places them; their
+            // charge goes to Qb now
+            if (S == SP_E) {
+                if (bkind == 1) {
+                    const unsigned r = nb1 + __popc(m1 & lt_mask);
+                    P.stage[B_E_FROM_E][r0 + r] = b1;
+                    P.stage[B_OP_FROM_E][r0 + r] = b2;
+                    deposit_add_global(P.Qb[SP_E], b1.x, inv_dx, Nc);
+                    deposit_add_global(P.Qb[SP_OP], b2.x, inv_dx, Nc);
+                } else if (bkind == 2) {
+                    P.stage[B_OM_FROM_E][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
+                    deposit_add_global(P.Qb[SP_OM], b1.x, inv_dx, Nc);
+                }
+            } else if (S == SP_OM) {
+                if (bkind == 2) {
+                    P.stage[B_E_FROM_OM][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
+                    deposit_add_global(P.Qb[SP_E], b1.x, inv_dx, Nc);
+                }
+            }
+            nb1 += __popc(m1);
+            nb2 += __popc(m2);
+        }
+        __syncwarp();
+    }
 }
 
 // Candidate queue of one warp of the particle kernel (shared memory): slot,
@@ -274,7 +411,8 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     unsigned long long* hist =
         reinterpret_cast<unsigned long long*>(smem + align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng));
     PushQueue& Q = *reinterpret_cast<PushQueue*>(hist + P.Ng);
-    float* Tt = reinterpret_cast<float*>(&Q + 1);        // electrons: total-rate column
+    float* Tt = reinterpret_cast<float*>(&Q + 1);        // total-rate column (filter in the kernel)
+    constexpr bool fused = (S == SP_E) || (O2PIC_FUSE_IONS != 0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     unsigned* qs = Q.slot[warp];
@@ -300,8 +438,12 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     const PhiloxPre pre = philox_pre(step_lo, SpeciesTraits<S>::tag, (uint32_t)(step >> 32), P.seed);
 
     for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0ull; }
-    if (S == SP_E) stage_total(P, S, Tt);
-    if (tid == 0) { sh.absorbed[0] = sh.absorbed[1] = 0u; sh.removed = 0u; sh.psteps = 0u; sh.nonfinite = 0u; sh.jsum = 0ull; }
+    if (fused) stage_total(P, S, Tt);
+    if (tid == 0) {
+        sh.absorbed[0] = sh.absorbed[1] = 0u; sh.removed = 0u; sh.psteps = 0u; sh.nonfinite = 0u; sh.wtries = 0u;
+        sh.jsum = 0ull;
+    }
+    if (fused && tid < MAXPROC) sh.events[tid] = 0u;
     __syncthreads();
 
     // this warp's contiguous slot range
@@ -311,17 +453,18 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
     const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
 
-    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0, wemax = 0;
+    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0, wemax = 0, wtries = 0;
     long long jacc = 0;   // conduction current: sum of trunc(256 v_x^{n+1/2}) (exact)
     unsigned nrec = 0;    // warp-uniform: records of this warp so far
     unsigned qn = 0;      // warp-uniform: queued candidates
 
     // The first m (<= 32) queued candidates, one per lane: the candidate's
-    // stream at this step (block 0) draws its next free flight (word 0) and,
-    // for electrons, the real/null test (word 1: energy against the total
-    // rate); records go to the warp's list in slot order, two uint4 each:
-    // electrons {slot, id, x, vx}{vy, vz, -, -} (real collisions), ions
-    // {slot, id, vx, vy}{vz, w1, w2, w3} (candidates, for the filter).
+    // stream at this step (block 0) draws its next free flight (word 0) and
+    // the real/null test (word 1 against the total rate at the particle's
+    // energy; ions: relative to a target from the gas Maxwellian); records go
+    // to the warp's list in slot order, two uint4 each: electrons {slot, id,
+    // x, vx}{vy, vz, -, -}, ions {slot, id, vx, vy}{vz, w1, w2, w3} (the real
+    // collisions; with the ion filter in its own kernel, every ion candidate).
     auto flush = [&](unsigned m) {
         const bool has = (unsigned)lane < m;
         const unsigned slot = has ? qs[lane] : 0u;
@@ -334,7 +477,8 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
         if (has) {
             w = philox_id(pre, id);
             TC[slot] = step_lo + sub * (1u + flight_gap(w.x, inv_lnq, kcap));
-            rec = (S == SP_E) ? electron_is_real(P, Tt, w.y, cvx, cvy, cvz, wemax) : true;
+            if (S == SP_E) rec = electron_is_real(P, Tt, w.y, cvx, cvy, cvz, wemax);
+            else rec = !fused || ion_is_real<S>(P, Tt, step, id, w, cvx, cvy, cvz, wtries, wemax);
         }
         const unsigned cm = __ballot_sync(0xffffffffu, rec);
         if (rec) {
@@ -412,18 +556,42 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     }
     __syncwarp();
     if (qn > 0u) flush(qn);
+    unsigned nrm = 0;
+    if (fused) {
+        // the real collisions, by the warp that recorded them (its lanes'
+        // records are visible to the whole warp after the barrier): the
+        // kinematics run while other warps still push, and a removed
+        // particle's charge comes off this block's histogram.  The filter
+        // counted the warnings of the part it shares with the kinematics.
+        __syncwarp();
+        unsigned nb1 = 0, nb2 = 0, wt2 = 0, we2 = 0;
+        collide_list<S, 32>(P, pre, step, r0, nrec, nrec, (unsigned)lane, 0xffffffffu, lt_mask, sh.events, hist,
+                            nb1, nb2, nrm, wt2, we2);
+        wtries += wt2;
+        if (P.births_possible[S] && lane == 0) {
+            if (S == SP_E) {
+                P.wcount[B_E_FROM_E][gw] = nb1;
+                P.wcount[B_OM_FROM_E][gw] = nb2;
+            } else if (S == SP_OM) {
+                P.wcount[B_E_FROM_OM][gw] = nb2;
+            }
+        }
+    } else if (lane == 0) {
+        P.ccount[S][gw] = nrec;
+    }
     pdl_trigger();
-    if (lane == 0) P.ccount[S][gw] = nrec;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) jacc += __shfl_down_sync(0xffffffffu, jacc, o);
     if (lane == 0 && jacc) atomicAdd(&sh.jsum, (unsigned long long)jacc);
     if (psteps) atomicAdd(&sh.psteps, psteps);
     if (nabs0) atomicAdd(&sh.absorbed[0], nabs0);
     if (nabs1) atomicAdd(&sh.absorbed[1], nabs1);
-    if (nabs0 + nabs1 + nnf) atomicAdd(&sh.removed, nabs0 + nabs1 + nnf);
+    if (nabs0 + nabs1 + nnf + nrm) atomicAdd(&sh.removed, nabs0 + nabs1 + nnf + nrm);
     if (nnf) atomicAdd(&sh.nonfinite, nnf);
-    if (S == SP_E && wemax) atomicAdd(&C->cnt.warn_emax, (unsigned long long)wemax);
+    if (wtries) atomicAdd(&sh.wtries, wtries);
+    if (wemax) atomicAdd(&C->cnt.warn_emax, (unsigned long long)wemax);
     __syncthreads();
+    if (fused && tid < np && sh.events[tid]) atomicAdd(&C->cnt.events[S][tid], (unsigned long long)sh.events[tid]);
     unsigned long long* __restrict__ Qcopy = P.Qf[S] + (size_t)(blk & (QCOPIES - 1)) * Ng;
     for (int c = tid; c < Nc; c += BLOCK) {
         const unsigned long long v = hist[c];
@@ -442,6 +610,7 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
             atomicAdd(&C->cnt.psteps[S], (unsigned long long)sh.psteps);
         }
         if (sh.nonfinite) atomicOr(&C->error_flags, ERR_NONFINITE);
+        if (sh.wtries) atomicAdd(&C->cnt.warn_tries, (unsigned long long)sh.wtries);
         if (sh.jsum) atomicAdd(&P.jring[(step & (JRING - 1)) * NSP + S], sh.jsum);
     }
 }
@@ -550,16 +719,13 @@ __device__ __forceinline__ void filter_body(const Params& P, unsigned blk, unsig
     }
 }
 
-// Real collisions of one species for this step.  Each warp takes two lists
-// of the particle kernel's warps at once, one per half-warp (16 lanes; a list
-// holds about a dozen records at the method's rates), and walks them in slot
-// order, 16 records per pass through the kinematics, so the
-// lists of a step run in one wave of resident warps.  Electron records carry
-// the particle (slot, id, x, v) and block 0 of its Philox stream is drawn
-// again; ion records carry the slot, id, v and that block (its first word,
-// the candidate draw, is spent), x is read from the array.  Births are
-// ranked with ballots within the half-warp and staged at the particle warp's
-// slot range with their count.
+// Real collisions of one ion species for this step (the electrons' run at
+// the end of their particle kernel).  Each warp takes two lists of the
+// particle kernel's warps at once, one per half-warp (16 lanes; a list holds
+// a few records at the method's rates), and walks them in slot order, 16
+// records per pass through the kinematics, so the lists of a step run in one
+// wave of resident warps.  Births are ranked with ballots within the
+// half-warp and staged at the particle warp's slot range with their count.
 constexpr int SEG = 16;
 constexpr int SEGS = 32 / SEG;
 
@@ -572,22 +738,13 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
     const unsigned seg = (unsigned)lane / SEG, sl = (unsigned)lane % SEG;
     const unsigned seg_mask = ((1u << SEG) - 1u) << (seg * SEG);
     const unsigned lt_mask = ((1u << lane) - 1u) & seg_mask;   // lanes below, same half-warp
-    const float* __restrict__ cum = P.cum[S];
     if (tid < MAXPROC) events[tid] = 0u;
     if (tid == 0) { sh_removed = 0u; sh_wtries = 0u; sh_wemax = 0u; }
     __syncthreads();
 
     DevCtrl* C = P.ctrl;
     const unsigned long long step = C->step;
-    const unsigned cb = C->cur[S];
     const unsigned nslots = (unsigned)((C->slots[S] < P.sp[S].cap) ? C->slots[S] : P.sp[S].cap);
-    float* __restrict__ X = P.sp[S].x[cb];
-    float* __restrict__ VX = P.sp[S].vx[cb];
-    float* __restrict__ VY = P.sp[S].vy[cb];
-    float* __restrict__ VZ = P.sp[S].vz[cb];
-    const uint4* __restrict__ CAND = P.cand[S];
-    const float inv_dx = P.inv_dx;
-    const int Nc = P.Nc;
     const bool births = P.births_possible[S] != 0;
     unsigned* cnt1 = (S == SP_E) ? P.wcount[B_E_FROM_E] : nullptr;
     unsigned* cnt2 = (S == SP_E) ? P.wcount[B_OM_FROM_E] : (S == SP_OM ? P.wcount[B_E_FROM_OM] : nullptr);
@@ -603,67 +760,8 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
         const unsigned n = valid ? P.ccount[S][gw] : 0u;
         const unsigned nmax = max(n, __shfl_xor_sync(0xffffffffu, n, SEG));
         unsigned nb1 = 0, nb2 = 0;   // half-warp-uniform
-        for (unsigned c0 = 0; c0 < nmax; c0 += SEG) {
-            const unsigned ci = c0 + sl;
-            const bool has = ci < n;
-            uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
-            if (has) { a = CAND[2 * (size_t)(r0 + ci)]; b = CAND[2 * (size_t)(r0 + ci) + 1]; }
-            const unsigned slot = a.x;
-            float x, vx, vy, vz;
-            uint4 w0;
-            if (S == SP_E) {
-                x = __uint_as_float(a.z); vx = __uint_as_float(a.w);
-                vy = __uint_as_float(b.x); vz = __uint_as_float(b.y);
-                w0 = has ? philox_id(pre, a.y) : make_uint4(0u, 0u, 0u, 0u);
-            } else {
-                x = has ? X[slot] : 0.0f;
-                vx = __uint_as_float(a.z); vy = __uint_as_float(a.w); vz = __uint_as_float(b.x);
-                w0 = make_uint4(0u, b.y, b.z, b.w);
-            }
-            w0.x = a.y;   // word 0 (the candidate draw) is spent: it carries the id
-            int bkind = 0;
-            float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
-            if (has) {
-                bool alive;
-                const int k = collide<S>(P, cum, np, step, a.y, w0, x, vx, vy, vz, alive, bkind, b1, b2, wtries, wemax);
-                if (k >= 0) {
-                    atomicAdd(&events[k], 1u);
-                    if (alive) {
-                        VX[slot] = vx; VY[slot] = vy; VZ[slot] = vz;
-                    } else {
-                        X[slot] = dead_marker();
-                        deposit_sub_global(P.Qf[S], x, inv_dx, Nc);
-                        ++nremoved;
-                    }
-                }
-            }
-            if (births) {
-                const unsigned m1 = __ballot_sync(0xffffffffu, bkind == 1) & seg_mask;
-                const unsigned m2 = __ballot_sync(0xffffffffu, bkind == 2) & seg_mask;
-                // staged for the end-of-step kernel, which places them; their
-                // charge goes to Qb now
-                if (S == SP_E) {
-                    if (bkind == 1) {
-                        const unsigned r = nb1 + __popc(m1 & lt_mask);
-                        P.stage[B_E_FROM_E][r0 + r] = b1;
-                        P.stage[B_OP_FROM_E][r0 + r] = b2;
-                        deposit_add_global(P.Qb[SP_E], b1.x, inv_dx, Nc);
-                        deposit_add_global(P.Qb[SP_OP], b2.x, inv_dx, Nc);
-                    } else if (bkind == 2) {
-                        P.stage[B_OM_FROM_E][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
-                        deposit_add_global(P.Qb[SP_OM], b1.x, inv_dx, Nc);
-                    }
-                } else if (S == SP_OM) {
-                    if (bkind == 2) {
-                        P.stage[B_E_FROM_OM][r0 + nb2 + __popc(m2 & lt_mask)] = b1;
-                        deposit_add_global(P.Qb[SP_E], b1.x, inv_dx, Nc);
-                    }
-                }
-                nb1 += __popc(m1);
-                nb2 += __popc(m2);
-            }
-            __syncwarp();
-        }
+        collide_list<S, SEG>(P, pre, step, r0, n, nmax, sl, seg_mask, lt_mask, events, nullptr, nb1, nb2,
+                             nremoved, wtries, wemax);
         if (births && valid && sl == 0) {
             if (cnt1) cnt1[gw] = nb1;
             if (cnt2) cnt2[gw] = nb2;
@@ -683,7 +781,10 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
 }
 
 template <int S>
-__global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push(Params P) {
+constexpr int push_min_blocks() { return S == SP_E ? O2PIC_PUSH_E_MIN_BLOCKS : O2PIC_PUSH_MIN_BLOCKS; }
+
+template <int S>
+__global__ void __launch_bounds__(BLOCK, push_min_blocks<S>()) k_push(Params P) {
     pdl_wait();
     push_body<S>(P, blockIdx.x, gridDim.x);
 }
@@ -708,7 +809,7 @@ __global__ void __launch_bounds__(BLOCK, O2PIC_FILTER_MIN_BLOCKS) k_filter(Param
 // map[b].y of map[b].z, with that discharge's parameters copied to shared
 // memory (load_params).
 template <int S>
-__global__ void __launch_bounds__(BLOCK, O2PIC_PUSH_MIN_BLOCKS) k_push_b(const Params* __restrict__ all,
+__global__ void __launch_bounds__(BLOCK, push_min_blocks<S>()) k_push_b(const Params* __restrict__ all,
                                                                         const uint4* __restrict__ map) {
     __shared__ Params sP;
     pdl_wait();
@@ -777,8 +878,10 @@ __global__ void __launch_bounds__(BLOCK) k_deposit(Params P) {
 size_t push_smem_bytes(int species, const Params& P) {
     const size_t base = align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng) +
                         sizeof(unsigned long long) * P.Ng + sizeof(PushQueue);
-    return species == SP_E ? base + sizeof(float) * NGRID : base;
+    return (species == SP_E || O2PIC_FUSE_IONS) ? base + sizeof(float) * NGRID : base;
 }
+
+bool ions_fused() { return O2PIC_FUSE_IONS != 0; }
 
 void launch_flight_init(int species, const Params& P, cudaStream_t s) {
     const unsigned long long cap = P.sp[species].cap;
@@ -802,9 +905,8 @@ void launch_push_batched(int species, const Params* all, const uint4* map, int n
 }
 
 void launch_cand_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s) {
-    if (species == SP_E) launch_pdl(k_cand_b<SP_E>, nblocks, BLOCK, 0, s, all, map);
-    else if (species == SP_OM) launch_pdl(k_cand_b<SP_OM>, nblocks, BLOCK, 0, s, all, map);
-    else launch_pdl(k_cand_b<SP_OP>, nblocks, BLOCK, 0, s, all, map);
+    if (species == SP_OM) launch_pdl(k_cand_b<SP_OM>, nblocks, BLOCK, 0, s, all, map);
+    else if (species == SP_OP) launch_pdl(k_cand_b<SP_OP>, nblocks, BLOCK, 0, s, all, map);
 }
 
 void launch_filter(int species, const Params& P, int grid, cudaStream_t s) {
@@ -818,9 +920,8 @@ void launch_filter_batched(int species, const Params* all, const uint4* map, int
 }
 
 void launch_cand(int species, const Params& P, int grid, cudaStream_t s) {
-    if (species == SP_E) launch_pdl(k_cand<SP_E>, grid, BLOCK, 0, s, P);
-    else if (species == SP_OM) launch_pdl(k_cand<SP_OM>, grid, BLOCK, 0, s, P);
-    else launch_pdl(k_cand<SP_OP>, grid, BLOCK, 0, s, P);
+    if (species == SP_OM) launch_pdl(k_cand<SP_OM>, grid, BLOCK, 0, s, P);
+    else if (species == SP_OP) launch_pdl(k_cand<SP_OP>, grid, BLOCK, 0, s, P);
 }
 
 void launch_deposit(int species, const Params& P, int grid, cudaStream_t s) {

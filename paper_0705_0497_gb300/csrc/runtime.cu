@@ -326,15 +326,14 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
     for (uint64_t k = 0; k < nsteps; ++k) {
         const bool ion = (c->host_step % S) == 0;
         launch(c, KK_PUSH_E, s, [&] { launch_push(SP_E, P, c->grid_push[SP_E], s); });
-        if (P.nproc[SP_E]) launch(c, KK_CAND_E, s, [&] { launch_cand(SP_E, P, c->grid_push[SP_E], s); });
         if (ion) {
             launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
-            if (P.nproc[SP_OM]) {
+            if (P.nproc[SP_OM] && !ions_fused()) {
                 launch(c, KK_FILT_OM, s, [&] { launch_filter(SP_OM, P, c->grid_push[SP_OM], s); });
                 launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
             }
             launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
-            if (P.nproc[SP_OP]) {
+            if (P.nproc[SP_OP] && !ions_fused()) {
                 launch(c, KK_FILT_OP, s, [&] { launch_filter(SP_OP, P, c->grid_push[SP_OP], s); });
                 launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
             }
@@ -1239,14 +1238,16 @@ void enqueue_fused(o2pic_batch* b, cudaStream_t s) {
     for (uint64_t k = 0; k < b->K; ++k) {
         const bool ion = (step % S) == 0;
         launch_push_batched(SP_E, b->dP, b->dmap + b->map_push[SP_E], b->nb_push[SP_E], b->smem_push, s);
-        launch_cand_batched(SP_E, b->dP, b->dmap + b->map_push[SP_E], b->nb_push[SP_E], s);
-        launches += 2;
+        launches += 1;
         if (ion) {
             for (int sp = SP_OM; sp <= SP_OP; ++sp) {
                 launch_push_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], b->smem_push, s);
-                launch_filter_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
-                launch_cand_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
-                launches += 3;
+                launches += 1;
+                if (!ions_fused()) {
+                    launch_filter_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
+                    launch_cand_batched(sp, b->dP, b->dmap + b->map_push[sp], b->nb_push[sp], s);
+                    launches += 2;
+                }
             }
             if (b->any_edet) {
                 launch_pair_hist_batched(b->dP, b->dD, b->dmap + b->map_dh, b->nb_dh, b->smem_hist, s);

@@ -5,9 +5,12 @@ RF cycles until its cycle-averaged density profiles stop changing.  Here a
 small MLP (`api.MLP`: the library's own forward, backward and Adam kernels)
 learns, from runs the method itself produced, the map
 
-    (U, p, L, C)  ->  cycle-averaged log densities of e, O-, O2+ on the cells,
+    (U, p, L, C)  ->  cycle-averaged log densities of e, O-, O2+ on the cells
+                      and their log mean energies on 32 bins,
 
-and a new run is loaded from the predicted profiles instead of uniformly.
+and a new run is loaded from the predicted profiles instead of uniformly
+(positions from the densities, Maxwellian velocities at two thirds of the
+local mean energy).
 The cold start stays the fallback and the judge of the result: a warm-started
 run is still the method, only its initial condition differs.
 
@@ -73,12 +76,15 @@ def warm_state(cfg, cells, T_eV, seed):
     return out
 
 
-def make_discharges(api, runs, procs, capacity_factor=8, compact_check=200):
-    """Library contexts for [(cfg, state)] (all processes set, particles loaded)."""
+def make_discharges(api, runs, procs, capacity_factor=8, compact_check=200, n_floor=1000):
+    """Library contexts for [(cfg, state)] (all processes set, particles
+    loaded); capacity_factor slots per loaded particle, counted as at least
+    n_floor (a warm start may load few of a species that then grows)."""
     gs = []
     for cfg, st in runs:
         n = [len(p["x"]) for p in st]
-        g = api.Discharge(cfg, tuple(capacity_factor * max(k, 1000) + 65536 for k in n), compact_check=compact_check)
+        g = api.Discharge(cfg, tuple(capacity_factor * max(k, n_floor) + 65536 for k in n),
+                          compact_check=compact_check)
         g.set_processes(procs)
         g.load_state(st)
         gs.append(g)
@@ -140,79 +146,293 @@ def profile_error(cells, ref):
             for s in range(3)]
 
 
-def experiment(n_train=64, n_held=8, N=20000, cycles=1200, window=100, eval_cycles=600, eval_window=20,
-               train_steps=4000, seed=2024, log=print):
-    """The warm-start study: cold runs of n_train + n_held discharges of the
-    batched sweep's (U, p) ranges (N e + N O- + 2N O2+ each) for `cycles`
-    RF cycles give the reference profiles (average of the last `window`
-    cycles); the MLP learns the first n_train; each held-out discharge is
-    then started warm (predicted profiles) and cold (uniform, new seed) and
-    run for `eval_cycles`.  A run has converged once its `eval_window`-cycle
-    profile is within tol of the reference, tol = max(0.1, 2 x the
-    reference run's own change between its last two windows) (rms over the
-    inner cells, per species, largest species).  Returns a summary dict."""
+BINS = 32
+E_FLOOR = 1.0e-3            # eV: mean energies below are clipped before the log
+
+
+def binned(cells, bins=BINS):
+    """Bin averages [3][bins] of cell profiles [3][Nc]."""
+    c = np.asarray(cells, np.float64)
+    return c.reshape(c.shape[0], bins, -1).mean(axis=2)
+
+
+def binned_error(cells, ref, bins=BINS):
+    """rms over the inner 3/4 of the bins of (n - n_ref) / mean(n_ref), per species."""
+    a, b = binned(cells, bins), binned(ref, bins)
+    inner = slice(bins // 8, bins - bins // 8)
+    return [float(np.sqrt(np.mean((a[s][inner] - b[s][inner]) ** 2)) / max(b[s][inner].mean(), 1.0))
+            for s in range(3)]
+
+
+def energy_profiles(g, cfg, bins=BINS):
+    """Mean kinetic energy [eV] of each species on the bins, from the live
+    particles of a discharge (a snapshot)."""
+    out = np.zeros((3, bins))
+    for s in range(3):
+        p = g.particles(s)
+        if len(p["x"]) == 0:
+            continue
+        m = inputs.species_mass(cfg, s)
+        e = 0.5 * m * (p["vx"].astype(np.float64) ** 2 + p["vy"] ** 2 + p["vz"] ** 2) / inputs.QE
+        k = np.minimum((p["x"] / cfg["L"] * bins).astype(np.int64), bins - 1)
+        cnt = np.bincount(k, minlength=bins)
+        out[s] = np.bincount(k, weights=e, minlength=bins) / np.maximum(cnt, 1)
+    return out
+
+
+def to_target2(cells, energy):
+    return np.concatenate([to_target(cells),
+                           np.log(np.maximum(np.asarray(energy, np.float64), E_FLOOR)).astype(np.float32).ravel()])
+
+
+def from_target2(y, n_cells=N_CELLS, bins=BINS):
+    y = np.asarray(y, np.float64)
+    return from_target(y[:3 * n_cells]), np.exp(y[3 * n_cells:]).reshape(3, bins)
+
+
+def warm_state2(cfg, cells, energy, seed, T_floor=(0.05, 0.026, 0.026)):
+    """Particles drawn from cell densities [3][Nc] (stochastic rounding per
+    cell, uniform within the cell) with isotropic Maxwellian velocities at
+    the local temperature (2/3) <E> of their bin."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Nc = cells.shape[1]
+    bins = energy.shape[1]
+    dx = cfg["L"] / Nc
+    out = []
+    for s in range(3):
+        mean = cells[s] * dx * cfg["area"] / cfg["weight"]
+        k = np.floor(mean + rng.random(Nc)).astype(np.int64)
+        n = int(k.sum())
+        c = np.repeat(np.arange(Nc), k)
+        x = ((c + rng.random(n)) * dx).astype(np.float32)
+        x = np.minimum(x, np.float32(cfg["L"]) * np.float32(1 - 2 ** -23))
+        T = np.maximum(2.0 / 3.0 * energy[s][np.minimum(c * bins // Nc, bins - 1)], T_floor[s])
+        sig = np.sqrt(T * inputs.QE / inputs.species_mass(cfg, s))
+        v = (rng.standard_normal((3, n)) * sig).astype(np.float32)
+        out.append(dict(x=x, vx=v[0].copy(), vy=v[1].copy(), vz=v[2].copy(), id=np.arange(n, dtype=np.uint32)))
+    return out
+
+
+def run_windows(api, gs, cycles, window, steps_per_launch=200, tune=True, snapshots=0):
+    """Advance the discharges together; per `window` cycles the cycle-averaged
+    cell densities of each, the wall time at the end of each window, and (if
+    snapshots) the mean-energy profiles averaged over that many snapshots in
+    the last window."""
+    import time
+    spc = gs[0].cfg["steps_per_cycle"]
+    per_cycle = spc // steps_per_launch
+    b = api.Batch(gs, steps_per_launch)
+    if tune:
+        b.autotune()
+        b.synchronize()
+    hist, walls, en = [], [], None
+    t0 = time.perf_counter()
+    nwin = (cycles + window - 1) // window
+    for w in range(nwin):
+        c = min(window, cycles - w * window)
+        for g in gs:
+            g.moments(reset=True)
+        if snapshots and w == nwin - 1:
+            en = [np.zeros((3, BINS)) for _ in gs]
+            per = max(1, c // snapshots)
+            done = 0
+            while done < c:
+                k = min(per, c - done)
+                b.step(per_cycle * k)
+                b.synchronize()
+                for i, g in enumerate(gs):
+                    en[i] += energy_profiles(g, g.cfg) / snapshots
+                done += k
+        else:
+            b.step(per_cycle * c)
+        b.synchronize()
+        walls.append(time.perf_counter() - t0)
+        hist.append([cell_profiles(g.moments()[0]) for g in gs])
+    b.close()
+    return hist, walls, en
+
+
+def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000, eval_cycles=1000, window=200,
+           tol=0.02, train_steps=6000, seed=4242, log=print, save=None):
+    """The warm-start study at the 2 % criterion.
+
+    1. n0 discharges of the sweep's (U, p, L, C) ranges started cold run
+       ref_cycles; their last window (average of `window` cycles) is the
+       reference, kept if its change from the window before is below tol/2
+       (converged), with mean-energy profiles from snapshots.
+    2. The network (4 -> 256 x 3 -> 3 x 256 log densities + 3 x 32 log mean
+       energies) learns them; n1 more discharges start warm from it and run
+       boot_cycles; the converged ones join the training set (the method
+       produces them, faster); the network learns all.
+    3. n_held held-out discharges start warm (batched) and cold (batched: the
+       same results as single runs, bit for bit) and run eval_cycles and
+       ref_cycles; the mean of the cold run's last two windows is the
+       reference; a run has converged at the first window within tol of it
+       (rms over the inner bins, the largest of the three species).
+    4. Wall time: the plain cold start on its own (a one-discharge step graph)
+       is timed per cycle on a few held-out discharges; a cold run's wall time
+       = its cycles to converge x that; a warm run's = its cycles to converge
+       x the warm batch's wall time per cycle / its discharges, plus its share
+       of training, inference and loading.
+
+    `save(summary)` (optional) is called after every phase with the results
+    so far."""
     import time
     import torch
     from . import api, xsec
     procs = xsec.oxygen_set()
     T = (3.0, 0.026, 0.026)
-    sweep = inputs.batch_sweep(n_train + n_held, seed=seed, count_range=(N, N))
-    runs = [(cfg, cold_state(cfg, counts, T, seed=seed + i)) for i, (cfg, counts, _) in enumerate(sweep)]
-    gs = make_discharges(api, runs, procs)
-    t0 = time.time()
-    ref, hist = run_cycles(api, gs, cycles, window,
-                           progress=lambda c, h: log(f"  reference: {c} cycles, {time.time() - t0:.0f} s"))
-    t_ref = time.time() - t0
-    noise = [max(profile_error(hist[-1][i], hist[-2][i])) for i in range(len(gs))]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    total = n0 + n1 + n_held
+    sweep = inputs.batch_sweep(total, seed=seed, count_range=(N, N))
+    # widen L and C (the sweep fixes them) so that all four inputs vary; C
+    # from 0.05 up: with fewer metastables the O- lose their excess only by
+    # neutralization, on a time scale of ~1e4 RF cycles (no converged runs
+    # to learn from in a study of this length)
+    for cfg, counts, _ in sweep:
+        cfg["L"] = float(rng.uniform(0.02, 0.03))
+        cfg["C_meta"] = float(rng.uniform(0.05, 1.0 / 6.0))
+        cfg["weight"] = 1.0e15 * cfg["L"] / N
+        cfg["dt"] = 1.0 / (cfg["f"] * cfg["steps_per_cycle"])
+    summary = {"n0": n0, "n1": n1, "n_held": n_held, "N": N, "ref_cycles": ref_cycles, "boot_cycles": boot_cycles,
+               "eval_cycles": eval_cycles, "window": window, "tol": tol, "bins": BINS}
+
+    def converged_change(h, i):
+        return max(binned_error(h[-1][i], h[-2][i]))
+
+    def checkpoint():
+        if save:
+            save(summary)
+
+    # 1. cold references
+    t0 = time.perf_counter()
+    runs = [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + i)) for i in range(n0)]
+    gs = make_discharges(api, runs, procs, capacity_factor=6, n_floor=N)
+    h0, w0, en0 = run_windows(api, gs, ref_cycles, window, snapshots=5)
     for g in gs:
         g.close()
-    log(f"reference runs: {len(gs)} discharges x {cycles} cycles in {t_ref:.1f} s; "
-        f"last-window change median {np.median(noise):.3f}")
-    train_idx, held = list(range(n_train)), list(range(n_train, n_train + n_held))
-    X = np.stack([features(sweep[i][0]) for i in train_idx])
-    Y = np.stack([to_target(ref[i]) for i in train_idx])
-    mlp = api.MLP([4, 256, 256, 256, 768], seed=seed)
-    t0 = time.time()
-    losses = train(api, mlp, X, Y, steps=train_steps)
+    t_ref = time.perf_counter() - t0
+    train_X, train_Y = [], []
+    ch0 = [converged_change(h0, i) for i in range(n0)]
+    for i in range(n0):
+        if ch0[i] < tol:
+            train_X.append(features(sweep[i][0]))
+            train_Y.append(to_target2(h0[-1][i], en0[i]))
+    n_conv0 = len(train_X)
+    summary["phase1_all_used"] = n_conv0 < 4   # too few converged: learn from all (short test runs)
+    if summary["phase1_all_used"]:
+        train_X = [features(sweep[i][0]) for i in range(n0)]
+        train_Y = [to_target2(h0[-1][i], en0[i]) for i in range(n0)]
+    log(f"phase 1: {n0} cold runs x {ref_cycles} cycles in {t_ref:.0f} s; converged (last change < {tol}) "
+        f"{n_conv0}; change median {np.median(ch0):.4f}")
+    summary.update(phase1_s=t_ref, phase1_kept=n_conv0, phase1_change_median=float(np.median(ch0)),
+                   phase1_changes=[float(v) for v in ch0])
+    checkpoint()
+    mlp = api.MLP([4, 256, 256, 256, 3 * N_CELLS + 3 * BINS], seed=seed)
+    t1 = time.perf_counter()
+    train(api, mlp, np.stack(train_X), np.stack(train_Y), steps=train_steps)
     torch.cuda.synchronize()
-    t_train = time.time() - t0
-    t0 = time.time()
-    pred = predict(mlp, [sweep[i][0] for i in held])
-    t_pred = time.time() - t0
-    pred_err = [max(profile_error(pred[k], ref[i])) for k, i in enumerate(held)]
-    log(f"training {train_steps} Adam steps in {t_train:.2f} s, loss {losses[0]:.3g} -> {losses[-1]:.3g}; "
-        f"held-out prediction error median {np.median(pred_err):.3f}")
-    cases = []
-    for k, i in enumerate(held):
-        cfg, counts, _ = sweep[i]
-        cases.append((cfg, warm_state(cfg, pred[k], T, seed=seed + 1000 + k)))
-        cases.append((cfg, cold_state(cfg, counts, T, seed=seed + 2000 + k)))
-    gs = make_discharges(api, cases, procs)
-    t0 = time.time()
-    _, eh = run_cycles(api, gs, eval_cycles, eval_window,
-                       progress=lambda c, h: log(f"  evaluation: {c} cycles, {time.time() - t0:.0f} s"))
-    t_eval = time.time() - t0
+    t_train1 = time.perf_counter() - t1
+
+    def predict2(cfgs):
+        X = torch.from_numpy(np.stack([features(c) for c in cfgs])).cuda()
+        return [from_target2(y) for y in mlp.forward(X).cpu().numpy()]
+
+    # 2. bootstrapped runs, started warm
+    t0 = time.perf_counter()
+    idx1 = list(range(n0, n0 + n1))
+    pred = predict2([sweep[i][0] for i in idx1])
+    runs = [(sweep[i][0], warm_state2(sweep[i][0], pred[k][0], pred[k][1], seed=seed + i)) for k, i in enumerate(idx1)]
+    gs = make_discharges(api, runs, procs, capacity_factor=6, n_floor=N)
+    h1, w1, en1 = run_windows(api, gs, boot_cycles, window, snapshots=5)
     for g in gs:
         g.close()
+    t_boot = time.perf_counter() - t0
+    ch1 = [converged_change(h1, k) for k in range(n1)]
+    kept1 = 0
+    for k in range(n1):
+        if ch1[k] < tol:
+            train_X.append(features(sweep[idx1[k]][0]))
+            train_Y.append(to_target2(h1[-1][k], en1[k]))
+            kept1 += 1
+    log(f"phase 2: {n1} warm runs x {boot_cycles} cycles in {t_boot:.0f} s; converged {kept1}; "
+        f"training set {len(train_X)}")
+    summary.update(phase2_s=t_boot, phase2_kept=kept1, n_train=len(train_X), phase2_changes=[float(v) for v in ch1])
+    checkpoint()
+    mlp.close()
+    mlp = api.MLP([4, 256, 256, 256, 3 * N_CELLS + 3 * BINS], seed=seed + 1)
+    t1 = time.perf_counter()
+    losses = train(api, mlp, np.stack(train_X), np.stack(train_Y), steps=train_steps)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    summary.update(train_s=t_train + t_train1, loss_first=losses[0], loss_last=losses[-1])
+    log(f"training: {train_steps} Adam steps x 2 in {t_train + t_train1:.1f} s, loss {losses[0]:.3g} -> {losses[-1]:.3g}")
+
+    # 3. held-out: warm (batched) and cold (batched == single), references from the cold runs
+    held = list(range(n0 + n1, total))
+    t1 = time.perf_counter()
+    pred = predict2([sweep[i][0] for i in held])
+    t_pred = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    wruns = [(sweep[i][0], warm_state2(sweep[i][0], pred[k][0], pred[k][1], seed=seed + 10000 + k))
+             for k, i in enumerate(held)]
+    gw = make_discharges(api, wruns, procs, capacity_factor=6, n_floor=N)
+    t_load = time.perf_counter() - t1
+    hw, ww, _ = run_windows(api, gw, eval_cycles, window)
+    for g in gw:
+        g.close()
+    cruns = [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + 20000 + k)) for k, i in enumerate(held)]
+    gc = make_discharges(api, cruns, procs, capacity_factor=6, n_floor=N)
+    hc, wc, _ = run_windows(api, gc, ref_cycles, window)
+    for g in gc:
+        g.close()
+    # 4. the plain cold start alone: seconds per RF cycle of a one-discharge graph
+    single = []
+    for k in range(min(3, n_held)):
+        i = held[k]
+        g = make_discharges(api, [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + 30000 + k))],
+                            procs, capacity_factor=6, n_floor=N)[0]
+        b = api.Batch([g], sweep[i][0]["steps_per_cycle"])
+        b.step(2)
+        b.synchronize()
+        ta = time.perf_counter()
+        b.step(20)
+        b.synchronize()
+        single.append((time.perf_counter() - ta) / 20)
+        b.close()
+        g.close()
+    s_cycle_single = float(np.median(single))
+    s_cycle_warm = ww[-1] / eval_cycles / len(held)      # per discharge, in the warm batch
+    overhead = (t_train + t_train1 + t_pred + t_load) / len(held)
     per = []
     for k, i in enumerate(held):
-        tol = max(0.1, 2.0 * noise[i])
-        ew = [max(profile_error(eh[w][2 * k], ref[i])) for w in range(len(eh))]
-        ec = [max(profile_error(eh[w][2 * k + 1], ref[i])) for w in range(len(eh))]
-        first = lambda e: next(((w + 1) * eval_window for w, v in enumerate(e) if v < tol), None)
-        per.append({"U": sweep[i][0]["U"], "p": sweep[i][0]["p"], "tol": tol, "warm_cycles": first(ew),
-                    "cold_cycles": first(ec), "warm_err": ew, "cold_err": ec, "pred_err": pred_err[k]})
-    done = [r for r in per if r["warm_cycles"] and r["cold_cycles"]]
-    ratio = [r["cold_cycles"] / r["warm_cycles"] for r in done]
-    summary = {"n_train": n_train, "n_held": n_held, "N": N, "cycles": cycles, "window": window,
-               "eval_cycles": eval_cycles, "eval_window": eval_window, "train_steps": train_steps,
-               "t_reference_s": t_ref, "t_train_s": t_train, "t_predict_s": t_pred, "t_eval_s": t_eval,
-               "loss_first": losses[0], "loss_last": losses[-1], "held_out": per,
-               "cycle_saving_median": float(np.median(ratio)) if ratio else None,
-               "converged_warm": sum(1 for r in per if r["warm_cycles"]),
-               "converged_cold": sum(1 for r in per if r["cold_cycles"])}
-    log(f"held-out: warm converged {summary['converged_warm']}/{n_held}, cold {summary['converged_cold']}/{n_held}, "
-        f"median cycle saving {summary['cycle_saving_median']}")
+        ref = 0.5 * (hc[-1][k] + hc[-2][k])
+        ref_change = max(binned_error(hc[-1][k], hc[-2][k]))
+        ew = [max(binned_error(hw[w][k], ref)) for w in range(len(hw))]
+        ec = [max(binned_error(hc[w][k], ref)) for w in range(len(hc) - 2)]
+        first = lambda e: next(((w + 1) * window for w, v in enumerate(e) if v < tol), None)
+        cw, cc = first(ew), first(ec)
+        rec = {"U": sweep[i][0]["U"], "p": sweep[i][0]["p"], "L": sweep[i][0]["L"], "C": sweep[i][0]["C_meta"],
+               "ref_change": ref_change, "pred_err": max(binned_error(pred[k][0], ref)), "warm_cycles": cw,
+               "cold_cycles": cc, "warm_err": ew, "cold_err": ec}
+        if cw and cc:
+            rec["wall_cold_single_s"] = cc * s_cycle_single
+            rec["wall_warm_batched_s"] = cw * s_cycle_warm + overhead
+            rec["wall_ratio"] = rec["wall_cold_single_s"] / rec["wall_warm_batched_s"]
+            rec["cycle_ratio"] = cc / cw
+        per.append(rec)
+    ok = [r for r in per if "wall_ratio" in r]
+    summary.update(held_out=per, s_cycle_single=s_cycle_single, s_cycle_warm_batched=s_cycle_warm,
+                   overhead_per_run_s=overhead, predict_s=t_pred, load_s=t_load,
+                   converged_warm=sum(1 for r in per if r["warm_cycles"]),
+                   converged_cold=sum(1 for r in per if r["cold_cycles"]),
+                   wall_ratio_median=float(np.median([r["wall_ratio"] for r in ok])) if ok else None,
+                   cycle_ratio_median=float(np.median([r["cycle_ratio"] for r in ok])) if ok else None,
+                   ref_change_median=float(np.median([r["ref_change"] for r in per])))
+    checkpoint()
+    log(f"held-out: warm converged {summary['converged_warm']}/{n_held}, cold {summary['converged_cold']}/{n_held}; "
+        f"median cycles cold/warm {summary['cycle_ratio_median']}, wall cold-single/warm-batched "
+        f"{summary['wall_ratio_median']}")
     mlp.close()
     return summary
 
@@ -220,19 +440,24 @@ def experiment(n_train=64, n_held=8, N=20000, cycles=1200, window=100, eval_cycl
 if __name__ == "__main__":
     import argparse
     import json
-    ap = argparse.ArgumentParser(description="learned warm start study")
-    ap.add_argument("--train", type=int, default=64)
-    ap.add_argument("--held", type=int, default=8)
-    ap.add_argument("--N", type=int, default=20000)
-    ap.add_argument("--cycles", type=int, default=1200)
-    ap.add_argument("--window", type=int, default=100)
-    ap.add_argument("--eval-cycles", type=int, default=600)
-    ap.add_argument("--eval-window", type=int, default=20)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--out", default=None)
+    ap = argparse.ArgumentParser(description="learned warm start study at the 2 % criterion")
+    ap.add_argument("--n0", type=int, default=48, help="cold reference runs (phase 1)")
+    ap.add_argument("--n1", type=int, default=96, help="warm bootstrapped runs (phase 2)")
+    ap.add_argument("--held", type=int, default=32, help="held-out discharges")
+    ap.add_argument("--N", type=int, default=100000, help="particles loaded per species (cold start)")
+    ap.add_argument("--cycles", type=int, default=4000, help="RF cycles of the cold runs")
+    ap.add_argument("--boot-cycles", type=int, default=1000)
+    ap.add_argument("--eval-cycles", type=int, default=1000, help="RF cycles of the warm held-out runs")
+    ap.add_argument("--window", type=int, default=200, help="RF cycles per averaging window")
+    ap.add_argument("--steps", type=int, default=6000, help="Adam steps per training")
+    ap.add_argument("--out", default=None, help="JSON summary (rewritten after every phase)")
     a = ap.parse_args()
-    s = experiment(a.train, a.held, a.N, a.cycles, a.window, a.eval_cycles, a.eval_window, a.steps,
-                   log=lambda m: print(m, flush=True))
-    if a.out:
-        with open(a.out, "w") as f:
-            json.dump(s, f, indent=1)
+
+    def save(summary):
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(summary, f, indent=1)
+
+    study2(n0=a.n0, n1=a.n1, n_held=a.held, N=a.N, ref_cycles=a.cycles, boot_cycles=a.boot_cycles,
+           eval_cycles=a.eval_cycles, window=a.window, train_steps=a.steps, log=lambda m: print(m, flush=True),
+           save=save)
