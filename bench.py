@@ -212,7 +212,16 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def run_cpu_oracle(cfg, counts, T, nsteps, threads, seed=0):
+def set_processes(obj, cfg, majorant):
+    """The oxygen process set on a library context or an oracle, with the
+    ions' majorant caps (majorant "capped") or nu_max over the whole grid
+    ("grid")."""
+    if majorant == "capped":
+        obj.set_majorant_cap(inputs.majorant_caps(cfg))
+    obj.set_processes(xsec.oxygen_set())
+
+
+def run_cpu_oracle(cfg, counts, T, nsteps, threads, majorant, seed=0):
     """The oracle on `threads` host threads on the first `nsteps` time steps
     of the workload with its full initial load; returns particle-steps/s,
     particle-steps, seconds and the threads used."""
@@ -221,7 +230,7 @@ def run_cpu_oracle(cfg, counts, T, nsteps, threads, seed=0):
     o = oracle.Oracle(cfg, 32)
     used = min(threads, o.set_threads(threads))
     o.set_threads(used)
-    o.set_processes(xsec.oxygen_set())
+    set_processes(o, cfg, majorant)
     for s, p in enumerate(st):
         o.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])
     del st
@@ -247,7 +256,7 @@ def bench_reference(args, world, rank):
     o = oracle.Oracle(cfg, 32)
     threads = o.set_threads(os.cpu_count() or 1)
     o.set_threads(threads)
-    o.set_processes(xsec.oxygen_set())
+    set_processes(o, cfg, args.majorant)
     for s, p in enumerate(st):
         o.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])
     del st
@@ -286,7 +295,7 @@ def bench_gpu(args, world, rank, local):
     # compaction check every 20 steps: a divisor of the RF cycle and of the
     # ion subcycle, so one RF cycle is one replay of the library's step graph
     g = api.Discharge(cfg, capacity(counts, wl), device=local, compact_check=20)
-    g.set_processes(xsec.oxygen_set())
+    set_processes(g, cfg, args.majorant)
     g.load_state(st)
     del st
     b = api.Batch([g], steps_per_launch=spc)
@@ -382,7 +391,8 @@ def bench_gpu(args, world, rank, local):
     launch_s = ms_e / n_e * 1e-3 if n_e else None
     achieved = per_launch * BYTES_PER_PARTICLE_STEP / launch_s / 1e9 if n_e else None
     traffic_pp, prof = profile_traffic()
-    roofline = {"bound": "hbm", "kernel": "k_push<e> (gather, push, absorb, free flights, deposit)",
+    roofline = {"bound": "hbm",
+                "kernel": "k_push<e> (gather, push, absorb, free flights, deposit, real collisions' kinematics)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs: copy bandwidth)",
@@ -404,8 +414,8 @@ def bench_gpu(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline:
         nsteps = CPU_SAMPLE_STEPS.get(wl, 10)
         allc = os.cpu_count() or 1
-        v, cps, cdt, used = run_cpu_oracle(cfg, counts, T, nsteps, allc)
-        v1, cps1, cdt1, _ = run_cpu_oracle(cfg, counts, T, nsteps, 1)
+        v, cps, cdt, used = run_cpu_oracle(cfg, counts, T, nsteps, allc, args.majorant)
+        v1, cps1, cdt1, _ = run_cpu_oracle(cfg, counts, T, nsteps, 1, args.majorant)
         cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
                "sample": f"first {nsteps} time steps of {wl} with the full {sum(counts):.3g}-particle load: "
                          f"{cps} particle-steps in {cdt:.2f} s on {used} threads",
@@ -418,6 +428,9 @@ def bench_gpu(args, world, rank, local):
                        "L_m": cfg["L"], "n_cells": cfg["n_cells"], "U_V": cfg["U"], "p_Pa": cfg["p"],
                        "C_meta": cfg["C_meta"], "ion_subcycle": cfg["ion_subcycle"],
                        "initial_particles": list(counts), "settle_cycles": settle,
+                       "majorant": args.majorant,
+                       "majorant_caps_eV": list(inputs.majorant_caps(cfg)) if args.majorant == "capped" else None,
+                       "warn_numax_timed": s1["warn_numax"] - s0["warn_numax"],
                        "live_at_timed_start": live0, "live_at_timed_end": live1,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": ("particle arrays (all species, x, vx, vy, vz, id, tc) exceed the 129 MB L2, no flush; "
@@ -441,13 +454,12 @@ def bench_batch(args, world, rank, local):
     from paper_0705_0497_gb300 import api
     torch.cuda.set_device(local)
     sweep = inputs.batch_sweep(64, seed=1000 * rank)
-    procs = xsec.oxygen_set()
     gs = []
     t_setup = time.perf_counter()
     for cfg, counts, T in sweep:
         cap = tuple(3 * n + (1 << 20) for n in counts)
         g = api.Discharge(cfg, cap, device=local, compact_check=20)
-        g.set_processes(procs)
+        set_processes(g, cfg, args.majorant)
         g.load_state(inputs.initial_state(cfg, counts, T))
         gs.append(g)
     t_setup = time.perf_counter() - t_setup
@@ -500,14 +512,14 @@ def bench_batch(args, world, rank, local):
     return 0
 
 
-def profile_steps(n):
+def profile_steps(n, majorant="capped"):
     """The workload stepped n single steps through the public API, nothing
     timed: a short, fixed launch sequence for ncu captures (with ion
     subcycling 10, the electron push of step 6 is launch 8 of k_push)."""
     from paper_0705_0497_gb300 import api, inputs, xsec
     cfg, counts, T, _ = inputs.workload(WORKLOAD)
     g = api.Discharge(cfg, tuple(int(c * 1.5) + 65536 for c in counts))
-    g.set_processes(xsec.oxygen_set())
+    set_processes(g, cfg, majorant)
     g.load_state(inputs.initial_state(cfg, counts, T))
     g.step(n)
     g.synchronize()
@@ -523,6 +535,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--majorant", default="capped", choices=["capped", "grid"],
+                    help="null-collision nu_max: ions capped at 2|U| + 50 eV (default) or the whole table grid")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "stress_2048", "parity_128", "batch_sweep_64"])
     ap.add_argument("--settle", type=int, default=-1,
                     help="RF cycles run before the warm-up (default: per workload, 100 for scale_512)")
@@ -530,7 +544,7 @@ def main():
                     help="only step the workload this many single steps (a fixed launch sequence for ncu) and exit")
     args = ap.parse_args()
     if args.profile_steps > 0:
-        return profile_steps(args.profile_steps)
+        return profile_steps(args.profile_steps, args.majorant)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

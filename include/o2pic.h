@@ -132,6 +132,7 @@ typedef struct {
     uint64_t recombined, rec_candidates;              /* (16): pairs removed, pairs tested */
     uint64_t edetached, edet_candidates;              /* (22): pairs reacted, pairs tested */
     uint64_t coulomb_pairs;                           /* (1)-(6): pairs scattered */
+    uint64_t warn_numax;     /* candidates whose total rate exceeded a capped nu_max */
 } o2pic_stats;
 
 /* Fills `cfg` with the defaults (parity-case geometry, T_gas = 300 K, O, O2
@@ -151,6 +152,18 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out);
  * processes per species, one NEUTRALIZE, one RECOMBINE, one EDETACH.
  * Errors: INVALID_ARG. */
 int o2pic_set_processes(o2pic_ctx* ctx, const o2pic_process* procs, int nproc);
+
+/* Majorant caps of the null-collision method (Sec. 2), per species in eV,
+ * taking effect at the next o2pic_set_processes: nu_max = the largest total
+ * rate nu(E_i) over the grid points up to the first one at or above the cap,
+ * instead of over the whole grid (NaN or +inf: the whole grid, the default).
+ * A cap is a bound on the energies the species reaches (for ions, the
+ * relative energy stays below the applied voltage's energy); a candidate
+ * whose total rate exceeds nu_max collides with probability 1 instead of
+ * nu(E) / nu_max and is counted in o2pic_stats.warn_numax, which is 0 when
+ * the cap holds.  `cap_eV` is a host array of O2PIC_NSPECIES doubles, read
+ * during the call.  Errors: INVALID_ARG (a cap that is not positive). */
+int o2pic_set_majorant_cap(o2pic_ctx* ctx, const double* cap_eV);
 
 /* Coulomb elastic collisions (1)-(6) of Table 1: e-e, O- - O-, O2+ - O2+,
  * e - O2+, e - O-, O- - O2+; bit r-1 of `mask` enables reaction r (0 = off,

@@ -37,7 +37,7 @@ COUNTER_NAMES = ([f"events_{s}_{k}" for s in range(NSP) for k in range(MAXPROC)]
                  [f"absorbed_{s}_{w}" for s in range(NSP) for w in range(2)] +
                  [f"born_{s}" for s in range(NSP)] +
                  ["neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries",
-                  "warn_pair_gt1", "id_overflow", "recombined", "rec_candidates", "edetached", "edet_candidates", "coulomb_pairs"])
+                  "warn_pair_gt1", "id_overflow", "recombined", "rec_candidates", "edetached", "edet_candidates", "coulomb_pairs", "warn_numax"])
 
 
 def lib():
@@ -54,6 +54,7 @@ def lib():
         L.oracle_load.argtypes = [vp, i32, vp, vp, vp, vp, vp, u64]
         L.oracle_set_next_id.argtypes = [vp, i32, u32]
         L.oracle_set_coulomb.argtypes = [vp, u32, dbl]
+        L.oracle_set_majorant_cap.argtypes = [vp, vp]
         L.oracle_set_threads.argtypes = [vp, i32]
         L.oracle_set_threads.restype = i32
         L.oracle_step.argtypes = [vp, u64]
@@ -110,6 +111,14 @@ def _cfg_struct(cfg):
 
 class Oracle:
     """One discharge in the oracle.  precision = 32 (FP32 mirror) or 64."""
+
+    def set_majorant_cap(self, caps):
+        """Majorant caps in eV per species (None: the whole grid), taking
+        effect at the next set_processes: nu_max = the largest total rate over
+        the grid points up to the first one at or above the cap."""
+        c = np.array([np.nan if v is None else float(v) for v in caps], np.float64)
+        if lib().oracle_set_majorant_cap(self.h, _ptr(c)) != 0:
+            raise ValueError("majorant cap must be positive")
 
     def set_coulomb(self, mask, ln_lambda=10.0):
         """Coulomb collisions (1)-(6): bit r-1 of mask enables reaction r."""

@@ -306,6 +306,7 @@ struct Counters {
     uint64_t edetached;            // pairs reacted by (22)
     uint64_t edet_candidates;      // pairs tested by (22)
     uint64_t coulomb_pairs;        // pairs scattered by (1)-(6)
+    uint64_t warn_numax;           // candidates whose total rate exceeds nu_max (capped majorant)
 };
 
 template <class R> struct Oracle {
@@ -330,6 +331,10 @@ template <class R> struct Oracle {
     int64_t jacc[NSP] = {0, 0, 0};
     R numax[NSP], Pmax[NSP];
     double numax64[NSP];
+    // majorant cap: nu_max of species s is the maximum of the total rate over
+    // the grid points up to the first one at or above ecap[s] (eV); +inf =
+    // the whole grid (the plain null-collision majorant)
+    double ecap[NSP];
     // free flights: species s is pushed every sub[s] steps (1 for electrons,
     // the ion subcycle for ions); inv_lnq = 1 / ln(1 - P_max) = -1 / (nu_max
     // dt_s); a gap is capped at kcap pushes (2^30 steps ahead, beyond any run)
@@ -381,7 +386,7 @@ template <class R> struct Oracle {
             a_m[s] = (R)(mass[s] / (mass[s] + cfg.M_gas));
             a_M[s] = (R)(cfg.M_gas / (mass[s] + cfg.M_gas));
             sig_birth[s] = (R)std::sqrt(KB * cfg.T_gas / mass[s]);
-            numax[s] = 0; Pmax[s] = 0; numax64[s] = 0;
+            numax[s] = 0; Pmax[s] = 0; numax64[s] = 0; ecap[s] = INFINITY;
             sub[s] = (s == SP_E) ? 1u : (uint32_t)cfg.ion_subcycle;
             inv_lnq[s] = (R)(-INFINITY);
             kcap[s] = (R)std::floor(1073741824.0 / (double)sub[s]);
@@ -444,6 +449,7 @@ template <class R> struct Oracle {
             nu64[s].assign((size_t)NGRID * std::max(np, 1), 0.0);
             double mu = (s == SP_E) ? mass[s] : mass[s] * cfg.M_gas / (mass[s] + cfg.M_gas);
             double mx = 0.0;
+            bool capped = false;      // past the first grid point at or above the cap
             for (int i = 0; i < NGRID; ++i) {
                 double Ei = grid_energy(i);
                 double g = std::sqrt(2.0 * QE * Ei / mu);
@@ -456,7 +462,8 @@ template <class R> struct Oracle {
                     acc += nu;
                     cum[s][(size_t)i * np + k] = (R)acc;
                 }
-                mx = std::max(mx, acc);
+                if (!capped) mx = std::max(mx, acc);
+                if (Ei >= ecap[s]) capped = true;
             }
             numax64[s] = mx;
             numax[s] = (R)mx;
@@ -700,7 +707,9 @@ template <class R> struct Oracle {
         // first k with u1 nu_max < sum_{i<=k} nu_i(E) (the last process if
         // rounding leaves none below it)
         R target = u1 * numax[s];
-        if (!(target < cum_at(s, np - 1, i, w))) return true;   // null collision
+        const R total = cum_at(s, np - 1, i, w);
+        if (total > numax[s]) cnt.warn_numax += 1;   // above a capped majorant
+        if (!(target < total)) return true;   // null collision
         int k = np - 1;
         for (int kk = 0; kk < np - 1; ++kk) {
             if (target < cum_at(s, kk, i, w)) { k = kk; break; }
@@ -1136,6 +1145,17 @@ int oracle_set_processes(void* p, const oracle_process* procs, int n) {
     Handle* h = (Handle*)p; int rc = 0;
     DISPATCH(h, rc = O.set_processes(procs, n));
     return rc;
+}
+
+// Majorant caps (eV) per species, taking effect at the next
+// oracle_set_processes: nu_max = the largest total rate over the grid points
+// up to the first one at or above the cap (+inf or NaN: the whole grid).
+// Returns -1 for a cap that is not positive.
+int oracle_set_majorant_cap(void* p, const double* cap) {
+    Handle* h = (Handle*)p;
+    for (int s = 0; s < NSP; ++s) if (!(cap[s] > 0) && !std::isnan(cap[s])) return -1;
+    DISPATCH(h, for (int s = 0; s < NSP; ++s) O.ecap[s] = std::isnan(cap[s]) ? INFINITY : cap[s]);
+    return 0;
 }
 
 int oracle_load(void* p, int s, const float* x, const float* vx, const float* vy, const float* vz,

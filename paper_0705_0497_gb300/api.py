@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
                 ("error_flags", ctypes.c_uint64), ("particle_steps_species", ctypes.c_uint64 * NSP),
                 ("recombined", ctypes.c_uint64), ("rec_candidates", ctypes.c_uint64),
                 ("edetached", ctypes.c_uint64), ("edet_candidates", ctypes.c_uint64),
-                ("coulomb_pairs", ctypes.c_uint64)]
+                ("coulomb_pairs", ctypes.c_uint64), ("warn_numax", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {}
@@ -79,7 +79,7 @@ class Stats(ctypes.Structure):
             d[f"particle_steps_{s}"] = int(self.particle_steps_species[s])
         for n in ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
                   "id_overflow", "step", "error_flags", "recombined", "rec_candidates", "edetached",
-                  "edet_candidates", "coulomb_pairs"):
+                  "edet_candidates", "coulomb_pairs", "warn_numax"):
             d[n] = int(getattr(self, n))
         return d
 
@@ -97,6 +97,7 @@ SIGNATURES = [
     ("o2pic_set_next_id", _i32, [_vp, _i32, _u32]),
     ("o2pic_load_flight", _i32, [_vp, _i32, _vp, _u64, _i32, _vp]),
     ("o2pic_set_coulomb", _i32, [_vp, _u32, ctypes.c_double]),
+    ("o2pic_set_majorant_cap", _i32, [_vp, _vp]),
     ("o2pic_read_flight", _i32, [_vp, _i32, _vp, _u64, _P(_u64), _i32]),
     ("o2pic_step", _i32, [_vp, _u64, _vp]),
     ("o2pic_synchronize", _i32, [_vp]),
@@ -344,6 +345,12 @@ class Discharge:
         st = Stats()
         _check(lib().o2pic_get_stats(self.h, ctypes.byref(st)), "o2pic_get_stats")
         return st.as_dict()
+
+    def set_majorant_cap(self, caps):
+        """Majorant caps in eV per species (None: the whole grid), taking
+        effect at the next set_processes (o2pic_set_majorant_cap)."""
+        c = np.array([np.nan if v is None else float(v) for v in caps], np.float64)
+        _check(lib().o2pic_set_majorant_cap(self.h, c.ctypes.data), "o2pic_set_majorant_cap")
 
     def set_coulomb(self, mask, ln_lambda=10.0):
         """Coulomb collisions (1)-(6): bit r-1 of mask enables reaction r."""

@@ -89,6 +89,7 @@ struct DevCounters {
     unsigned long long recombined, rec_candidates;
     unsigned long long edetached, edet_candidates;
     unsigned long long coulomb_pairs;
+    unsigned long long warn_numax;
 };
 
 // Births appended by one kernel into species d: births of the electron
@@ -145,6 +146,7 @@ struct Params {
     float inv_lnq[NSP], kcap[NSP];
     unsigned sub[NSP];
     int births_possible[NSP];
+    int cum_smem[NSP];           // particle kernel stages the cumulative table in shared memory
     // (17)
     const float* Ktab;           // [NGRID] sigma_n g
     float Kmax_hi;               // max(Ktab) inflated so the prefilter bounds every interpolant
@@ -263,6 +265,9 @@ void launch_cand(int species, const Params& P, int grid, cudaStream_t s);   // i
 // true when the ion filter and kinematics run inside the ion particle kernels
 // (then the filter and kinematics kernels are not launched)
 bool ions_fused();
+// true when the particle kernel may stage the cumulative rate table in shared
+// memory (it does when the table keeps its resident blocks per SM)
+bool cum_smem_allowed();
 void launch_filter(int species, const Params& P, int grid, cudaStream_t s);
 void launch_filter_batched(int species, const Params* all, const uint4* map, int nblocks, cudaStream_t s);
 void launch_pair_hist(const Params& P, const PairSpec& S, int grid, cudaStream_t s);

@@ -56,6 +56,24 @@
 #ifndef O2PIC_FUSE_IONS
 #define O2PIC_FUSE_IONS 0
 #endif
+// Deposit: one 64-bit shared-memory atomic per particle (0), or lanes of a
+// warp that hit the same cell first summed over __match_any_sync peers and
+// added by one lane (1).  Integers: both give the same charge.  The
+// aggregated form was far slower on the 512-cell discharge (76.7 against
+// 46.3 ms per RF cycle): the lanes of a warp rarely share a cell, and the
+// match and the shuffles cost more than the atomics they save.
+#ifndef O2PIC_DEPOSIT_AGG
+#define O2PIC_DEPOSIT_AGG 0
+#endif
+// The particle kernel that runs the kinematics stages the species' cumulative
+// rate table in shared memory when that keeps its resident blocks per SM (1),
+// or reads it from global memory through L1 (0).  Both give the same results;
+// on the 512-cell, 1.6e7-particle discharge at its periodic state the global
+// table was faster (46.3 against 47.5 ms per RF cycle): every block copies
+// the electrons' 34 KB table each step, and the kinematics read a few rows.
+#ifndef O2PIC_CUM_SMEM
+#define O2PIC_CUM_SMEM 0
+#endif
 #ifndef O2PIC_PUSH_UNROLL
 #define O2PIC_PUSH_UNROLL 4
 #endif
@@ -255,13 +273,15 @@ __device__ __forceinline__ void flush_hist(unsigned* hist, unsigned long long* Q
 // rate on the table grid (column `tot` = the last cumulative column) and the
 // comparison with u1 nu_max.
 __device__ __forceinline__ bool electron_is_real(const Params& P, const float* tot, uint32_t w1, float vx, float vy,
-                                                 float vz, unsigned& wemax) {
+                                                 float vz, unsigned& wemax, unsigned& wnumax) {
     const float u1 = uniform(w1);
     const float E = P.kappa[SP_E] * dot3(vx, vy, vz, vx, vy, vz);
     int i; float w; bool above;
     grid_locate(E, i, w, above);
     if (above) ++wemax;
-    return (u1 * P.numax[SP_E]) < grid_interp(tot, 1, 0, i, w);
+    const float total = grid_interp(tot, 1, 0, i, w);
+    if (total > P.numax[SP_E]) ++wnumax;   // above a capped majorant
+    return (u1 * P.numax[SP_E]) < total;
 }
 
 // Filter of an ion candidate: the target sampled from the gas Maxwellian
@@ -271,7 +291,7 @@ __device__ __forceinline__ bool electron_is_real(const Params& P, const float* t
 template <int S>
 __device__ __forceinline__ bool ion_is_real(const Params& P, const float* tot, unsigned long long step, uint32_t id,
                                             uint4 w, float vx, float vy, float vz, unsigned& wtries,
-                                            unsigned& wemax) {
+                                            unsigned& wemax, unsigned& wnumax) {
     Stream st;
     st.resume(id, P.seed, step, SpeciesTraits<S>::tag, w, 1);
     const float u1 = uniform(st.next());
@@ -282,7 +302,9 @@ __device__ __forceinline__ bool ion_is_real(const Params& P, const float* tot, u
     int i; float wt; bool above;
     grid_locate(E, i, wt, above);
     if (above) ++wemax;
-    return (u1 * P.numax[S]) < grid_interp(tot, 1, 0, i, wt);
+    const float total = grid_interp(tot, 1, 0, i, wt);
+    if (total > P.numax[S]) ++wnumax;   // above a capped majorant
+    return (u1 * P.numax[S]) < total;
 }
 
 // Total-rate column (the last cumulative column) of species S into shared memory.
@@ -300,19 +322,20 @@ __device__ __forceinline__ void stage_total(const Params& P, int S, float* tot) 
 // Electron records carry the particle (slot, id, x, v) and block 0 of its
 // Philox stream is drawn again; ion records carry the slot, id, v and that
 // block (its first word, the candidate draw, is spent), x is read from the
-// array.  A removed particle's charge comes off the block's histogram when
+// array.  `cum` is the species' cumulative rate table (global or shared
+// memory).  A removed particle's charge comes off the block's histogram when
 // `hist` is given (the particle kernel: the particle was deposited there),
 // else off the step's deposit in global memory.  Births are ranked with
 // ballots within the segment and staged at the particle warp's slot range;
 // nb1, nb2 count them.
 template <int S, int SEGW>
-__device__ __forceinline__ void collide_list(const Params& P, const PhiloxPre& pre, unsigned long long step,
+__device__ __forceinline__ void collide_list(const Params& P, const float* cum, const PhiloxPre& pre,
+                                             unsigned long long step,
                                              unsigned r0, unsigned n, unsigned nmax, unsigned sl,
                                              unsigned seg_mask, unsigned lt_mask, unsigned* events,
                                              unsigned long long* hist, unsigned& nb1, unsigned& nb2,
                                              unsigned& nremoved, unsigned& wtries, unsigned& wemax) {
     const int np = P.nproc[S];
-    const float* __restrict__ cum = P.cum[S];
     const unsigned cb = P.ctrl->cur[S];
     float* __restrict__ X = P.sp[S].x[cb];
     float* __restrict__ VX = P.sp[S].vx[cb];
@@ -412,7 +435,10 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
         reinterpret_cast<unsigned long long*>(smem + align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng));
     PushQueue& Q = *reinterpret_cast<PushQueue*>(hist + P.Ng);
     float* Tt = reinterpret_cast<float*>(&Q + 1);        // total-rate column (filter in the kernel)
+    float* Ct = Tt + NGRID;                              // cumulative table (if staged)
     constexpr bool fused = (S == SP_E) || (O2PIC_FUSE_IONS != 0);
+    const bool cum_staged = fused && P.cum_smem[S] != 0;
+    const float* cum = cum_staged ? Ct : P.cum[S];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     unsigned* qs = Q.slot[warp];
@@ -439,6 +465,10 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
 
     for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0ull; }
     if (fused) stage_total(P, S, Tt);
+    if (cum_staged) {
+        const float* __restrict__ g = P.cum[S];
+        for (int j = tid; j < NGRID * np; j += BLOCK) Ct[j] = g[j];
+    }
     if (tid == 0) {
         sh.absorbed[0] = sh.absorbed[1] = 0u; sh.removed = 0u; sh.psteps = 0u; sh.nonfinite = 0u; sh.wtries = 0u;
         sh.jsum = 0ull;
@@ -453,7 +483,7 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
     const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
 
-    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0, wemax = 0, wtries = 0;
+    unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0, wemax = 0, wtries = 0, wnumax = 0;
     long long jacc = 0;   // conduction current: sum of trunc(256 v_x^{n+1/2}) (exact)
     unsigned nrec = 0;    // warp-uniform: records of this warp so far
     unsigned qn = 0;      // warp-uniform: queued candidates
@@ -477,8 +507,8 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
         if (has) {
             w = philox_id(pre, id);
             TC[slot] = step_lo + sub * (1u + flight_gap(w.x, inv_lnq, kcap));
-            if (S == SP_E) rec = electron_is_real(P, Tt, w.y, cvx, cvy, cvz, wemax);
-            else rec = !fused || ion_is_real<S>(P, Tt, step, id, w, cvx, cvy, cvz, wtries, wemax);
+            if (S == SP_E) rec = electron_is_real(P, Tt, w.y, cvx, cvy, cvz, wemax, wnumax);
+            else rec = !fused || ion_is_real<S>(P, Tt, step, id, w, cvx, cvy, cvz, wtries, wemax, wnumax);
         }
         const unsigned cm = __ballot_sync(0xffffffffu, rec);
         if (rec) {
@@ -511,6 +541,8 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
             const unsigned i = g0 + 32u * k + lane;
             float x = xs[k], vx = vxs[k];
             bool cand = false;
+            int dcell = -1;                  // cell deposited into (-1: none)
+            unsigned long long dval = 0ull;
             if (!is_dead(x)) {
                 int j; float frac;
                 cell_of(x, inv_dx, Nc, j, frac);
@@ -527,12 +559,22 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
                     // 2^16 count_c - rsum_c, node c+1 gets rsum_c
                     int j2; float f2;
                     cell_of(x, inv_dx, Nc, j2, f2);
-                    atomicAdd(&hist[j2], (1ull << 40) + (unsigned long long)cic_r(f2));
+                    dcell = j2;
+                    dval = (1ull << 40) + (unsigned long long)cic_r(f2);
+                    if (!O2PIC_DEPOSIT_AGG) atomicAdd(&hist[j2], dval);
                     // its free flight ends at this step: a collision candidate
                     cand = (np > 0) && (tcs[k] == step_lo);
                 }
                 X[i] = x;
                 VX[i] = vx;
+            }
+            if (O2PIC_DEPOSIT_AGG) {
+                // the lanes of one cell add their values (peer by peer, in
+                // lane order) and the lowest of them adds the sum
+                const unsigned peers = __match_any_sync(0xffffffffu, dcell);
+                unsigned long long sum = 0ull;
+                for (unsigned m = peers; m; m &= m - 1u) sum += __shfl_sync(peers, dval, __ffs(m) - 1);
+                if (dcell >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[dcell], sum);
             }
             const unsigned cm = __ballot_sync(0xffffffffu, cand);
             if (cand) {
@@ -565,7 +607,7 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
         // counted the warnings of the part it shares with the kinematics.
         __syncwarp();
         unsigned nb1 = 0, nb2 = 0, wt2 = 0, we2 = 0;
-        collide_list<S, 32>(P, pre, step, r0, nrec, nrec, (unsigned)lane, 0xffffffffu, lt_mask, sh.events, hist,
+        collide_list<S, 32>(P, cum, pre, step, r0, nrec, nrec, (unsigned)lane, 0xffffffffu, lt_mask, sh.events, hist,
                             nb1, nb2, nrm, wt2, we2);
         wtries += wt2;
         if (P.births_possible[S] && lane == 0) {
@@ -590,6 +632,7 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     if (nnf) atomicAdd(&sh.nonfinite, nnf);
     if (wtries) atomicAdd(&sh.wtries, wtries);
     if (wemax) atomicAdd(&C->cnt.warn_emax, (unsigned long long)wemax);
+    if (wnumax) atomicAdd(&C->cnt.warn_numax, (unsigned long long)wnumax);
     __syncthreads();
     if (fused && tid < np && sh.events[tid]) atomicAdd(&C->cnt.events[S][tid], (unsigned long long)sh.events[tid]);
     unsigned long long* __restrict__ Qcopy = P.Qf[S] + (size_t)(blk & (QCOPIES - 1)) * Ng;
@@ -665,7 +708,7 @@ __device__ __forceinline__ void filter_body(const Params& P, unsigned blk, unsig
     const unsigned W = P.push_warps[S];
     const unsigned R = warp_range_len(nslots, W);
     const float numax = P.numax[S], kap = P.kappa[S], sig = P.sig_gas;
-    unsigned wtries = 0, wemax = 0;
+    unsigned wtries = 0, wemax = 0, wnumax = 0;
     for (unsigned gw = blk * WARPS + warp; gw < W; gw += nblk * WARPS) {
         const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
         const unsigned n = P.ccount[S][gw];
@@ -696,7 +739,9 @@ __device__ __forceinline__ void filter_body(const Params& P, unsigned blk, unsig
                     int i; float w; bool above;
                     grid_locate(E, i, w, above);
                     if (above) ++wemax;
-                    real = (u1 * numax) < grid_interp(tot, 1, 0, i, w);
+                    const float total = grid_interp(tot, 1, 0, i, w);
+                    if (total > numax) ++wnumax;   // above a capped majorant
+                    real = (u1 * numax) < total;
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, real);
                 if (real) {
@@ -712,6 +757,7 @@ __device__ __forceinline__ void filter_body(const Params& P, unsigned blk, unsig
     pdl_trigger();
     if (wtries) atomicAdd(&sh_wtries, wtries);
     if (wemax) atomicAdd(&sh_wemax, wemax);
+    if (wnumax) atomicAdd(&C->cnt.warn_numax, (unsigned long long)wnumax);
     __syncthreads();
     if (tid == 0) {
         if (sh_wtries) atomicAdd(&C->cnt.warn_tries, (unsigned long long)sh_wtries);
@@ -760,7 +806,7 @@ __device__ __forceinline__ void cand_body(const Params& P, unsigned blk, unsigne
         const unsigned n = valid ? P.ccount[S][gw] : 0u;
         const unsigned nmax = max(n, __shfl_xor_sync(0xffffffffu, n, SEG));
         unsigned nb1 = 0, nb2 = 0;   // half-warp-uniform
-        collide_list<S, SEG>(P, pre, step, r0, n, nmax, sl, seg_mask, lt_mask, events, nullptr, nb1, nb2,
+        collide_list<S, SEG>(P, P.cum[S], pre, step, r0, n, nmax, sl, seg_mask, lt_mask, events, nullptr, nb1, nb2,
                              nremoved, wtries, wemax);
         if (births && valid && sl == 0) {
             if (cnt1) cnt1[gw] = nb1;
@@ -878,10 +924,14 @@ __global__ void __launch_bounds__(BLOCK) k_deposit(Params P) {
 size_t push_smem_bytes(int species, const Params& P) {
     const size_t base = align16(align16(sizeof(PushShared)) + sizeof(float) * P.Ng) +
                         sizeof(unsigned long long) * P.Ng + sizeof(PushQueue);
-    return (species == SP_E || O2PIC_FUSE_IONS) ? base + sizeof(float) * NGRID : base;
+    if (!(species == SP_E || O2PIC_FUSE_IONS)) return base;
+    const size_t table = P.cum_smem[species] ? sizeof(float) * NGRID * (size_t)P.nproc[species] : 0;
+    return base + sizeof(float) * NGRID + table;
 }
 
 bool ions_fused() { return O2PIC_FUSE_IONS != 0; }
+
+bool cum_smem_allowed() { return O2PIC_CUM_SMEM != 0; }
 
 void launch_flight_init(int species, const Params& P, cudaStream_t s) {
     const unsigned long long cap = P.sp[species].cap;

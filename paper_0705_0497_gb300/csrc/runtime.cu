@@ -91,6 +91,7 @@ struct o2pic_ctx {
     bool have_tables = false;
     bool loaded[NSP] = {false, false, false};
     bool flight_ok[NSP] = {false, false, false};   // free flights known (else drawn by prepare)
+    double ecap[NSP] = {INFINITY, INFINITY, INFINITY};   // majorant caps (eV) of the next set_processes
     bool coul_alloc = false;                       // Coulomb cell-sort buffers allocated
     int latched = 0;
     int grid_push[NSP] = {0, 0, 0};
@@ -512,13 +513,14 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     size_t smax = 0;
     for (int s = 0; s < NSP; ++s) {
         P.nproc[s] = MAXPROC;
+        P.cum_smem[s] = 1;
         smax = std::max(smax, push_smem_bytes(s, P));
     }
     smax = std::max(smax, sizeof(unsigned) * (size_t)Ng);
     TRY(configure_push_smem(smax));
     TRY(configure_field_smem(field_smem_bytes(P)));
     TRY(configure_pair_hist_smem(Nc));
-    for (int s = 0; s < NSP; ++s) P.nproc[s] = 0;
+    for (int s = 0; s < NSP; ++s) { P.nproc[s] = 0; P.cum_smem[s] = 0; }
     c->grid_pair = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(tiles_ion, 8ull * c->num_sms));
     c->grid_pair_e = (int)std::max<unsigned long long>(
         1, std::min<unsigned long long>(ceil_div(cfg->capacity[SP_E], TILE) + 1, 8ull * c->num_sms));
@@ -595,7 +597,11 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
         const int np = (int)sp[s].size();
         std::vector<float> cum((size_t)NGRID * std::max(np, 1), 0.0f);
         const double mu = (s == SP_E) ? mass[s] : mass[s] * g.M_gas / (mass[s] + g.M_gas);
+        // nu_max over the grid points up to the first one at or above the
+        // species' majorant cap (the whole grid without one): the linear
+        // interpolant below the cap stays below it
         double mx = 0.0;
+        bool capped = false;
         for (int i = 0; i < NGRID; ++i) {
             const double Ei = grid_energy(i);
             const double gv = std::sqrt(2.0 * QE * Ei / mu);
@@ -607,7 +613,8 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
                 acc += nu;
                 cum[(size_t)i * np + k] = (float)acc;
             }
-            mx = std::max(mx, acc);
+            if (!capped) mx = std::max(mx, acc);
+            if (Ei >= c->ecap[s]) capped = true;
         }
         const double dts = g.dt * (s == SP_E ? 1.0 : (double)g.ion_subcycle);
         P.nproc[s] = np;
@@ -681,8 +688,15 @@ int o2pic_set_processes(o2pic_ctx* c, const o2pic_process* procs, int nproc) {
     if (e != cudaSuccess) return cuda_fail(c, e);
     for (int s = 0; s < NSP; ++s) {
         int bps = 0;
+        P.cum_smem[s] = 0;
         if (push_occupancy(s, P, &bps) || bps < 1) bps = 1;
         if (bps > MAX_PUSH_BLOCKS_PER_SM) bps = MAX_PUSH_BLOCKS_PER_SM;
+        // the kinematics' table in shared memory when the blocks per SM stay
+        if (cum_smem_allowed() && P.nproc[s] > 0 && (s == SP_E || ions_fused())) {
+            int b2 = 0;
+            P.cum_smem[s] = 1;
+            if (push_occupancy(s, P, &b2) || std::min(b2, MAX_PUSH_BLOCKS_PER_SM) < bps) P.cum_smem[s] = 0;
+        }
         c->grid_push[s] = std::max(bps * c->num_sms, min_push_blocks(P.sp[s].cap));
         P.push_warps[s] = (unsigned)c->grid_push[s] * (BLOCK / 32);
     }
@@ -851,6 +865,14 @@ int o2pic_read_particles(o2pic_ctx* c, int species, float* x, float* vx, float* 
     for (void* q : tmp) cudaFree(q);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return check_flags(c);
+}
+
+int o2pic_set_majorant_cap(o2pic_ctx* c, const double* cap_eV) {
+    if (!c || !cap_eV) return O2PIC_E_INVALID_ARG;
+    for (int s = 0; s < NSP; ++s)
+        if (!(cap_eV[s] > 0) && !std::isnan(cap_eV[s])) return O2PIC_E_INVALID_ARG;
+    for (int s = 0; s < NSP; ++s) c->ecap[s] = std::isnan(cap_eV[s]) ? INFINITY : cap_eV[s];
+    return O2PIC_OK;
 }
 
 int o2pic_set_coulomb(o2pic_ctx* c, uint32_t mask, double ln_lambda) {
@@ -1079,6 +1101,7 @@ int o2pic_get_stats(o2pic_ctx* c, o2pic_stats* out) {
     out->edetached = h.cnt.edetached;
     out->edet_candidates = h.cnt.edet_candidates;
     out->coulomb_pairs = h.cnt.coulomb_pairs;
+    out->warn_numax = h.cnt.warn_numax;
     out->step = h.step;
     out->error_flags = h.error_flags;
     return rc;

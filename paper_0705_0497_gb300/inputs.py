@@ -97,6 +97,18 @@ def batch_sweep(n=64, seed=0, scale=1.0, count_range=(1.0e5, 2.0e6)):
     return out
 
 
+def majorant_caps(cfg):
+    """Majorant caps (eV) of the null-collision method per species (see
+    o2pic_set_majorant_cap): none for the electrons; 2 |U| + 50 eV for the
+    ions.  An ion's energy relative to a gas molecule stays below e times the
+    largest potential difference in the gap (|U| plus the plasma potential,
+    a few electron temperatures above the highest electrode) plus its thermal
+    energy, so the cap is twice that bound; a candidate above it would be
+    counted (warn_numax)."""
+    cap = 2.0 * abs(float(cfg["U"])) + 50.0
+    return (None, cap, cap)
+
+
 def species_mass(cfg, s):
     return (cfg["m_e"], cfg["m_OM"], cfg["m_OP"])[s]
 

@@ -213,11 +213,12 @@ def warm_state2(cfg, cells, energy, seed, T_floor=(0.05, 0.026, 0.026)):
     return out
 
 
-def run_windows(api, gs, cycles, window, steps_per_launch=200, tune=True, snapshots=0):
+def run_windows(api, gs, cycles, window, steps_per_launch=200, tune=True, snapshots=0, live=None):
     """Advance the discharges together; per `window` cycles the cycle-averaged
     cell densities of each, the wall time at the end of each window, and (if
     snapshots) the mean-energy profiles averaged over that many snapshots in
-    the last window."""
+    the last window; `live` (a list), if given, gets the live particle counts
+    of each discharge at the end of each window."""
     import time
     spc = gs[0].cfg["steps_per_cycle"]
     per_cycle = spc // steps_per_launch
@@ -248,18 +249,67 @@ def run_windows(api, gs, cycles, window, steps_per_launch=200, tune=True, snapsh
         b.synchronize()
         walls.append(time.perf_counter() - t0)
         hist.append([cell_profiles(g.moments()[0]) for g in gs])
+        if live is not None:
+            live.append([[g.count(sp) for sp in range(3)] for g in gs])
     b.close()
     return hist, walls, en
 
 
+def study_sweep(total, N, seed, p_range=(5.0, 50.0), C_range=(0.05, 1.0 / 6.0), U_range=(100.0, 500.0)):
+    """Discharges with U uniform on U_range, p log-uniform on p_range, L
+    uniform on [2, 3] cm and C uniform on C_range, N particles per species
+    loaded at 1e15 m^-3 (the batched sweep's other settings)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sweep = inputs.batch_sweep(total, seed=seed, count_range=(N, N))
+    for cfg, counts, _ in sweep:
+        cfg["U"] = float(rng.uniform(*U_range))
+        cfg["L"] = float(rng.uniform(0.02, 0.03))
+        cfg["C_meta"] = float(rng.uniform(*C_range))
+        cfg["p"] = float(math.exp(rng.uniform(math.log(p_range[0]), math.log(p_range[1]))))
+        cfg["weight"] = 1.0e15 * cfg["L"] / N
+        cfg["dt"] = 1.0 / (cfg["f"] * cfg["steps_per_cycle"])
+    return sweep
+
+
+def cold_survey(api, sweep, idx, N, cycles, window, seed, capacity_factor=20, log=print):
+    """Cold runs of the discharges sweep[idx] for `cycles` RF cycles: per
+    window the binned density profiles [windows][runs][3][BINS] and live
+    counts, the change between the last two windows, and the training
+    targets (log densities of the mean of the last two windows, log mean
+    energies from snapshots of the last one)."""
+    import time
+    from . import xsec
+    T = (3.0, 0.026, 0.026)
+    t0 = time.perf_counter()
+    runs = [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + i)) for i in idx]
+    gs = make_discharges(api, runs, xsec.oxygen_set(), capacity_factor=capacity_factor, n_floor=N)
+    live = []
+    h, _, en = run_windows(api, gs, cycles, window, snapshots=5, live=live)
+    for g in gs:
+        g.close()
+    sec = time.perf_counter() - t0
+    n = len(idx)
+    ref = [0.5 * (h[-1][k] + h[-2][k]) for k in range(n)]
+    out = {"idx": np.array(idx), "seconds": sec,
+           "X": np.stack([features(sweep[i][0]) for i in idx]),
+           "Y": np.stack([to_target2(ref[k], en[k]) for k in range(n)]),
+           "binned": np.array([[binned(h[w][k]) for k in range(n)] for w in range(len(h))]),
+           "live": np.array(live), "change": np.array([max(binned_error(h[-1][k], h[-2][k])) for k in range(n)])}
+    log(f"cold survey: {n} runs x {cycles} cycles in {sec:.0f} s; last-window change median "
+        f"{np.median(out['change']):.4f}, below 0.02: {int((out['change'] < 0.02).sum())}")
+    return out
+
+
 def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000, eval_cycles=1000, window=200,
-           tol=0.02, train_steps=6000, seed=4242, log=print, save=None):
+           tol=0.02, train_steps=6000, seed=4242, p_range=(5.0, 50.0), C_range=(0.05, 1.0 / 6.0),
+           U_range=(100.0, 500.0), capacity_factor=20, phase1=None, log=print, save=None):
     """The warm-start study at the 2 % criterion.
 
-    1. n0 discharges of the sweep's (U, p, L, C) ranges started cold run
-       ref_cycles; their last window (average of `window` cycles) is the
-       reference, kept if its change from the window before is below tol/2
-       (converged), with mean-energy profiles from snapshots.
+    1. n0 discharges of the sweep (`study_sweep`) started cold run ref_cycles
+       (`cold_survey`; or its saved result `phase1`, a dict of arrays); the
+       mean of the last two windows (`window` cycles each) is the reference,
+       kept for training if the change between the two is below tol, with
+       mean-energy profiles from snapshots.
     2. The network (4 -> 256 x 3 -> 3 x 256 log densities + 3 x 32 log mean
        energies) learns them; n1 more discharges start warm from it and run
        boot_cycles; the converged ones join the training set (the method
@@ -275,58 +325,41 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
        x the warm batch's wall time per cycle / its discharges, plus its share
        of training, inference and loading.
 
-    `save(summary)` (optional) is called after every phase with the results
-    so far."""
+    `save(summary, arrays)` (optional) is called after every phase with the
+    results so far (arrays: the phase-1 survey)."""
     import time
     import torch
     from . import api, xsec
     procs = xsec.oxygen_set()
     T = (3.0, 0.026, 0.026)
-    rng = np.random.Generator(np.random.PCG64(seed))
     total = n0 + n1 + n_held
-    sweep = inputs.batch_sweep(total, seed=seed, count_range=(N, N))
-    # widen L and C (the sweep fixes them) so that all four inputs vary; C
-    # from 0.05 up: with fewer metastables the O- lose their excess only by
-    # neutralization, on a time scale of ~1e4 RF cycles (no converged runs
-    # to learn from in a study of this length)
-    for cfg, counts, _ in sweep:
-        cfg["L"] = float(rng.uniform(0.02, 0.03))
-        cfg["C_meta"] = float(rng.uniform(0.05, 1.0 / 6.0))
-        cfg["weight"] = 1.0e15 * cfg["L"] / N
-        cfg["dt"] = 1.0 / (cfg["f"] * cfg["steps_per_cycle"])
+    sweep = study_sweep(total, N, seed, p_range, C_range, U_range)
     summary = {"n0": n0, "n1": n1, "n_held": n_held, "N": N, "ref_cycles": ref_cycles, "boot_cycles": boot_cycles,
-               "eval_cycles": eval_cycles, "window": window, "tol": tol, "bins": BINS}
+               "eval_cycles": eval_cycles, "window": window, "tol": tol, "bins": BINS, "p_range": list(p_range),
+               "C_range": list(C_range), "U_range": list(U_range), "capacity_factor": capacity_factor}
 
     def converged_change(h, i):
         return max(binned_error(h[-1][i], h[-2][i]))
 
+    # 1. cold references
+    if phase1 is None:
+        phase1 = cold_survey(api, sweep, list(range(n0)), N, ref_cycles, window, seed, capacity_factor, log)
+    arrays = phase1
+
     def checkpoint():
         if save:
-            save(summary)
+            save(summary, arrays)
 
-    # 1. cold references
-    t0 = time.perf_counter()
-    runs = [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + i)) for i in range(n0)]
-    gs = make_discharges(api, runs, procs, capacity_factor=6, n_floor=N)
-    h0, w0, en0 = run_windows(api, gs, ref_cycles, window, snapshots=5)
-    for g in gs:
-        g.close()
-    t_ref = time.perf_counter() - t0
-    train_X, train_Y = [], []
-    ch0 = [converged_change(h0, i) for i in range(n0)]
-    for i in range(n0):
-        if ch0[i] < tol:
-            train_X.append(features(sweep[i][0]))
-            train_Y.append(to_target2(h0[-1][i], en0[i]))
-    n_conv0 = len(train_X)
-    summary["phase1_all_used"] = n_conv0 < 4   # too few converged: learn from all (short test runs)
+    ch0 = np.asarray(phase1["change"])
+    keep = np.nonzero(ch0 < tol)[0]
+    summary["phase1_all_used"] = len(keep) < 4   # too few converged: learn from all (short test runs)
     if summary["phase1_all_used"]:
-        train_X = [features(sweep[i][0]) for i in range(n0)]
-        train_Y = [to_target2(h0[-1][i], en0[i]) for i in range(n0)]
-    log(f"phase 1: {n0} cold runs x {ref_cycles} cycles in {t_ref:.0f} s; converged (last change < {tol}) "
-        f"{n_conv0}; change median {np.median(ch0):.4f}")
-    summary.update(phase1_s=t_ref, phase1_kept=n_conv0, phase1_change_median=float(np.median(ch0)),
-                   phase1_changes=[float(v) for v in ch0])
+        keep = np.arange(len(ch0))
+    train_X = [phase1["X"][k] for k in keep]
+    train_Y = [phase1["Y"][k] for k in keep]
+    summary.update(phase1_s=float(phase1["seconds"]), phase1_kept=int((ch0 < tol).sum()),
+                   phase1_change_median=float(np.median(ch0)), phase1_changes=[float(v) for v in ch0])
+    log(f"phase 1: kept {summary['phase1_kept']} of {len(ch0)} (change < {tol})")
     checkpoint()
     mlp = api.MLP([4, 256, 256, 256, 3 * N_CELLS + 3 * BINS], seed=seed)
     t1 = time.perf_counter()
@@ -343,7 +376,7 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
     idx1 = list(range(n0, n0 + n1))
     pred = predict2([sweep[i][0] for i in idx1])
     runs = [(sweep[i][0], warm_state2(sweep[i][0], pred[k][0], pred[k][1], seed=seed + i)) for k, i in enumerate(idx1)]
-    gs = make_discharges(api, runs, procs, capacity_factor=6, n_floor=N)
+    gs = make_discharges(api, runs, procs, capacity_factor=capacity_factor, n_floor=N)
     h1, w1, en1 = run_windows(api, gs, boot_cycles, window, snapshots=5)
     for g in gs:
         g.close()
@@ -353,7 +386,7 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
     for k in range(n1):
         if ch1[k] < tol:
             train_X.append(features(sweep[idx1[k]][0]))
-            train_Y.append(to_target2(h1[-1][k], en1[k]))
+            train_Y.append(to_target2(0.5 * (h1[-1][k] + h1[-2][k]), en1[k]))
             kept1 += 1
     log(f"phase 2: {n1} warm runs x {boot_cycles} cycles in {t_boot:.0f} s; converged {kept1}; "
         f"training set {len(train_X)}")
@@ -376,13 +409,13 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
     t1 = time.perf_counter()
     wruns = [(sweep[i][0], warm_state2(sweep[i][0], pred[k][0], pred[k][1], seed=seed + 10000 + k))
              for k, i in enumerate(held)]
-    gw = make_discharges(api, wruns, procs, capacity_factor=6, n_floor=N)
+    gw = make_discharges(api, wruns, procs, capacity_factor=capacity_factor, n_floor=N)
     t_load = time.perf_counter() - t1
     hw, ww, _ = run_windows(api, gw, eval_cycles, window)
     for g in gw:
         g.close()
     cruns = [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + 20000 + k)) for k, i in enumerate(held)]
-    gc = make_discharges(api, cruns, procs, capacity_factor=6, n_floor=N)
+    gc = make_discharges(api, cruns, procs, capacity_factor=capacity_factor, n_floor=N)
     hc, wc, _ = run_windows(api, gc, ref_cycles, window)
     for g in gc:
         g.close()
@@ -391,7 +424,7 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
     for k in range(min(3, n_held)):
         i = held[k]
         g = make_discharges(api, [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + 30000 + k))],
-                            procs, capacity_factor=6, n_floor=N)[0]
+                            procs, capacity_factor=capacity_factor, n_floor=N)[0]
         b = api.Batch([g], sweep[i][0]["steps_per_cycle"])
         b.step(2)
         b.synchronize()
@@ -450,14 +483,31 @@ if __name__ == "__main__":
     ap.add_argument("--eval-cycles", type=int, default=1000, help="RF cycles of the warm held-out runs")
     ap.add_argument("--window", type=int, default=200, help="RF cycles per averaging window")
     ap.add_argument("--steps", type=int, default=6000, help="Adam steps per training")
-    ap.add_argument("--out", default=None, help="JSON summary (rewritten after every phase)")
+    ap.add_argument("--p-range", type=float, nargs=2, default=(5.0, 50.0))
+    ap.add_argument("--C-range", type=float, nargs=2, default=(0.05, 1.0 / 6.0))
+    ap.add_argument("--U-range", type=float, nargs=2, default=(100.0, 500.0))
+    ap.add_argument("--survey-only", action="store_true", help="phase 1 only (the cold survey)")
+    ap.add_argument("--phase1", default=None, help="phase-1 arrays (.npz) from an earlier run")
+    ap.add_argument("--out", default=None, help="JSON summary (rewritten after every phase) and <out>.npz")
     a = ap.parse_args()
 
-    def save(summary):
+    def save(summary, arrays=None):
         if a.out:
             with open(a.out, "w") as f:
                 json.dump(summary, f, indent=1)
+            if arrays is not None:
+                np.savez(a.out.rsplit(".", 1)[0] + ".npz", **arrays)
 
-    study2(n0=a.n0, n1=a.n1, n_held=a.held, N=a.N, ref_cycles=a.cycles, boot_cycles=a.boot_cycles,
-           eval_cycles=a.eval_cycles, window=a.window, train_steps=a.steps, log=lambda m: print(m, flush=True),
-           save=save)
+    log = lambda m: print(m, flush=True)
+    if a.survey_only:
+        from . import api as _api
+        sw = study_sweep(a.n0, a.N, 4242, tuple(a.p_range), tuple(a.C_range), tuple(a.U_range))
+        out = cold_survey(_api, sw, list(range(a.n0)), a.N, a.cycles, a.window, 4242, log=log)
+        save({"n0": a.n0, "N": a.N, "cycles": a.cycles, "window": a.window, "seconds": out["seconds"],
+              "configs": [{k: sw[i][0][k] for k in ("U", "p", "L", "C_meta")} for i in range(a.n0)],
+              "change": out["change"].tolist(), "live_last": out["live"][-1].tolist()}, out)
+    else:
+        ph1 = dict(np.load(a.phase1)) if a.phase1 else None
+        study2(n0=a.n0, n1=a.n1, n_held=a.held, N=a.N, ref_cycles=a.cycles, boot_cycles=a.boot_cycles,
+               eval_cycles=a.eval_cycles, window=a.window, train_steps=a.steps, p_range=tuple(a.p_range),
+               C_range=tuple(a.C_range), U_range=tuple(a.U_range), phase1=ph1, log=log, save=save)

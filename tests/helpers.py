@@ -11,22 +11,26 @@ from paper_0705_0497_gb300 import inputs, xsec
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 COUNTERS_COMPARED = ("neutralized", "pair_candidates", "particle_steps", "warn_emax", "warn_tries", "warn_pair_gt1",
                      "recombined", "rec_candidates", "id_overflow", "edetached", "edet_candidates",
-                     "coulomb_pairs")
+                     "coulomb_pairs", "warn_numax")
 
 
 def capacity_for(counts, factor=2.0, extra=4096):
     return tuple(int(n * factor) + extra for n in counts)
 
 
-def make_pair(cfg, counts, T_eV, procs, capacity=None, compact_check=0, state=None):
-    """A library context and an FP32 oracle loaded with the same particles."""
+def make_pair(cfg, counts, T_eV, procs, capacity=None, compact_check=0, state=None, caps=None):
+    """A library context and an FP32 oracle loaded with the same particles
+    (caps: majorant caps per species in eV, or None)."""
     import oracle
     from paper_0705_0497_gb300 import api
     st = state if state is not None else inputs.initial_state(cfg, counts, T_eV)
     g = api.Discharge(cfg, capacity or capacity_for([len(p["x"]) for p in st]), compact_check=compact_check)
+    o = oracle.Oracle(cfg, 32)
+    if caps is not None:
+        g.set_majorant_cap(caps)
+        o.set_majorant_cap(caps)
     g.set_processes(procs)
     g.load_state(st)
-    o = oracle.Oracle(cfg, 32)
     o.set_processes(procs)
     for s, p in enumerate(st):
         o.load(s, p["x"], p["vx"], p["vy"], p["vz"], p["id"])

@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(lib):
     # o2pic_config: 13 doubles, 4 x 32-bit, 3 x u64, 2 x i32
     assert ctypes.sizeof(api.Config) == 13 * 8 + 4 * 4 + 3 * 8 + 2 * 4
     assert ctypes.sizeof(api.Process) == 4 * 4 + 8 + 2 * 8
-    assert ctypes.sizeof(api.Stats) == 8 * (48 + 6 + 3 + 7 + 1 + 3 + 3 + 3 + 1 + 3 + 2 + 2 + 1)
+    assert ctypes.sizeof(api.Stats) == 8 * (48 + 6 + 3 + 7 + 1 + 3 + 3 + 3 + 1 + 3 + 2 + 2 + 1 + 1)
 
 
 def test_config_validation_without_gpu(lib):

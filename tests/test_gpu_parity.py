@@ -83,6 +83,22 @@ def test_parity_100_steps(torch_cuda):
     assert gs["step"] == 100
 
 
+@pytest.mark.parametrize("caps,violations", [((2.0, 0.5, 0.5), True), ((None, 600.0, 600.0), False)])
+def test_parity_majorant_cap(torch_cuda, caps, violations):
+    """Capped majorants: nu_max from the grid points up to the cap on both
+    sides, the same candidates, collisions and warn_numax counts; caps far
+    below the particles' energies give violations, caps above them none."""
+    cfg, counts, T, _ = inputs.workload("parity_128", ion_subcycle=2)
+    procs = xsec.oxygen_set()
+    g, o, _ = make_pair(cfg, counts, T, procs, caps=caps)
+    for chunk in (1, 20, 39):
+        g.step(chunk)
+        o.step(chunk)
+        compare_particles(g, o)
+        compare_counters(g.stats(), o.counters(), nproc_of(procs))
+    assert (g.stats()["warn_numax"] > 0) == violations
+
+
 @pytest.mark.parametrize("n", [0, 1, 3, 1023, 1025, 8191, 8193, 20001])
 def test_parity_ragged_sizes(torch_cuda, n):
     """Empty, single, ragged and multi-tile particle counts (tiles of 8192,

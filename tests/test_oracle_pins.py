@@ -894,6 +894,75 @@ def test_process_choice_mono_energetic_beams(oracle_mod, precision):
         assert abs(tot - N * q_tot) < 5 * math.sqrt(N * q_tot) + 1
 
 
+# ------------------------------------------------------------ capped majorant
+def _const_sigma_electron(s0=5e-20):
+    E = np.array([1e-3, 4096.0])
+    return [dict(species=0, kind=xsec.ELASTIC, target=xsec.T_O2, threshold_eV=0.0, E=E, sigma=np.full(2, s0))]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_majorant_cap_sets_numax(oracle_mod, precision):
+    """nu_max under a majorant cap: for a constant cross section nu(E) = n
+    sigma sqrt(2 e E / m_e) grows with E, so the maximum over the grid points
+    up to the first one at or above the cap is nu at that point E*, the
+    smallest grid energy >= cap on the grid of 32 evenly spaced points per
+    octave, E = 2^e (1 + j/32), e = -10 .. 11, and 2^12 eV; no cap: E* =
+    2^12 eV.  A cap that is not positive is refused."""
+    grid = sorted([2.0 ** e * (1 + j / 32) for e in range(-10, 12) for j in range(32)] + [4096.0])
+    s0 = 5e-20
+    cfg = _cfg(p=20.0)
+    nO2 = cfg["p"] / (KB * cfg["T_gas"])
+    for cap in (None, 1.0, 7.3, 150.0, 4096.0, 1e6):
+        o = oracle_mod.Oracle(cfg, precision)
+        o.set_majorant_cap([cap, None, None])
+        o.set_processes(_const_sigma_electron(s0))
+        Es = 4096.0 if cap is None else next((E for E in grid if E >= cap), 4096.0)
+        want = nO2 * s0 * math.sqrt(2 * QE * Es / ME)
+        numax, pmax = o.table(0)[2:]
+        assert numax == pytest.approx(want, rel=1e-12), (cap, numax, want)
+        assert pmax == pytest.approx(-math.expm1(-want * cfg["dt"]), rel=1e-6)
+    o = oracle_mod.Oracle(cfg, precision)
+    with pytest.raises(ValueError):
+        o.set_majorant_cap([0.0, None, None])
+    with pytest.raises(ValueError):
+        o.set_majorant_cap([None, -1.0, None])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_majorant_cap_violations_counted(oracle_mod, precision):
+    """A beam of N electrons at E0, one step, one constant-sigma process,
+    majorant cap 2 eV.  Below the cap (E0 = 1.5 eV) the null-collision law
+    holds: Binomial(N, P_max nu(E0) / nu_max) collisions, no warning.  Above
+    it (E0 = 40 eV, nu(E0) > nu_max) every candidate collides and is counted
+    in warn_numax: Binomial(N, P_max) of each, equal."""
+    s0 = 5e-20
+    cfg = _cfg(p=20.0)
+    nO2 = cfg["p"] / (KB * cfg["T_gas"])
+    kap = 0.5 * ME / QE
+    N = 100_000
+    for E0 in (1.5, 40.0):
+        o = oracle_mod.Oracle(cfg, precision)
+        o.set_majorant_cap([2.0, None, None])
+        o.set_processes(_const_sigma_electron(s0))
+        numax, pmax = o.table(0)[2:]
+        v = np.float32(math.sqrt(E0 / kap))
+        p = dict(x=np.full(N, 0.5 * cfg["L"], np.float32), vx=np.zeros(N, np.float32),
+                 vy=np.full(N, v, np.float32), vz=np.zeros(N, np.float32), id=np.arange(N, dtype=np.uint32))
+        _empty(o)
+        _load(o, 0, p)
+        o.step(1)
+        c = o.counters()
+        nu0 = nO2 * s0 * math.sqrt(2 * QE * E0 / ME)
+        if nu0 < numax:
+            q = pmax * nu0 / numax
+            assert c["warn_numax"] == 0
+        else:
+            q = pmax
+            assert c["warn_numax"] == c["events_0_0"]
+        got = c["events_0_0"]
+        assert abs(got - N * q) < 5 * math.sqrt(N * q * (1 - q)) + 1, (E0, got, N * q)
+
+
 # ------------------------------------------------------------ free flights
 @pytest.mark.parametrize("precision", [64, 32])
 def test_free_flight_gaps_are_geometric(oracle_mod, precision):
