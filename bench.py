@@ -512,18 +512,52 @@ def bench_batch(args, world, rank, local):
     return 0
 
 
-def profile_steps(n, majorant="capped"):
+def profile_steps(n, majorant="capped", state=None):
     """The workload stepped n single steps through the public API, nothing
     timed: a short, fixed launch sequence for ncu captures (with ion
-    subcycling 10, the electron push of step 6 is launch 8 of k_push)."""
-    from paper_0705_0497_gb300 import api, inputs, xsec
+    subcycling 10, the electron push of step 6 is launch 8 of k_push).  With
+    `state` (a file written by save_settled) the discharge starts from that
+    saved state at its step instead of the initial load."""
+    from paper_0705_0497_gb300 import api, inputs
     cfg, counts, T, _ = inputs.workload(WORKLOAD)
-    g = api.Discharge(cfg, tuple(int(c * 1.5) + 65536 for c in counts))
+    if state:
+        z = np.load(state)
+        st = [{k: z[f"{k}{s}"] for k in ("x", "vx", "vy", "vz", "id", "tc")} for s in range(3)]
+        step = int(z["step"])
+    else:
+        st, step = inputs.initial_state(cfg, counts, T), 0
+    g = api.Discharge(cfg, capacity(counts))
     set_processes(g, cfg, majorant)
-    g.load_state(inputs.initial_state(cfg, counts, T))
+    g.load_state(st)
+    if step:
+        g.set_step(step)
     g.step(n)
     g.synchronize()
     print(json.dumps({"profile_steps": n, "step": g.stats()["step"], "live": [g.count(s) for s in range(3)]}))
+    g.close()
+    return 0
+
+
+def save_settled(path, cycles, majorant="capped"):
+    """The workload settled `cycles` RF cycles (the bench's own graph path)
+    and its particles, free flights and step saved to `path` (.npz) for
+    profile_steps."""
+    from paper_0705_0497_gb300 import api, inputs
+    cfg, counts, T, _ = inputs.workload(WORKLOAD)
+    g = api.Discharge(cfg, capacity(counts), compact_check=20)
+    set_processes(g, cfg, majorant)
+    g.load_state(inputs.initial_state(cfg, counts, T))
+    b = api.Batch([g], steps_per_launch=cfg["steps_per_cycle"])
+    b.step(cycles)
+    b.synchronize()
+    b.close()
+    out = {"step": np.array(g.stats()["step"])}
+    for s in range(3):
+        p = g.particles(s, flight=True)
+        for k in ("x", "vx", "vy", "vz", "id", "tc"):
+            out[f"{k}{s}"] = p[k]
+    np.savez(path, **out)
+    print(json.dumps({"saved": path, "step": int(out["step"]), "live": [g.count(s) for s in range(3)]}))
     g.close()
     return 0
 
@@ -542,9 +576,15 @@ def main():
                     help="RF cycles run before the warm-up (default: per workload, 100 for scale_512)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only step the workload this many single steps (a fixed launch sequence for ncu) and exit")
+    ap.add_argument("--profile-state", default=None,
+                    help="with --profile-steps: start from this saved state (see --save-settled)")
+    ap.add_argument("--save-settled", default=None,
+                    help="settle the workload --settle RF cycles (default 100), save its state here (.npz) and exit")
     args = ap.parse_args()
+    if args.save_settled:
+        return save_settled(args.save_settled, args.settle if args.settle >= 0 else SETTLE[WORKLOAD], args.majorant)
     if args.profile_steps > 0:
-        return profile_steps(args.profile_steps, args.majorant)
+        return profile_steps(args.profile_steps, args.majorant, args.profile_state)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

@@ -322,10 +322,9 @@ int o2pic_check_bounded_wait(double* seconds, void* stream);
  * process exits); n beyond that returns INVALID_ARG.  Every call looks up the
  * array's device address on the current device (which must be the device of
  * the pointers).  The call copies its error word back and synchronizes
- * `stream`, so it cannot be made while `stream` is being captured.  All calls
- * on a device share the array, so calls whose GPU work overlaps (e.g. on two
- * streams at once) race: serialize them.  The call resets what must start at
- * zero itself and returns once the work on `stream` is done. */
+ * `stream` before it returns.  All calls on a device share the array, so
+ * calls whose GPU work overlaps (e.g. on two streams at once) race: serialize
+ * them.  The call resets what must start at zero itself. */
 #define O2PIC_NOALLOC_MAX_PARTICLES (1ull << 25)
 int o2pic_compact_particles_noalloc(const float* x, const float* vx, const float* vy, const float* vz,
                                     const uint32_t* id, uint64_t n, float* ox, float* ovx, float* ovy, float* ovz,

@@ -463,6 +463,28 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     const int Nc = P.Nc, Ng = P.Ng;
     const PhiloxPre pre = philox_pre(step_lo, SpeciesTraits<S>::tag, (uint32_t)(step >> 32), P.seed);
 
+    // this warp's contiguous slot range, and its first round of x, v_x, tc
+    // requested before the block's set-up (their latency overlaps it)
+    const unsigned W = nblk * WARPS;
+    const unsigned gw = blk * WARPS + warp;
+    const unsigned R = warp_range_len(nslots, W);
+    const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
+    const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
+    float xs[4], vxs[4];
+    uint32_t tcs[4];
+    auto load_round = [&](unsigned g0) {
+        const bool full = g0 + ROUND <= r1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned i = g0 + 32u * k + lane;
+            const bool inr = full || i < r1;
+            xs[k] = inr ? X[i] : dead_marker();
+            vxs[k] = inr ? VX[i] : 0.0f;
+            tcs[k] = inr ? TC[i] : 0u;
+        }
+    };
+    if (r0 < r1) load_round(r0);
+
     for (int j = tid; j < Ng; j += BLOCK) { Es[j] = P.Ef[j]; hist[j] = 0ull; }
     if (fused) stage_total(P, S, Tt);
     if (cum_staged) {
@@ -475,13 +497,6 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     }
     if (fused && tid < MAXPROC) sh.events[tid] = 0u;
     __syncthreads();
-
-    // this warp's contiguous slot range
-    const unsigned W = nblk * WARPS;
-    const unsigned gw = blk * WARPS + warp;
-    const unsigned R = warp_range_len(nslots, W);
-    const unsigned r0 = (gw * (unsigned long long)R < nslots) ? gw * R : nslots;
-    const unsigned r1 = (r0 + R < nslots) ? r0 + R : nslots;
 
     unsigned psteps = 0, nabs0 = 0, nabs1 = 0, nnf = 0, wemax = 0, wtries = 0, wnumax = 0;
     long long jacc = 0;   // conduction current: sum of trunc(256 v_x^{n+1/2}) (exact)
@@ -525,17 +540,7 @@ __device__ __forceinline__ void push_body(const Params& P, unsigned blk, unsigne
     };
 
     for (unsigned g0 = r0; g0 < r1; g0 += ROUND) {
-        const bool full = g0 + ROUND <= r1;
-        float xs[4], vxs[4];
-        uint32_t tcs[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const unsigned i = g0 + 32u * k + lane;
-            const bool inr = full || i < r1;
-            xs[k] = inr ? X[i] : dead_marker();
-            vxs[k] = inr ? VX[i] : 0.0f;
-            tcs[k] = inr ? TC[i] : 0u;
-        }
+        if (g0 != r0) load_round(g0);
 #pragma unroll PUSH_UNROLL
         for (int k = 0; k < 4; ++k) {
             const unsigned i = g0 + 32u * k + lane;

@@ -301,14 +301,15 @@ def cold_survey(api, sweep, idx, N, cycles, window, seed, capacity_factor=20, lo
 
 
 def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000, eval_cycles=1000, window=200,
-           tol=0.02, train_steps=6000, seed=4242, p_range=(5.0, 50.0), C_range=(0.05, 1.0 / 6.0),
+           tol=0.02, accept=None, train_steps=6000, seed=4242, p_range=(5.0, 50.0), C_range=(0.05, 1.0 / 6.0),
            U_range=(100.0, 500.0), capacity_factor=20, phase1=None, log=print, save=None):
     """The warm-start study at the 2 % criterion.
 
     1. n0 discharges of the sweep (`study_sweep`) started cold run ref_cycles
        (`cold_survey`; or its saved result `phase1`, a dict of arrays); the
        mean of the last two windows (`window` cycles each) is the reference,
-       kept for training if the change between the two is below tol, with
+       kept for training if the change between the two is below `accept`
+       (default tol; the windows' own noise sets how low it can be), with
        mean-energy profiles from snapshots.
     2. The network (4 -> 256 x 3 -> 3 x 256 log densities + 3 x 32 log mean
        energies) learns them; n1 more discharges start warm from it and run
@@ -350,16 +351,19 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
         if save:
             save(summary, arrays)
 
+    if accept is None:
+        accept = tol
+    summary["accept"] = accept
     ch0 = np.asarray(phase1["change"])
-    keep = np.nonzero(ch0 < tol)[0]
+    keep = np.nonzero(ch0 < accept)[0]
     summary["phase1_all_used"] = len(keep) < 4   # too few converged: learn from all (short test runs)
     if summary["phase1_all_used"]:
         keep = np.arange(len(ch0))
     train_X = [phase1["X"][k] for k in keep]
     train_Y = [phase1["Y"][k] for k in keep]
-    summary.update(phase1_s=float(phase1["seconds"]), phase1_kept=int((ch0 < tol).sum()),
+    summary.update(phase1_s=float(phase1["seconds"]), phase1_kept=int((ch0 < accept).sum()),
                    phase1_change_median=float(np.median(ch0)), phase1_changes=[float(v) for v in ch0])
-    log(f"phase 1: kept {summary['phase1_kept']} of {len(ch0)} (change < {tol})")
+    log(f"phase 1: kept {summary['phase1_kept']} of {len(ch0)} (change < {accept})")
     checkpoint()
     mlp = api.MLP([4, 256, 256, 256, 3 * N_CELLS + 3 * BINS], seed=seed)
     t1 = time.perf_counter()
@@ -384,7 +388,7 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
     ch1 = [converged_change(h1, k) for k in range(n1)]
     kept1 = 0
     for k in range(n1):
-        if ch1[k] < tol:
+        if ch1[k] < accept:
             train_X.append(features(sweep[idx1[k]][0]))
             train_Y.append(to_target2(0.5 * (h1[-1][k] + h1[-2][k]), en1[k]))
             kept1 += 1
@@ -483,6 +487,8 @@ if __name__ == "__main__":
     ap.add_argument("--eval-cycles", type=int, default=1000, help="RF cycles of the warm held-out runs")
     ap.add_argument("--window", type=int, default=200, help="RF cycles per averaging window")
     ap.add_argument("--steps", type=int, default=6000, help="Adam steps per training")
+    ap.add_argument("--accept", type=float, default=None,
+                    help="largest change between the last two windows of a run kept for training (default 0.02)")
     ap.add_argument("--p-range", type=float, nargs=2, default=(5.0, 50.0))
     ap.add_argument("--C-range", type=float, nargs=2, default=(0.05, 1.0 / 6.0))
     ap.add_argument("--U-range", type=float, nargs=2, default=(100.0, 500.0))
@@ -510,4 +516,5 @@ if __name__ == "__main__":
         ph1 = dict(np.load(a.phase1)) if a.phase1 else None
         study2(n0=a.n0, n1=a.n1, n_held=a.held, N=a.N, ref_cycles=a.cycles, boot_cycles=a.boot_cycles,
                eval_cycles=a.eval_cycles, window=a.window, train_steps=a.steps, p_range=tuple(a.p_range),
-               C_range=tuple(a.C_range), U_range=tuple(a.U_range), phase1=ph1, log=log, save=save)
+               C_range=tuple(a.C_range), U_range=tuple(a.U_range), accept=a.accept, phase1=ph1, log=log,
+               save=save)
