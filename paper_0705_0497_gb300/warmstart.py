@@ -372,8 +372,13 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
     t_train1 = time.perf_counter() - t1
 
     def predict2(cfgs):
+        # no extrapolation beyond the training targets: each output is held
+        # to the range it took in the training set (a wild log density or
+        # energy would load a discharge far from any the method produced)
         X = torch.from_numpy(np.stack([features(c) for c in cfgs])).cuda()
-        return [from_target2(y) for y in mlp.forward(X).cpu().numpy()]
+        Ts = np.stack(train_Y)
+        lo, hi = Ts.min(axis=0), Ts.max(axis=0)
+        return [from_target2(np.clip(y, lo, hi)) for y in mlp.forward(X).cpu().numpy()]
 
     # 2. bootstrapped runs, started warm
     t0 = time.perf_counter()
@@ -415,12 +420,18 @@ def study2(n0=48, n1=96, n_held=32, N=100000, ref_cycles=4000, boot_cycles=1000,
              for k, i in enumerate(held)]
     gw = make_discharges(api, wruns, procs, capacity_factor=capacity_factor, n_floor=N)
     t_load = time.perf_counter() - t1
-    hw, ww, _ = run_windows(api, gw, eval_cycles, window)
+    log(f"held-out warm loads: {[sum(len(p['x']) for p in st) for _, st in wruns]} particles")
+    lw = []
+    hw, ww, _ = run_windows(api, gw, eval_cycles, window, live=lw)
+    log(f"held-out warm runs: {eval_cycles} cycles in {ww[-1]:.0f} s; largest live count {int(np.max(lw))}")
+    summary.update(held_warm_s=ww[-1], held_warm_live_max=int(np.max(lw)))
+    checkpoint()
     for g in gw:
         g.close()
     cruns = [(sweep[i][0], cold_state(sweep[i][0], sweep[i][1], T, seed=seed + 20000 + k)) for k, i in enumerate(held)]
     gc = make_discharges(api, cruns, procs, capacity_factor=capacity_factor, n_floor=N)
     hc, wc, _ = run_windows(api, gc, ref_cycles, window)
+    log(f"held-out cold runs: {ref_cycles} cycles in {wc[-1]:.0f} s")
     for g in gc:
         g.close()
     # 4. the plain cold start alone: seconds per RF cycle of a one-discharge graph
