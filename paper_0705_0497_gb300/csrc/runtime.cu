@@ -22,6 +22,20 @@
 
 namespace o2 {
 thread_local bool pdl_enabled = true;
+
+// Ion chains on their own streams on ion steps (1), or all on the step's
+// stream (0); programmatic dependent launches inside the graph of a batch of
+// one discharge (1), or only outside graphs (0).  Both keep the results.  On
+// the 512-cell, 1.6e7-particle discharge at its periodic state the fork took
+// the RF cycle from 46.2 to 44.3 ms; the programmatic launches inside the
+// one-discharge graph gained nothing (46.7 ms without the fork, 44.1 with).
+#ifndef O2PIC_ION_FORK
+#define O2PIC_ION_FORK 1
+#endif
+#ifndef O2PIC_GRAPH_PDL_SINGLE
+#define O2PIC_GRAPH_PDL_SINGLE 0
+#endif
+constexpr bool ION_FORK = O2PIC_ION_FORK != 0;
 }
 
 // particle kernels run at most this many blocks per SM (bounds the per-warp
@@ -81,6 +95,10 @@ struct o2pic_ctx {
     int num_sms = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t last = nullptr;
+    // ion steps: the O- and O2+ chains on their own streams beside the
+    // electron kernel (forked from and joined back into the step's stream)
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     Params P;
     DevCtrl* d_ctrl = nullptr;
     std::vector<void*> allocs;
@@ -326,17 +344,33 @@ void enqueue_steps(o2pic_ctx* c, uint64_t nsteps, cudaStream_t s) {
     const unsigned S = (unsigned)c->cfg.ion_subcycle;
     for (uint64_t k = 0; k < nsteps; ++k) {
         const bool ion = (c->host_step % S) == 0;
+        // on ion steps the three species' particle chains share nothing but
+        // order-free atomics until the pair processes, so (unless the launches
+        // are being timed one by one) the ion chains run on their own streams
+        const bool fork = ion && ION_FORK && !c->timing;
+        const cudaStream_t so = fork ? c->aux[0] : s, sp2 = fork ? c->aux[1] : s;
+        if (fork) {
+            cudaEventRecord(c->ev_fork, s);
+            cudaStreamWaitEvent(so, c->ev_fork, 0);
+            cudaStreamWaitEvent(sp2, c->ev_fork, 0);
+        }
         launch(c, KK_PUSH_E, s, [&] { launch_push(SP_E, P, c->grid_push[SP_E], s); });
         if (ion) {
-            launch(c, KK_PUSH_OM, s, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], s); });
+            launch(c, KK_PUSH_OM, so, [&] { launch_push(SP_OM, P, c->grid_push[SP_OM], so); });
             if (P.nproc[SP_OM] && !ions_fused()) {
-                launch(c, KK_FILT_OM, s, [&] { launch_filter(SP_OM, P, c->grid_push[SP_OM], s); });
-                launch(c, KK_CAND_OM, s, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], s); });
+                launch(c, KK_FILT_OM, so, [&] { launch_filter(SP_OM, P, c->grid_push[SP_OM], so); });
+                launch(c, KK_CAND_OM, so, [&] { launch_cand(SP_OM, P, c->grid_push[SP_OM], so); });
             }
-            launch(c, KK_PUSH_OP, s, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], s); });
+            launch(c, KK_PUSH_OP, sp2, [&] { launch_push(SP_OP, P, c->grid_push[SP_OP], sp2); });
             if (P.nproc[SP_OP] && !ions_fused()) {
-                launch(c, KK_FILT_OP, s, [&] { launch_filter(SP_OP, P, c->grid_push[SP_OP], s); });
-                launch(c, KK_CAND_OP, s, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], s); });
+                launch(c, KK_FILT_OP, sp2, [&] { launch_filter(SP_OP, P, c->grid_push[SP_OP], sp2); });
+                launch(c, KK_CAND_OP, sp2, [&] { launch_cand(SP_OP, P, c->grid_push[SP_OP], sp2); });
+            }
+            if (fork) {
+                cudaEventRecord(c->ev_join[0], so);
+                cudaEventRecord(c->ev_join[1], sp2);
+                cudaStreamWaitEvent(s, c->ev_join[0], 0);
+                cudaStreamWaitEvent(s, c->ev_join[1], 0);
             }
             if (P.coul_mask) {
                 int k = 0;
@@ -417,7 +451,24 @@ int o2pic_create(const o2pic_config* cfg, o2pic_ctx** out) {
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { delete c; return O2PIC_E_CUDA; }
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (int i = 0; i < 2; ++i) {
+            if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+            if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+        }
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        for (int i = 0; i < 2; ++i) {
+        if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+        if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return O2PIC_E_CUDA;
+    }
     c->last = c->stream;
     set_constants(c);
     Params& P = c->P;
@@ -1323,7 +1374,9 @@ int batch_capture(o2pic_batch* b) {
     if (b->fused) {
         enqueue_fused(b, b->stream);
     } else {
-        pdl_enabled = false;
+        // several branches: no early-launched blocks that could crowd out
+        // the single-block kernels of other branches
+        pdl_enabled = O2PIC_GRAPH_PDL_SINGLE && n == 1;
         cudaEventRecord(b->fork, b->stream);
         for (size_t i = 0; i < n; ++i) {
             cudaStreamWaitEvent(b->branch[i], b->fork, 0);
