@@ -234,7 +234,9 @@ __device__ __forceinline__ void pair_body(const Params& P, const PairSpec& Sp, u
     const float* __restrict__ XM = P.sp[Sp.A].x[cm];
     const uint32_t* __restrict__ IDM = P.sp[Sp.A].id[cm];
     const unsigned* __restrict__ tot = Sp.tot;
-    const uint4 ctr = make_uint4((uint32_t)step, Sp.tag_pair, 0u, (uint32_t)(step >> 32));
+    // the acceptance draw's Philox block (counter (step, tag, 0), key (id,
+    // seed)) with its id-free first-round products computed once
+    const PhiloxPre pre = philox_pre((uint32_t)step, Sp.tag_pair, (uint32_t)(step >> 32), P.seed);
     unsigned gt1 = 0;
 
     if (blk == 0) {
@@ -271,7 +273,7 @@ __device__ __forceinline__ void pair_body(const Params& P, const PairSpec& Sp, u
                     cell_of(xs[i], P.inv_dx, Nc, c, fr);
                     const unsigned a = __ldg(&tot[c]), b = __ldg(&tot[Nc + c]);
                     const unsigned M = a < b ? b : a;
-                    const float u = uniform(philox4x32_10(ctr, make_uint2(ids[i], P.seed)).x);
+                    const float u = uniform(philox_id(pre, ids[i]).x);
                     cc = (unsigned short)c;
                     if (u < Sp.Kmax_hi * (P.pair_factor * (float)M)) {
                         cc |= CELL_FLAG;
