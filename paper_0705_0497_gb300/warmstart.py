@@ -10,9 +10,9 @@ learns, from runs the method itself produced, the map
 
 and a new run is loaded from the predicted profiles instead of uniformly
 (positions from the densities, Maxwellian velocities at two thirds of the
-local mean energy).
-The cold start stays the fallback and the judge of the result: a warm-started
-run is still the method, only its initial condition differs.
+local mean energy).  The cold start stays the fallback and the reference
+for the error: a warm-started run is still the method, only its initial
+condition differs.
 
 Functions here do argument marshalling and bookkeeping; the discharge steps,
 the training and the inference run in the library's CUDA kernels.  Particle
