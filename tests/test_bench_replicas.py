@@ -54,3 +54,27 @@ def test_single_process_aggregate_is_identity():
     import bench
     agg = bench.aggregate(5.0, 1e9, 4e8, 3.0, 1.5)
     assert agg == {"t_max_ms": 5.0, "e2e_t_max": 1.5, "ps_sum": 1e9, "pe_sum": 4e8, "e2e_ps_sum": 3.0}
+
+
+def test_reference_arm_line_on_the_cpu():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the contract's keys: the same metric and unit as the GPU
+    arm, the cores it used, and an end-to-end figure equal to its value with
+    no host-device bytes."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "parity_128", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3 and d["higher_is_better"] is True
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "parity_128"
