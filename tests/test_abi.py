@@ -69,3 +69,10 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.o2pic_step(None, 1, None) == -1
     assert lib.o2pic_synchronize(None) == -1
     assert lib.o2pic_set_processes(None, None, 0) == -1
+
+
+def test_majorant_cap_validation_without_gpu(lib):
+    import numpy as np
+    caps = np.array([np.nan, 650.0, 650.0])
+    assert lib.o2pic_set_majorant_cap(None, caps.ctypes.data) == -1
+    assert lib.o2pic_set_majorant_cap(None, None) == -1
