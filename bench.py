@@ -24,7 +24,6 @@ cores on bounded samples of the same workload.
 import argparse
 import hashlib
 import json
-import math
 import os
 import platform
 import subprocess

@@ -6,7 +6,6 @@ package.  It imports nothing from the CUDA package; both receive the same
 seeded inputs from ``paper_0705_0497_gb300.inputs`` / ``.xsec`` (data only).
 """
 import ctypes
-import os
 
 import numpy as np
 

@@ -1,6 +1,5 @@
 """Shared helpers of the GPU tests: run the same seeded workload through the
 CUDA library and the oracle and compare."""
-import math
 import os
 import subprocess
 
